@@ -1,0 +1,406 @@
+"""Benchmark: phase-space events/s on B300 for the N-body generator sweep and the Dalitz integral.
+
+One step = one pass of the whole hot path over the synthetic workload:
+  * generate: N = 2..10 daughters, massless and massive (m_i ~ U[0, M/(2N)], seeded),
+    M = 10 GeV, 1e8 events per (N, masses, precision), FP32 and FP64 kinematics and
+    outputs (structure of arrays (E, px, py, pz) per daughter + weight), 36 launches;
+  * integrate: the 3-body Dalitz matrix element |BW(m12) + 0.5 e^{1.2i} BW(m23)|^2 over
+    1e9 events (M = 1.865 GeV), FP32 kinematics, FP64 compensated sums, no event storage.
+value = (events generated + events integrated) / step time, timed with CUDA events on the
+launching stream; outputs (5-33 GB per launch) are far larger than L2, so no L2 flush is
+needed.  `e2e` times the same step through the host-output C-ABI entry point (every event
+copied to pinned host memory inside the timed region).
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun (N > 1) each rank runs the same per-rank workload on disjoint counter-event
+ranges (weak scaling, no data-path collective); timing is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+GEN_N = workloads.SWEEP_N
+GEN_EVENTS = workloads.SWEEP_NEVENTS
+INT_CFG = workloads.D0_DALITZ
+
+
+def bytes_per_event(n: int, dtype: str) -> int:
+    """Algorithmic output bytes per generated event: 4n components + 1 weight."""
+    return (4 * n + 1) * (4 if dtype == "f32" else 8)
+
+
+def sweep_items():
+    items = []
+    for dtype in ("f32", "f64"):
+        for massive in (False, True):
+            for n in GEN_N:
+                items.append((dtype, massive, n))
+    return items
+
+
+def load_peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            pk = json.load(fh)
+        return {"hbm_gbs": float(pk["hbm_gbs"]), "src": "measured"}
+    except Exception:
+        return {"hbm_gbs": 6400.0, "src": "fallback"}
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.rows: list[list[str]] = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm = []
+        mx = None
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+            except (ValueError, IndexError):
+                continue
+            for k, nm in enumerate(names):
+                if len(r) > 5 + k and r[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        sm.sort()
+        med = sm[len(sm) // 2] if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- our arm
+def run_ours(args) -> None:
+    import torch
+    import paper_1711_05683_b300 as hp
+    from paper_1711_05683_b300 import build as hp_build
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    if rank == 0:
+        hp_build.build()
+    if world > 1:
+        dist.barrier()
+    hp.lib()
+
+    nev = args.events
+    int_events = args.int_events
+    items = sweep_items()
+    max_elems = max((4 * n + 1) for n in GEN_N) * nev
+    buf64 = torch.empty(max_elems, dtype=torch.float64, device="cuda")  # reused by every launch
+    buf32 = buf64.view(torch.float32)
+    stream = torch.cuda.current_stream()
+    base_offset = rank * (nev + int_events)  # disjoint counter-event ranges per rank
+
+    def views(n, dtype):
+        ld = nev
+        b = buf32 if dtype == "f32" else buf64
+        out = b[: 4 * n * ld].view(n, 4, ld)
+        w = b[4 * n * ld: (4 * n + 1) * ld]
+        return out, w
+
+    ev_pairs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                for _ in range(len(items) + 1)]
+
+    def step(record: bool):
+        for k, (dtype, massive, n) in enumerate(items):
+            out, w = views(n, dtype)
+            masses = workloads.sweep_masses(n, massive)
+            if record:
+                ev_pairs[k][0].record(stream)
+            hp.generate_into(workloads.SWEEP_M, masses, nev, 1000 + n, out, w, dtype=dtype,
+                             event_offset=base_offset)
+            if record:
+                ev_pairs[k][1].record(stream)
+        if record:
+            ev_pairs[-1][0].record(stream)
+        res = hp.integrate(INT_CFG["M"], INT_CFG["masses"], int_events, INT_CFG["seed"],
+                           kin_dtype="f32", me=hp.ME_DALITZ_2BW, params=INT_CFG["params"],
+                           event_offset=base_offset)
+        if record:
+            ev_pairs[-1][1].record(stream)
+        return res
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step(False)
+    barrier()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    per_launch_ms = [0.0] * (len(items) + 1)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    t0.record(stream)
+    for _ in range(args.steps):
+        res = step(True)
+        torch.cuda.synchronize()
+        for k, (a, b) in enumerate(ev_pairs):
+            per_launch_ms[k] += a.elapsed_time(b)
+    t1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    total_ms = t0.elapsed_time(t1)
+    if world > 1:
+        tt = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    ms_per_step = total_ms / args.steps
+    per_step_events = len(items) * nev + int_events
+    value = per_step_events * world / (ms_per_step / 1e3)
+
+    # e2e through the host-output entry point: every generated event copied to pinned host
+    # memory inside the timed region; the integral's result is read back by the call itself.
+    e2e = None
+    if not args.no_e2e:
+        host_elems = max_elems
+        hbuf64 = torch.empty(host_elems, dtype=torch.float64, pin_memory=True)
+        hbuf32 = hbuf64.view(torch.float32)
+        d2h = 0
+        h2d = 0
+
+        def e2e_step():
+            nonlocal d2h, h2d
+            d2h = h2d = 0
+            for dtype, massive, n in items:
+                b = hbuf32 if dtype == "f32" else hbuf64
+                out = b[: 4 * n * nev].view(n, 4, nev)
+                w = b[4 * n * nev: (4 * n + 1) * nev]
+                hp.generate_host_into(workloads.SWEEP_M, workloads.sweep_masses(n, massive), nev,
+                                      1000 + n, out, w, dtype=dtype, event_offset=base_offset)
+                d2h += bytes_per_event(n, dtype) * nev
+                h2d += 8 * n  # the host array of daughter masses
+            hp.integrate(INT_CFG["M"], INT_CFG["masses"], int_events, INT_CFG["seed"], kin_dtype="f32",
+                         me=hp.ME_DALITZ_2BW, params=INT_CFG["params"], event_offset=base_offset)
+            d2h += 56  # hydra_integral
+            h2d += 8 * 3 + 8 * 6
+
+        e2e_steps = max(1, min(args.steps, args.e2e_steps))
+        e2e_step()  # warm-up (allocates staging)
+        barrier()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(e2e_steps):
+            e2e_step()
+        b.record(stream)
+        barrier()
+        e2e_ms = a.elapsed_time(b) / e2e_steps
+        if world > 1:
+            tt = torch.tensor([e2e_ms], device="cuda", dtype=torch.float64)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            e2e_ms = float(tt.item())
+        e2e = {"value": per_step_events * world / (e2e_ms / 1e3), "unit": "events/s",
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": e2e_steps,
+               "ms_per_step": e2e_ms}
+        del hbuf64, hbuf32
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    peaks = load_peaks()
+    breakdown = []
+    for k, (dtype, massive, n) in enumerate(items):
+        ms = per_launch_ms[k] / args.steps
+        gbs = bytes_per_event(n, dtype) * nev / (ms / 1e3) / 1e9
+        breakdown.append({"kernel": f"phsp_generate_kernel<{n},{'float' if dtype == 'f32' else 'double'}>",
+                          "n": n, "dtype": dtype, "massive": massive, "events": nev,
+                          "ms": round(ms, 4), "events_per_s": nev / (ms / 1e3),
+                          "hbm_gbs": round(gbs, 1), "hbm_frac": round(gbs / peaks["hbm_gbs"], 4)})
+    int_ms = per_launch_ms[-1] / args.steps
+    breakdown.append({"kernel": "phsp_integrate_tiles<3,float,DALITZ_2BW>+reduce", "events": int_events,
+                      "ms": round(int_ms, 4), "events_per_s": int_events / (int_ms / 1e3),
+                      "mean": res["mean"], "sigma": math.sqrt(res["var_mean"])})
+
+    # dominant kernel family by total time
+    fam = {}
+    for b in breakdown[:-1]:
+        fam.setdefault(b["dtype"], []).append(b)
+    fam_ms = {k: sum(x["ms"] for x in v) for k, v in fam.items()}
+    fam_ms["integrate"] = int_ms
+    dominant = max(fam_ms, key=fam_ms.get)
+    f32 = fam["f32"]
+    f32_bytes = sum(bytes_per_event(x["n"], "f32") * x["events"] for x in f32)
+    f32_ms = fam_ms["f32"]
+    roof = None
+    if dominant in ("f32", "f64"):
+        rows = fam[dominant]
+        tot_bytes = sum(bytes_per_event(x["n"], dominant) * x["events"] for x in rows)
+        achieved = tot_bytes / (fam_ms[dominant] / 1e3) / 1e9 / len(rows) * len(rows)
+        roof = {"bound": "hbm", "kernel": f"phsp_generate_kernel<N,{'float' if dominant == 'f32' else 'double'}> (N=2..10)",
+                "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": round(achieved / peaks["hbm_gbs"], 4), "peak_src": peaks["src"] + " (MEASURED_PEAKS hbm_gbs copy)",
+                "traffic": None}
+    line = {
+        "metric": "phase-space events/s (N=2..10 generator sweep FP32+FP64, plus Dalitz integral)",
+        "value": value, "unit": "events/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32,f64", "data": "synthetic",
+        "config": {"workload": "N-body sweep N=2..10 massless+massive, M=10 GeV, 1e8 events per "
+                               "(N, masses, precision), FP32 and FP64 SoA outputs; plus Dalitz "
+                               "|BW+0.5e^{1.2i}BW|^2 integral over 1e9 events (FP32 kinematics)",
+                   "events_per_launch": nev, "integrate_events": int_events,
+                   "events_per_step_per_gpu": per_step_events, "l2": "outputs >> L2 (126 MB); no flush",
+                   "parallelism": f"replicas x{world}"},
+        "gpu_launches": args.steps * (len(items) + 2 * math.ceil(int_events / 2 ** 26) + 1),
+        "roofline": roof,
+        "fp32_generator_roofline": {"bound": "hbm", "achieved": round(f32_bytes / (f32_ms / 1e3) / 1e9, 1),
+                                    "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                                    "frac": round(f32_bytes / (f32_ms / 1e3) / 1e9 / peaks["hbm_gbs"], 4)},
+        "dominant": dominant, "family_ms_per_step": {k: round(v, 3) for k, v in fam_ms.items()},
+        "breakdown": breakdown, "clocks": clk, "e2e": e2e,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds, nev, int_events)
+        line["cpu_baseline"]["value_ratio_note"] = "oracle, single thread, FP64; not a tuning target"
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------- CPU oracle arm
+def cpu_baseline(seconds: float, nev_full: int, int_full: int) -> dict:
+    """The oracle (single-threaded FP64 C) on a bounded sample of every item of the step;
+    each item's time is scaled to its full event count."""
+    import oracle
+    oracle.build()
+    items = sweep_items()
+    budget = seconds / (len(items) + 1)
+    total_t = 0.0
+    total_ev = 0
+    sample = {}
+    for dtype, massive, n in items:
+        masses = workloads.sweep_masses(n, massive)
+        m = 2000
+        t = 0.0
+        while True:
+            t0 = time.perf_counter()
+            oracle.generate(workloads.SWEEP_M, masses, m, 1000 + n)
+            t = time.perf_counter() - t0
+            if t > budget / 4 or m >= nev_full:
+                break
+            m *= 4
+        total_t += t * nev_full / m
+        total_ev += nev_full
+        sample[f"{dtype}/{'massive' if massive else 'massless'}/N{n}"] = m
+    m = 2000
+    while True:
+        t0 = time.perf_counter()
+        oracle.integrate(INT_CFG["M"], INT_CFG["masses"], m, INT_CFG["seed"], me=1, params=INT_CFG["params"])
+        t = time.perf_counter() - t0
+        if t > budget / 4 or m >= int_full:
+            break
+        m *= 4
+    total_t += t * int_full / m
+    total_ev += int_full
+    sample["integrate"] = m
+    return {"value": total_ev / total_t, "unit": "events/s", "cores": 1, "kind": "oracle",
+            "sample": "per item of the step: the oracle on the first k events (k doubled x4 until "
+                      "about %.1f s), time scaled to the item's full count; FP64 oracle stands in for both "
+                      "precisions" % (budget / 4), "sample_events": sample,
+            "host_cores_available": os.cpu_count()}
+
+
+def run_reference(args) -> None:
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    t0 = time.perf_counter()
+    cb = cpu_baseline(args.cpu_seconds / max(1, args.steps + args.warmup) * (args.steps + args.warmup),
+                      args.events, args.int_events)
+    wall = time.perf_counter() - t0
+    per_step_events = len(sweep_items()) * args.events + args.int_events
+    line = {"impl": "reference", "metric": "phase-space events/s (N=2..10 generator sweep FP32+FP64, plus Dalitz integral)",
+            "value": cb["value"], "unit": "events/s", "n_gpus": int(os.environ.get("WORLD_SIZE", "1")),
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step_events / cb["value"] * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "same as the CUDA arm; timed on a bounded sample per item and scaled",
+                       "events_per_launch": args.events, "integrate_events": args.int_events},
+            "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": cb["sample"], "value": cb["value"]},
+            "e2e": {"value": cb["value"], "unit": "events/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": round(wall, 1)}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--events", type=int, default=GEN_EVENTS)
+    ap.add_argument("--int-events", type=int, default=INT_CFG["nevents"])
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,172 @@
+/*
+ * hydra_phsp.h -- C ABI of the B300 (sm_103a) phase-space Monte Carlo library.
+ *
+ * The library implements the data-parallel hot path of the phase-space Monte Carlo of
+ * Hydra (arXiv:1711.05683, section 4.2 "Phase-Space Monte Carlo"): the Raubold-Lynch
+ * N-body event generator with per-event weights (F. James, "Monte Carlo Phase Space",
+ * CERN 68-15), and the weighted phase-space integral of a matrix element over its events
+ * (section 3, "phase-space Monte Carlo integration").  The paper's user API is Listing 4:
+ * PhaseSpace<N>(mother_mass, daughter_masses) and Generate(mother, events) filling a
+ * structure-of-arrays container of N 4-vectors plus a weight per event.
+ *
+ * Conventions shared by every entry point
+ *   - A decay is a parent of mass M > 0 at rest decaying to n daughters, 2 <= n <= 10,
+ *     with masses m_i >= 0 and kinetic energy T = M - sum m_i > 0 (computed in FP64 on the
+ *     host).  Masses are in any unit (GeV in the tests); outputs are in the same unit.
+ *   - 4-vectors are (E, px, py, pz), energy first (Listing 4, Vector4R(M, 0, 0, 0)).
+ *   - Random numbers: Philox4x32-10 (Salmon et al., SC'11) keyed by the 64-bit seed
+ *     (key = (seed low word, seed high word)).  Event e of a call uses the counter-event
+ *     index event_offset + e; draw d of that event is word d%4 of the Philox block with
+ *     counter (index low word, index high word, d/4, 0).  Each event uses 3n-4 draws: the
+ *     n-2 intermediate-mass draws, then (cos theta, phi) for each of the n-1 two-body
+ *     decays, parent first.  Hence one call over [0, a+b) equals two calls over [0, a)
+ *     and [a, a+b) (event_offset = a), bit for bit, at any launch shape.
+ *   - Weights: w = C_n * prod_k p*_k, with C_n = pi^(n-1) 2^(n-2) T^(n-2) / ((n-2)! M),
+ *     so that E[w] = R_n = Int prod d3p_i/(2 E_i) delta4(P - sum p_i) (no 2 pi factors;
+ *     the conventional Phi_n = R_n (2 pi)^(4-3n)).
+ *   - Streams: hydra_stream_t is the CUDA runtime's cudaStream_t (NULL = legacy default
+ *     stream).  Device pointers belong to the device current on the calling thread.
+ *   - Errors: every entry point returns a hydra_status; nothing is thrown across the ABI.
+ *     On an error nothing has been launched, except HYDRA_ERR_CUDA which reports a CUDA
+ *     error from a launch or copy.  hydra_last_error() gives a message for the calling
+ *     thread's most recent failure.
+ *   - Memory: the caller owns every buffer passed in.  The library owns a small scratch
+ *     area per device for the integral's partial sums (allocated on first use, released
+ *     by hydra_shutdown).
+ */
+#ifndef HYDRA_PHSP_H
+#define HYDRA_PHSP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *hydra_stream_t;
+
+typedef enum hydra_status {
+    HYDRA_OK = 0,
+    HYDRA_ERR_INVALID_ARG = 1,     /* bad value: non-finite/negative mass, M <= 0, NULL, ld < nevents, ... */
+    HYDRA_ERR_BELOW_THRESHOLD = 2, /* sum of daughter masses >= M */
+    HYDRA_ERR_UNSUPPORTED_N = 3,   /* n outside [2, 10] (or an ME id that needs another n) */
+    HYDRA_ERR_MISALIGNED = 4,      /* buffer not 16-byte aligned or ld not a multiple of 4 */
+    HYDRA_ERR_OOM = 5,             /* the library could not allocate its scratch memory */
+    HYDRA_ERR_CUDA = 6,            /* a CUDA runtime call or kernel launch failed */
+    HYDRA_ERR_TIMEOUT = 7,         /* a bounded device-side wait ran out */
+    HYDRA_ERR_BUSY = 8             /* admission refused: over the memory budget */
+} hydra_status;
+
+typedef enum hydra_dtype {
+    HYDRA_F32 = 0, /* FP32 kinematics, float outputs and weights */
+    HYDRA_F64 = 1  /* FP64 kinematics, double outputs and weights */
+} hydra_dtype;
+
+typedef enum hydra_me_id {
+    HYDRA_ME_FLAT = 0,      /* |ME|^2 = 1: the integral is the phase-space volume R_n */
+    HYDRA_ME_DALITZ_2BW = 1 /* n = 3 only; params = (m0a, Ga, m0b, Gb, |c|, arg c):
+                               |BW(s12; m0a, Ga) + |c| e^{i arg c} BW(s23; m0b, Gb)|^2,
+                               BW(s; m0, G) = 1 / (m0^2 - s - i m0 G), s_ij = (p_i + p_j)^2 */
+} hydra_me_id;
+
+/* Result of a phase-space integral of f = w |ME|^2 over n events. */
+typedef struct hydra_integral {
+    double mean;     /* sum_f / n: the MC estimate of Int |ME|^2 dR_n */
+    double var_mean; /* variance of that mean: (sum_f2/n - mean^2) / (n - 1) */
+    double sum_f;    /* sum of f */
+    double sum_f2;   /* sum of f^2 */
+    double sum_w;    /* sum of w (sum_w / n estimates R_n) */
+    double sum_w2;   /* sum of w^2 */
+    uint64_t n;      /* number of events */
+} hydra_integral;
+
+/* Message for the calling thread's most recent failing call ("" if none). */
+const char *hydra_last_error(void);
+
+/* Static name of a status code. */
+const char *hydra_status_string(hydra_status status);
+
+/*
+ * Weight constant C_n = pi^(n-1) 2^(n-2) T^(n-2) / ((n-2)! M) of the decay (host only).
+ * Section 4.2, "weighted samples": w = C_n prod p*_k has mean R_n.
+ * C_n (out, host) receives the value.  Errors: INVALID_ARG, UNSUPPORTED_N, BELOW_THRESHOLD.
+ */
+hydra_status hydra_phsp_volume_factor(double M, int n, const double *masses, double *C_n);
+
+/*
+ * Generate nevents weighted phase-space events (section 4.2; Listing 4's Generate).
+ *
+ *   M, n, masses  parent mass and the n daughter masses (host array of n doubles).
+ *   nevents       events to generate; 0 is a no-op that returns HYDRA_OK.
+ *   seed          Philox key.  event_offset: counter-event index of event 0 (see above);
+ *                 event_offset + nevents must not exceed 2^64.
+ *   dtype         HYDRA_F32 (float) or HYDRA_F64 (double) for kinematics and outputs.
+ *   out           device buffer, structure of arrays [n][4][ld] of dtype: component c
+ *                 (E, px, py, pz) of daughter i (masses[i]) for event e is at
+ *                 out[(i*4 + c)*ld + e].  16-byte aligned; ld >= nevents, ld % 4 == 0.
+ *   weights       device buffer of nevents dtype values, 16-byte aligned.
+ *   stream        CUDA stream; the call is asynchronous with respect to the host.
+ *
+ * Errors: UNSUPPORTED_N, INVALID_ARG (M, masses, dtype, NULL buffers, ld < nevents,
+ * offset overflow), BELOW_THRESHOLD, MISALIGNED, CUDA (launch failure).
+ */
+hydra_status hydra_phsp_generate(double M, int n, const double *masses, uint64_t nevents,
+                                 uint64_t seed, uint64_t event_offset, hydra_dtype dtype,
+                                 void *out, uint64_t ld, void *weights, hydra_stream_t stream);
+
+/*
+ * hydra_phsp_generate with HOST output buffers (end-to-end use: events land in host memory).
+ *
+ * Same arguments and event definition as hydra_phsp_generate, except that out_host
+ * ([n][4][ld], any ld >= nevents) and weights_host are host buffers; page-locked memory
+ * (cudaMallocHost / cudaHostRegister) gives full copy bandwidth.  The library generates
+ * chunks of 2^22 events into two device staging buffers it owns and copies each chunk to
+ * the host on its own copy stream while the next chunk is generated on `stream`.  The call
+ * blocks until every event is in host memory.  Errors: as hydra_phsp_generate (no
+ * alignment rule for host buffers), plus OOM for the staging buffers.
+ */
+hydra_status hydra_phsp_generate_host(double M, int n, const double *masses, uint64_t nevents,
+                                      uint64_t seed, uint64_t event_offset, hydra_dtype dtype,
+                                      void *out_host, uint64_t ld, void *weights_host,
+                                      hydra_stream_t stream);
+
+/*
+ * Phase-space integral of f = w |ME|^2 over nevents events (section 3, "phase-space Monte
+ * Carlo integration"; the events are those hydra_phsp_generate would produce for the same
+ * seed and event_offset, computed on the device and never stored).
+ *
+ *   kin_dtype     HYDRA_F32: FP32 kinematics and matrix element, FP64 accumulation;
+ *                 HYDRA_F64: FP64 throughout.
+ *   me, params, nparams  matrix element id and its parameters (host array).
+ *   result        host struct that receives the sums, mean and variance of the mean.
+ *
+ * Sums are accumulated in a fixed order that depends only on the event indices (tiles of
+ * 2048 events in FP64, then FP64 compensated sums over tiles and segments), so the result
+ * is the same bit for bit at every launch shape.  The call blocks until the result is on
+ * the host.  Errors: as hydra_phsp_generate, plus UNSUPPORTED_N for an ME that needs
+ * another n, INVALID_ARG for too few params or nevents == 0, OOM for scratch memory.
+ */
+hydra_status hydra_phsp_integrate(double M, int n, const double *masses, uint64_t nevents,
+                                  uint64_t seed, uint64_t event_offset, hydra_dtype kin_dtype,
+                                  hydra_me_id me, const double *params, int nparams,
+                                  hydra_integral *result, hydra_stream_t stream);
+
+/*
+ * The raw random numbers of nevents events: the 3n-4 Philox4x32-10 draws of each event in
+ * draw order (section 4.2's generator consumes them as described at the top of this file).
+ * out: device buffer of uint32, structure of arrays out[d * ld + e], ld >= nevents.
+ * Asynchronous.  Errors: UNSUPPORTED_N, INVALID_ARG, CUDA.
+ */
+hydra_status hydra_phsp_draws(int n, uint64_t nevents, uint64_t seed, uint64_t event_offset,
+                              uint32_t *out, uint64_t ld, hydra_stream_t stream);
+
+/* Release the per-device scratch memory of the library (all devices).  Not thread safe
+ * with respect to calls in flight. */
+hydra_status hydra_shutdown(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HYDRA_PHSP_H */

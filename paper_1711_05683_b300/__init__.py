@@ -1,0 +1,190 @@
+"""B300-native phase-space Monte Carlo (Hydra, arXiv:1711.05683, section 4.2).
+
+Thin Python binding of the C ABI in ``include/hydra_phsp.h``: it marshals arguments,
+allocates outputs with PyTorch on the current CUDA device and passes the current stream.
+Every step of the generator and of the integral runs in the CUDA kernels of
+``libhydra_phsp.so``; there is no other implementation here.  If the library is missing
+the import fails.
+
+    import paper_1711_05683_b300 as hp
+    p, w = hp.generate(5.2795, (3.0969, 0.4937, 0.1396), 100_000, seed=42, dtype="f64")
+    # p: [3, 4, ld] (E, px, py, pz) per daughter on the GPU; w: [nevents] weights
+    res = hp.integrate(1.865, (0.4937, 0.1396, 0.4937), 10**9, seed=7,
+                       me=hp.ME_DALITZ_2BW, params=(0.892, 0.05, 1.02, 0.004, 0.5, 1.2))
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libhydra_phsp.so")
+HEADER = os.path.join(os.path.dirname(_PKG), "include", "hydra_phsp.h")
+
+F32, F64 = 0, 1
+ME_FLAT, ME_DALITZ_2BW = 0, 1
+
+STATUS = {0: "HYDRA_OK", 1: "HYDRA_ERR_INVALID_ARG", 2: "HYDRA_ERR_BELOW_THRESHOLD",
+          3: "HYDRA_ERR_UNSUPPORTED_N", 4: "HYDRA_ERR_MISALIGNED", 5: "HYDRA_ERR_OOM",
+          6: "HYDRA_ERR_CUDA", 7: "HYDRA_ERR_TIMEOUT", 8: "HYDRA_ERR_BUSY"}
+
+
+class HydraError(RuntimeError):
+    """A non-OK hydra_status from the C ABI."""
+
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+        self.name = STATUS.get(status, str(status))
+
+
+class Integral(ctypes.Structure):
+    _fields_ = [("mean", ctypes.c_double), ("var_mean", ctypes.c_double),
+                ("sum_f", ctypes.c_double), ("sum_f2", ctypes.c_double),
+                ("sum_w", ctypes.c_double), ("sum_w2", ctypes.c_double),
+                ("n", ctypes.c_uint64)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded C library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: run `python -m paper_1711_05683_b300.build` "
+                              "(nvcc, sm_103a) first; there is no fallback implementation")
+        L = ctypes.CDLL(LIB_PATH)
+        d, i, u64, vp = ctypes.c_double, ctypes.c_int, ctypes.c_uint64, ctypes.c_void_p
+        dp = ctypes.POINTER(ctypes.c_double)
+        L.hydra_last_error.restype = ctypes.c_char_p
+        L.hydra_status_string.restype = ctypes.c_char_p
+        L.hydra_status_string.argtypes = [i]
+        L.hydra_phsp_volume_factor.argtypes = [d, i, dp, dp]
+        L.hydra_phsp_generate.argtypes = [d, i, dp, u64, u64, u64, i, vp, u64, vp, vp]
+        L.hydra_phsp_integrate.argtypes = [d, i, dp, u64, u64, u64, i, i, dp, i,
+                                           ctypes.POINTER(Integral), vp]
+        L.hydra_phsp_draws.argtypes = [i, u64, u64, u64, vp, u64, vp]
+        L.hydra_phsp_generate_host.argtypes = [d, i, dp, u64, u64, u64, i, vp, u64, vp, vp]
+        for name in ("hydra_phsp_volume_factor", "hydra_phsp_generate", "hydra_phsp_integrate",
+                     "hydra_phsp_draws", "hydra_phsp_generate_host", "hydra_shutdown"):
+            getattr(L, name).restype = i
+        _lib = L
+    return _lib
+
+
+def header_functions() -> list[str]:
+    """Names of the functions declared in include/hydra_phsp.h."""
+    with open(HEADER) as fh:
+        text = fh.read()
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(hydra_\w+)\s*\(", text, re.M)))
+
+
+def _check(status: int) -> None:
+    if status != 0:
+        raise HydraError(status, lib().hydra_last_error().decode())
+
+
+def _dbl(values) -> ctypes.Array:
+    vals = [float(v) for v in values]
+    return (ctypes.c_double * max(1, len(vals)))(*vals)
+
+
+def _dtype_code(dtype) -> int:
+    if dtype in (F32, "f32", "float32"):
+        return F32
+    if dtype in (F64, "f64", "float64"):
+        return F64
+    raise ValueError(f"dtype must be 'f32' or 'f64', got {dtype!r}")
+
+
+def _stream_handle(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def volume_factor(M: float, masses) -> float:
+    """C_n = pi^(n-1) 2^(n-2) T^(n-2) / ((n-2)! M) (host only)."""
+    out = ctypes.c_double()
+    _check(lib().hydra_phsp_volume_factor(float(M), len(masses), _dbl(masses), ctypes.byref(out)))
+    return out.value
+
+
+def padded_ld(nevents: int) -> int:
+    """Smallest leading dimension >= nevents accepted by generate (a multiple of 4)."""
+    return max(4, (int(nevents) + 3) // 4 * 4)
+
+
+def generate_into(M: float, masses, nevents: int, seed: int, out, weights, *, dtype="f32",
+                  event_offset: int = 0, stream=None) -> None:
+    """hydra_phsp_generate into caller tensors: out [n, 4, ld] and weights [>= nevents]."""
+    code = _dtype_code(dtype)
+    ld = int(out.shape[-1]) if nevents else 0
+    _check(lib().hydra_phsp_generate(float(M), len(masses), _dbl(masses), int(nevents), int(seed),
+                                     int(event_offset), code, ctypes.c_void_p(out.data_ptr()),
+                                     ld, ctypes.c_void_p(weights.data_ptr()),
+                                     _stream_handle(stream)))
+
+
+def generate_host_into(M: float, masses, nevents: int, seed: int, out, weights, *, dtype="f32",
+                       event_offset: int = 0, stream=None) -> None:
+    """hydra_phsp_generate_host into host (CPU, ideally pinned) tensors out [n, 4, ld] and
+    weights [>= nevents]; blocks until the events are in host memory."""
+    ld = int(out.shape[-1]) if nevents else 0
+    _check(lib().hydra_phsp_generate_host(float(M), len(masses), _dbl(masses), int(nevents),
+                                          int(seed), int(event_offset), _dtype_code(dtype),
+                                          ctypes.c_void_p(out.data_ptr()), ld,
+                                          ctypes.c_void_p(weights.data_ptr()),
+                                          _stream_handle(stream)))
+
+
+def generate(M: float, masses, nevents: int, seed: int, *, dtype="f32", event_offset: int = 0,
+             stream=None, device=None):
+    """Generate nevents weighted phase-space events on the GPU (section 4.2, Listing 4).
+
+    Returns (p, w): p is a [n, 4, ld] tensor (ld = nevents rounded up to a multiple of 4)
+    with p[i, c, e] the component c of (E, px, py, pz) of daughter i in event e, and w
+    the [nevents] event weights.  Asynchronous on the current stream."""
+    import torch
+    tdt = torch.float32 if _dtype_code(dtype) == F32 else torch.float64
+    ld = padded_ld(nevents)
+    dev = device if device is not None else torch.device("cuda", torch.cuda.current_device())
+    out = torch.empty((len(masses), 4, ld), dtype=tdt, device=dev)
+    w = torch.empty((ld,), dtype=tdt, device=dev)
+    generate_into(M, masses, nevents, seed, out, w, dtype=dtype, event_offset=event_offset,
+                  stream=stream)
+    return out, w[:nevents]
+
+
+def integrate(M: float, masses, nevents: int, seed: int, *, kin_dtype="f32", me: int = ME_FLAT,
+              params=(), event_offset: int = 0, stream=None) -> dict:
+    """Phase-space MC integral of f = w |ME|^2 over nevents events (blocking).
+
+    Returns dict(mean, var_mean, sum_f, sum_f2, sum_w, sum_w2, n)."""
+    res = Integral()
+    _check(lib().hydra_phsp_integrate(float(M), len(masses), _dbl(masses), int(nevents), int(seed),
+                                      int(event_offset), _dtype_code(kin_dtype), int(me),
+                                      _dbl(params), len(params), ctypes.byref(res),
+                                      _stream_handle(stream)))
+    return res.as_dict()
+
+
+def draws(n: int, nevents: int, seed: int, *, event_offset: int = 0, stream=None):
+    """The raw 3n-4 Philox draws per event as an int64 tensor [3n-4, nevents] (uint32 values)."""
+    import torch
+    ld = padded_ld(nevents)
+    out = torch.empty((3 * n - 4, ld), dtype=torch.int32, device="cuda")
+    _check(lib().hydra_phsp_draws(int(n), int(nevents), int(seed), int(event_offset),
+                                  ctypes.c_void_p(out.data_ptr()), ld, _stream_handle(stream)))
+    return out[:, :nevents].to(torch.int64) & 0xFFFFFFFF
+
+
+def shutdown() -> None:
+    _check(lib().hydra_shutdown())

@@ -1,0 +1,772 @@
+// phsp.cu -- kernels and C ABI of the B300 phase-space Monte Carlo library.
+//
+// Hot path of Hydra section 4.2 (Raubold-Lynch phase-space generation with weighted
+// events) and of the phase-space MC integral (section 3), written for sm_103a:
+//   phsp_generate_kernel<N, R>       one event per thread, grid-stride; every output
+//                                    component is one fully coalesced warp store into the
+//                                    structure-of-arrays buffer [n][4][ld].
+//   phsp_integrate_tiles<N, R, ME>   one warp per tile of 2048 events; the kinematics stay
+//                                    in registers; the tile's sums of (f, f^2, w, w^2) are
+//                                    formed in a fixed order and written as FP64.
+//   reduce_segments / finalize_integral   FP64 compensated (Neumaier / TwoSum) sums over
+//                                    tiles, then segments, in fixed trees over the event
+//                                    index, so an integral is bit-identical at every launch
+//                                    shape and chunking.
+// The C ABI is declared in include/hydra_phsp.h.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "hydra_phsp.h"
+#include "phsp_device.cuh"
+
+namespace hydra {
+
+// ------------------------------------------------------------------------------------
+// Fixed reduction geometry of the integral (part of the result's definition).
+// ------------------------------------------------------------------------------------
+constexpr int kTileEvents = 2048;                         // events per warp tile
+constexpr int kGroupEvents = 8;                           // events a lane sums in R before FP64
+constexpr int kLaneIters = kTileEvents / 32;              // 64 events per lane per tile
+constexpr int kSegTiles = 1024;                           // tiles per segment (2^21 events)
+constexpr uint64_t kChunkTiles = 32768;                   // tiles per launch (2^26 events)
+static_assert(kChunkTiles % kSegTiles == 0, "a chunk holds whole segments");
+static_assert(kLaneIters % kGroupEvents == 0, "groups tile the lane's events");
+
+// Matrix-element parameters in both precisions.
+struct MEConsts {
+    double a_m2, a_mg, b_m2, b_mg, c_re, c_im;  // m0^2, m0*Gamma, Re c, Im c
+    float a_m2f, a_mgf, b_m2f, b_mgf, c_ref, c_imf;
+};
+
+// ------------------------------------------------------------------------------------
+// Generation
+// ------------------------------------------------------------------------------------
+template <typename R>
+struct StoreSink {
+    R* __restrict__ base;  // out + e
+    R* __restrict__ wout;  // weights + e
+    uint64_t ld;
+    __device__ __forceinline__ void subsystem_mass(int, R) {}
+    __device__ __forceinline__ void daughter(int i, R E, R px, R py, R pz) {
+        R* p = base + static_cast<uint64_t>(4 * i) * ld;
+        p[0] = E;
+        p[ld] = px;
+        p[2 * ld] = py;
+        p[3 * ld] = pz;
+    }
+    __device__ __forceinline__ void weight(R w) { *wout = w; }
+};
+
+template <int N, typename R>
+__global__ void __launch_bounds__(256) phsp_generate_kernel(const __grid_constant__ DecayConsts C,
+                                                            uint64_t nevents, uint64_t event_offset,
+                                                            R* __restrict__ out, uint64_t ld,
+                                                            R* __restrict__ weights) {
+    const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+    for (uint64_t e = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < nevents;
+         e += stride) {
+        StoreSink<R> sink{out + e, weights + e, ld};
+        raubold_lynch_event<N, R>(C, event_offset + e, sink);
+    }
+}
+
+// The 3n-4 raw Philox draws of each event, structure of arrays out[d * ld + e].
+template <int N>
+__global__ void __launch_bounds__(256) phsp_draws_kernel(const __grid_constant__ DecayConsts C,
+                                                         uint64_t nevents, uint64_t event_offset,
+                                                         uint32_t* __restrict__ out, uint64_t ld) {
+    constexpr int kDraws = 3 * N - 4;
+    const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+    for (uint64_t e = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < nevents;
+         e += stride) {
+        const uint64_t ev = event_offset + e;
+        uint32_t x[4];
+#pragma unroll
+        for (int d = 0; d < kDraws; ++d) {
+            if (d % 4 == 0)
+                philox4x32_10(static_cast<uint32_t>(ev), static_cast<uint32_t>(ev >> 32), d / 4, 0u,
+                              C.rk0, C.rk1, x);
+            out[static_cast<uint64_t>(d) * ld + e] = x[d % 4];
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// Integration: f = w |ME|^2
+// ------------------------------------------------------------------------------------
+template <int N, typename R, int ME>
+struct IntegrandSink {
+    R E1 = R(0), M2 = R(0), w = R(0);
+    __device__ __forceinline__ void subsystem_mass(int k, R Mk) {
+        if (k == 2) M2 = Mk;
+    }
+    __device__ __forceinline__ void daughter(int i, R E, R, R, R) {
+        if (i == 0) E1 = E;
+    }
+    __device__ __forceinline__ void weight(R wv) { w = wv; }
+};
+
+template <typename R> __device__ __forceinline__ R me_param(double d, float f);
+template <> __device__ __forceinline__ float me_param<float>(double, float f) { return f; }
+template <> __device__ __forceinline__ double me_param<double>(double d, float) { return d; }
+
+// |BW(s12; a) + c BW(s23; b)|^2, BW(s) = (m0^2 - s + i m0 G) / ((m0^2 - s)^2 + (m0 G)^2).
+template <typename R>
+__device__ __forceinline__ R dalitz_2bw(const MEConsts& P, R s12, R s23) {
+    const R xa = me_param<R>(P.a_m2, P.a_m2f) - s12, ya = me_param<R>(P.a_mg, P.a_mgf);
+    const R xb = me_param<R>(P.b_m2, P.b_m2f) - s23, yb = me_param<R>(P.b_mg, P.b_mgf);
+    const R ia = R(1) / (xa * xa + ya * ya);
+    const R ib = R(1) / (xb * xb + yb * yb);
+    const R cr = me_param<R>(P.c_re, P.c_ref), ci = me_param<R>(P.c_im, P.c_imf);
+    const R re = xa * ia + (cr * xb - ci * yb) * ib;
+    const R im = ya * ia + (cr * yb + ci * xb) * ib;
+    return re * re + im * im;
+}
+
+template <int N, typename R, int ME>
+__device__ __forceinline__ void integrand(const DecayConsts& C, const MEConsts& P, uint64_t ev,
+                                          R& f, R& w) {
+    IntegrandSink<N, R, ME> s;
+    raubold_lynch_event<N, R>(C, ev, s);
+    w = s.w;
+    if constexpr (ME == HYDRA_ME_DALITZ_2BW) {
+        // s12 = M_2^2 (subsystem of daughters 1, 2); s23 = (P - p1)^2 = M^2 + m1^2 - 2 M E1
+        const R M = Prec<R>::M(C);
+        const R s12 = s.M2 * s.M2;
+        const R s23 = M * M + Prec<R>::m2(C, 0) - R(2) * M * s.E1;
+        f = s.w * dalitz_2bw<R>(P, s12, s23);
+    } else {
+        f = s.w;
+    }
+}
+
+struct TileSums {
+    double f, f2, w, w2;
+};
+
+// One warp per tile of kTileEvents events.  Lane l takes events tile*2048 + 32*i + l,
+// i = 0..63, sums them in R in groups of 8 (fixed order), folds each group into FP64, and
+// the warp combines lanes by a fixed xor butterfly; lane 0's total is the tile partial.
+template <int N, typename R, int ME>
+__global__ void __launch_bounds__(256) phsp_integrate_tiles(const __grid_constant__ DecayConsts C,
+                                                            const __grid_constant__ MEConsts P,
+                                                            uint64_t nevents, uint64_t event_offset,
+                                                            uint64_t tile_begin, uint64_t ntiles,
+                                                            TileSums* __restrict__ partials) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t warp = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = (static_cast<uint64_t>(gridDim.x) * blockDim.x) >> 5;
+    for (uint64_t t = warp; t < ntiles; t += nwarps) {
+        const uint64_t base = (tile_begin + t) * kTileEvents;
+        double af = 0.0, af2 = 0.0, aw = 0.0, aw2 = 0.0;
+#pragma unroll 1
+        for (int g = 0; g < kLaneIters / kGroupEvents; ++g) {
+            R sf = R(0), sf2 = R(0), sw = R(0), sw2 = R(0);
+#pragma unroll 2
+            for (int i = 0; i < kGroupEvents; ++i) {
+                const uint64_t e = base + static_cast<uint64_t>(32 * (g * kGroupEvents + i) + lane);
+                if (e < nevents) {
+                    R f, w;
+                    integrand<N, R, ME>(C, P, event_offset + e, f, w);
+                    sf += f;
+                    sf2 += f * f;
+                    sw += w;
+                    sw2 += w * w;
+                }
+            }
+            af += static_cast<double>(sf);
+            af2 += static_cast<double>(sf2);
+            aw += static_cast<double>(sw);
+            aw2 += static_cast<double>(sw2);
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            af += __shfl_xor_sync(0xffffffffu, af, off);
+            af2 += __shfl_xor_sync(0xffffffffu, af2, off);
+            aw += __shfl_xor_sync(0xffffffffu, aw, off);
+            aw2 += __shfl_xor_sync(0xffffffffu, aw2, off);
+        }
+        if (lane == 0) partials[t] = TileSums{af, af2, aw, aw2};
+    }
+}
+
+// Compensated FP64 accumulator (Neumaier's variant of Kahan summation).
+struct Comp {
+    double s = 0.0, c = 0.0;
+    __device__ __forceinline__ void add(double x) {
+        const double t = s + x;
+        if (fabs(s) >= fabs(x)) c += (s - t) + x;
+        else c += (x - t) + s;
+        s = t;
+    }
+    // Combine with another accumulator: TwoSum of the leading parts, compensations added.
+    __device__ __forceinline__ void merge(double s2, double c2) {
+        const double t = s + s2;
+        const double bb = t - s;
+        const double err = (s - (t - bb)) + (s2 - bb);
+        s = t;
+        c = c + c2 + err;
+    }
+};
+
+__device__ __forceinline__ void warp_merge(Comp& a) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const double s2 = __shfl_xor_sync(0xffffffffu, a.s, off);
+        const double c2 = __shfl_xor_sync(0xffffffffu, a.c, off);
+        a.merge(s2, c2);
+    }
+}
+
+// Segment partials: 8 doubles per segment, (s, c) for f, f^2, w, w^2.
+// One warp per segment of kSegTiles tiles; lane l accumulates tiles l, l+32, ... in order.
+__global__ void __launch_bounds__(128) reduce_segments(const TileSums* __restrict__ partials,
+                                                       uint64_t ntiles, uint64_t seg_begin,
+                                                       double* __restrict__ seg_out) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t seg = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nseg = (ntiles + kSegTiles - 1) / kSegTiles;
+    if (seg >= nseg) return;
+    Comp f, f2, w, w2;
+    for (int j = 0; j < kSegTiles / 32; ++j) {
+        const uint64_t t = seg * kSegTiles + static_cast<uint64_t>(j * 32 + lane);
+        if (t < ntiles) {
+            const TileSums p = partials[t];
+            f.add(p.f);
+            f2.add(p.f2);
+            w.add(p.w);
+            w2.add(p.w2);
+        }
+    }
+    warp_merge(f);
+    warp_merge(f2);
+    warp_merge(w);
+    warp_merge(w2);
+    if (lane == 0) {
+        double* o = seg_out + (seg_begin + seg) * 8;
+        o[0] = f.s; o[1] = f.c; o[2] = f2.s; o[3] = f2.c;
+        o[4] = w.s; o[5] = w.c; o[6] = w2.s; o[7] = w2.c;
+    }
+}
+
+// One warp folds all segments (lane l: segments l, l+32, ...) and writes the result.
+__global__ void __launch_bounds__(32) finalize_integral(const double* __restrict__ seg,
+                                                        uint64_t nseg, uint64_t nevents,
+                                                        hydra_integral* __restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    Comp q[4];
+    for (uint64_t s = lane; s < nseg; s += 32) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            q[k].add(seg[s * 8 + 2 * k]);
+            q[k].add(seg[s * 8 + 2 * k + 1]);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) warp_merge(q[k]);
+    if (lane == 0) {
+        const double n = static_cast<double>(nevents);
+        const double sf = q[0].s + q[0].c, sf2 = q[1].s + q[1].c;
+        const double sw = q[2].s + q[2].c, sw2 = q[3].s + q[3].c;
+        const double mean = sf / n;
+        const double var = nevents > 1 ? (sf2 / n - mean * mean) / (n - 1.0) : 0.0;
+        out->mean = mean;
+        out->var_mean = var;
+        out->sum_f = sf;
+        out->sum_f2 = sf2;
+        out->sum_w = sw;
+        out->sum_w2 = sw2;
+        out->n = nevents;
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// Host side
+// ------------------------------------------------------------------------------------
+thread_local std::string g_last_error;
+
+static hydra_status fail(hydra_status st, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+static hydra_status fail(hydra_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return st;
+}
+
+static hydra_status cuda_fail(cudaError_t err, const char* what) {
+    return fail(HYDRA_ERR_CUDA, "%s: %s (%s)", what, cudaGetErrorName(err), cudaGetErrorString(err));
+}
+
+// Validates a decay and fills the launch constants.  T = M - sum m in FP64.
+static hydra_status make_consts(double M, int n, const double* masses, uint64_t seed,
+                                DecayConsts* C) {
+    if (n < 2 || n > kNMax) return fail(HYDRA_ERR_UNSUPPORTED_N, "n = %d outside [2, %d]", n, kNMax);
+    if (!masses) return fail(HYDRA_ERR_INVALID_ARG, "masses is NULL");
+    if (!std::isfinite(M) || !(M > 0.0)) return fail(HYDRA_ERR_INVALID_ARG, "parent mass M = %g must be finite and > 0", M);
+    std::memset(C, 0, sizeof *C);
+    double sum = 0.0;
+    for (int i = 0; i < n; ++i) {
+        const double m = masses[i];
+        if (!std::isfinite(m) || !(m >= 0.0))
+            return fail(HYDRA_ERR_INVALID_ARG, "daughter mass %d = %g must be finite and >= 0", i, m);
+        sum += m;
+        C->m[i] = m;
+        C->mu[i] = sum;
+        C->m2[i] = m * m;
+    }
+    const double T = M - sum;
+    if (!(T > 0.0))
+        return fail(HYDRA_ERR_BELOW_THRESHOLD, "sum of daughter masses %.17g >= M = %.17g", sum, M);
+    // C_n = pi^(n-1) 2^(n-2) T^(n-2) / ((n-2)! M)
+    double Cn = 1.0;
+    for (int i = 0; i < n - 1; ++i) Cn *= M_PI;
+    for (int i = 0; i < n - 2; ++i) Cn *= 2.0 * T;
+    for (int i = 2; i <= n - 2; ++i) Cn /= static_cast<double>(i);
+    Cn /= M;
+    C->M = M;
+    C->Ts = std::ldexp(T, -32);
+    C->Ts_half = std::ldexp(T, -33);
+    C->C = Cn;
+    C->Mf = static_cast<float>(M);
+    C->Tsf = static_cast<float>(C->Ts);
+    C->Ts_halff = static_cast<float>(C->Ts_half);
+    C->Cf = static_cast<float>(Cn);
+    for (int i = 0; i < n; ++i) {
+        C->mf[i] = static_cast<float>(C->m[i]);
+        C->muf[i] = static_cast<float>(C->mu[i]);
+        C->m2f[i] = static_cast<float>(C->m2[i]);
+    }
+    uint32_t k0 = static_cast<uint32_t>(seed), k1 = static_cast<uint32_t>(seed >> 32);
+    for (int r = 0; r < 10; ++r) {
+        C->rk0[r] = k0;
+        C->rk1[r] = k1;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return HYDRA_OK;
+}
+
+// Grid size for a grid-stride kernel: resident blocks per SM x SM count.
+static int grid_for(const void* kernel, int block, uint64_t work_items) {
+    int dev = 0, sms = 148, per_sm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, 0);
+    if (per_sm < 1) per_sm = 1;
+    const uint64_t full = static_cast<uint64_t>(sms) * per_sm;
+    const uint64_t need = (work_items + block - 1) / block;
+    return static_cast<int>(need < full ? (need ? need : 1) : full);
+}
+
+template <typename R>
+static const void* generate_kernel_for(int n) {
+    switch (n) {
+        case 2: return reinterpret_cast<const void*>(&phsp_generate_kernel<2, R>);
+        case 3: return reinterpret_cast<const void*>(&phsp_generate_kernel<3, R>);
+        case 4: return reinterpret_cast<const void*>(&phsp_generate_kernel<4, R>);
+        case 5: return reinterpret_cast<const void*>(&phsp_generate_kernel<5, R>);
+        case 6: return reinterpret_cast<const void*>(&phsp_generate_kernel<6, R>);
+        case 7: return reinterpret_cast<const void*>(&phsp_generate_kernel<7, R>);
+        case 8: return reinterpret_cast<const void*>(&phsp_generate_kernel<8, R>);
+        case 9: return reinterpret_cast<const void*>(&phsp_generate_kernel<9, R>);
+        case 10: return reinterpret_cast<const void*>(&phsp_generate_kernel<10, R>);
+    }
+    return nullptr;
+}
+
+static const void* draws_kernel_for(int n) {
+    switch (n) {
+        case 2: return reinterpret_cast<const void*>(&phsp_draws_kernel<2>);
+        case 3: return reinterpret_cast<const void*>(&phsp_draws_kernel<3>);
+        case 4: return reinterpret_cast<const void*>(&phsp_draws_kernel<4>);
+        case 5: return reinterpret_cast<const void*>(&phsp_draws_kernel<5>);
+        case 6: return reinterpret_cast<const void*>(&phsp_draws_kernel<6>);
+        case 7: return reinterpret_cast<const void*>(&phsp_draws_kernel<7>);
+        case 8: return reinterpret_cast<const void*>(&phsp_draws_kernel<8>);
+        case 9: return reinterpret_cast<const void*>(&phsp_draws_kernel<9>);
+        case 10: return reinterpret_cast<const void*>(&phsp_draws_kernel<10>);
+    }
+    return nullptr;
+}
+
+template <typename R, int ME>
+static const void* integrate_kernel_for(int n) {
+    if constexpr (ME == HYDRA_ME_DALITZ_2BW) {
+        return n == 3 ? reinterpret_cast<const void*>(&phsp_integrate_tiles<3, R, ME>) : nullptr;
+    } else {
+        switch (n) {
+            case 2: return reinterpret_cast<const void*>(&phsp_integrate_tiles<2, R, ME>);
+            case 3: return reinterpret_cast<const void*>(&phsp_integrate_tiles<3, R, ME>);
+            case 4: return reinterpret_cast<const void*>(&phsp_integrate_tiles<4, R, ME>);
+            case 5: return reinterpret_cast<const void*>(&phsp_integrate_tiles<5, R, ME>);
+            case 6: return reinterpret_cast<const void*>(&phsp_integrate_tiles<6, R, ME>);
+            case 7: return reinterpret_cast<const void*>(&phsp_integrate_tiles<7, R, ME>);
+            case 8: return reinterpret_cast<const void*>(&phsp_integrate_tiles<8, R, ME>);
+            case 9: return reinterpret_cast<const void*>(&phsp_integrate_tiles<9, R, ME>);
+            case 10: return reinterpret_cast<const void*>(&phsp_integrate_tiles<10, R, ME>);
+        }
+        return nullptr;
+    }
+}
+
+constexpr int kGenBlock = 256;
+constexpr int kIntBlock = 256;
+
+// Per-device scratch for integrals: tile partials of one chunk, segment partials of one
+// request, the device-side result and a pinned host copy.  Guarded by its mutex.
+struct DeviceScratch {
+    std::mutex mu;
+    TileSums* tiles = nullptr;
+    double* segs = nullptr;
+    uint64_t seg_cap = 0;  // segments
+    hydra_integral* d_result = nullptr;
+    hydra_integral* h_result = nullptr;
+    // host-output generation: two device staging buffers, a copy stream and events
+    void* stage[2] = {nullptr, nullptr};
+    size_t stage_bytes = 0;
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t gen_done[2] = {nullptr, nullptr};
+    cudaEvent_t copy_done[2] = {nullptr, nullptr};
+};
+
+static std::mutex g_scratch_mu;
+static std::vector<DeviceScratch*> g_scratch;
+
+static DeviceScratch* scratch_for_current_device() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    std::lock_guard<std::mutex> lk(g_scratch_mu);
+    if (static_cast<int>(g_scratch.size()) <= dev) g_scratch.resize(dev + 1, nullptr);
+    if (!g_scratch[dev]) g_scratch[dev] = new DeviceScratch();
+    return g_scratch[dev];
+}
+
+static hydra_status ensure_scratch(DeviceScratch* s, uint64_t nseg) {
+    if (!s->tiles) {
+        if (cudaMalloc(&s->tiles, kChunkTiles * sizeof(TileSums)) != cudaSuccess) {
+            s->tiles = nullptr;
+            cudaGetLastError();
+            return fail(HYDRA_ERR_OOM, "cannot allocate %zu bytes of tile scratch",
+                        static_cast<size_t>(kChunkTiles * sizeof(TileSums)));
+        }
+    }
+    if (!s->d_result) {
+        if (cudaMalloc(&s->d_result, sizeof(hydra_integral)) != cudaSuccess ||
+            cudaMallocHost(&s->h_result, sizeof(hydra_integral)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(HYDRA_ERR_OOM, "cannot allocate the integral result buffers");
+        }
+    }
+    if (nseg > s->seg_cap) {
+        uint64_t cap = s->seg_cap ? s->seg_cap : 64;
+        while (cap < nseg) cap *= 2;
+        double* p = nullptr;
+        if (cudaMalloc(&p, cap * 8 * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(HYDRA_ERR_OOM, "cannot allocate segment scratch for %llu segments",
+                        static_cast<unsigned long long>(nseg));
+        }
+        if (s->segs) cudaFree(s->segs);
+        s->segs = p;
+        s->seg_cap = cap;
+    }
+    return HYDRA_OK;
+}
+
+// Events per staging chunk of hydra_phsp_generate_host (a multiple of 4).
+constexpr uint64_t kStageEvents = uint64_t(1) << 22;
+
+static hydra_status ensure_staging(DeviceScratch* s, size_t bytes) {
+    if (!s->copy_stream) {
+        if (cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            s->copy_stream = nullptr;
+            return fail(HYDRA_ERR_CUDA, "cannot create the copy stream");
+        }
+        for (int b = 0; b < 2; ++b) {
+            if (cudaEventCreateWithFlags(&s->gen_done[b], cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreateWithFlags(&s->copy_done[b], cudaEventDisableTiming) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(HYDRA_ERR_CUDA, "cannot create staging events");
+            }
+        }
+    }
+    if (bytes > s->stage_bytes) {
+        for (int b = 0; b < 2; ++b) {
+            if (s->stage[b]) cudaFree(s->stage[b]);
+            s->stage[b] = nullptr;
+        }
+        s->stage_bytes = 0;
+        for (int b = 0; b < 2; ++b) {
+            if (cudaMalloc(&s->stage[b], bytes) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(HYDRA_ERR_OOM, "cannot allocate %zu bytes of staging memory", bytes);
+            }
+        }
+        s->stage_bytes = bytes;
+    }
+    return HYDRA_OK;
+}
+
+static hydra_status make_me(hydra_me_id me, int n, const double* params, int nparams, MEConsts* P) {
+    std::memset(P, 0, sizeof *P);
+    if (me == HYDRA_ME_FLAT) return HYDRA_OK;
+    if (me != HYDRA_ME_DALITZ_2BW) return fail(HYDRA_ERR_INVALID_ARG, "unknown matrix element id %d", static_cast<int>(me));
+    if (n != 3) return fail(HYDRA_ERR_UNSUPPORTED_N, "the Dalitz matrix element needs n = 3 (got %d)", n);
+    if (!params || nparams < 6) return fail(HYDRA_ERR_INVALID_ARG, "the Dalitz matrix element needs 6 params (got %d)", nparams);
+    for (int i = 0; i < 6; ++i)
+        if (!std::isfinite(params[i])) return fail(HYDRA_ERR_INVALID_ARG, "param %d is not finite", i);
+    P->a_m2 = params[0] * params[0];
+    P->a_mg = params[0] * params[1];
+    P->b_m2 = params[2] * params[2];
+    P->b_mg = params[2] * params[3];
+    P->c_re = params[4] * std::cos(params[5]);
+    P->c_im = params[4] * std::sin(params[5]);
+    P->a_m2f = static_cast<float>(P->a_m2);
+    P->a_mgf = static_cast<float>(P->a_mg);
+    P->b_m2f = static_cast<float>(P->b_m2);
+    P->b_mgf = static_cast<float>(P->b_mg);
+    P->c_ref = static_cast<float>(P->c_re);
+    P->c_imf = static_cast<float>(P->c_im);
+    return HYDRA_OK;
+}
+
+template <typename R>
+static hydra_status launch_integrate_chunks(const void* kern, const DecayConsts& C, const MEConsts& P,
+                                            uint64_t nevents, uint64_t event_offset,
+                                            DeviceScratch* s, cudaStream_t st) {
+    const uint64_t ntiles = (nevents + kTileEvents - 1) / kTileEvents;
+    for (uint64_t t0 = 0; t0 < ntiles; t0 += kChunkTiles) {
+        const uint64_t nt = ntiles - t0 < kChunkTiles ? ntiles - t0 : kChunkTiles;
+        const int grid = grid_for(kern, kIntBlock, nt * 32);
+        TileSums* tiles = s->tiles;
+        void* args[] = {const_cast<DecayConsts*>(&C), const_cast<MEConsts*>(&P), &nevents,
+                        &event_offset, const_cast<uint64_t*>(&t0), const_cast<uint64_t*>(&nt),
+                        &tiles};
+        cudaError_t err = cudaLaunchKernel(kern, dim3(grid), dim3(kIntBlock), args, 0, st);
+        if (err != cudaSuccess) return cuda_fail(err, "integrate launch");
+        const uint64_t nseg = (nt + kSegTiles - 1) / kSegTiles;
+        const uint64_t seg_begin = t0 / kSegTiles;
+        const int rgrid = static_cast<int>((nseg * 32 + 127) / 128);
+        reduce_segments<<<rgrid, 128, 0, st>>>(s->tiles, nt, seg_begin, s->segs);
+        err = cudaGetLastError();
+        if (err != cudaSuccess) return cuda_fail(err, "segment reduction launch");
+    }
+    return HYDRA_OK;
+}
+
+}  // namespace hydra
+
+using namespace hydra;
+
+extern "C" {
+
+const char* hydra_last_error(void) { return g_last_error.c_str(); }
+
+const char* hydra_status_string(hydra_status status) {
+    switch (status) {
+        case HYDRA_OK: return "HYDRA_OK";
+        case HYDRA_ERR_INVALID_ARG: return "HYDRA_ERR_INVALID_ARG";
+        case HYDRA_ERR_BELOW_THRESHOLD: return "HYDRA_ERR_BELOW_THRESHOLD";
+        case HYDRA_ERR_UNSUPPORTED_N: return "HYDRA_ERR_UNSUPPORTED_N";
+        case HYDRA_ERR_MISALIGNED: return "HYDRA_ERR_MISALIGNED";
+        case HYDRA_ERR_OOM: return "HYDRA_ERR_OOM";
+        case HYDRA_ERR_CUDA: return "HYDRA_ERR_CUDA";
+        case HYDRA_ERR_TIMEOUT: return "HYDRA_ERR_TIMEOUT";
+        case HYDRA_ERR_BUSY: return "HYDRA_ERR_BUSY";
+    }
+    return "HYDRA_ERR_UNKNOWN";
+}
+
+hydra_status hydra_phsp_volume_factor(double M, int n, const double* masses, double* C_n) {
+    if (!C_n) return fail(HYDRA_ERR_INVALID_ARG, "C_n is NULL");
+    DecayConsts C;
+    const hydra_status st = make_consts(M, n, masses, 0, &C);
+    if (st != HYDRA_OK) return st;
+    *C_n = C.C;
+    return HYDRA_OK;
+}
+
+hydra_status hydra_phsp_generate(double M, int n, const double* masses, uint64_t nevents,
+                                 uint64_t seed, uint64_t event_offset, hydra_dtype dtype,
+                                 void* out, uint64_t ld, void* weights, hydra_stream_t stream) {
+    DecayConsts C;
+    hydra_status st = make_consts(M, n, masses, seed, &C);
+    if (st != HYDRA_OK) return st;
+    if (dtype != HYDRA_F32 && dtype != HYDRA_F64) return fail(HYDRA_ERR_INVALID_ARG, "unknown dtype %d", static_cast<int>(dtype));
+    if (event_offset + nevents < event_offset) return fail(HYDRA_ERR_INVALID_ARG, "event_offset + nevents overflows 64 bits");
+    if (nevents == 0) return HYDRA_OK;
+    if (!out || !weights) return fail(HYDRA_ERR_INVALID_ARG, "out and weights must not be NULL");
+    if (ld < nevents) return fail(HYDRA_ERR_INVALID_ARG, "ld = %llu < nevents = %llu", static_cast<unsigned long long>(ld), static_cast<unsigned long long>(nevents));
+    if ((reinterpret_cast<uintptr_t>(out) & 15u) || (reinterpret_cast<uintptr_t>(weights) & 15u))
+        return fail(HYDRA_ERR_MISALIGNED, "out and weights must be 16-byte aligned");
+    if (ld % 4 != 0) return fail(HYDRA_ERR_MISALIGNED, "ld = %llu must be a multiple of 4", static_cast<unsigned long long>(ld));
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const void* kern = dtype == HYDRA_F32 ? generate_kernel_for<float>(n) : generate_kernel_for<double>(n);
+    const int grid = grid_for(kern, kGenBlock, nevents);
+    void* args[] = {&C, &nevents, &event_offset, &out, &ld, &weights};
+    const cudaError_t err = cudaLaunchKernel(kern, dim3(grid), dim3(kGenBlock), args, 0, s);
+    if (err != cudaSuccess) return cuda_fail(err, "generate launch");
+    return HYDRA_OK;
+}
+
+hydra_status hydra_phsp_generate_host(double M, int n, const double* masses, uint64_t nevents,
+                                      uint64_t seed, uint64_t event_offset, hydra_dtype dtype,
+                                      void* out_host, uint64_t ld, void* weights_host,
+                                      hydra_stream_t stream) {
+    DecayConsts C;
+    hydra_status st = make_consts(M, n, masses, seed, &C);
+    if (st != HYDRA_OK) return st;
+    if (dtype != HYDRA_F32 && dtype != HYDRA_F64) return fail(HYDRA_ERR_INVALID_ARG, "unknown dtype %d", static_cast<int>(dtype));
+    if (event_offset + nevents < event_offset) return fail(HYDRA_ERR_INVALID_ARG, "event_offset + nevents overflows 64 bits");
+    if (nevents == 0) return HYDRA_OK;
+    if (!out_host || !weights_host) return fail(HYDRA_ERR_INVALID_ARG, "out and weights must not be NULL");
+    if (ld < nevents) return fail(HYDRA_ERR_INVALID_ARG, "ld = %llu < nevents = %llu", static_cast<unsigned long long>(ld), static_cast<unsigned long long>(nevents));
+    const size_t elem = dtype == HYDRA_F32 ? sizeof(float) : sizeof(double);
+    const uint64_t chunk = nevents < kStageEvents ? (nevents + 3) / 4 * 4 : kStageEvents;
+    const size_t arrays = static_cast<size_t>(4 * n + 1);
+    DeviceScratch* s = scratch_for_current_device();
+    if (!s) return fail(HYDRA_ERR_CUDA, "no current CUDA device");
+    std::lock_guard<std::mutex> lk(s->mu);
+    st = ensure_staging(s, arrays * chunk * elem);
+    if (st != HYDRA_OK) return st;
+    cudaStream_t gs = reinterpret_cast<cudaStream_t>(stream);
+    const void* kern = dtype == HYDRA_F32 ? generate_kernel_for<float>(n) : generate_kernel_for<double>(n);
+    cudaError_t err = cudaSuccess;
+    // the copy stream must not run ahead of work already queued on the caller's stream
+    err = cudaEventRecord(s->gen_done[1], gs);
+    if (err == cudaSuccess) err = cudaStreamWaitEvent(s->copy_stream, s->gen_done[1], 0);
+    if (err != cudaSuccess) return cuda_fail(err, "host generate ordering");
+    uint64_t i = 0;
+    for (uint64_t e0 = 0; e0 < nevents; e0 += chunk, ++i) {
+        const int b = static_cast<int>(i & 1);
+        const uint64_t cnt = nevents - e0 < chunk ? nevents - e0 : chunk;
+        char* stage = static_cast<char*>(s->stage[b]);
+        if (i >= 2) {
+            err = cudaStreamWaitEvent(gs, s->copy_done[b], 0);  // staging buffer b is free again
+            if (err != cudaSuccess) return cuda_fail(err, "staging wait");
+        }
+        void* dout = stage;
+        void* dw = stage + static_cast<size_t>(4 * n) * chunk * elem;
+        uint64_t off = event_offset + e0;
+        uint64_t sld = chunk;
+        uint64_t cnt_v = cnt;
+        const int grid = grid_for(kern, kGenBlock, cnt);
+        void* args[] = {&C, &cnt_v, &off, &dout, &sld, &dw};
+        err = cudaLaunchKernel(kern, dim3(grid), dim3(kGenBlock), args, 0, gs);
+        if (err == cudaSuccess) err = cudaEventRecord(s->gen_done[b], gs);
+        if (err == cudaSuccess) err = cudaStreamWaitEvent(s->copy_stream, s->gen_done[b], 0);
+        if (err == cudaSuccess)
+            err = cudaMemcpy2DAsync(static_cast<char*>(out_host) + e0 * elem, ld * elem, dout, chunk * elem,
+                                    cnt * elem, static_cast<size_t>(4 * n), cudaMemcpyDeviceToHost, s->copy_stream);
+        if (err == cudaSuccess)
+            err = cudaMemcpyAsync(static_cast<char*>(weights_host) + e0 * elem, dw, cnt * elem,
+                                  cudaMemcpyDeviceToHost, s->copy_stream);
+        if (err == cudaSuccess) err = cudaEventRecord(s->copy_done[b], s->copy_stream);
+        if (err != cudaSuccess) return cuda_fail(err, "host generate chunk");
+    }
+    err = cudaStreamSynchronize(s->copy_stream);
+    if (err != cudaSuccess) return cuda_fail(err, "host generate synchronize");
+    return HYDRA_OK;
+}
+
+hydra_status hydra_phsp_draws(int n, uint64_t nevents, uint64_t seed, uint64_t event_offset,
+                              uint32_t* out, uint64_t ld, hydra_stream_t stream) {
+    if (n < 2 || n > kNMax) return fail(HYDRA_ERR_UNSUPPORTED_N, "n = %d outside [2, %d]", n, kNMax);
+    if (event_offset + nevents < event_offset) return fail(HYDRA_ERR_INVALID_ARG, "event_offset + nevents overflows 64 bits");
+    if (nevents == 0) return HYDRA_OK;
+    if (!out) return fail(HYDRA_ERR_INVALID_ARG, "out must not be NULL");
+    if (ld < nevents) return fail(HYDRA_ERR_INVALID_ARG, "ld < nevents");
+    DecayConsts C;
+    std::memset(&C, 0, sizeof C);
+    uint32_t k0 = static_cast<uint32_t>(seed), k1 = static_cast<uint32_t>(seed >> 32);
+    for (int r = 0; r < 10; ++r) {
+        C.rk0[r] = k0;
+        C.rk1[r] = k1;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    const void* kern = draws_kernel_for(n);
+    const int grid = grid_for(kern, kGenBlock, nevents);
+    void* args[] = {&C, &nevents, &event_offset, &out, &ld};
+    const cudaError_t err = cudaLaunchKernel(kern, dim3(grid), dim3(kGenBlock), args, 0,
+                                             reinterpret_cast<cudaStream_t>(stream));
+    if (err != cudaSuccess) return cuda_fail(err, "draws launch");
+    return HYDRA_OK;
+}
+
+hydra_status hydra_phsp_integrate(double M, int n, const double* masses, uint64_t nevents,
+                                  uint64_t seed, uint64_t event_offset, hydra_dtype kin_dtype,
+                                  hydra_me_id me, const double* params, int nparams,
+                                  hydra_integral* result, hydra_stream_t stream) {
+    DecayConsts C;
+    hydra_status st = make_consts(M, n, masses, seed, &C);
+    if (st != HYDRA_OK) return st;
+    if (kin_dtype != HYDRA_F32 && kin_dtype != HYDRA_F64) return fail(HYDRA_ERR_INVALID_ARG, "unknown dtype %d", static_cast<int>(kin_dtype));
+    if (!result) return fail(HYDRA_ERR_INVALID_ARG, "result is NULL");
+    if (nevents == 0) return fail(HYDRA_ERR_INVALID_ARG, "nevents must be > 0");
+    if (event_offset + nevents < event_offset) return fail(HYDRA_ERR_INVALID_ARG, "event_offset + nevents overflows 64 bits");
+    MEConsts P;
+    st = make_me(me, n, params, nparams, &P);
+    if (st != HYDRA_OK) return st;
+    const void* kern = nullptr;
+    if (kin_dtype == HYDRA_F32)
+        kern = me == HYDRA_ME_FLAT ? integrate_kernel_for<float, HYDRA_ME_FLAT>(n) : integrate_kernel_for<float, HYDRA_ME_DALITZ_2BW>(n);
+    else
+        kern = me == HYDRA_ME_FLAT ? integrate_kernel_for<double, HYDRA_ME_FLAT>(n) : integrate_kernel_for<double, HYDRA_ME_DALITZ_2BW>(n);
+    if (!kern) return fail(HYDRA_ERR_UNSUPPORTED_N, "no kernel for n = %d and me = %d", n, static_cast<int>(me));
+
+    DeviceScratch* s = scratch_for_current_device();
+    if (!s) return fail(HYDRA_ERR_CUDA, "no current CUDA device");
+    std::lock_guard<std::mutex> lk(s->mu);
+    const uint64_t ntiles = (nevents + kTileEvents - 1) / kTileEvents;
+    const uint64_t nseg = (ntiles + kSegTiles - 1) / kSegTiles;
+    st = ensure_scratch(s, nseg);
+    if (st != HYDRA_OK) return st;
+    cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+    st = kin_dtype == HYDRA_F32 ? launch_integrate_chunks<float>(kern, C, P, nevents, event_offset, s, cs)
+                                : launch_integrate_chunks<double>(kern, C, P, nevents, event_offset, s, cs);
+    if (st != HYDRA_OK) return st;
+    finalize_integral<<<1, 32, 0, cs>>>(s->segs, nseg, nevents, s->d_result);
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return cuda_fail(err, "finalize launch");
+    err = cudaMemcpyAsync(s->h_result, s->d_result, sizeof(hydra_integral), cudaMemcpyDeviceToHost, cs);
+    if (err != cudaSuccess) return cuda_fail(err, "result copy");
+    err = cudaStreamSynchronize(cs);
+    if (err != cudaSuccess) return cuda_fail(err, "integrate synchronize");
+    *result = *s->h_result;
+    return HYDRA_OK;
+}
+
+hydra_status hydra_shutdown(void) {
+    std::lock_guard<std::mutex> lk(g_scratch_mu);
+    for (DeviceScratch*& s : g_scratch) {
+        if (!s) continue;
+        if (s->tiles) cudaFree(s->tiles);
+        if (s->segs) cudaFree(s->segs);
+        if (s->d_result) cudaFree(s->d_result);
+        if (s->h_result) cudaFreeHost(s->h_result);
+        for (int b = 0; b < 2; ++b) {
+            if (s->stage[b]) cudaFree(s->stage[b]);
+            if (s->gen_done[b]) cudaEventDestroy(s->gen_done[b]);
+            if (s->copy_done[b]) cudaEventDestroy(s->copy_done[b]);
+        }
+        if (s->copy_stream) cudaStreamDestroy(s->copy_stream);
+        delete s;
+        s = nullptr;
+    }
+    return HYDRA_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,214 @@
+// phsp_device.cuh -- device building blocks of the phase-space Monte Carlo hot path.
+//
+// One event of the Raubold-Lynch generator (Hydra section 4.2; F. James, CERN 68-15) held
+// entirely in registers: Philox4x32-10 draws, a sorting network over the intermediate-mass
+// draws, intermediate masses from exact integer gaps, two-body momenta, the event weight,
+// isotropic directions and the top-down chain of two-body decays with pure boosts.  The
+// caller supplies a Sink that receives daughters and the weight; unused outputs are removed
+// by the compiler (an integral over a flat matrix element never computes an angle).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace hydra {
+
+constexpr int kNMax = 10;
+
+// Per-decay constants, computed once per call on the host in FP64 and passed by value.
+struct DecayConsts {
+    // FP64 copies
+    double M;           // parent mass
+    double Ts;          // T * 2^-32 (T = M - sum m)
+    double Ts_half;     // T * 2^-33
+    double C;           // weight constant C_n
+    double m[kNMax];    // daughter masses m_1..m_n at [0..n-1]
+    double mu[kNMax];   // mu[k-1] = m_1 + ... + m_k
+    double m2[kNMax];   // m_i^2
+    // FP32 copies (rounded from the FP64 values)
+    float Mf, Tsf, Ts_halff, Cf;
+    float mf[kNMax], muf[kNMax], m2f[kNMax];
+    // Philox round keys: key + r * (W0, W1), r = 0..9
+    uint32_t rk0[10], rk1[10];
+};
+
+// ------------------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): counter (c0..c3), round keys rk*.
+// ------------------------------------------------------------------------------------
+__device__ __forceinline__ void philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                              const uint32_t* __restrict__ rk0,
+                                              const uint32_t* __restrict__ rk1, uint32_t out[4]) {
+    constexpr uint32_t kM0 = 0xD2511F53u, kM1 = 0xCD9E8D57u;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint64_t p0 = static_cast<uint64_t>(kM0) * c0;
+        const uint64_t p1 = static_cast<uint64_t>(kM1) * c2;
+        const uint32_t hi0 = static_cast<uint32_t>(p0 >> 32), lo0 = static_cast<uint32_t>(p0);
+        const uint32_t hi1 = static_cast<uint32_t>(p1 >> 32), lo1 = static_cast<uint32_t>(p1);
+        c0 = hi1 ^ c1 ^ rk0[r];
+        c1 = lo1;
+        c2 = hi0 ^ c3 ^ rk1[r];
+        c3 = lo0;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+// ------------------------------------------------------------------------------------
+// Ascending sort of the first K draws: Batcher's odd-even merge network for 8 inputs,
+// with comparators that touch an index >= K removed (equivalent to padding with +inf).
+// ------------------------------------------------------------------------------------
+__device__ __forceinline__ void compare_exchange(uint32_t& a, uint32_t& b) {
+    const uint32_t lo = min(a, b), hi = max(a, b);
+    a = lo;
+    b = hi;
+}
+
+template <int K>
+__device__ __forceinline__ void sort_mass_draws(uint32_t* x) {
+    constexpr int kPairs[19][2] = {{0, 1}, {2, 3}, {4, 5}, {6, 7}, {0, 2}, {1, 3}, {4, 6},
+                                   {5, 7}, {1, 2}, {5, 6}, {0, 4}, {1, 5}, {2, 6}, {3, 7},
+                                   {2, 4}, {3, 5}, {1, 2}, {3, 4}, {5, 6}};
+#pragma unroll
+    for (int i = 0; i < 19; ++i)
+        if (kPairs[i][1] < K) compare_exchange(x[kPairs[i][0]], x[kPairs[i][1]]);
+}
+
+// ------------------------------------------------------------------------------------
+// Precision traits.  FP32 kinematics use CUDA's correctly rounded sqrtf and sincospif;
+// FP64 uses sqrt and sincospi.  Conversions of 32-bit draws are exact in FP64.
+// ------------------------------------------------------------------------------------
+template <typename R> struct Prec;
+
+template <> struct Prec<float> {
+    __device__ static float u32(uint32_t v) { return __uint2float_rn(v); }
+    __device__ static float i32(int32_t v) { return __int2float_rn(v); }
+    __device__ static float sqrt_(float v) { return sqrtf(v); }
+    __device__ static float fma_(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+    __device__ static void sincospi_(float a, float* s, float* c) { sincospif(a, s, c); }
+    __device__ static float M(const DecayConsts& C) { return C.Mf; }
+    __device__ static float Ts(const DecayConsts& C) { return C.Tsf; }
+    __device__ static float Ts_half(const DecayConsts& C) { return C.Ts_halff; }
+    __device__ static float Cn(const DecayConsts& C) { return C.Cf; }
+    __device__ static float m(const DecayConsts& C, int i) { return C.mf[i]; }
+    __device__ static float mu(const DecayConsts& C, int i) { return C.muf[i]; }
+    __device__ static float m2(const DecayConsts& C, int i) { return C.m2f[i]; }
+};
+
+template <> struct Prec<double> {
+    __device__ static double u32(uint32_t v) { return __uint2double_rn(v); }
+    __device__ static double i32(int32_t v) { return __int2double_rn(v); }
+    __device__ static double sqrt_(double v) { return sqrt(v); }
+    __device__ static double fma_(double a, double b, double c) { return __fma_rn(a, b, c); }
+    __device__ static void sincospi_(double a, double* s, double* c) { sincospi(a, s, c); }
+    __device__ static double M(const DecayConsts& C) { return C.M; }
+    __device__ static double Ts(const DecayConsts& C) { return C.Ts; }
+    __device__ static double Ts_half(const DecayConsts& C) { return C.Ts_half; }
+    __device__ static double Cn(const DecayConsts& C) { return C.C; }
+    __device__ static double m(const DecayConsts& C, int i) { return C.m[i]; }
+    __device__ static double mu(const DecayConsts& C, int i) { return C.mu[i]; }
+    __device__ static double m2(const DecayConsts& C, int i) { return C.m2[i]; }
+};
+
+// ------------------------------------------------------------------------------------
+// One Raubold-Lynch event.
+//
+// Draws: d = 0..n-3 intermediate masses; for top-down step j = 0..n-2 (j = 0 is the
+// parent's decay) cos(theta) from draw n-2+2j and phi from draw n-1+2j.
+//
+// With y_1 <= ... <= y_{n-2} the sorted mass draws, r_j = (y_j + 1/2) 2^-32, r_0 = 0,
+// r_{n-1} = 1:  M_1 = m_1, M_k = mu_k + r_{k-1} T, M_n = M, and the kinetic gaps
+// Delta_k = T (r_k - r_{k-1}) are formed from exact 32-bit integer differences.
+// p_k = sqrt(Delta (Delta + 2 M_k)(Delta + 2 m_{k+1})(Delta + 2 M_k + 2 m_{k+1})) / (2 M_{k+1})
+// (Kallen's lambda, factorised; no cancellation near threshold).  w = C_n prod p_k.
+//
+// Top-down: Q = lab 4-momentum of subsystem k+1 (daughters 1..k+1), Q = (M, 0) for k = n-1.
+// In its rest frame subsystem k moves along +p_k n and daughter k+1 along -p_k n.  The
+// subsystem is boosted to the lab, E' = (Q0 E + Q.p)/M_{k+1},
+// p' = p + Q (E' + E)/(Q0 + M_{k+1}); daughter k+1 = Q - Q' by 4-momentum conservation.
+//
+// Sink interface:
+//   sink.daughter(i, E, px, py, pz)  daughter index i = 0..n-1 (daughter i+1)
+//   sink.subsystem_mass(k, Mk)       M_k for k = 1..n-1
+//   sink.weight(w)
+// ------------------------------------------------------------------------------------
+template <int N, typename R, typename Sink>
+__device__ __forceinline__ void raubold_lynch_event(const DecayConsts& C, uint64_t event,
+                                                    Sink& sink) {
+    using P = Prec<R>;
+    constexpr int kDraws = 3 * N - 4;
+    constexpr int kBlocks = (kDraws + 3) / 4;
+    const uint32_t ev_lo = static_cast<uint32_t>(event);
+    const uint32_t ev_hi = static_cast<uint32_t>(event >> 32);
+
+    uint32_t x[4 * kBlocks];
+#pragma unroll
+    for (int b = 0; b < kBlocks; ++b) philox4x32_10(ev_lo, ev_hi, b, 0u, C.rk0, C.rk1, &x[4 * b]);
+
+    if constexpr (N > 3) sort_mass_draws<N - 2>(x);
+
+    const R M = P::M(C);
+    const R Ts = P::Ts(C);
+    const R Ts_half = P::Ts_half(C);
+    constexpr R kTwoM31 = R(4.656612873077392578125e-10);  // 2^-31
+    constexpr R kTwoM32 = R(2.3283064365386962890625e-10); // 2^-32
+
+    R w = P::Cn(C);
+    R Q0 = M, Qx = R(0), Qy = R(0), Qz = R(0);
+    R Mnext = M;  // M_{k+1}
+
+#pragma unroll
+    for (int k = N - 1; k >= 1; --k) {
+        const int j = N - 1 - k;
+        // intermediate mass M_k
+        R Mk;
+        if (k == 1) Mk = P::m(C, 0);
+        else Mk = P::fma_(P::u32(x[k - 2]) + R(0.5), Ts, P::mu(C, k - 1));
+        // kinetic gap Delta_k = T (r_k - r_{k-1}) from integer differences
+        R gap;
+        if constexpr (N == 2) {
+            gap = Ts * R(4294967296.0);  // T exactly: Ts = T * 2^-32
+        } else if (k == 1) {
+            gap = P::fma_(P::u32(x[0]), Ts, Ts_half);
+        } else if (k == N - 1) {
+            gap = P::fma_(P::u32(~x[N - 3]), Ts, Ts_half);
+        } else {
+            gap = P::u32(x[k - 1] - x[k - 2]) * Ts;
+        }
+        sink.subsystem_mass(k, Mk);
+        // two-body momentum
+        const R mk1 = P::m(C, k);
+        const R twoMk = R(2) * Mk;
+        const R lam = gap * (gap + twoMk) * (gap + R(2) * mk1) * (gap + twoMk + R(2) * mk1);
+        const R invM = R(1) / Mnext;
+        const R p = P::sqrt_(lam) * (R(0.5) * invM);
+        w *= p;
+        // isotropic direction of subsystem k in the rest frame of subsystem k+1
+        const uint32_t xc = x[N - 2 + 2 * j];
+        const uint32_t xp = x[N - 1 + 2 * j];
+        const R cos_t = P::fma_(P::i32(static_cast<int32_t>(xc ^ 0x80000000u)), kTwoM31, kTwoM32);
+        const R one_m = P::fma_(P::u32(~xc), kTwoM31, kTwoM32);  // 1 - cos(theta)
+        const R one_p = P::fma_(P::u32(xc), kTwoM31, kTwoM32);   // 1 + cos(theta)
+        const R sin_t = P::sqrt_(one_m * one_p);
+        R sphi, cphi;
+        P::sincospi_(P::fma_(P::u32(xp), kTwoM31, kTwoM32), &sphi, &cphi);  // phi = 2 pi u
+        const R px = p * sin_t * cphi, py = p * sin_t * sphi, pz = p * cos_t;
+        const R Es = P::sqrt_(P::fma_(p, p, Mk * Mk));
+        if (k == N - 1) {
+            // parent at rest: no boost
+            sink.daughter(k, M - Es, -px, -py, -pz);
+            Q0 = Es; Qx = px; Qy = py; Qz = pz;
+        } else {
+            const R qp = Qx * px + Qy * py + Qz * pz;
+            const R E1 = (Q0 * Es + qp) * invM;
+            const R f = (E1 + Es) / (Q0 + Mnext);
+            const R n0 = E1, nx = P::fma_(f, Qx, px), ny = P::fma_(f, Qy, py), nz = P::fma_(f, Qz, pz);
+            sink.daughter(k, Q0 - n0, Qx - nx, Qy - ny, Qz - nz);
+            Q0 = n0; Qx = nx; Qy = ny; Qz = nz;
+        }
+        Mnext = Mk;
+    }
+    sink.daughter(0, Q0, Qx, Qy, Qz);
+    sink.weight(w);
+}
+
+}  // namespace hydra

@@ -1,0 +1,103 @@
+"""The C ABI without a GPU: the library loads, exports every declared symbol, and rejects
+bad arguments with the documented status codes before touching the device."""
+import ctypes
+import math
+
+import pytest
+
+import oracle
+import paper_1711_05683_b300 as hp
+from paper_1711_05683_b300 import build as hp_build
+
+
+@pytest.fixture(scope="module")
+def L():
+    hp_build.build()
+    return hp.lib()
+
+
+def _dbl(v):
+    return (ctypes.c_double * len(v))(*v)
+
+
+def test_exports_every_declared_symbol(L):
+    names = hp.header_functions()
+    assert "hydra_phsp_generate" in names and "hydra_phsp_integrate" in names
+    for name in names:
+        assert hasattr(L, name), name
+
+
+def test_status_strings(L):
+    for code, name in hp.STATUS.items():
+        assert L.hydra_status_string(code).decode() == name
+
+
+def test_volume_factor_matches_oracle(L):
+    for M, masses in [(10.0, (0.0,) * 10), (5.2795, (3.0969, 0.4937, 0.1396)), (2.0, (0.1, 0.2))]:
+        assert hp.volume_factor(M, masses) == pytest.approx(oracle.volume_factor(M, masses), rel=1e-15)
+
+
+def _gen(L, M=5.0, n=3, masses=None, nevents=8, seed=1, offset=0, dtype=0, out=16, ld=8, w=16):
+    masses = masses if masses is not None else [0.1] * n
+    return L.hydra_phsp_generate(M, n, _dbl(masses) if masses else None, nevents, seed, offset,
+                                 dtype, ctypes.c_void_p(out) if out is not None else None, ld,
+                                 ctypes.c_void_p(w) if w is not None else None, None)
+
+
+@pytest.mark.parametrize("kwargs,status", [
+    (dict(n=1, masses=[0.1]), "HYDRA_ERR_UNSUPPORTED_N"),
+    (dict(n=11, masses=[0.1] * 11), "HYDRA_ERR_UNSUPPORTED_N"),
+    (dict(M=0.0), "HYDRA_ERR_INVALID_ARG"),
+    (dict(M=-1.0), "HYDRA_ERR_INVALID_ARG"),
+    (dict(M=math.inf), "HYDRA_ERR_INVALID_ARG"),
+    (dict(M=math.nan), "HYDRA_ERR_INVALID_ARG"),
+    (dict(masses=[0.1, -0.1, 0.1]), "HYDRA_ERR_INVALID_ARG"),
+    (dict(masses=[0.1, math.nan, 0.1]), "HYDRA_ERR_INVALID_ARG"),
+    (dict(M=0.3, masses=[0.1, 0.1, 0.1]), "HYDRA_ERR_BELOW_THRESHOLD"),
+    (dict(M=0.2, masses=[0.1, 0.1, 0.1]), "HYDRA_ERR_BELOW_THRESHOLD"),
+    (dict(dtype=7), "HYDRA_ERR_INVALID_ARG"),
+    (dict(out=None), "HYDRA_ERR_INVALID_ARG"),
+    (dict(w=None), "HYDRA_ERR_INVALID_ARG"),
+    (dict(ld=4), "HYDRA_ERR_INVALID_ARG"),
+    (dict(out=20), "HYDRA_ERR_MISALIGNED"),
+    (dict(w=24), "HYDRA_ERR_MISALIGNED"),
+    (dict(ld=10), "HYDRA_ERR_MISALIGNED"),
+    (dict(offset=2 ** 64 - 4), "HYDRA_ERR_INVALID_ARG"),
+])
+def test_generate_rejects(L, kwargs, status):
+    rc = _gen(L, **kwargs)
+    assert hp.STATUS[rc] == status, L.hydra_last_error()
+    assert L.hydra_last_error().decode() != ""
+
+
+def test_generate_zero_events_is_noop(L):
+    assert _gen(L, nevents=0, out=None, w=None, ld=0) == 0
+
+
+def test_integrate_rejects(L):
+    res = hp.Integral()
+    par = _dbl([0.892, 0.05, 1.02, 0.004, 0.5, 1.2])
+    cases = [
+        (dict(n=4, masses=[0.1] * 4, me=1, npar=6), "HYDRA_ERR_UNSUPPORTED_N"),
+        (dict(me=1, npar=5), "HYDRA_ERR_INVALID_ARG"),
+        (dict(me=9), "HYDRA_ERR_INVALID_ARG"),
+        (dict(nevents=0), "HYDRA_ERR_INVALID_ARG"),
+        (dict(M=0.25), "HYDRA_ERR_BELOW_THRESHOLD"),
+        (dict(dtype=3), "HYDRA_ERR_INVALID_ARG"),
+    ]
+    for kw, status in cases:
+        n = kw.get("n", 3)
+        masses = kw.get("masses", [0.1] * n)
+        rc = L.hydra_phsp_integrate(kw.get("M", 2.0), n, _dbl(masses), kw.get("nevents", 100), 1, 0,
+                                    kw.get("dtype", 0), kw.get("me", 0), par, kw.get("npar", 0),
+                                    ctypes.byref(res), None)
+        assert hp.STATUS[rc] == status, (kw, L.hydra_last_error())
+    rc = L.hydra_phsp_integrate(2.0, 3, _dbl([0.1] * 3), 100, 1, 0, 0, 0, par, 0, None, None)
+    assert hp.STATUS[rc] == "HYDRA_ERR_INVALID_ARG"
+
+
+def test_draws_rejects(L):
+    assert hp.STATUS[L.hydra_phsp_draws(11, 10, 1, 0, ctypes.c_void_p(16), 16, None)] == "HYDRA_ERR_UNSUPPORTED_N"
+    assert hp.STATUS[L.hydra_phsp_draws(3, 10, 1, 0, None, 16, None)] == "HYDRA_ERR_INVALID_ARG"
+    assert hp.STATUS[L.hydra_phsp_draws(3, 10, 1, 0, ctypes.c_void_p(16), 8, None)] == "HYDRA_ERR_INVALID_ARG"
+    assert L.hydra_phsp_draws(3, 0, 1, 0, None, 0, None) == 0

@@ -1,0 +1,286 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle, event by event.
+
+Tolerances (from the arithmetic of each precision):
+* FP64 kinematics: |gpu - oracle| <= 1e-12 x event scale, the scale being max(M, E_i) of the
+  event (px, py, pz can be ~0, so a per-component relative error is meaningless); weights
+  <= 1e-12 relative.  Both sides compute in FP64; they differ only in rounding order.
+* FP32 kinematics: <= 2e-5 x event scale on every component, weights <= 2e-5 relative.
+  Every FP32 step (integer gap -> float, factorised lambda, sqrt, reciprocal, sincospif,
+  boost) adds a few units of 2^-24 ~ 6e-8; nine chained steps stay two orders below 2e-5.
+* Integrals: FP64 sums <= 1e-12 relative to the oracle on the same events.  FP32: sum_w
+  <= 1e-5 relative; sum_f <= 2e-4 relative, because near the narrow Breit-Wigner pole
+  (m0 Gamma = 4.08e-3 GeV^2) an FP32 rounding of ~5e-7 GeV^2 in s23 moves |BW|^2 by up to
+  2 x 5e-7 / 4.08e-3 ~ 2.5e-4 per event, and a sum of positive terms errs by at most its
+  largest relative term error.
+"""
+import ctypes
+import math
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
+import paper_1711_05683_b300 as hp  # noqa: E402
+import workloads  # noqa: E402
+from conftest import ROOT, load_kat  # noqa: E402
+from refmath import dalitz_me_integral_quad  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+TOL_P = {"f64": 1e-12, "f32": 2e-5}
+TOL_W = {"f64": 1e-12, "f32": 2e-5}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1711_05683_b300 import build as hp_build
+    hp_build.build()
+    torch.cuda.set_device(0)
+    yield
+    torch.cuda.synchronize()
+
+
+def compare_events(M, masses, nev, seed, dtype, offset=0):
+    """Max component error at event scale and max relative weight error vs the oracle."""
+    p, w = hp.generate(M, masses, nev, seed, dtype=dtype, event_offset=offset)
+    torch.cuda.synchronize()
+    ref_p, ref_w = oracle.generate(M, masses, nev, seed, event_offset=offset)
+    gp = p[:, :, :nev].double().cpu().numpy()
+    gw = w.double().cpu().numpy()
+    scale = np.maximum(M, ref_p[:, 0, :].max(axis=0))
+    err_p = float((np.abs(gp - ref_p) / scale).max()) if nev else 0.0
+    err_w = float((np.abs(gw - ref_w) / np.maximum(np.abs(ref_w), 1e-300)).max()) if nev else 0.0
+    return err_p, err_w
+
+
+# ----------------------------------------------------------------------------- RNG
+def test_device_draws_match_oracle_bit_exact():
+    for n, offset in [(3, 0), (10, 2 ** 32 - 700), (7, 2 ** 40 + 3)]:
+        nev = 1500
+        seed = 0x1234_5678_9ABC_DEF0 + n
+        g = hp.draws(n, nev, seed, event_offset=offset).cpu().numpy()
+        for e in range(0, nev, 7):
+            ref = oracle.draws(seed, offset + e, n)
+            assert np.array_equal(g[:, e].astype(np.uint64), ref), (n, e)
+
+
+def test_curand_philox_agrees_with_oracle(tmp_path):
+    """cuRAND's raw Philox4x32-10 block function (called, not copied) against the oracle's,
+    on the published known-answer vectors and on random counters and keys."""
+    so = tmp_path / "curand_probe.so"
+    src = os.path.join(ROOT, "tests", "gpu_probes", "curand_philox_probe.cu")
+    subprocess.check_call(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-O2",
+                           "-Xcompiler", "-fPIC", "-shared", "-cudart", "shared", "-o", str(so), src])
+    lib = ctypes.CDLL(str(so))
+    rows = [r[:6] for r in load_kat("philox4x32_10_kat.txt")]
+    rng = np.random.default_rng(5)
+    rows += [list(int(v) for v in rng.integers(0, 2 ** 32, size=6)) for _ in range(200)]
+    flat = (ctypes.c_uint32 * (6 * len(rows)))(*[v for r in rows for v in r])
+    out = (ctypes.c_uint32 * (4 * len(rows)))()
+    assert lib.probe_curand_philox(flat, len(rows), out) == 0
+    for i, r in enumerate(rows):
+        assert tuple(out[4 * i:4 * i + 4]) == oracle.philox4x32_10(r[:4], r[4:6])
+
+
+# ----------------------------------------------------------------------------- generation
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("massive", [False, True])
+@pytest.mark.parametrize("n", range(2, 11))
+def test_generate_sweep_parity(n, massive, dtype):
+    masses = workloads.sweep_masses(n, massive)
+    # a ragged count whose counter-event indices cross the 2^32 boundary
+    err_p, err_w = compare_events(workloads.SWEEP_M, masses, 3001, 1000 + n, dtype,
+                                  offset=2 ** 32 - 1500)
+    assert err_p <= TOL_P[dtype], err_p
+    assert err_w <= TOL_W[dtype], err_w
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_generate_random_decays(dtype):
+    rng = np.random.default_rng(2024)
+    for n in range(2, 11):
+        for _ in range(2):
+            M, masses = workloads.random_decay(rng, n)
+            err_p, err_w = compare_events(M, masses, 777, int(rng.integers(1, 2 ** 63)), dtype)
+            assert err_p <= TOL_P[dtype] and err_w <= TOL_W[dtype], (n, M, masses, err_p, err_w)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_generate_near_threshold(dtype):
+    for n in (2, 3, 6, 10):
+        M, masses = workloads.near_threshold_decay(n, rel_gap=1e-7)
+        err_p, err_w = compare_events(M, masses, 1000, 31, dtype)
+        assert err_p <= TOL_P[dtype] and err_w <= TOL_W[dtype], (n, err_p, err_w)
+
+
+@pytest.mark.parametrize("nev", [1, 2, 3, 4, 5, 31, 33, 255, 257, 4097])
+def test_generate_edge_sizes(nev):
+    for dtype in ("f64", "f32"):
+        err_p, err_w = compare_events(3.0, (0.1, 0.2, 0.3, 0.4), nev, 5, dtype)
+        assert err_p <= TOL_P[dtype] and err_w <= TOL_W[dtype]
+
+
+def test_generate_b_to_jpsi_k_pi_fp64():
+    """The FP64 3-body workload: 1e5 events, seed 42, parity plus conservation on the GPU."""
+    cfg = workloads.B_TO_JPSI_K_PI
+    M, masses, nev = cfg["M"], cfg["masses"], cfg["nevents"]
+    err_p, err_w = compare_events(M, masses, nev, cfg["seed"], "f64")
+    assert err_p <= 1e-12 and err_w <= 1e-12
+    p, w = hp.generate(M, masses, nev, cfg["seed"], dtype="f64")
+    p = p[:, :, :nev]
+    tot = p.sum(dim=0)
+    assert float((tot[0] - M).abs().max()) <= 1e-13 * M
+    assert float(tot[1:].abs().max()) <= 1e-13 * M
+    for i, m in enumerate(masses):
+        m2 = p[i, 0] ** 2 - (p[i, 1] ** 2 + p[i, 2] ** 2 + p[i, 3] ** 2)
+        assert float((m2 - m * m).abs().max()) <= 1e-12 * M * M
+
+
+def test_generate_chunked_calls_are_bit_identical():
+    M, masses = 10.0, workloads.sweep_masses(7, True)
+    for dtype in ("f32", "f64"):
+        full_p, full_w = hp.generate(M, masses, 10_000, 77, dtype=dtype)
+        tdt = full_p.dtype
+        out = torch.empty((7, 4, 10_000), dtype=tdt, device="cuda")
+        w = torch.empty(10_000, dtype=tdt, device="cuda")
+        for a, b in [(0, 4000), (4000, 4004), (4004, 10_000)]:
+            hp.generate_into(M, masses, b - a, 77, out_view(out, a), w[a:], dtype=dtype,
+                             event_offset=a)
+        torch.cuda.synchronize()
+        assert torch.equal(out, full_p[:, :, :10_000]) and torch.equal(w, full_w)
+
+
+def out_view(out, a):
+    """A [n, 4, ld] view starting at event a (same leading dimension)."""
+    return _StridedOut(out, a)
+
+
+class _StridedOut:
+    """Duck-typed tensor for generate_into: data_ptr at event a, shape[-1] = ld of `out`."""
+
+    def __init__(self, out, a):
+        self._out, self._a = out, a
+        self.shape = out.shape
+
+    def data_ptr(self):
+        return self._out.data_ptr() + self._a * self._out.element_size()
+
+
+# ----------------------------------------------------------------------------- integration
+@pytest.mark.parametrize("kin", ["f64", "f32"])
+def test_integrate_dalitz_parity(kin):
+    d = workloads.D0_DALITZ
+    nev = 2 * 2048 * 9 + 1234  # several tiles and a ragged tail
+    for offset in (0, 2 ** 33 - 5000):
+        g = hp.integrate(d["M"], d["masses"], nev, d["seed"], kin_dtype=kin, me=hp.ME_DALITZ_2BW,
+                         params=d["params"], event_offset=offset)
+        r = oracle.integrate_sums(d["M"], d["masses"], nev, d["seed"], me=1, params=d["params"],
+                                  event_offset=offset)
+        tol_f, tol_w = (1e-12, 1e-12) if kin == "f64" else (2e-4, 1e-5)
+        assert g["n"] == nev
+        assert abs(g["sum_f"] - r[0]) <= tol_f * r[0], (g, r)
+        assert abs(g["sum_f2"] - r[1]) <= 2 * tol_f * r[1]
+        assert abs(g["sum_w"] - r[2]) <= tol_w * r[2]
+        assert abs(g["sum_w2"] - r[3]) <= 2 * tol_w * r[3]
+        assert g["mean"] == pytest.approx(g["sum_f"] / nev, rel=1e-15)
+
+
+@pytest.mark.parametrize("kin", ["f64", "f32"])
+@pytest.mark.parametrize("n", range(2, 11))
+def test_integrate_flat_parity(n, kin):
+    masses = workloads.sweep_masses(n, True)
+    nev = 5 * 2048 + 17
+    g = hp.integrate(workloads.SWEEP_M, masses, nev, 3 + n, kin_dtype=kin)
+    r = oracle.integrate_sums(workloads.SWEEP_M, masses, nev, 3 + n)
+    tol = 1e-12 if kin == "f64" else 1e-5
+    assert abs(g["sum_w"] - r[2]) <= tol * r[2]
+    assert abs(g["sum_w2"] - r[3]) <= 2 * tol * r[3]
+    assert g["sum_f"] == g["sum_w"]
+
+
+def test_integrate_is_deterministic():
+    d = workloads.D0_DALITZ
+    a = hp.integrate(d["M"], d["masses"], 3_000_001, d["seed"], me=hp.ME_DALITZ_2BW, params=d["params"])
+    b = hp.integrate(d["M"], d["masses"], 3_000_001, d["seed"], me=hp.ME_DALITZ_2BW, params=d["params"])
+    assert a == b
+
+
+def test_integrate_many_chunks_and_segments_two_body():
+    """Two-body weights are all equal (w = pi p*/M), so over 2^26 * 2 + 3 * 2^21 + 777 events
+    (three launches, 67 segments) the FP64 sums must be n w and n w^2 to rounding."""
+    M, masses = 3.0, (0.5, 1.1)
+    nev = 2 ** 27 + 3 * 2 ** 21 + 777
+    w0 = oracle.generate(M, masses, 1, 1)[1][0]
+    g = hp.integrate(M, masses, nev, 1, kin_dtype="f64")
+    assert g["sum_w"] == pytest.approx(nev * w0, rel=1e-13)
+    assert g["sum_w2"] == pytest.approx(nev * w0 * w0, rel=1e-13)
+    assert g["var_mean"] == pytest.approx(0.0, abs=1e-20 * w0 * w0)
+
+
+# ----------------------------------------------------------------------------- full size
+@pytest.mark.parametrize("n,dtype", [(3, "f32"), (10, "f32"), (10, "f64"), (2, "f64")])
+def test_full_size_sweep_sampled(n, dtype):
+    """1e8 events in the benchmark's launch configuration; 300 sampled events recomputed by
+    the oracle one by one, and conservation checked over every event on the GPU."""
+    M, masses, nev = workloads.SWEEP_M, workloads.sweep_masses(n, True), workloads.SWEEP_NEVENTS
+    seed = 1000 + n
+    p, w = hp.generate(M, masses, nev, seed, dtype=dtype)
+    torch.cuda.synchronize()
+    idx = np.sort(np.random.default_rng(n).choice(nev, size=300, replace=False))
+    idx[-1] = nev - 1
+    gp = p[:, :, torch.as_tensor(idx, device="cuda")].double().cpu().numpy()
+    gw = w[torch.as_tensor(idx, device="cuda")].double().cpu().numpy()
+    for j, e in enumerate(idx):
+        rp, rw = oracle.generate(M, masses, 1, seed, event_offset=int(e))
+        scale = max(M, float(rp[:, 0, 0].max()))
+        assert float(np.abs(gp[:, :, j] - rp[:, :, 0]).max()) <= TOL_P[dtype] * scale
+        assert abs(gw[j] - rw[0]) <= TOL_W[dtype] * rw[0]
+    tol = 1e-13 if dtype == "f64" else 2e-6
+    for c in range(4):
+        tot = p[:, c, :nev].sum(dim=0, dtype=torch.float64)
+        target = M if c == 0 else 0.0
+        assert float((tot - target).abs().max()) <= tol * M * (10 if dtype == "f32" else 1)
+    assert bool(torch.isfinite(w).all()) and float(w.min()) >= 0.0
+    del p, w
+    torch.cuda.empty_cache()
+
+
+def test_full_size_dalitz_integral_within_3_sigma():
+    """1e9 events, FP32 kinematics, FP64 compensated sums, against 2-D quadrature."""
+    d = workloads.D0_DALITZ
+    exact, _ = dalitz_me_integral_quad(d["M"], d["masses"], d["params"])
+    g = hp.integrate(d["M"], d["masses"], d["nevents"], d["seed"], kin_dtype="f32",
+                     me=hp.ME_DALITZ_2BW, params=d["params"])
+    sigma = math.sqrt(g["var_mean"])
+    assert g["n"] == d["nevents"]
+    assert abs(g["mean"] - exact) <= 3 * sigma, (g["mean"], exact, sigma)
+    # the volume from the same events against the 3-body quadrature
+    from refmath import R3_quad
+    R3 = R3_quad(d["M"], d["masses"])
+    n = g["n"]
+    vol = g["sum_w"] / n
+    vol_sigma = math.sqrt((g["sum_w2"] / n - vol * vol) / (n - 1))
+    assert abs(vol - R3) <= 3 * vol_sigma, (vol, R3, vol_sigma)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_generate_host_matches_device(dtype):
+    """The host-output entry point writes exactly the events of the device entry point,
+    across several staging chunks (2^22 events each) and a ragged tail, with ld > nevents."""
+    M, masses = 10.0, workloads.sweep_masses(5, True)
+    nev = 2 * 2 ** 22 + 12345
+    p, w = hp.generate(M, masses, nev, 99, dtype=dtype, event_offset=17)
+    tdt = p.dtype
+    ld = nev + 3
+    hout = torch.empty((5, 4, ld), dtype=tdt, pin_memory=True)
+    hw = torch.empty(nev, dtype=tdt, pin_memory=True)
+    hp.generate_host_into(M, masses, nev, 99, hout, hw, dtype=dtype, event_offset=17)
+    torch.cuda.synchronize()
+    assert torch.equal(hout[:, :, :nev], p[:, :, :nev].cpu())
+    assert torch.equal(hw, w.cpu())
