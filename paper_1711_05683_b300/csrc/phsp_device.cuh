@@ -119,7 +119,7 @@ template <> struct Prec<double> {
 // r_{n-1} = 1:  M_1 = m_1, M_k = mu_k + r_{k-1} T, M_n = M, and the kinetic gaps
 // Delta_k = T (r_k - r_{k-1}) are formed from exact 32-bit integer differences.
 // p_k = sqrt(Delta (Delta + 2 M_k)(Delta + 2 m_{k+1})(Delta + 2 M_k + 2 m_{k+1})) / (2 M_{k+1})
-// (Kallen's lambda, factorised; no cancellation near threshold).  w = C_n prod p_k.
+// (Kallen's lambda, factorised; no cancellation near threshold).  w = (prod p_k) C_n.
 //
 // Top-down: Q = lab 4-momentum of subsystem k+1 (daughters 1..k+1), Q = (M, 0) for k = n-1.
 // In its rest frame subsystem k moves along +p_k n and daughter k+1 along -p_k n.  The
@@ -152,7 +152,7 @@ __device__ __forceinline__ void raubold_lynch_event(const DecayConsts& C, uint64
     constexpr R kTwoM31 = R(4.656612873077392578125e-10);  // 2^-31
     constexpr R kTwoM32 = R(2.3283064365386962890625e-10); // 2^-32
 
-    R w = P::Cn(C);
+    R w = R(1);  // prod p_k; C_n is applied last so only the final product can leave the normal range
     R Q0 = M, Qx = R(0), Qy = R(0), Qz = R(0);
     R Mnext = M;  // M_{k+1}
 
@@ -208,7 +208,7 @@ __device__ __forceinline__ void raubold_lynch_event(const DecayConsts& C, uint64
         Mnext = Mk;
     }
     sink.daughter(0, Q0, Qx, Qy, Qz);
-    sink.weight(w);
+    sink.weight(w * P::Cn(C));
 }
 
 }  // namespace hydra

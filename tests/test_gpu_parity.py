@@ -33,6 +33,9 @@ pytestmark = pytest.mark.gpu
 
 TOL_P = {"f64": 1e-12, "f32": 2e-5}
 TOL_W = {"f64": 1e-12, "f32": 2e-5}
+# Smallest FP32 subnormal: an FP32 weight below the normal range (2^-126, e.g. n >= 6 within
+# T ~ 1e-7 M of threshold, where w ~ T^((3n-4)/2)) carries an absolute error of a few of these.
+F32_QUANTUM = 2.0 ** -149
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -55,7 +58,9 @@ def compare_events(M, masses, nev, seed, dtype, offset=0):
     gw = w.double().cpu().numpy()
     scale = np.maximum(M, ref_p[:, 0, :].max(axis=0))
     err_p = float((np.abs(gp - ref_p) / scale).max()) if nev else 0.0
-    err_w = float((np.abs(gw - ref_w) / np.maximum(np.abs(ref_w), 1e-300)).max()) if nev else 0.0
+    floor = 8 * F32_QUANTUM if dtype == "f32" else 0.0
+    err_w = float((np.maximum(np.abs(gw - ref_w) - floor, 0.0) / np.maximum(np.abs(ref_w), 1e-300)).max()) \
+        if nev else 0.0
     return err_p, err_w
 
 
