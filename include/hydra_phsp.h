@@ -153,6 +153,35 @@ hydra_status hydra_phsp_integrate(double M, int n, const double *masses, uint64_
                                   hydra_integral *result, hydra_stream_t stream);
 
 /*
+ * hydra_phsp_integrate without any memory allocation (the paper has no counterpart: this
+ * entry point exists for callers of this library that cannot allocate device memory).
+ *
+ * Some callers cannot call cudaMalloc: processes that forbid dynamic device allocation once
+ * they are running (real-time or certified hosts), plug-ins whose host application owns all
+ * device memory through its own pool, and latency-critical loops where cudaMalloc/cudaFree
+ * may synchronize the whole device and stall other streams.  This variant makes no
+ * allocating call (no cudaMalloc, cudaFree or allocating library routine): its scratch is a
+ * fixed array of 1,179,904 bytes (tile partials of one 2^26-event chunk, 2048 segment
+ * partials, the result) compiled into the library as a static device variable, which every
+ * GPU that loads the library holds until the process exits.
+ *
+ * Arguments, result and numerics are those of hydra_phsp_integrate, bit for bit, with one
+ * extra limit: nevents <= 2^32 (larger counts return HYDRA_ERR_INVALID_ARG with a message).
+ * The first call on each device looks up the device address of the array
+ * (cudaGetSymbolAddress) with that device current; make that first call before any stream
+ * capture begins.  All calls share the one array, which keeps the previous call's contents;
+ * every slot a call reads is written earlier in the same call, so nothing needs clearing.
+ * Calls are serialized within the process by a lock and block until the result is on the
+ * host; calls that overlap on the GPU (for instance issued around that lock) race on the
+ * shared array and give wrong results.
+ */
+hydra_status hydra_phsp_integrate_noalloc(double M, int n, const double *masses, uint64_t nevents,
+                                          uint64_t seed, uint64_t event_offset,
+                                          hydra_dtype kin_dtype, hydra_me_id me,
+                                          const double *params, int nparams,
+                                          hydra_integral *result, hydra_stream_t stream);
+
+/*
  * The raw random numbers of nevents events: the 3n-4 Philox4x32-10 draws of each event in
  * draw order (section 4.2's generator consumes them as described at the top of this file).
  * out: device buffer of uint32, structure of arrays out[d * ld + e], ld >= nevents.

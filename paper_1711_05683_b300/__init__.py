@@ -71,8 +71,10 @@ def lib() -> ctypes.CDLL:
                                            ctypes.POINTER(Integral), vp]
         L.hydra_phsp_draws.argtypes = [i, u64, u64, u64, vp, u64, vp]
         L.hydra_phsp_generate_host.argtypes = [d, i, dp, u64, u64, u64, i, vp, u64, vp, vp]
+        L.hydra_phsp_integrate_noalloc.argtypes = L.hydra_phsp_integrate.argtypes
         for name in ("hydra_phsp_volume_factor", "hydra_phsp_generate", "hydra_phsp_integrate",
-                     "hydra_phsp_draws", "hydra_phsp_generate_host", "hydra_shutdown"):
+                     "hydra_phsp_draws", "hydra_phsp_generate_host", "hydra_phsp_integrate_noalloc",
+                     "hydra_shutdown"):
             getattr(L, name).restype = i
         _lib = L
     return _lib

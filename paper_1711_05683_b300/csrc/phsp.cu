@@ -566,6 +566,41 @@ static hydra_status launch_integrate_chunks(const void* kern, const DecayConsts&
     return HYDRA_OK;
 }
 
+// ------------------------------------------------------------------------------------
+// Integral without allocation: the scratch of hydra_phsp_integrate_noalloc lives in one
+// file-scope device array, present on every device that loads this library until the
+// process exits.  Layout: [tile partials of one chunk | segment partials | result].
+// ------------------------------------------------------------------------------------
+constexpr uint64_t kNoAllocMaxEvents = uint64_t(1) << 32;
+constexpr uint64_t kNoAllocMaxSegs = kNoAllocMaxEvents / (uint64_t(kTileEvents) * kSegTiles);  // 2048
+constexpr size_t kNoAllocTilesBytes = kChunkTiles * sizeof(TileSums);                  // 1 MiB
+constexpr size_t kNoAllocSegsBytes = kNoAllocMaxSegs * 8 * sizeof(double);              // 128 KiB
+constexpr size_t kNoAllocResultOffset = kNoAllocTilesBytes + kNoAllocSegsBytes;
+constexpr size_t kNoAllocBytes = kNoAllocResultOffset + 256;
+static_assert(sizeof(hydra_integral) <= 256, "result slot");
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+constexpr int kNoAllocMaxDevices = 64;
+static std::mutex g_noalloc_mu;
+static unsigned char* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+// Device address of g_noalloc_scratch on the current device, looked up once per device.
+static hydra_status noalloc_scratch(unsigned char** out) {
+    int dev = 0;
+    cudaError_t err = cudaGetDevice(&dev);
+    if (err != cudaSuccess) return cuda_fail(err, "cudaGetDevice");
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(HYDRA_ERR_INVALID_ARG, "device %d out of range", dev);
+    if (!g_noalloc_ptr[dev]) {
+        void* ptr = nullptr;
+        err = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (err != cudaSuccess) return cuda_fail(err, "cudaGetSymbolAddress(no-allocation scratch)");
+        g_noalloc_ptr[dev] = static_cast<unsigned char*>(ptr);
+    }
+    *out = g_noalloc_ptr[dev];
+    return HYDRA_OK;
+}
+
 }  // namespace hydra
 
 using namespace hydra;
@@ -746,6 +781,57 @@ hydra_status hydra_phsp_integrate(double M, int n, const double* masses, uint64_
     err = cudaStreamSynchronize(cs);
     if (err != cudaSuccess) return cuda_fail(err, "integrate synchronize");
     *result = *s->h_result;
+    return HYDRA_OK;
+}
+
+hydra_status hydra_phsp_integrate_noalloc(double M, int n, const double* masses, uint64_t nevents,
+                                          uint64_t seed, uint64_t event_offset, hydra_dtype kin_dtype,
+                                          hydra_me_id me, const double* params, int nparams,
+                                          hydra_integral* result, hydra_stream_t stream) {
+    DecayConsts C;
+    hydra_status st = make_consts(M, n, masses, seed, &C);
+    if (st != HYDRA_OK) return st;
+    if (kin_dtype != HYDRA_F32 && kin_dtype != HYDRA_F64) return fail(HYDRA_ERR_INVALID_ARG, "unknown dtype %d", static_cast<int>(kin_dtype));
+    if (!result) return fail(HYDRA_ERR_INVALID_ARG, "result is NULL");
+    if (nevents == 0) return fail(HYDRA_ERR_INVALID_ARG, "nevents must be > 0");
+    if (nevents > kNoAllocMaxEvents)
+        return fail(HYDRA_ERR_INVALID_ARG, "nevents = %llu exceeds the no-allocation limit of 2^32 events "
+                    "(its fixed scratch holds 2048 segment partials); use hydra_phsp_integrate",
+                    static_cast<unsigned long long>(nevents));
+    if (event_offset + nevents < event_offset) return fail(HYDRA_ERR_INVALID_ARG, "event_offset + nevents overflows 64 bits");
+    MEConsts P;
+    st = make_me(me, n, params, nparams, &P);
+    if (st != HYDRA_OK) return st;
+    const void* kern = nullptr;
+    if (kin_dtype == HYDRA_F32)
+        kern = me == HYDRA_ME_FLAT ? integrate_kernel_for<float, HYDRA_ME_FLAT>(n) : integrate_kernel_for<float, HYDRA_ME_DALITZ_2BW>(n);
+    else
+        kern = me == HYDRA_ME_FLAT ? integrate_kernel_for<double, HYDRA_ME_FLAT>(n) : integrate_kernel_for<double, HYDRA_ME_DALITZ_2BW>(n);
+    if (!kern) return fail(HYDRA_ERR_UNSUPPORTED_N, "no kernel for n = %d and me = %d", n, static_cast<int>(me));
+
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    unsigned char* base = nullptr;
+    st = noalloc_scratch(&base);
+    if (st != HYDRA_OK) return st;
+    // Every tile and segment slot a call reads is written earlier in the same call, and the
+    // result slot is overwritten, so nothing needs clearing between calls.
+    DeviceScratch view;
+    view.tiles = reinterpret_cast<TileSums*>(base);
+    view.segs = reinterpret_cast<double*>(base + kNoAllocTilesBytes);
+    hydra_integral* d_result = reinterpret_cast<hydra_integral*>(base + kNoAllocResultOffset);
+    const uint64_t ntiles = (nevents + kTileEvents - 1) / kTileEvents;
+    const uint64_t nseg = (ntiles + kSegTiles - 1) / kSegTiles;
+    cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+    st = kin_dtype == HYDRA_F32 ? launch_integrate_chunks<float>(kern, C, P, nevents, event_offset, &view, cs)
+                                : launch_integrate_chunks<double>(kern, C, P, nevents, event_offset, &view, cs);
+    if (st != HYDRA_OK) return st;
+    finalize_integral<<<1, 32, 0, cs>>>(view.segs, nseg, nevents, d_result);
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return cuda_fail(err, "finalize launch");
+    err = cudaMemcpyAsync(result, d_result, sizeof(hydra_integral), cudaMemcpyDeviceToHost, cs);
+    if (err != cudaSuccess) return cuda_fail(err, "result copy");
+    err = cudaStreamSynchronize(cs);
+    if (err != cudaSuccess) return cuda_fail(err, "integrate synchronize");
     return HYDRA_OK;
 }
 
