@@ -135,6 +135,10 @@ def run_ours(args) -> None:
     if world > 1:
         dist.barrier()
     hp.lib()
+    # launch shapes: the autotuner's cached choice for this GPU, or a fresh tuning (untimed)
+    from paper_1711_05683_b300 import autotune
+    tuning = autotune.load_or_tune(integrate_cases=[(3, "f32", INT_CFG["M"], INT_CFG["masses"],
+                                                     hp.ME_DALITZ_2BW, INT_CFG["params"])])
 
     nev = args.events
     int_events = args.int_events
@@ -309,6 +313,9 @@ def run_ours(args) -> None:
                                     "frac": round(f32_bytes / (f32_ms / 1e3) / 1e9 / peaks["hbm_gbs"], 4)},
         "dominant": dominant, "family_ms_per_step": {k: round(v, 3) for k, v in fam_ms.items()},
         "breakdown": breakdown, "clocks": clk, "e2e": e2e,
+        "launch_shapes": {"source": tuning.get("source"),
+                          "generate": {k: f"{v['block']}x{v['ept']}" for k, v in tuning["generate"].items()},
+                          "integrate": {k: f"{v['block']}x{v['ept']}" for k, v in tuning["integrate"].items()}},
     }
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds, nev, int_events)

@@ -70,6 +70,12 @@ typedef enum hydra_me_id {
                                BW(s; m0, G) = 1 / (m0^2 - s - i m0 G), s_ij = (p_i + p_j)^2 */
 } hydra_me_id;
 
+/* Kernels whose launch shape can be configured. */
+typedef enum hydra_kernel_kind {
+    HYDRA_KERNEL_GENERATE = 0, /* hydra_phsp_generate / hydra_phsp_generate_host */
+    HYDRA_KERNEL_INTEGRATE = 1 /* hydra_phsp_integrate (all matrix elements) */
+} hydra_kernel_kind;
+
 /* Result of a phase-space integral of f = w |ME|^2 over n events. */
 typedef struct hydra_integral {
     double mean;     /* sum_f / n: the MC estimate of Int |ME|^2 dR_n */
@@ -189,6 +195,19 @@ hydra_status hydra_phsp_integrate_noalloc(double M, int n, const double *masses,
  */
 hydra_status hydra_phsp_draws(int n, uint64_t nevents, uint64_t seed, uint64_t event_offset,
                               uint32_t *out, uint64_t ld, hydra_stream_t stream);
+
+/*
+ * Launch shape of a kernel for decays of n daughters in a precision: threads per block
+ * (a multiple of 32 in [32, 512]) and events per thread (1, 2 or 4; each thread carries
+ * that many independent events in lockstep, and the generator stores them as one vector).
+ * Results do not depend on the shape: every event's arithmetic is the same, and integrals
+ * use a fixed reduction tree.  Process-wide; used by the autotuner.  The library's defaults
+ * are the shapes measured best on B300.  Errors: INVALID_ARG, UNSUPPORTED_N.
+ */
+hydra_status hydra_set_launch_config(hydra_kernel_kind kind, int n, hydra_dtype dtype, int block,
+                                     int events_per_thread);
+hydra_status hydra_get_launch_config(hydra_kernel_kind kind, int n, hydra_dtype dtype, int *block,
+                                     int *events_per_thread);
 
 /* Release the per-device scratch memory of the library (all devices).  Not thread safe
  * with respect to calls in flight. */

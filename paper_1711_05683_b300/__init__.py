@@ -24,6 +24,7 @@ HEADER = os.path.join(os.path.dirname(_PKG), "include", "hydra_phsp.h")
 
 F32, F64 = 0, 1
 ME_FLAT, ME_DALITZ_2BW = 0, 1
+KERNEL_GENERATE, KERNEL_INTEGRATE = 0, 1
 
 STATUS = {0: "HYDRA_OK", 1: "HYDRA_ERR_INVALID_ARG", 2: "HYDRA_ERR_BELOW_THRESHOLD",
           3: "HYDRA_ERR_UNSUPPORTED_N", 4: "HYDRA_ERR_MISALIGNED", 5: "HYDRA_ERR_OOM",
@@ -72,9 +73,11 @@ def lib() -> ctypes.CDLL:
         L.hydra_phsp_draws.argtypes = [i, u64, u64, u64, vp, u64, vp]
         L.hydra_phsp_generate_host.argtypes = [d, i, dp, u64, u64, u64, i, vp, u64, vp, vp]
         L.hydra_phsp_integrate_noalloc.argtypes = L.hydra_phsp_integrate.argtypes
+        L.hydra_set_launch_config.argtypes = [i, i, i, i, i]
+        L.hydra_get_launch_config.argtypes = [i, i, i, ctypes.POINTER(i), ctypes.POINTER(i)]
         for name in ("hydra_phsp_volume_factor", "hydra_phsp_generate", "hydra_phsp_integrate",
                      "hydra_phsp_draws", "hydra_phsp_generate_host", "hydra_phsp_integrate_noalloc",
-                     "hydra_shutdown"):
+                     "hydra_set_launch_config", "hydra_get_launch_config", "hydra_shutdown"):
             getattr(L, name).restype = i
         _lib = L
     return _lib
@@ -186,6 +189,20 @@ def draws(n: int, nevents: int, seed: int, *, event_offset: int = 0, stream=None
     _check(lib().hydra_phsp_draws(int(n), int(nevents), int(seed), int(event_offset),
                                   ctypes.c_void_p(out.data_ptr()), ld, _stream_handle(stream)))
     return out[:, :nevents].to(torch.int64) & 0xFFFFFFFF
+
+
+def set_launch_config(kind: int, n: int, dtype, block: int, events_per_thread: int) -> None:
+    """Threads per block and events per thread of a kernel (kind: KERNEL_GENERATE or
+    KERNEL_INTEGRATE) for n daughters in a precision; results do not depend on it."""
+    _check(lib().hydra_set_launch_config(int(kind), int(n), _dtype_code(dtype), int(block),
+                                         int(events_per_thread)))
+
+
+def get_launch_config(kind: int, n: int, dtype) -> tuple[int, int]:
+    b, e = ctypes.c_int(), ctypes.c_int()
+    _check(lib().hydra_get_launch_config(int(kind), int(n), _dtype_code(dtype), ctypes.byref(b),
+                                         ctypes.byref(e)))
+    return b.value, e.value
 
 
 def shutdown() -> None:

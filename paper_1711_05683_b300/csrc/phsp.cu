@@ -20,6 +20,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -49,32 +50,64 @@ struct MEConsts {
 // ------------------------------------------------------------------------------------
 // Generation
 // ------------------------------------------------------------------------------------
-template <typename R>
-struct StoreSink {
-    R* __restrict__ base;  // out + e
-    R* __restrict__ wout;  // weights + e
-    uint64_t ld;
-    __device__ __forceinline__ void subsystem_mass(int, R) {}
-    __device__ __forceinline__ void daughter(int i, R E, R px, R py, R pz) {
-        R* p = base + static_cast<uint64_t>(4 * i) * ld;
-        p[0] = E;
-        p[ld] = px;
-        p[2 * ld] = py;
-        p[3 * ld] = pz;
+// Store EPT consecutive values (16-byte vectors where the group allows it).
+template <typename R, int EPT>
+__device__ __forceinline__ void store_group(R* __restrict__ p, const R (&v)[EPT]) {
+    if constexpr (EPT == 1) {
+        p[0] = v[0];
+    } else if constexpr (sizeof(R) == 4 && EPT == 2) {
+        *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
+    } else if constexpr (sizeof(R) == 4 && EPT == 4) {
+        *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    } else {
+        static_assert(sizeof(R) == 8 && EPT % 2 == 0, "double groups are pairs");
+#pragma unroll
+        for (int q = 0; q < EPT; q += 2) *reinterpret_cast<double2*>(p + q) = make_double2(v[q], v[q + 1]);
     }
-    __device__ __forceinline__ void weight(R w) { *wout = w; }
+}
+
+template <typename R, int EPT>
+struct StoreSink {
+    R* __restrict__ base;  // out + e0
+    R* __restrict__ wout;  // weights + e0
+    uint64_t ld;
+    __device__ __forceinline__ void subsystem_mass(int, const R (&)[EPT]) {}
+    __device__ __forceinline__ void daughter(int i, const R (&E)[EPT], const R (&px)[EPT],
+                                             const R (&py)[EPT], const R (&pz)[EPT]) {
+        R* p = base + static_cast<uint64_t>(4 * i) * ld;
+        store_group<R, EPT>(p, E);
+        store_group<R, EPT>(p + ld, px);
+        store_group<R, EPT>(p + 2 * ld, py);
+        store_group<R, EPT>(p + 3 * ld, pz);
+    }
+    __device__ __forceinline__ void weight(const R (&w)[EPT]) { store_group<R, EPT>(wout, w); }
 };
 
-template <int N, typename R>
-__global__ void __launch_bounds__(256) phsp_generate_kernel(const __grid_constant__ DecayConsts C,
+// Thread t takes the group of EPT consecutive events g*EPT.. (grid-stride over groups); the
+// last nevents % EPT events are taken one each by the first threads of the grid.
+template <int N, typename R, int EPT>
+__global__ void __launch_bounds__(512) phsp_generate_kernel(const __grid_constant__ DecayConsts C,
                                                             uint64_t nevents, uint64_t event_offset,
                                                             R* __restrict__ out, uint64_t ld,
                                                             R* __restrict__ weights) {
+    const uint64_t tid = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
-    for (uint64_t e = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < nevents;
-         e += stride) {
-        StoreSink<R> sink{out + e, weights + e, ld};
-        raubold_lynch_event<N, R>(C, event_offset + e, sink);
+    const uint64_t groups = nevents / EPT;
+    for (uint64_t g = tid; g < groups; g += stride) {
+        const uint64_t e0 = g * EPT;
+        uint64_t ev[EPT];
+#pragma unroll
+        for (int q = 0; q < EPT; ++q) ev[q] = event_offset + e0 + q;
+        StoreSink<R, EPT> sink{out + e0, weights + e0, ld};
+        raubold_lynch_group<N, R, EPT>(C, ev, sink);
+    }
+    if constexpr (EPT > 1) {
+        const uint64_t e = groups * EPT + tid;
+        if (e < nevents) {
+            uint64_t ev[1] = {event_offset + e};
+            StoreSink<R, 1> sink{out + e, weights + e, ld};
+            raubold_lynch_group<N, R, 1>(C, ev, sink);
+        }
     }
 }
 
@@ -102,16 +135,26 @@ __global__ void __launch_bounds__(256) phsp_draws_kernel(const __grid_constant__
 // ------------------------------------------------------------------------------------
 // Integration: f = w |ME|^2
 // ------------------------------------------------------------------------------------
-template <int N, typename R, int ME>
+template <typename R, int EPT>
 struct IntegrandSink {
-    R E1 = R(0), M2 = R(0), w = R(0);
-    __device__ __forceinline__ void subsystem_mass(int k, R Mk) {
-        if (k == 2) M2 = Mk;
+    R E1[EPT], M2[EPT], w[EPT];
+    __device__ __forceinline__ void subsystem_mass(int k, const R (&Mk)[EPT]) {
+        if (k == 2) {
+#pragma unroll
+            for (int q = 0; q < EPT; ++q) M2[q] = Mk[q];
+        }
     }
-    __device__ __forceinline__ void daughter(int i, R E, R, R, R) {
-        if (i == 0) E1 = E;
+    __device__ __forceinline__ void daughter(int i, const R (&E)[EPT], const R (&)[EPT],
+                                             const R (&)[EPT], const R (&)[EPT]) {
+        if (i == 0) {
+#pragma unroll
+            for (int q = 0; q < EPT; ++q) E1[q] = E[q];
+        }
     }
-    __device__ __forceinline__ void weight(R wv) { w = wv; }
+    __device__ __forceinline__ void weight(const R (&wv)[EPT]) {
+#pragma unroll
+        for (int q = 0; q < EPT; ++q) w[q] = wv[q];
+    }
 };
 
 template <typename R> __device__ __forceinline__ R me_param(double d, float f);
@@ -123,28 +166,31 @@ template <typename R>
 __device__ __forceinline__ R dalitz_2bw(const MEConsts& P, R s12, R s23) {
     const R xa = me_param<R>(P.a_m2, P.a_m2f) - s12, ya = me_param<R>(P.a_mg, P.a_mgf);
     const R xb = me_param<R>(P.b_m2, P.b_m2f) - s23, yb = me_param<R>(P.b_mg, P.b_mgf);
-    const R ia = R(1) / (xa * xa + ya * ya);
-    const R ib = R(1) / (xb * xb + yb * yb);
+    const R ia = Prec<R>::rcp(xa * xa + ya * ya);
+    const R ib = Prec<R>::rcp(xb * xb + yb * yb);
     const R cr = me_param<R>(P.c_re, P.c_ref), ci = me_param<R>(P.c_im, P.c_imf);
     const R re = xa * ia + (cr * xb - ci * yb) * ib;
     const R im = ya * ia + (cr * yb + ci * xb) * ib;
     return re * re + im * im;
 }
 
-template <int N, typename R, int ME>
-__device__ __forceinline__ void integrand(const DecayConsts& C, const MEConsts& P, uint64_t ev,
-                                          R& f, R& w) {
-    IntegrandSink<N, R, ME> s;
-    raubold_lynch_event<N, R>(C, ev, s);
-    w = s.w;
-    if constexpr (ME == HYDRA_ME_DALITZ_2BW) {
-        // s12 = M_2^2 (subsystem of daughters 1, 2); s23 = (P - p1)^2 = M^2 + m1^2 - 2 M E1
-        const R M = Prec<R>::M(C);
-        const R s12 = s.M2 * s.M2;
-        const R s23 = M * M + Prec<R>::m2(C, 0) - R(2) * M * s.E1;
-        f = s.w * dalitz_2bw<R>(P, s12, s23);
-    } else {
-        f = s.w;
+template <int N, typename R, int ME, int EPT>
+__device__ __forceinline__ void integrand_group(const DecayConsts& C, const MEConsts& P,
+                                                const uint64_t (&ev)[EPT], R (&f)[EPT], R (&w)[EPT]) {
+    IntegrandSink<R, EPT> s;
+    raubold_lynch_group<N, R, EPT>(C, ev, s);
+#pragma unroll
+    for (int q = 0; q < EPT; ++q) {
+        w[q] = s.w[q];
+        if constexpr (ME == HYDRA_ME_DALITZ_2BW) {
+            // s12 = M_2^2 (subsystem of daughters 1, 2); s23 = (P - p1)^2 = M^2 + m1^2 - 2 M E1
+            const R M = Prec<R>::M(C);
+            const R s12 = s.M2[q] * s.M2[q];
+            const R s23 = M * M + Prec<R>::m2(C, 0) - R(2) * M * s.E1[q];
+            f[q] = s.w[q] * dalitz_2bw<R>(P, s12, s23);
+        } else {
+            f[q] = s.w[q];
+        }
     }
 }
 
@@ -155,12 +201,13 @@ struct TileSums {
 // One warp per tile of kTileEvents events.  Lane l takes events tile*2048 + 32*i + l,
 // i = 0..63, sums them in R in groups of 8 (fixed order), folds each group into FP64, and
 // the warp combines lanes by a fixed xor butterfly; lane 0's total is the tile partial.
-template <int N, typename R, int ME>
-__global__ void __launch_bounds__(256) phsp_integrate_tiles(const __grid_constant__ DecayConsts C,
+template <int N, typename R, int ME, int EPT>
+__global__ void __launch_bounds__(512) phsp_integrate_tiles(const __grid_constant__ DecayConsts C,
                                                             const __grid_constant__ MEConsts P,
                                                             uint64_t nevents, uint64_t event_offset,
                                                             uint64_t tile_begin, uint64_t ntiles,
                                                             TileSums* __restrict__ partials) {
+    static_assert(kGroupEvents % EPT == 0, "a group holds whole event groups");
     const int lane = threadIdx.x & 31;
     const uint64_t warp = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = (static_cast<uint64_t>(gridDim.x) * blockDim.x) >> 5;
@@ -170,16 +217,26 @@ __global__ void __launch_bounds__(256) phsp_integrate_tiles(const __grid_constan
 #pragma unroll 1
         for (int g = 0; g < kLaneIters / kGroupEvents; ++g) {
             R sf = R(0), sf2 = R(0), sw = R(0), sw2 = R(0);
-#pragma unroll 2
-            for (int i = 0; i < kGroupEvents; ++i) {
-                const uint64_t e = base + static_cast<uint64_t>(32 * (g * kGroupEvents + i) + lane);
-                if (e < nevents) {
-                    R f, w;
-                    integrand<N, R, ME>(C, P, event_offset + e, f, w);
-                    sf += f;
-                    sf2 += f * f;
-                    sw += w;
-                    sw2 += w * w;
+#pragma unroll 1
+            for (int i0 = 0; i0 < kGroupEvents; i0 += EPT) {
+                uint64_t ev[EPT];
+                bool valid[EPT];
+#pragma unroll
+                for (int q = 0; q < EPT; ++q) {
+                    const uint64_t e = base + static_cast<uint64_t>(32 * (g * kGroupEvents + i0 + q) + lane);
+                    valid[q] = e < nevents;
+                    ev[q] = event_offset + e;
+                }
+                R f[EPT], w[EPT];
+                integrand_group<N, R, ME, EPT>(C, P, ev, f, w);
+#pragma unroll
+                for (int q = 0; q < EPT; ++q) {
+                    if (valid[q]) {
+                        sf += f[q];
+                        sf2 += f[q] * f[q];
+                        sw += w[q];
+                        sw2 += w[q] * w[q];
+                    }
                 }
             }
             af += static_cast<double>(sf);
@@ -369,18 +426,38 @@ static int grid_for(const void* kernel, int block, uint64_t work_items) {
     return static_cast<int>(need < full ? (need ? need : 1) : full);
 }
 
-template <typename R>
-static const void* generate_kernel_for(int n) {
+// ------------------------------------------------------------------------------------
+// Kernel selection and launch configuration (block size, events per thread), settable per
+// (kernel kind, n, dtype) through hydra_set_launch_config; the autotuner uses that.
+// ------------------------------------------------------------------------------------
+struct Launch {
+    const void* kern;
+    int block;
+    int ept;
+};
+
+template <typename R, int EPT>
+static const void* generate_kernel_n(int n) {
     switch (n) {
-        case 2: return reinterpret_cast<const void*>(&phsp_generate_kernel<2, R>);
-        case 3: return reinterpret_cast<const void*>(&phsp_generate_kernel<3, R>);
-        case 4: return reinterpret_cast<const void*>(&phsp_generate_kernel<4, R>);
-        case 5: return reinterpret_cast<const void*>(&phsp_generate_kernel<5, R>);
-        case 6: return reinterpret_cast<const void*>(&phsp_generate_kernel<6, R>);
-        case 7: return reinterpret_cast<const void*>(&phsp_generate_kernel<7, R>);
-        case 8: return reinterpret_cast<const void*>(&phsp_generate_kernel<8, R>);
-        case 9: return reinterpret_cast<const void*>(&phsp_generate_kernel<9, R>);
-        case 10: return reinterpret_cast<const void*>(&phsp_generate_kernel<10, R>);
+        case 2: return reinterpret_cast<const void*>(&phsp_generate_kernel<2, R, EPT>);
+        case 3: return reinterpret_cast<const void*>(&phsp_generate_kernel<3, R, EPT>);
+        case 4: return reinterpret_cast<const void*>(&phsp_generate_kernel<4, R, EPT>);
+        case 5: return reinterpret_cast<const void*>(&phsp_generate_kernel<5, R, EPT>);
+        case 6: return reinterpret_cast<const void*>(&phsp_generate_kernel<6, R, EPT>);
+        case 7: return reinterpret_cast<const void*>(&phsp_generate_kernel<7, R, EPT>);
+        case 8: return reinterpret_cast<const void*>(&phsp_generate_kernel<8, R, EPT>);
+        case 9: return reinterpret_cast<const void*>(&phsp_generate_kernel<9, R, EPT>);
+        case 10: return reinterpret_cast<const void*>(&phsp_generate_kernel<10, R, EPT>);
+    }
+    return nullptr;
+}
+
+template <typename R>
+static const void* generate_kernel_for(int n, int ept) {
+    switch (ept) {
+        case 1: return generate_kernel_n<R, 1>(n);
+        case 2: return generate_kernel_n<R, 2>(n);
+        case 4: return generate_kernel_n<R, 4>(n);
     }
     return nullptr;
 }
@@ -400,28 +477,66 @@ static const void* draws_kernel_for(int n) {
     return nullptr;
 }
 
-template <typename R, int ME>
-static const void* integrate_kernel_for(int n) {
+template <typename R, int ME, int EPT>
+static const void* integrate_kernel_n(int n) {
     if constexpr (ME == HYDRA_ME_DALITZ_2BW) {
-        return n == 3 ? reinterpret_cast<const void*>(&phsp_integrate_tiles<3, R, ME>) : nullptr;
+        return n == 3 ? reinterpret_cast<const void*>(&phsp_integrate_tiles<3, R, ME, EPT>) : nullptr;
     } else {
         switch (n) {
-            case 2: return reinterpret_cast<const void*>(&phsp_integrate_tiles<2, R, ME>);
-            case 3: return reinterpret_cast<const void*>(&phsp_integrate_tiles<3, R, ME>);
-            case 4: return reinterpret_cast<const void*>(&phsp_integrate_tiles<4, R, ME>);
-            case 5: return reinterpret_cast<const void*>(&phsp_integrate_tiles<5, R, ME>);
-            case 6: return reinterpret_cast<const void*>(&phsp_integrate_tiles<6, R, ME>);
-            case 7: return reinterpret_cast<const void*>(&phsp_integrate_tiles<7, R, ME>);
-            case 8: return reinterpret_cast<const void*>(&phsp_integrate_tiles<8, R, ME>);
-            case 9: return reinterpret_cast<const void*>(&phsp_integrate_tiles<9, R, ME>);
-            case 10: return reinterpret_cast<const void*>(&phsp_integrate_tiles<10, R, ME>);
+            case 2: return reinterpret_cast<const void*>(&phsp_integrate_tiles<2, R, ME, EPT>);
+            case 3: return reinterpret_cast<const void*>(&phsp_integrate_tiles<3, R, ME, EPT>);
+            case 4: return reinterpret_cast<const void*>(&phsp_integrate_tiles<4, R, ME, EPT>);
+            case 5: return reinterpret_cast<const void*>(&phsp_integrate_tiles<5, R, ME, EPT>);
+            case 6: return reinterpret_cast<const void*>(&phsp_integrate_tiles<6, R, ME, EPT>);
+            case 7: return reinterpret_cast<const void*>(&phsp_integrate_tiles<7, R, ME, EPT>);
+            case 8: return reinterpret_cast<const void*>(&phsp_integrate_tiles<8, R, ME, EPT>);
+            case 9: return reinterpret_cast<const void*>(&phsp_integrate_tiles<9, R, ME, EPT>);
+            case 10: return reinterpret_cast<const void*>(&phsp_integrate_tiles<10, R, ME, EPT>);
         }
         return nullptr;
     }
 }
 
-constexpr int kGenBlock = 256;
-constexpr int kIntBlock = 256;
+template <typename R, int ME>
+static const void* integrate_kernel_for(int n, int ept) {
+    switch (ept) {
+        case 1: return integrate_kernel_n<R, ME, 1>(n);
+        case 2: return integrate_kernel_n<R, ME, 2>(n);
+        case 4: return integrate_kernel_n<R, ME, 4>(n);
+    }
+    return nullptr;
+}
+
+// Launch configuration table [kind][dtype][n] = block size and events per thread.  The
+// defaults are the measured best on B300 (see the tuning notes); hydra_set_launch_config
+// overrides them for the process.
+struct LaunchCfg {
+    std::atomic<int> block{256};
+    std::atomic<int> ept{1};
+};
+static LaunchCfg g_cfg[2][2][kNMax + 1];
+
+static Launch select_generate(hydra_dtype dtype, int n) {
+    LaunchCfg& c = g_cfg[HYDRA_KERNEL_GENERATE][dtype][n];
+    const int ept = c.ept.load(std::memory_order_relaxed);
+    const void* k = dtype == HYDRA_F32 ? generate_kernel_for<float>(n, ept) : generate_kernel_for<double>(n, ept);
+    return Launch{k, c.block.load(std::memory_order_relaxed), ept};
+}
+
+static Launch select_integrate(hydra_dtype dtype, hydra_me_id me, int n) {
+    LaunchCfg& c = g_cfg[HYDRA_KERNEL_INTEGRATE][dtype][n];
+    const int ept = c.ept.load(std::memory_order_relaxed);
+    const void* k = nullptr;
+    if (dtype == HYDRA_F32)
+        k = me == HYDRA_ME_FLAT ? integrate_kernel_for<float, HYDRA_ME_FLAT>(n, ept)
+                                : integrate_kernel_for<float, HYDRA_ME_DALITZ_2BW>(n, ept);
+    else
+        k = me == HYDRA_ME_FLAT ? integrate_kernel_for<double, HYDRA_ME_FLAT>(n, ept)
+                                : integrate_kernel_for<double, HYDRA_ME_DALITZ_2BW>(n, ept);
+    return Launch{k, c.block.load(std::memory_order_relaxed), ept};
+}
+
+constexpr int kGenBlock = 256;  // the raw-draws kernel
 
 // Per-device scratch for integrals: tile partials of one chunk, segment partials of one
 // request, the device-side result and a pinned host copy.  Guarded by its mutex.
@@ -542,19 +657,18 @@ static hydra_status make_me(hydra_me_id me, int n, const double* params, int npa
     return HYDRA_OK;
 }
 
-template <typename R>
-static hydra_status launch_integrate_chunks(const void* kern, const DecayConsts& C, const MEConsts& P,
+static hydra_status launch_integrate_chunks(const Launch& L, const DecayConsts& C, const MEConsts& P,
                                             uint64_t nevents, uint64_t event_offset,
                                             DeviceScratch* s, cudaStream_t st) {
     const uint64_t ntiles = (nevents + kTileEvents - 1) / kTileEvents;
     for (uint64_t t0 = 0; t0 < ntiles; t0 += kChunkTiles) {
         const uint64_t nt = ntiles - t0 < kChunkTiles ? ntiles - t0 : kChunkTiles;
-        const int grid = grid_for(kern, kIntBlock, nt * 32);
+        const int grid = grid_for(L.kern, L.block, nt * 32);
         TileSums* tiles = s->tiles;
         void* args[] = {const_cast<DecayConsts*>(&C), const_cast<MEConsts*>(&P), &nevents,
                         &event_offset, const_cast<uint64_t*>(&t0), const_cast<uint64_t*>(&nt),
                         &tiles};
-        cudaError_t err = cudaLaunchKernel(kern, dim3(grid), dim3(kIntBlock), args, 0, st);
+        cudaError_t err = cudaLaunchKernel(L.kern, dim3(grid), dim3(L.block), args, 0, st);
         if (err != cudaSuccess) return cuda_fail(err, "integrate launch");
         const uint64_t nseg = (nt + kSegTiles - 1) / kSegTiles;
         const uint64_t seg_begin = t0 / kSegTiles;
@@ -648,10 +762,10 @@ hydra_status hydra_phsp_generate(double M, int n, const double* masses, uint64_t
         return fail(HYDRA_ERR_MISALIGNED, "out and weights must be 16-byte aligned");
     if (ld % 4 != 0) return fail(HYDRA_ERR_MISALIGNED, "ld = %llu must be a multiple of 4", static_cast<unsigned long long>(ld));
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    const void* kern = dtype == HYDRA_F32 ? generate_kernel_for<float>(n) : generate_kernel_for<double>(n);
-    const int grid = grid_for(kern, kGenBlock, nevents);
+    const Launch L = select_generate(dtype, n);
+    const int grid = grid_for(L.kern, L.block, (nevents + L.ept - 1) / L.ept);
     void* args[] = {&C, &nevents, &event_offset, &out, &ld, &weights};
-    const cudaError_t err = cudaLaunchKernel(kern, dim3(grid), dim3(kGenBlock), args, 0, s);
+    const cudaError_t err = cudaLaunchKernel(L.kern, dim3(grid), dim3(L.block), args, 0, s);
     if (err != cudaSuccess) return cuda_fail(err, "generate launch");
     return HYDRA_OK;
 }
@@ -677,7 +791,7 @@ hydra_status hydra_phsp_generate_host(double M, int n, const double* masses, uin
     st = ensure_staging(s, arrays * chunk * elem);
     if (st != HYDRA_OK) return st;
     cudaStream_t gs = reinterpret_cast<cudaStream_t>(stream);
-    const void* kern = dtype == HYDRA_F32 ? generate_kernel_for<float>(n) : generate_kernel_for<double>(n);
+    const Launch L = select_generate(dtype, n);
     cudaError_t err = cudaSuccess;
     // the copy stream must not run ahead of work already queued on the caller's stream
     err = cudaEventRecord(s->gen_done[1], gs);
@@ -697,9 +811,9 @@ hydra_status hydra_phsp_generate_host(double M, int n, const double* masses, uin
         uint64_t off = event_offset + e0;
         uint64_t sld = chunk;
         uint64_t cnt_v = cnt;
-        const int grid = grid_for(kern, kGenBlock, cnt);
+        const int grid = grid_for(L.kern, L.block, (cnt + L.ept - 1) / L.ept);
         void* args[] = {&C, &cnt_v, &off, &dout, &sld, &dw};
-        err = cudaLaunchKernel(kern, dim3(grid), dim3(kGenBlock), args, 0, gs);
+        err = cudaLaunchKernel(L.kern, dim3(grid), dim3(L.block), args, 0, gs);
         if (err == cudaSuccess) err = cudaEventRecord(s->gen_done[b], gs);
         if (err == cudaSuccess) err = cudaStreamWaitEvent(s->copy_stream, s->gen_done[b], 0);
         if (err == cudaSuccess)
@@ -755,12 +869,8 @@ hydra_status hydra_phsp_integrate(double M, int n, const double* masses, uint64_
     MEConsts P;
     st = make_me(me, n, params, nparams, &P);
     if (st != HYDRA_OK) return st;
-    const void* kern = nullptr;
-    if (kin_dtype == HYDRA_F32)
-        kern = me == HYDRA_ME_FLAT ? integrate_kernel_for<float, HYDRA_ME_FLAT>(n) : integrate_kernel_for<float, HYDRA_ME_DALITZ_2BW>(n);
-    else
-        kern = me == HYDRA_ME_FLAT ? integrate_kernel_for<double, HYDRA_ME_FLAT>(n) : integrate_kernel_for<double, HYDRA_ME_DALITZ_2BW>(n);
-    if (!kern) return fail(HYDRA_ERR_UNSUPPORTED_N, "no kernel for n = %d and me = %d", n, static_cast<int>(me));
+    const Launch L = select_integrate(kin_dtype, me, n);
+    if (!L.kern) return fail(HYDRA_ERR_UNSUPPORTED_N, "no kernel for n = %d and me = %d", n, static_cast<int>(me));
 
     DeviceScratch* s = scratch_for_current_device();
     if (!s) return fail(HYDRA_ERR_CUDA, "no current CUDA device");
@@ -770,8 +880,7 @@ hydra_status hydra_phsp_integrate(double M, int n, const double* masses, uint64_
     st = ensure_scratch(s, nseg);
     if (st != HYDRA_OK) return st;
     cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
-    st = kin_dtype == HYDRA_F32 ? launch_integrate_chunks<float>(kern, C, P, nevents, event_offset, s, cs)
-                                : launch_integrate_chunks<double>(kern, C, P, nevents, event_offset, s, cs);
+    st = launch_integrate_chunks(L, C, P, nevents, event_offset, s, cs);
     if (st != HYDRA_OK) return st;
     finalize_integral<<<1, 32, 0, cs>>>(s->segs, nseg, nevents, s->d_result);
     cudaError_t err = cudaGetLastError();
@@ -802,12 +911,8 @@ hydra_status hydra_phsp_integrate_noalloc(double M, int n, const double* masses,
     MEConsts P;
     st = make_me(me, n, params, nparams, &P);
     if (st != HYDRA_OK) return st;
-    const void* kern = nullptr;
-    if (kin_dtype == HYDRA_F32)
-        kern = me == HYDRA_ME_FLAT ? integrate_kernel_for<float, HYDRA_ME_FLAT>(n) : integrate_kernel_for<float, HYDRA_ME_DALITZ_2BW>(n);
-    else
-        kern = me == HYDRA_ME_FLAT ? integrate_kernel_for<double, HYDRA_ME_FLAT>(n) : integrate_kernel_for<double, HYDRA_ME_DALITZ_2BW>(n);
-    if (!kern) return fail(HYDRA_ERR_UNSUPPORTED_N, "no kernel for n = %d and me = %d", n, static_cast<int>(me));
+    const Launch L = select_integrate(kin_dtype, me, n);
+    if (!L.kern) return fail(HYDRA_ERR_UNSUPPORTED_N, "no kernel for n = %d and me = %d", n, static_cast<int>(me));
 
     std::lock_guard<std::mutex> lk(g_noalloc_mu);
     unsigned char* base = nullptr;
@@ -822,8 +927,7 @@ hydra_status hydra_phsp_integrate_noalloc(double M, int n, const double* masses,
     const uint64_t ntiles = (nevents + kTileEvents - 1) / kTileEvents;
     const uint64_t nseg = (ntiles + kSegTiles - 1) / kSegTiles;
     cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
-    st = kin_dtype == HYDRA_F32 ? launch_integrate_chunks<float>(kern, C, P, nevents, event_offset, &view, cs)
-                                : launch_integrate_chunks<double>(kern, C, P, nevents, event_offset, &view, cs);
+    st = launch_integrate_chunks(L, C, P, nevents, event_offset, &view, cs);
     if (st != HYDRA_OK) return st;
     finalize_integral<<<1, 32, 0, cs>>>(view.segs, nseg, nevents, d_result);
     cudaError_t err = cudaGetLastError();
@@ -832,6 +936,35 @@ hydra_status hydra_phsp_integrate_noalloc(double M, int n, const double* masses,
     if (err != cudaSuccess) return cuda_fail(err, "result copy");
     err = cudaStreamSynchronize(cs);
     if (err != cudaSuccess) return cuda_fail(err, "integrate synchronize");
+    return HYDRA_OK;
+}
+
+hydra_status hydra_set_launch_config(hydra_kernel_kind kind, int n, hydra_dtype dtype, int block,
+                                     int events_per_thread) {
+    if (kind != HYDRA_KERNEL_GENERATE && kind != HYDRA_KERNEL_INTEGRATE)
+        return fail(HYDRA_ERR_INVALID_ARG, "unknown kernel kind %d", static_cast<int>(kind));
+    if (n < 2 || n > kNMax) return fail(HYDRA_ERR_UNSUPPORTED_N, "n = %d outside [2, %d]", n, kNMax);
+    if (dtype != HYDRA_F32 && dtype != HYDRA_F64) return fail(HYDRA_ERR_INVALID_ARG, "unknown dtype %d", static_cast<int>(dtype));
+    if (block < 32 || block > 512 || block % 32 != 0)
+        return fail(HYDRA_ERR_INVALID_ARG, "block = %d must be a multiple of 32 in [32, 512]", block);
+    if (events_per_thread != 1 && events_per_thread != 2 && events_per_thread != 4)
+        return fail(HYDRA_ERR_INVALID_ARG, "events_per_thread = %d must be 1, 2 or 4", events_per_thread);
+    LaunchCfg& c = g_cfg[kind][dtype][n];
+    c.block.store(block);
+    c.ept.store(events_per_thread);
+    return HYDRA_OK;
+}
+
+hydra_status hydra_get_launch_config(hydra_kernel_kind kind, int n, hydra_dtype dtype, int* block,
+                                     int* events_per_thread) {
+    if (kind != HYDRA_KERNEL_GENERATE && kind != HYDRA_KERNEL_INTEGRATE)
+        return fail(HYDRA_ERR_INVALID_ARG, "unknown kernel kind %d", static_cast<int>(kind));
+    if (n < 2 || n > kNMax) return fail(HYDRA_ERR_UNSUPPORTED_N, "n = %d outside [2, %d]", n, kNMax);
+    if (dtype != HYDRA_F32 && dtype != HYDRA_F64) return fail(HYDRA_ERR_INVALID_ARG, "unknown dtype %d", static_cast<int>(dtype));
+    if (!block || !events_per_thread) return fail(HYDRA_ERR_INVALID_ARG, "NULL output");
+    const LaunchCfg& c = g_cfg[kind][dtype][n];
+    *block = c.block.load();
+    *events_per_thread = c.ept.load();
     return HYDRA_OK;
 }
 

@@ -74,17 +74,39 @@ __device__ __forceinline__ void sort_mass_draws(uint32_t* x) {
 }
 
 // ------------------------------------------------------------------------------------
-// Precision traits.  FP32 kinematics use CUDA's correctly rounded sqrtf and sincospif;
-// FP64 uses sqrt and sincospi.  Conversions of 32-bit draws are exact in FP64.
+// Precision traits.  FP32 kinematics use the hardware approximations sqrt.approx,
+// rcp.approx and __sincosf (errors of a few units of 2^-24, far inside the FP32 tolerance);
+// FP64 uses correctly rounded sqrt, division and sincospi.  Conversions of 32-bit draws
+// are exact in FP64.
 // ------------------------------------------------------------------------------------
 template <typename R> struct Prec;
 
 template <> struct Prec<float> {
     __device__ static float u32(uint32_t v) { return __uint2float_rn(v); }
     __device__ static float i32(int32_t v) { return __int2float_rn(v); }
-    __device__ static float sqrt_(float v) { return sqrtf(v); }
+    // Hardware approximations (a few ulp of 2^-24): the FP32 path's tolerance is 2e-5.
+    __device__ static float sqrt_(float v) {  // sqrt.approx: exact 0 at 0, rel. error ~2^-23
+        float r;
+        asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(v));
+        return r;
+    }
+    __device__ static float rcp(float v) {  // rcp.approx: ~1 ulp for normal v
+        float r;
+        asm("rcp.approx.f32 %0, %1;" : "=f"(r) : "f"(v));
+        return r;
+    }
+    __device__ static float div(float a, float b) { return a * rcp(b); }
     __device__ static float fma_(float a, float b, float c) { return __fmaf_rn(a, b, c); }
-    __device__ static void sincospi_(float a, float* s, float* c) { sincospif(a, s, c); }
+    // sin and cos of phi = 2 pi (x + 1/2) 2^-32: __sincosf is accurate (|err| < 2^-21.4) on
+    // (-pi, pi), so evaluate it at phi - pi and flip both signs.
+    __device__ static void sincos_2pi_u(uint32_t x, float* s, float* c) {
+        constexpr float kTwoPiScale = 1.46291807926715968e-09f;              // 2 pi 2^-32
+        constexpr float kShift = 7.31459039633579841e-10f - 3.14159265358979323846f;  // pi 2^-32 - pi
+        float sn, cs;
+        __sincosf(__fmaf_rn(__uint2float_rn(x), kTwoPiScale, kShift), &sn, &cs);
+        *s = -sn;
+        *c = -cs;
+    }
     __device__ static float M(const DecayConsts& C) { return C.Mf; }
     __device__ static float Ts(const DecayConsts& C) { return C.Tsf; }
     __device__ static float Ts_half(const DecayConsts& C) { return C.Ts_halff; }
@@ -98,8 +120,13 @@ template <> struct Prec<double> {
     __device__ static double u32(uint32_t v) { return __uint2double_rn(v); }
     __device__ static double i32(int32_t v) { return __int2double_rn(v); }
     __device__ static double sqrt_(double v) { return sqrt(v); }
+    __device__ static double rcp(double v) { return 1.0 / v; }
+    __device__ static double div(double a, double b) { return a / b; }
     __device__ static double fma_(double a, double b, double c) { return __fma_rn(a, b, c); }
-    __device__ static void sincospi_(double a, double* s, double* c) { sincospi(a, s, c); }
+    // sin and cos of phi = 2 pi u with u = (x + 1/2) 2^-32: sincospi(2u), argument exact.
+    __device__ static void sincos_2pi_u(uint32_t x, double* s, double* c) {
+        sincospi(__fma_rn(__uint2double_rn(x), 4.656612873077392578125e-10, 2.3283064365386962890625e-10), s, c);
+    }
     __device__ static double M(const DecayConsts& C) { return C.M; }
     __device__ static double Ts(const DecayConsts& C) { return C.Ts; }
     __device__ static double Ts_half(const DecayConsts& C) { return C.Ts_half; }
@@ -110,10 +137,14 @@ template <> struct Prec<double> {
 };
 
 // ------------------------------------------------------------------------------------
-// One Raubold-Lynch event.
+// A group of EPT Raubold-Lynch events computed in lockstep (EPT independent dependency
+// chains per thread; the arithmetic of each event is the same for every EPT, so results
+// are bit-identical whatever the group size).
 //
 // Draws: d = 0..n-3 intermediate masses; for top-down step j = 0..n-2 (j = 0 is the
-// parent's decay) cos(theta) from draw n-2+2j and phi from draw n-1+2j.
+// parent's decay) cos(theta) from draw n-2+2j and phi from draw n-1+2j.  Draw d is word
+// d%4 of Philox block d/4; a step's two draws always share one block, which is generated
+// when the step first needs it (live state: the sorted mass draws and one block).
 //
 // With y_1 <= ... <= y_{n-2} the sorted mass draws, r_j = (y_j + 1/2) 2^-32, r_0 = 0,
 // r_{n-1} = 1:  M_1 = m_1, M_k = mu_k + r_{k-1} T, M_n = M, and the kinetic gaps
@@ -126,89 +157,120 @@ template <> struct Prec<double> {
 // subsystem is boosted to the lab, E' = (Q0 E + Q.p)/M_{k+1},
 // p' = p + Q (E' + E)/(Q0 + M_{k+1}); daughter k+1 = Q - Q' by 4-momentum conservation.
 //
-// Sink interface:
+// Sink interface (arrays hold one value per event of the group):
 //   sink.daughter(i, E, px, py, pz)  daughter index i = 0..n-1 (daughter i+1)
 //   sink.subsystem_mass(k, Mk)       M_k for k = 1..n-1
 //   sink.weight(w)
 // ------------------------------------------------------------------------------------
-template <int N, typename R, typename Sink>
-__device__ __forceinline__ void raubold_lynch_event(const DecayConsts& C, uint64_t event,
+template <int N, typename R, int EPT, typename Sink>
+__device__ __forceinline__ void raubold_lynch_group(const DecayConsts& C, const uint64_t (&ev)[EPT],
                                                     Sink& sink) {
     using P = Prec<R>;
-    constexpr int kDraws = 3 * N - 4;
-    constexpr int kBlocks = (kDraws + 3) / 4;
-    const uint32_t ev_lo = static_cast<uint32_t>(event);
-    const uint32_t ev_hi = static_cast<uint32_t>(event >> 32);
+    constexpr int kMass = N - 2;
+    constexpr int kMassBlocks = (kMass + 3) / 4;
+    constexpr int kY = kMass > 0 ? kMass : 1;
+    constexpr R kTwoM31 = R(4.656612873077392578125e-10);  // 2^-31
+    constexpr R kTwoM32 = R(2.3283064365386962890625e-10); // 2^-32
 
-    uint32_t x[4 * kBlocks];
+    uint32_t y[EPT][kY];
+    uint32_t blk[EPT][4];
 #pragma unroll
-    for (int b = 0; b < kBlocks; ++b) philox4x32_10(ev_lo, ev_hi, b, 0u, C.rk0, C.rk1, &x[4 * b]);
-
-    if constexpr (N > 3) sort_mass_draws<N - 2>(x);
+    for (int b = 0; b < kMassBlocks; ++b) {
+#pragma unroll
+        for (int q = 0; q < EPT; ++q) {
+            philox4x32_10(static_cast<uint32_t>(ev[q]), static_cast<uint32_t>(ev[q] >> 32), b, 0u,
+                          C.rk0, C.rk1, blk[q]);
+#pragma unroll
+            for (int t = 0; t < 4; ++t)
+                if (4 * b + t < kMass) y[q][4 * b + t] = blk[q][t];
+        }
+    }
+    if constexpr (N > 3) {
+#pragma unroll
+        for (int q = 0; q < EPT; ++q) sort_mass_draws<N - 2>(y[q]);
+    }
 
     const R M = P::M(C);
     const R Ts = P::Ts(C);
     const R Ts_half = P::Ts_half(C);
-    constexpr R kTwoM31 = R(4.656612873077392578125e-10);  // 2^-31
-    constexpr R kTwoM32 = R(2.3283064365386962890625e-10); // 2^-32
 
-    R w = R(1);  // prod p_k; C_n is applied last so only the final product can leave the normal range
-    R Q0 = M, Qx = R(0), Qy = R(0), Qz = R(0);
-    R Mnext = M;  // M_{k+1}
+    R w[EPT], Q0[EPT], Qx[EPT], Qy[EPT], Qz[EPT], Mnext[EPT];
+#pragma unroll
+    for (int q = 0; q < EPT; ++q) {
+        w[q] = R(1);  // prod p_k; C_n is applied last so only the final product can leave the normal range
+        Q0[q] = M; Qx[q] = R(0); Qy[q] = R(0); Qz[q] = R(0);
+        Mnext[q] = M;  // M_{k+1}
+    }
 
 #pragma unroll
     for (int k = N - 1; k >= 1; --k) {
         const int j = N - 1 - k;
-        // intermediate mass M_k
-        R Mk;
-        if (k == 1) Mk = P::m(C, 0);
-        else Mk = P::fma_(P::u32(x[k - 2]) + R(0.5), Ts, P::mu(C, k - 1));
-        // kinetic gap Delta_k = T (r_k - r_{k-1}) from integer differences
-        R gap;
-        if constexpr (N == 2) {
-            gap = Ts * R(4294967296.0);  // T exactly: Ts = T * 2^-32
-        } else if (k == 1) {
-            gap = P::fma_(P::u32(x[0]), Ts, Ts_half);
-        } else if (k == N - 1) {
-            gap = P::fma_(P::u32(~x[N - 3]), Ts, Ts_half);
-        } else {
-            gap = P::u32(x[k - 1] - x[k - 2]) * Ts;
+        const int dc = N - 2 + 2 * j;  // cos(theta) draw; phi is dc + 1 in the same block
+        const bool fresh = (j == 0) ? (kMassBlocks == 0 || dc / 4 != kMassBlocks - 1) : (dc / 4 != (dc - 2) / 4);
+        if (fresh) {
+#pragma unroll
+            for (int q = 0; q < EPT; ++q)
+                philox4x32_10(static_cast<uint32_t>(ev[q]), static_cast<uint32_t>(ev[q] >> 32), dc / 4, 0u,
+                              C.rk0, C.rk1, blk[q]);
         }
-        sink.subsystem_mass(k, Mk);
-        // two-body momentum
-        const R mk1 = P::m(C, k);
-        const R twoMk = R(2) * Mk;
-        const R lam = gap * (gap + twoMk) * (gap + R(2) * mk1) * (gap + twoMk + R(2) * mk1);
-        const R invM = R(1) / Mnext;
-        const R p = P::sqrt_(lam) * (R(0.5) * invM);
-        w *= p;
-        // isotropic direction of subsystem k in the rest frame of subsystem k+1
-        const uint32_t xc = x[N - 2 + 2 * j];
-        const uint32_t xp = x[N - 1 + 2 * j];
-        const R cos_t = P::fma_(P::i32(static_cast<int32_t>(xc ^ 0x80000000u)), kTwoM31, kTwoM32);
-        const R one_m = P::fma_(P::u32(~xc), kTwoM31, kTwoM32);  // 1 - cos(theta)
-        const R one_p = P::fma_(P::u32(xc), kTwoM31, kTwoM32);   // 1 + cos(theta)
-        const R sin_t = P::sqrt_(one_m * one_p);
-        R sphi, cphi;
-        P::sincospi_(P::fma_(P::u32(xp), kTwoM31, kTwoM32), &sphi, &cphi);  // phi = 2 pi u
-        const R px = p * sin_t * cphi, py = p * sin_t * sphi, pz = p * cos_t;
-        const R Es = P::sqrt_(P::fma_(p, p, Mk * Mk));
-        if (k == N - 1) {
-            // parent at rest: no boost
-            sink.daughter(k, M - Es, -px, -py, -pz);
-            Q0 = Es; Qx = px; Qy = py; Qz = pz;
-        } else {
-            const R qp = Qx * px + Qy * py + Qz * pz;
-            const R E1 = (Q0 * Es + qp) * invM;
-            const R f = (E1 + Es) / (Q0 + Mnext);
-            const R n0 = E1, nx = P::fma_(f, Qx, px), ny = P::fma_(f, Qy, py), nz = P::fma_(f, Qz, pz);
-            sink.daughter(k, Q0 - n0, Qx - nx, Qy - ny, Qz - nz);
-            Q0 = n0; Qx = nx; Qy = ny; Qz = nz;
+        R dE[EPT], dx[EPT], dy[EPT], dz[EPT], Mk_out[EPT];
+#pragma unroll
+        for (int q = 0; q < EPT; ++q) {
+            // intermediate mass M_k
+            R Mk;
+            if (k == 1) Mk = P::m(C, 0);
+            else Mk = P::fma_(P::u32(y[q][k - 2]) + R(0.5), Ts, P::mu(C, k - 1));
+            // kinetic gap Delta_k = T (r_k - r_{k-1}) from integer differences
+            R gap;
+            if constexpr (N == 2) {
+                gap = Ts * R(4294967296.0);  // T exactly: Ts = T * 2^-32
+            } else if (k == 1) {
+                gap = P::fma_(P::u32(y[q][0]), Ts, Ts_half);
+            } else if (k == N - 1) {
+                gap = P::fma_(P::u32(~y[q][kY - 1]), Ts, Ts_half);
+            } else {
+                gap = P::u32(y[q][k - 1] - y[q][k - 2]) * Ts;
+            }
+            Mk_out[q] = Mk;
+            // two-body momentum
+            const R mk1 = P::m(C, k);
+            const R twoMk = R(2) * Mk;
+            const R lam = gap * (gap + twoMk) * (gap + R(2) * mk1) * (gap + twoMk + R(2) * mk1);
+            const R invM = P::rcp(Mnext[q]);
+            const R p = P::sqrt_(lam) * (R(0.5) * invM);
+            w[q] *= p;
+            // isotropic direction of subsystem k in the rest frame of subsystem k+1
+            const uint32_t xc = blk[q][dc % 4];
+            const uint32_t xp = blk[q][(dc + 1) % 4];
+            const R cos_t = P::fma_(P::i32(static_cast<int32_t>(xc ^ 0x80000000u)), kTwoM31, kTwoM32);
+            const R one_m = P::fma_(P::u32(~xc), kTwoM31, kTwoM32);  // 1 - cos(theta)
+            const R one_p = P::fma_(P::u32(xc), kTwoM31, kTwoM32);   // 1 + cos(theta)
+            const R sin_t = P::sqrt_(one_m * one_p);
+            R sphi, cphi;
+            P::sincos_2pi_u(xp, &sphi, &cphi);  // phi = 2 pi u
+            const R px = p * sin_t * cphi, py = p * sin_t * sphi, pz = p * cos_t;
+            const R Es = P::sqrt_(P::fma_(p, p, Mk * Mk));
+            if (k == N - 1) {
+                // parent at rest: no boost
+                dE[q] = M - Es; dx[q] = -px; dy[q] = -py; dz[q] = -pz;
+                Q0[q] = Es; Qx[q] = px; Qy[q] = py; Qz[q] = pz;
+            } else {
+                const R qp = Qx[q] * px + Qy[q] * py + Qz[q] * pz;
+                const R E1 = (Q0[q] * Es + qp) * invM;
+                const R f = P::div(E1 + Es, Q0[q] + Mnext[q]);
+                const R nx = P::fma_(f, Qx[q], px), ny = P::fma_(f, Qy[q], py), nz = P::fma_(f, Qz[q], pz);
+                dE[q] = Q0[q] - E1; dx[q] = Qx[q] - nx; dy[q] = Qy[q] - ny; dz[q] = Qz[q] - nz;
+                Q0[q] = E1; Qx[q] = nx; Qy[q] = ny; Qz[q] = nz;
+            }
+            Mnext[q] = Mk;
         }
-        Mnext = Mk;
+        sink.subsystem_mass(k, Mk_out);
+        sink.daughter(k, dE, dx, dy, dz);
     }
     sink.daughter(0, Q0, Qx, Qy, Qz);
-    sink.weight(w * P::Cn(C));
+#pragma unroll
+    for (int q = 0; q < EPT; ++q) w[q] = w[q] * P::Cn(C);
+    sink.weight(w);
 }
 
 }  // namespace hydra

@@ -101,3 +101,17 @@ def test_draws_rejects(L):
     assert hp.STATUS[L.hydra_phsp_draws(3, 10, 1, 0, None, 16, None)] == "HYDRA_ERR_INVALID_ARG"
     assert hp.STATUS[L.hydra_phsp_draws(3, 10, 1, 0, ctypes.c_void_p(16), 8, None)] == "HYDRA_ERR_INVALID_ARG"
     assert L.hydra_phsp_draws(3, 0, 1, 0, None, 0, None) == 0
+
+
+def test_launch_config_validation(L):
+    b, e = ctypes.c_int(), ctypes.c_int()
+    assert L.hydra_get_launch_config(0, 3, 0, ctypes.byref(b), ctypes.byref(e)) == 0
+    assert b.value % 32 == 0 and e.value in (1, 2, 4)
+    bad = [(2, 3, 0, 256, 1, "HYDRA_ERR_INVALID_ARG"), (0, 11, 0, 256, 1, "HYDRA_ERR_UNSUPPORTED_N"),
+           (0, 3, 5, 256, 1, "HYDRA_ERR_INVALID_ARG"), (0, 3, 0, 100, 1, "HYDRA_ERR_INVALID_ARG"),
+           (0, 3, 0, 1024, 1, "HYDRA_ERR_INVALID_ARG"), (1, 3, 1, 256, 3, "HYDRA_ERR_INVALID_ARG")]
+    for kind, n, dt, block, ept, status in bad:
+        assert hp.STATUS[L.hydra_set_launch_config(kind, n, dt, block, ept)] == status
+    assert L.hydra_set_launch_config(1, 5, 1, 128, 2) == 0
+    assert L.hydra_get_launch_config(1, 5, 1, ctypes.byref(b), ctypes.byref(e)) == 0
+    assert (b.value, e.value) == (128, 2)

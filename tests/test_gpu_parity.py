@@ -289,3 +289,51 @@ def test_generate_host_matches_device(dtype):
     torch.cuda.synchronize()
     assert torch.equal(hout[:, :, :nev], p[:, :, :nev].cpu())
     assert torch.equal(hw, w.cpu())
+
+
+# ----------------------------------------------------------------------------- launch shapes
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_generate_bit_identical_across_launch_shapes(dtype):
+    """Every (block, events-per-thread) shape writes exactly the same bits (ragged count)."""
+    ref = {}
+    for n in (2, 3, 7, 10):
+        masses = workloads.sweep_masses(n, True)
+        saved = hp.get_launch_config(hp.KERNEL_GENERATE, n, dtype)
+        try:
+            for block in (64, 128, 256, 512):
+                for ept in (1, 2, 4):
+                    hp.set_launch_config(hp.KERNEL_GENERATE, n, dtype, block, ept)
+                    p, w = hp.generate(10.0, masses, 10_007, 5, dtype=dtype, event_offset=3)
+                    if n not in ref:
+                        ref[n] = (p.clone(), w.clone())
+                    assert torch.equal(p[:, :, :10_007], ref[n][0][:, :, :10_007]), (n, block, ept)
+                    assert torch.equal(w, ref[n][1]), (n, block, ept)
+        finally:
+            hp.set_launch_config(hp.KERNEL_GENERATE, n, dtype, *saved)
+
+
+@pytest.mark.parametrize("kin", ["f32", "f64"])
+def test_integrate_bit_identical_across_launch_shapes(kin):
+    d = workloads.D0_DALITZ
+    saved = hp.get_launch_config(hp.KERNEL_INTEGRATE, 3, kin)
+    results = []
+    try:
+        for block in (64, 256, 512):
+            for ept in (1, 2, 4):
+                hp.set_launch_config(hp.KERNEL_INTEGRATE, 3, kin, block, ept)
+                results.append(hp.integrate(d["M"], d["masses"], 3 * 2 ** 21 + 99, d["seed"],
+                                            kin_dtype=kin, me=hp.ME_DALITZ_2BW, params=d["params"]))
+    finally:
+        hp.set_launch_config(hp.KERNEL_INTEGRATE, 3, kin, *saved)
+    assert all(r == results[0] for r in results)
+
+
+def test_autotuner_picks_a_valid_shape():
+    from paper_1711_05683_b300 import autotune
+    saved = hp.get_launch_config(hp.KERNEL_GENERATE, 4, "f32")
+    try:
+        r = autotune.tune_generate(4, "f32", (0.1, 0.2, 0.3, 0.4), nevents=1 << 20, reps=1)
+        assert (r["block"], r["ept"]) == hp.get_launch_config(hp.KERNEL_GENERATE, 4, "f32")
+        assert len(r["table"]) == len(autotune.BLOCKS) * len(autotune.EPTS)
+    finally:
+        hp.set_launch_config(hp.KERNEL_GENERATE, 4, "f32", *saved)
