@@ -24,8 +24,10 @@ def nvcc() -> str:
 
 
 def command(out: str = LIB, extra: list[str] | None = None) -> list[str]:
+    # -fmad=false: no implicit contraction; the kernels write every fused multiply-add out,
+    # so each event's rounding is fixed by the source at every launch shape.
     return [nvcc(), "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo",
-            "-std=c++17", "-Xcompiler", "-fPIC,-O2", "-shared", "-cudart", "shared",
+            "-fmad=false", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "-shared", "-cudart", "shared",
             "-I", INCLUDE, "-Xlinker", "-rpath,/usr/local/cuda/lib64",
             *(extra or []), "-o", out, *SOURCES]
 

@@ -166,12 +166,13 @@ template <typename R>
 __device__ __forceinline__ R dalitz_2bw(const MEConsts& P, R s12, R s23) {
     const R xa = me_param<R>(P.a_m2, P.a_m2f) - s12, ya = me_param<R>(P.a_mg, P.a_mgf);
     const R xb = me_param<R>(P.b_m2, P.b_m2f) - s23, yb = me_param<R>(P.b_mg, P.b_mgf);
-    const R ia = Prec<R>::rcp(xa * xa + ya * ya);
-    const R ib = Prec<R>::rcp(xb * xb + yb * yb);
+    using Q = Prec<R>;
+    const R ia = Q::rcp(Q::fma_(xa, xa, ya * ya));
+    const R ib = Q::rcp(Q::fma_(xb, xb, yb * yb));
     const R cr = me_param<R>(P.c_re, P.c_ref), ci = me_param<R>(P.c_im, P.c_imf);
-    const R re = xa * ia + (cr * xb - ci * yb) * ib;
-    const R im = ya * ia + (cr * yb + ci * xb) * ib;
-    return re * re + im * im;
+    const R re = Q::fma_(xa, ia, Q::fma_(cr, xb, -(ci * yb)) * ib);
+    const R im = Q::fma_(ya, ia, Q::fma_(cr, yb, ci * xb) * ib);
+    return Q::fma_(re, re, im * im);
 }
 
 template <int N, typename R, int ME, int EPT>
@@ -186,7 +187,7 @@ __device__ __forceinline__ void integrand_group(const DecayConsts& C, const MECo
             // s12 = M_2^2 (subsystem of daughters 1, 2); s23 = (P - p1)^2 = M^2 + m1^2 - 2 M E1
             const R M = Prec<R>::M(C);
             const R s12 = s.M2[q] * s.M2[q];
-            const R s23 = M * M + Prec<R>::m2(C, 0) - R(2) * M * s.E1[q];
+            const R s23 = Prec<R>::fma_(R(-2) * M, s.E1[q], Prec<R>::fma_(M, M, Prec<R>::m2(C, 0)));
             f[q] = s.w[q] * dalitz_2bw<R>(P, s12, s23);
         } else {
             f[q] = s.w[q];
@@ -233,9 +234,9 @@ __global__ void __launch_bounds__(512) phsp_integrate_tiles(const __grid_constan
                 for (int q = 0; q < EPT; ++q) {
                     if (valid[q]) {
                         sf += f[q];
-                        sf2 += f[q] * f[q];
+                        sf2 = Prec<R>::fma_(f[q], f[q], sf2);
                         sw += w[q];
-                        sw2 += w[q] * w[q];
+                        sw2 = Prec<R>::fma_(w[q], w[q], sw2);
                     }
                 }
             }

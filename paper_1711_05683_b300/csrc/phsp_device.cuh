@@ -138,13 +138,14 @@ template <> struct Prec<double> {
 
 // ------------------------------------------------------------------------------------
 // A group of EPT Raubold-Lynch events computed in lockstep (EPT independent dependency
-// chains per thread; the arithmetic of each event is the same for every EPT, so results
-// are bit-identical whatever the group size).
+// chains per thread).  The library is compiled with -fmad=false and every fused
+// multiply-add is written out, so the rounding of each event is fixed by this source and
+// results are bit-identical whatever the group size, block size or batch composition.
 //
 // Draws: d = 0..n-3 intermediate masses; for top-down step j = 0..n-2 (j = 0 is the
 // parent's decay) cos(theta) from draw n-2+2j and phi from draw n-1+2j.  Draw d is word
-// d%4 of Philox block d/4; a step's two draws always share one block, which is generated
-// when the step first needs it (live state: the sorted mass draws and one block).
+// d%4 of Philox block d/4; each block is generated when a draw first needs it (live state:
+// the sorted mass draws and one block).
 //
 // With y_1 <= ... <= y_{n-2} the sorted mass draws, r_j = (y_j + 1/2) 2^-32, r_0 = 0,
 // r_{n-1} = 1:  M_1 = m_1, M_k = mu_k + r_{k-1} T, M_n = M, and the kinetic gaps
@@ -202,17 +203,30 @@ __device__ __forceinline__ void raubold_lynch_group(const DecayConsts& C, const 
         Mnext[q] = M;  // M_{k+1}
     }
 
+    int cur = kMassBlocks - 1;  // Philox block held in blk (-1: none); known at compile time
 #pragma unroll
     for (int k = N - 1; k >= 1; --k) {
         const int j = N - 1 - k;
-        const int dc = N - 2 + 2 * j;  // cos(theta) draw; phi is dc + 1 in the same block
-        const bool fresh = (j == 0) ? (kMassBlocks == 0 || dc / 4 != kMassBlocks - 1) : (dc / 4 != (dc - 2) / 4);
-        if (fresh) {
+        const int dc = N - 2 + 2 * j;  // cos(theta) draw; the phi draw dc + 1 may open the next block
+        uint32_t xcs[EPT], xps[EPT];
+        if (dc / 4 != cur) {
 #pragma unroll
             for (int q = 0; q < EPT; ++q)
                 philox4x32_10(static_cast<uint32_t>(ev[q]), static_cast<uint32_t>(ev[q] >> 32), dc / 4, 0u,
                               C.rk0, C.rk1, blk[q]);
+            cur = dc / 4;
         }
+#pragma unroll
+        for (int q = 0; q < EPT; ++q) xcs[q] = blk[q][dc % 4];
+        if ((dc + 1) / 4 != cur) {
+#pragma unroll
+            for (int q = 0; q < EPT; ++q)
+                philox4x32_10(static_cast<uint32_t>(ev[q]), static_cast<uint32_t>(ev[q] >> 32), (dc + 1) / 4,
+                              0u, C.rk0, C.rk1, blk[q]);
+            cur = (dc + 1) / 4;
+        }
+#pragma unroll
+        for (int q = 0; q < EPT; ++q) xps[q] = blk[q][(dc + 1) % 4];
         R dE[EPT], dx[EPT], dy[EPT], dz[EPT], Mk_out[EPT];
 #pragma unroll
         for (int q = 0; q < EPT; ++q) {
@@ -235,28 +249,30 @@ __device__ __forceinline__ void raubold_lynch_group(const DecayConsts& C, const 
             // two-body momentum
             const R mk1 = P::m(C, k);
             const R twoMk = R(2) * Mk;
-            const R lam = gap * (gap + twoMk) * (gap + R(2) * mk1) * (gap + twoMk + R(2) * mk1);
+            const R twom = R(2) * mk1;
+            const R lam = ((gap * (gap + twoMk)) * (gap + twom)) * ((gap + twoMk) + twom);
             const R invM = P::rcp(Mnext[q]);
             const R p = P::sqrt_(lam) * (R(0.5) * invM);
             w[q] *= p;
             // isotropic direction of subsystem k in the rest frame of subsystem k+1
-            const uint32_t xc = blk[q][dc % 4];
-            const uint32_t xp = blk[q][(dc + 1) % 4];
+            const uint32_t xc = xcs[q];
+            const uint32_t xp = xps[q];
             const R cos_t = P::fma_(P::i32(static_cast<int32_t>(xc ^ 0x80000000u)), kTwoM31, kTwoM32);
             const R one_m = P::fma_(P::u32(~xc), kTwoM31, kTwoM32);  // 1 - cos(theta)
             const R one_p = P::fma_(P::u32(xc), kTwoM31, kTwoM32);   // 1 + cos(theta)
             const R sin_t = P::sqrt_(one_m * one_p);
             R sphi, cphi;
             P::sincos_2pi_u(xp, &sphi, &cphi);  // phi = 2 pi u
-            const R px = p * sin_t * cphi, py = p * sin_t * sphi, pz = p * cos_t;
+            const R ps = p * sin_t;
+            const R px = ps * cphi, py = ps * sphi, pz = p * cos_t;
             const R Es = P::sqrt_(P::fma_(p, p, Mk * Mk));
             if (k == N - 1) {
                 // parent at rest: no boost
                 dE[q] = M - Es; dx[q] = -px; dy[q] = -py; dz[q] = -pz;
                 Q0[q] = Es; Qx[q] = px; Qy[q] = py; Qz[q] = pz;
             } else {
-                const R qp = Qx[q] * px + Qy[q] * py + Qz[q] * pz;
-                const R E1 = (Q0[q] * Es + qp) * invM;
+                const R qp = P::fma_(Qz[q], pz, P::fma_(Qy[q], py, Qx[q] * px));
+                const R E1 = P::fma_(Q0[q], Es, qp) * invM;
                 const R f = P::div(E1 + Es, Q0[q] + Mnext[q]);
                 const R nx = P::fma_(f, Qx[q], px), ny = P::fma_(f, Qy[q], py), nz = P::fma_(f, Qz[q], pz);
                 dE[q] = Q0[q] - E1; dx[q] = Qx[q] - nx; dy[q] = Qy[q] - ny; dz[q] = Qz[q] - nz;
