@@ -317,12 +317,141 @@ def run_ours(args) -> None:
                           "generate": {k: f"{v['block']}x{v['ept']}" for k, v in tuning["generate"].items()},
                           "integrate": {k: f"{v['block']}x{v['ept']}" for k, v in tuning["integrate"].items()}},
     }
+    if not args.no_batch:
+        line["batch"] = run_batch_workload()
+    if not args.no_serve:
+        line["serve"] = run_serve_workload(duration_s=args.serve_seconds)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds, nev, int_events)
         line["cpu_baseline"]["value_ratio_note"] = "oracle, single thread, FP64; not a tuning target"
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------- batched requests
+ARENA_BYTES = 40 * 10 ** 9  # HBM budget for the outputs of one wave
+
+
+def batch_waves(reqs, arena_bytes=ARENA_BYTES):
+    """Greedy waves of consecutive requests whose FP32 outputs fit the arena; returns
+    (wave list of (request, byte offset, ld)) ."""
+    waves, cur, off = [], [], 0
+    for r in reqs:
+        ld = (r.nevents + 3) // 4 * 4
+        nbytes = (4 * len(r.masses) + 1) * ld * 4
+        if cur and off + nbytes > arena_bytes:
+            waves.append(cur)
+            cur, off = [], 0
+        cur.append((r, off, ld))
+        off += (nbytes + 255) // 256 * 256
+    if cur:
+        waves.append(cur)
+    return waves
+
+
+def run_batch_workload(count: int = 4096, reps: int = 2) -> dict:
+    """Uneven generate requests (N 2..8, M 1..10 GeV, masses U[0, M/2N], events log-uniform
+    1e3..1e7, per-request seeds): one persistent batch launch (graph) per wave against one
+    plain launch per request, same waves, same 40 GB output arena (overwritten per wave)."""
+    import numpy as np
+    import torch
+    import paper_1711_05683_b300 as hp
+    reqs = workloads.batch_requests(count)
+    waves = batch_waves(reqs)
+    arena = torch.empty(ARENA_BYTES // 4, dtype=torch.float32, device="cuda")
+    base = arena.data_ptr()
+    tables = []
+    for wave in waves:
+        t = np.zeros(len(wave), dtype=hp.request_dtype())
+        for i, (r, off, ld) in enumerate(wave):
+            n = len(r.masses)
+            rec = t[i]
+            rec["kind"], rec["n"], rec["dtype"], rec["M"] = hp.REQ_GENERATE, n, hp.F32, r.M
+            rec["masses"][:n] = r.masses
+            rec["seed"], rec["count"], rec["ld"] = r.seed, r.nevents, ld
+            rec["out"] = base + off
+            rec["weights"] = base + off + 4 * n * ld * 4
+        tables.append(t)
+    batch = hp.Batch(max(len(w) for w in waves))
+    stream = torch.cuda.current_stream()
+    L = hp.lib()
+    import ctypes
+    sh = ctypes.c_void_p(stream.cuda_stream)
+    plain_args = []
+    for wave in waves:
+        for r, off, ld in wave:
+            n = len(r.masses)
+            plain_args.append((r.M, n, (ctypes.c_double * n)(*r.masses), r.nevents, r.seed,
+                               ctypes.c_void_p(base + off), ld, ctypes.c_void_p(base + off + 4 * n * ld * 4)))
+
+    def batched(use_graph=True):
+        for t in tables:
+            batch.run(t, use_graph=use_graph, stream=stream)
+
+    def plain():
+        for M, n, m, nev, seed, out, ld, w in plain_args:
+            rc = L.hydra_phsp_generate(M, n, m, nev, seed, 0, 0, out, ld, w, sh)
+            if rc:
+                raise hp.HydraError(rc, L.hydra_last_error().decode())
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        best_dev, best_wall = float("inf"), float("inf")
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            best_wall = min(best_wall, time.perf_counter() - t0)
+            best_dev = min(best_dev, a.elapsed_time(b) / 1e3)
+        return best_dev, best_wall
+
+    total = sum(r.nevents for r in reqs)
+    out_bytes = sum((4 * len(r.masses) + 1) * r.nevents * 4 for r in reqs)
+    bd, bw = timed(batched)
+    gd, gw = timed(lambda: batched(False))
+    pd, pw = timed(plain)
+    batch.close()
+    del arena
+    torch.cuda.empty_cache()
+    return {"requests": count, "events": total, "output_bytes": out_bytes, "waves": len(waves),
+            "arena_bytes": ARENA_BYTES,
+            "batched_graph": {"events_per_s": total / bw, "s": bw, "device_s": bd,
+                              "hbm_gbs": out_bytes / bw / 1e9},
+            "batched_no_graph": {"events_per_s": total / gw, "s": gw, "device_s": gd},
+            "plain_launches": {"events_per_s": total / pw, "s": pw, "device_s": pd,
+                               "hbm_gbs": out_bytes / pw / 1e9},
+            "speedup_vs_plain": pw / bw}
+
+
+# ----------------------------------------------------------------------------- serving loop
+def run_serve_workload(duration_s: float = 30.0, rate_hz: float = 2000.0) -> dict:
+    """Poisson stream (mean rate_hz) of generate (N 2..8, 1e3..1e6 events, float32 out to
+    pinned host memory) and Dalitz integrate (1e5..1e8 events) requests, 50/50, served by
+    the continuous-batching server and by one-at-a-time plain calls; p50/p99 latency from
+    arrival to result in host memory, and events/s."""
+    import torch
+    from paper_1711_05683_b300 import serve
+    reqs = workloads.serve_stream(rate_hz=rate_hz, duration_s=duration_s)
+    warm = workloads.serve_stream(rate_hz=rate_hz, duration_s=0.5, rng_seed=1)
+    srv = serve.Server()
+    srv.run(warm)
+    res_b = srv.run(reqs)
+    srv.close()
+    torch.cuda.synchronize()
+    plain = serve.PlainServer()
+    plain.run(warm)
+    res_p = plain.run(reqs, max_wall=duration_s * 3)
+    for r in (res_b, res_p):
+        r.pop("done", None)
+    return {"requests": len(reqs), "duration_s": duration_s, "rate_hz": rate_hz,
+            "offered_events": sum(r.nevents for r in reqs), "batched": res_b, "plain": res_p,
+            "p99_ratio_plain_over_batched": res_p["p99_ms"] / res_b["p99_ms"] if res_b["p99_ms"] else None}
 
 
 # ----------------------------------------------------------------------------- CPU oracle arm
@@ -401,10 +530,30 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "batch", "serve"])
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch":
+        import torch
+        import paper_1711_05683_b300 as hp
+        from paper_1711_05683_b300 import build as hp_build
+        hp_build.build()
+        torch.cuda.set_device(0)
+        hp.lib()
+        print(json.dumps({"workload": "batch", **run_batch_workload()}), flush=True)
+    elif args.workload == "serve":
+        import torch
+        import paper_1711_05683_b300 as hp
+        from paper_1711_05683_b300 import build as hp_build
+        hp_build.build()
+        torch.cuda.set_device(0)
+        hp.lib()
+        print(json.dumps({"workload": "serve", **run_serve_workload(duration_s=args.serve_seconds)}), flush=True)
     else:
         run_ours(args)
 

@@ -209,6 +209,78 @@ hydra_status hydra_set_launch_config(hydra_kernel_kind kind, int n, hydra_dtype 
 hydra_status hydra_get_launch_config(hydra_kernel_kind kind, int n, hydra_dtype dtype, int *block,
                                      int *events_per_thread);
 
+/* ------------------------------------------------------------------------------------
+ * Batches: many uneven requests in one persistent launch (CUDA-graph replay).
+ *
+ * A batch is a list of request slices.  The persistent kernel's warps take tiles of 2048
+ * events from all slices in turn (an atomic tile counter), so thousands of small and large
+ * requests with different n, masses and event counts keep every SM busy in one launch.
+ * Each slice gives exactly the events (and, for integrals, exactly the bits) that the
+ * single-request entry points give for the same arguments.
+ * ------------------------------------------------------------------------------------ */
+typedef enum hydra_request_kind {
+    HYDRA_REQ_GENERATE = 0,
+    HYDRA_REQ_INTEGRATE = 1
+} hydra_request_kind;
+
+typedef struct hydra_request {
+    int32_t kind;           /* hydra_request_kind */
+    int32_t n;              /* daughters, 2..10 */
+    int32_t dtype;          /* hydra_dtype; all slices of one batch run share it */
+    int32_t me;             /* integrate: hydra_me_id */
+    double M;               /* parent mass */
+    double masses[10];      /* daughter masses (first n used) */
+    double params[6];       /* integrate: matrix-element parameters */
+    uint64_t seed;          /* Philox key */
+    uint64_t event_offset;  /* counter-event index of the request's event 0 */
+    uint64_t first;         /* first event of this slice within the request */
+    uint64_t count;         /* events in this slice (> 0) */
+    /* generate: device buffers of this slice: event first + j of the request goes to
+     * out[(i*4 + c)*ld + j] and weights[j]; 16-byte aligned, ld % 4 == 0, ld >= count. */
+    void *out;
+    uint64_t ld;
+    void *weights;
+    /* integrate: total events of the request; the slice must start on a multiple of 2^21
+     * events and, unless it ends the request, hold a multiple of 2^21 events.  seg_partials
+     * is a device array of 8 doubles per 2^21-event segment of the whole request, owned by
+     * the caller and kept between the slices of one request.  When a slice ends the request
+     * (first + count == total) its result is available from hydra_batch_result. */
+    uint64_t total;
+    double *seg_partials;
+} hydra_request;
+
+typedef struct hydra_batch hydra_batch; /* opaque; bound to the device current at creation */
+
+/*
+ * Create a batch runner for up to max_requests slices per run and up to max_integrate_tiles
+ * tiles (2048 events each) of integral slices per run.  Allocates its device and pinned host
+ * buffers and captures the CUDA graph of a run (tile-counter reset, persistent batch kernel,
+ * segment reduction, finalization).  Errors: INVALID_ARG, OOM, CUDA.
+ */
+hydra_status hydra_batch_create(int max_requests, uint64_t max_integrate_tiles, hydra_batch **out);
+
+/*
+ * Enqueue one run of nreq slices on `stream` (asynchronous): one host-to-device copy of
+ * the slice table, one graph launch (use_graph != 0) or the same kernels launched one by
+ * one, and one device-to-host copy of the results of the integral slices.  A run may be
+ * issued while the previous run of the same batch is still executing; the call waits for
+ * that run's slice table to be consumed before reusing its staging memory.
+ * Errors: INVALID_ARG (validation of every slice, capacity), UNSUPPORTED_N,
+ * BELOW_THRESHOLD, MISALIGNED, CUDA.
+ */
+hydra_status hydra_batch_run(hydra_batch *batch, const hydra_request *reqs, int nreq, int use_graph,
+                             hydra_stream_t stream);
+
+/*
+ * Result of slice i of the latest run (an integral slice that ended its request).  Blocks
+ * until that run has finished.  Errors: INVALID_ARG (index, kind, or a slice that did not
+ * end its request), CUDA.
+ */
+hydra_status hydra_batch_result(hydra_batch *batch, int i, hydra_integral *result);
+
+/* Wait for the latest run and release the batch runner. */
+hydra_status hydra_batch_destroy(hydra_batch *batch);
+
 /* Release the per-device scratch memory of the library (all devices).  Not thread safe
  * with respect to calls in flight. */
 hydra_status hydra_shutdown(void);

@@ -74,10 +74,15 @@ def lib() -> ctypes.CDLL:
         L.hydra_phsp_generate_host.argtypes = [d, i, dp, u64, u64, u64, i, vp, u64, vp, vp]
         L.hydra_phsp_integrate_noalloc.argtypes = L.hydra_phsp_integrate.argtypes
         L.hydra_set_launch_config.argtypes = [i, i, i, i, i]
+        L.hydra_batch_create.argtypes = [i, u64, ctypes.POINTER(vp)]
+        L.hydra_batch_run.argtypes = [vp, vp, i, i, vp]
+        L.hydra_batch_result.argtypes = [vp, i, ctypes.POINTER(Integral)]
+        L.hydra_batch_destroy.argtypes = [vp]
         L.hydra_get_launch_config.argtypes = [i, i, i, ctypes.POINTER(i), ctypes.POINTER(i)]
         for name in ("hydra_phsp_volume_factor", "hydra_phsp_generate", "hydra_phsp_integrate",
                      "hydra_phsp_draws", "hydra_phsp_generate_host", "hydra_phsp_integrate_noalloc",
-                     "hydra_set_launch_config", "hydra_get_launch_config", "hydra_shutdown"):
+                     "hydra_set_launch_config", "hydra_get_launch_config", "hydra_batch_create",
+                     "hydra_batch_run", "hydra_batch_result", "hydra_batch_destroy", "hydra_shutdown"):
             getattr(L, name).restype = i
         _lib = L
     return _lib
@@ -203,6 +208,60 @@ def get_launch_config(kind: int, n: int, dtype) -> tuple[int, int]:
     _check(lib().hydra_get_launch_config(int(kind), int(n), _dtype_code(dtype), ctypes.byref(b),
                                          ctypes.byref(e)))
     return b.value, e.value
+
+
+# ----------------------------------------------------------------------------- batches
+REQ_GENERATE, REQ_INTEGRATE = 0, 1
+SEGMENT_EVENTS = 1 << 21  # integral slices start on (and, unless last, hold) multiples of this
+
+
+def request_dtype():
+    """numpy record type with the layout of the C struct hydra_request (224 bytes)."""
+    import numpy as np
+    dt = np.dtype([("kind", "<i4"), ("n", "<i4"), ("dtype", "<i4"), ("me", "<i4"), ("M", "<f8"),
+                   ("masses", "<f8", (10,)), ("params", "<f8", (6,)), ("seed", "<u8"),
+                   ("event_offset", "<u8"), ("first", "<u8"), ("count", "<u8"), ("out", "<u8"),
+                   ("ld", "<u8"), ("weights", "<u8"), ("total", "<u8"), ("seg_partials", "<u8")],
+                  align=True)
+    assert dt.itemsize == 224
+    return dt
+
+
+def segments(total: int) -> int:
+    """Segments of 2^21 events in an integral request (size of its seg_partials / 8)."""
+    return (int(total) + SEGMENT_EVENTS - 1) // SEGMENT_EVENTS
+
+
+class Batch:
+    """Runner for many uneven request slices in one persistent launch (hydra_batch_*)."""
+
+    def __init__(self, max_requests: int = 4096, max_integrate_tiles: int = 1 << 20):
+        h = ctypes.c_void_p()
+        _check(lib().hydra_batch_create(int(max_requests), int(max_integrate_tiles), ctypes.byref(h)))
+        self._h = h
+        self.max_requests = max_requests
+
+    def run(self, table, nreq: int | None = None, *, use_graph: bool = True, stream=None) -> None:
+        """Enqueue a run of the first nreq records of `table` (a request_dtype() array)."""
+        n = len(table) if nreq is None else int(nreq)
+        _check(lib().hydra_batch_run(self._h, ctypes.c_void_p(table.ctypes.data), n, int(use_graph),
+                                     _stream_handle(stream)))
+
+    def result(self, i: int) -> dict:
+        res = Integral()
+        _check(lib().hydra_batch_result(self._h, int(i), ctypes.byref(res)))
+        return res.as_dict()
+
+    def close(self) -> None:
+        if self._h:
+            lib().hydra_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def shutdown() -> None:

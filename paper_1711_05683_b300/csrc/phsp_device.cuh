@@ -289,4 +289,40 @@ __device__ __forceinline__ void raubold_lynch_group(const DecayConsts& C, const 
     sink.weight(w);
 }
 
+// ------------------------------------------------------------------------------------
+// Generation sink: structure-of-arrays stores out[(i*4 + c)*ld + e], weights[e].
+// ------------------------------------------------------------------------------------
+// Store EPT consecutive values (16-byte vectors where the group allows it).
+template <typename R, int EPT>
+__device__ __forceinline__ void store_group(R* __restrict__ p, const R (&v)[EPT]) {
+    if constexpr (EPT == 1) {
+        p[0] = v[0];
+    } else if constexpr (sizeof(R) == 4 && EPT == 2) {
+        *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
+    } else if constexpr (sizeof(R) == 4 && EPT == 4) {
+        *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    } else {
+        static_assert(sizeof(R) == 8 && EPT % 2 == 0, "double groups are pairs");
+#pragma unroll
+        for (int q = 0; q < EPT; q += 2) *reinterpret_cast<double2*>(p + q) = make_double2(v[q], v[q + 1]);
+    }
+}
+
+template <typename R, int EPT>
+struct StoreSink {
+    R* __restrict__ base;  // out + e0
+    R* __restrict__ wout;  // weights + e0
+    uint64_t ld;
+    __device__ __forceinline__ void subsystem_mass(int, const R (&)[EPT]) {}
+    __device__ __forceinline__ void daughter(int i, const R (&E)[EPT], const R (&px)[EPT],
+                                             const R (&py)[EPT], const R (&pz)[EPT]) {
+        R* p = base + static_cast<uint64_t>(4 * i) * ld;
+        store_group<R, EPT>(p, E);
+        store_group<R, EPT>(p + ld, px);
+        store_group<R, EPT>(p + 2 * ld, py);
+        store_group<R, EPT>(p + 3 * ld, pz);
+    }
+    __device__ __forceinline__ void weight(const R (&w)[EPT]) { store_group<R, EPT>(wout, w); }
+};
+
 }  // namespace hydra

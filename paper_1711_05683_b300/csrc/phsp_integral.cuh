@@ -1,0 +1,234 @@
+// phsp_integral.cuh -- device side of the phase-space integral (section 3, "phase-space
+// Monte Carlo integration"): the integrand f = w |ME|^2 over Raubold-Lynch events, the
+// fixed-order tile sums, and the compensated FP64 accumulators of the reduction tree.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "hydra_phsp.h"
+#include "phsp_device.cuh"
+
+namespace hydra {
+
+// ------------------------------------------------------------------------------------
+// Fixed reduction geometry of the integral (part of the result's definition).
+// ------------------------------------------------------------------------------------
+constexpr int kTileEvents = 2048;                         // events per warp tile
+constexpr int kGroupEvents = 8;                           // events a lane sums in R before FP64
+constexpr int kLaneIters = kTileEvents / 32;              // 64 events per lane per tile
+constexpr int kSegTiles = 1024;                           // tiles per segment (2^21 events)
+constexpr uint64_t kChunkTiles = 32768;                   // tiles per launch (2^26 events)
+static_assert(kChunkTiles % kSegTiles == 0, "a chunk holds whole segments");
+static_assert(kLaneIters % kGroupEvents == 0, "groups tile the lane's events");
+
+struct TileSums {
+    double f, f2, w, w2;
+};
+
+// Matrix-element parameters in both precisions.
+struct MEConsts {
+    double a_m2, a_mg, b_m2, b_mg, c_re, c_im;  // m0^2, m0*Gamma, Re c, Im c
+    float a_m2f, a_mgf, b_m2f, b_mgf, c_ref, c_imf;
+};
+
+template <typename R, int EPT>
+struct IntegrandSink {
+    R E1[EPT], M2[EPT], w[EPT];
+    __device__ __forceinline__ void subsystem_mass(int k, const R (&Mk)[EPT]) {
+        if (k == 2) {
+#pragma unroll
+            for (int q = 0; q < EPT; ++q) M2[q] = Mk[q];
+        }
+    }
+    __device__ __forceinline__ void daughter(int i, const R (&E)[EPT], const R (&)[EPT],
+                                             const R (&)[EPT], const R (&)[EPT]) {
+        if (i == 0) {
+#pragma unroll
+            for (int q = 0; q < EPT; ++q) E1[q] = E[q];
+        }
+    }
+    __device__ __forceinline__ void weight(const R (&wv)[EPT]) {
+#pragma unroll
+        for (int q = 0; q < EPT; ++q) w[q] = wv[q];
+    }
+};
+
+template <typename R> __device__ __forceinline__ R me_param(double d, float f);
+template <> __device__ __forceinline__ float me_param<float>(double, float f) { return f; }
+template <> __device__ __forceinline__ double me_param<double>(double d, float) { return d; }
+
+// |BW(s12; a) + c BW(s23; b)|^2, BW(s) = (m0^2 - s + i m0 G) / ((m0^2 - s)^2 + (m0 G)^2).
+template <typename R>
+__device__ __forceinline__ R dalitz_2bw(const MEConsts& P, R s12, R s23) {
+    const R xa = me_param<R>(P.a_m2, P.a_m2f) - s12, ya = me_param<R>(P.a_mg, P.a_mgf);
+    const R xb = me_param<R>(P.b_m2, P.b_m2f) - s23, yb = me_param<R>(P.b_mg, P.b_mgf);
+    using Q = Prec<R>;
+    const R ia = Q::rcp(Q::fma_(xa, xa, ya * ya));
+    const R ib = Q::rcp(Q::fma_(xb, xb, yb * yb));
+    const R cr = me_param<R>(P.c_re, P.c_ref), ci = me_param<R>(P.c_im, P.c_imf);
+    const R re = Q::fma_(xa, ia, Q::fma_(cr, xb, -(ci * yb)) * ib);
+    const R im = Q::fma_(ya, ia, Q::fma_(cr, yb, ci * xb) * ib);
+    return Q::fma_(re, re, im * im);
+}
+
+template <int N, typename R, int ME, int EPT>
+__device__ __forceinline__ void integrand_group(const DecayConsts& C, const MEConsts& P,
+                                                const uint64_t (&ev)[EPT], R (&f)[EPT], R (&w)[EPT]) {
+    IntegrandSink<R, EPT> s;
+    raubold_lynch_group<N, R, EPT>(C, ev, s);
+#pragma unroll
+    for (int q = 0; q < EPT; ++q) {
+        w[q] = s.w[q];
+        if constexpr (ME == HYDRA_ME_DALITZ_2BW) {
+            // s12 = M_2^2 (subsystem of daughters 1, 2); s23 = (P - p1)^2 = M^2 + m1^2 - 2 M E1
+            const R M = Prec<R>::M(C);
+            const R s12 = s.M2[q] * s.M2[q];
+            const R s23 = Prec<R>::fma_(R(-2) * M, s.E1[q], Prec<R>::fma_(M, M, Prec<R>::m2(C, 0)));
+            f[q] = s.w[q] * dalitz_2bw<R>(P, s12, s23);
+        } else {
+            f[q] = s.w[q];
+        }
+    }
+}
+
+
+// One warp per tile of kTileEvents events.  Lane l takes events tile*2048 + 32*i + l,
+// i = 0..63, sums them in R in groups of 8 (fixed order), folds each group into FP64, and
+// the warp combines lanes by a fixed xor butterfly; lane 0's total is the tile partial.
+// Sums of (f, f^2, w, w^2) over tile `tile` (events tile*2048 .. tile*2048+2047 of a
+// request; events >= nevents are skipped).  Lane l takes events 32 i + l, i = 0..63, sums
+// them in R in groups of 8 (fixed order), folds each group into FP64, and the warp combines
+// lanes by a fixed xor butterfly; lane 0's value is the tile partial.  Every integral entry
+// point uses this routine, so a request gives the same bits alone or in a batch.
+template <int N, typename R, int ME, int EPT>
+__device__ __forceinline__ TileSums tile_sums(const DecayConsts& C, const MEConsts& P, uint64_t nevents,
+                                              uint64_t event_offset, uint64_t tile, int lane) {
+    static_assert(kGroupEvents % EPT == 0, "a group holds whole event groups");
+    const uint64_t base = tile * kTileEvents;
+    double af = 0.0, af2 = 0.0, aw = 0.0, aw2 = 0.0;
+#pragma unroll 1
+    for (int g = 0; g < kLaneIters / kGroupEvents; ++g) {
+        R sf = R(0), sf2 = R(0), sw = R(0), sw2 = R(0);
+#pragma unroll 1
+        for (int i0 = 0; i0 < kGroupEvents; i0 += EPT) {
+            uint64_t ev[EPT];
+            bool valid[EPT];
+#pragma unroll
+            for (int q = 0; q < EPT; ++q) {
+                const uint64_t e = base + static_cast<uint64_t>(32 * (g * kGroupEvents + i0 + q) + lane);
+                valid[q] = e < nevents;
+                ev[q] = event_offset + e;
+            }
+            R f[EPT], w[EPT];
+            integrand_group<N, R, ME, EPT>(C, P, ev, f, w);
+#pragma unroll
+            for (int q = 0; q < EPT; ++q) {
+                if (valid[q]) {
+                    sf += f[q];
+                    sf2 = Prec<R>::fma_(f[q], f[q], sf2);
+                    sw += w[q];
+                    sw2 = Prec<R>::fma_(w[q], w[q], sw2);
+                }
+            }
+        }
+        af += static_cast<double>(sf);
+        af2 += static_cast<double>(sf2);
+        aw += static_cast<double>(sw);
+        aw2 += static_cast<double>(sw2);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        af += __shfl_xor_sync(0xffffffffu, af, off);
+        af2 += __shfl_xor_sync(0xffffffffu, af2, off);
+        aw += __shfl_xor_sync(0xffffffffu, aw, off);
+        aw2 += __shfl_xor_sync(0xffffffffu, aw2, off);
+    }
+    return TileSums{af, af2, aw, aw2};
+}
+
+// Compensated FP64 accumulator (Neumaier's variant of Kahan summation).
+struct Comp {
+    double s = 0.0, c = 0.0;
+    __device__ __forceinline__ void add(double x) {
+        const double t = s + x;
+        if (fabs(s) >= fabs(x)) c += (s - t) + x;
+        else c += (x - t) + s;
+        s = t;
+    }
+    // Combine with another accumulator: TwoSum of the leading parts, compensations added.
+    __device__ __forceinline__ void merge(double s2, double c2) {
+        const double t = s + s2;
+        const double bb = t - s;
+        const double err = (s - (t - bb)) + (s2 - bb);
+        s = t;
+        c = c + c2 + err;
+    }
+};
+
+__device__ __forceinline__ void warp_merge(Comp& a) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const double s2 = __shfl_xor_sync(0xffffffffu, a.s, off);
+        const double c2 = __shfl_xor_sync(0xffffffffu, a.c, off);
+        a.merge(s2, c2);
+    }
+}
+
+// Compensated sums of nt (<= kSegTiles) consecutive tile partials: lane l takes tiles
+// l, l+32, ... in order, then a fixed TwoSum butterfly; lane 0 writes 8 doubles (s, c) for
+// f, f^2, w, w^2 to out.
+__device__ __forceinline__ void segment_sums(const TileSums* __restrict__ partials, uint64_t nt, int lane,
+                                             double* __restrict__ out) {
+    Comp f, f2, w, w2;
+    for (int j = 0; j < kSegTiles / 32; ++j) {
+        const uint64_t t = static_cast<uint64_t>(j * 32 + lane);
+        if (t < nt) {
+            const TileSums p = partials[t];
+            f.add(p.f);
+            f2.add(p.f2);
+            w.add(p.w);
+            w2.add(p.w2);
+        }
+    }
+    warp_merge(f);
+    warp_merge(f2);
+    warp_merge(w);
+    warp_merge(w2);
+    if (lane == 0) {
+        out[0] = f.s; out[1] = f.c; out[2] = f2.s; out[3] = f2.c;
+        out[4] = w.s; out[5] = w.c; out[6] = w2.s; out[7] = w2.c;
+    }
+}
+
+// One warp folds nseg segment partials (lane l: segments l, l+32, ...), merges lanes and
+// lane 0 writes mean, variance of the mean and the sums.
+__device__ __forceinline__ void fold_segments(const double* __restrict__ seg, uint64_t nseg, uint64_t nevents,
+                                              int lane, hydra_integral* __restrict__ out) {
+    Comp q[4];
+    for (uint64_t s = lane; s < nseg; s += 32) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            q[k].add(seg[s * 8 + 2 * k]);
+            q[k].add(seg[s * 8 + 2 * k + 1]);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) warp_merge(q[k]);
+    if (lane == 0) {
+        const double n = static_cast<double>(nevents);
+        const double sf = q[0].s + q[0].c, sf2 = q[1].s + q[1].c;
+        const double sw = q[2].s + q[2].c, sw2 = q[3].s + q[3].c;
+        const double mean = sf / n;
+        const double var = nevents > 1 ? (sf2 / n - mean * mean) / (n - 1.0) : 0.0;
+        out->mean = mean;
+        out->var_mean = var;
+        out->sum_f = sf;
+        out->sum_f2 = sf2;
+        out->sum_w = sw;
+        out->sum_w2 = sw2;
+        out->n = nevents;
+    }
+}
+
+}  // namespace hydra

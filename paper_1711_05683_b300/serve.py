@@ -1,0 +1,277 @@
+"""Continuous-batching server for phase-space requests (generate and integrate).
+
+Requests arrive over time.  Each tick the server admits arrived requests while their
+device memory fits the HBM budget, then packs one slice of every active request into one
+batch run (hydra_batch_run: one persistent launch, replayed CUDA graph):
+  * a generate request is one slice (its whole event count); its events land in a device
+    staging buffer and are copied to pinned host memory right after the run;
+  * an integrate request advances by up to `int_slice_segments` segments of 2^21 events per
+    tick; its running state is device resident: the next counter-event index (the Philox
+    counter, kept on the host as an integer) and its compensated segment partial sums
+    (a caller-owned device array the batch kernels update in place).  A long integral
+    therefore shares the GPU with requests that arrive while it runs.
+Two batch runners alternate so that tick i+1 is packed and enqueued while tick i runs.  A
+request completes when the host observes the event recorded after its last slice (and, for
+generation, after its copy to host memory); latency = completion time - arrival time.
+
+Every slice computes exactly the events of the single-request entry points, so a request's
+result is the same alone and in the mix (tests check this bit for bit).
+
+`PlainServer` is the comparison: one request at a time in arrival order with the
+single-request entry points (generate + copy to host, or integrate).
+"""
+from __future__ import annotations
+
+import dataclasses
+import time
+from collections import deque
+
+import numpy as np
+
+import paper_1711_05683_b300 as hp
+
+
+@dataclasses.dataclass
+class _Active:
+    rid: int
+    req: object                     # workloads.Request
+    arrival: float                  # absolute wall time
+    next_first: int = 0             # next event index (the request's RNG counter)
+    nbytes: int = 0
+    dev_out: object = None          # generate: device staging [n, 4, ld]
+    dev_w: object = None
+    host_out: object = None         # generate: pinned host copy
+    host_w: object = None
+    seg: object = None              # integrate: device segment partials
+    result: dict | None = None
+    done_tick: int = -1
+
+
+class PinnedRing:
+    """Pinned host memory handed out in arrival order (a ring); blocks are released when
+    their request is harvested."""
+
+    def __init__(self, nbytes: int):
+        import torch
+        self.buf = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+        self.size = nbytes
+        self.head = 0
+        self.live = deque()  # (start, end) in allocation order
+
+    def alloc(self, nbytes: int):
+        nbytes = (nbytes + 255) // 256 * 256
+        if nbytes > self.size:
+            return None
+        start = self.head if self.head + nbytes <= self.size else 0
+        end = start + nbytes
+        for s, e in self.live:
+            if s < end and start < e:
+                return None
+        self.head = end
+        self.live.append((start, end))
+        return start
+
+    def free(self, start: int):
+        for i, (s, _e) in enumerate(self.live):
+            if s == start:
+                del self.live[i]
+                return
+
+
+class Server:
+    def __init__(self, budget_bytes: int = 40 * 10 ** 9, max_slices: int = 4096,
+                 int_slice_segments: int = 8, pinned_bytes: int = 4 << 30,
+                 keep_outputs: bool = False, use_graph: bool = True):
+        import torch
+        self.torch = torch
+        self.budget = budget_bytes
+        self.used = 0
+        self.int_slice = int_slice_segments * hp.SEGMENT_EVENTS
+        self.runners = [hp.Batch(max_slices, max_integrate_tiles=max_slices * int_slice_segments * 1024),
+                        hp.Batch(max_slices, max_integrate_tiles=max_slices * int_slice_segments * 1024)]
+        self.table = np.zeros(max_slices, dtype=hp.request_dtype())
+        self.max_slices = max_slices
+        self.ring = PinnedRing(pinned_bytes)
+        self.keep_outputs = keep_outputs
+        self.use_graph = use_graph
+        self.stream = torch.cuda.current_stream()
+
+    # ------------------------------------------------------------------ state per request
+    def _admit(self, a: _Active) -> bool:
+        torch = self.torch
+        r = a.req
+        n = len(r.masses)
+        if r.kind == "generate":
+            ld = hp.padded_ld(r.nevents)
+            nbytes = (4 * n + 1) * ld * 4
+            if self.used + nbytes > self.budget:
+                return False
+            host = self.ring.alloc(nbytes)
+            if host is None:
+                return False
+            a.ring_start = host
+            hb = self.ring.buf[host: host + (4 * n + 1) * ld * 4].view(torch.float32)
+            a.host_out = hb[: 4 * n * ld].view(n, 4, ld)
+            a.host_w = hb[4 * n * ld:]
+            a.dev_out = torch.empty((n, 4, ld), dtype=torch.float32, device="cuda")
+            a.dev_w = torch.empty(ld, dtype=torch.float32, device="cuda")
+        else:
+            nbytes = 64 * hp.segments(r.nevents)
+            if self.used + nbytes > self.budget:
+                return False
+            a.seg = torch.empty(8 * hp.segments(r.nevents), dtype=torch.float64, device="cuda")
+        a.nbytes = nbytes
+        self.used += nbytes
+        return True
+
+    def _release(self, a: _Active):
+        self.used -= a.nbytes
+        if a.req.kind == "generate":
+            if not self.keep_outputs:
+                self.ring.free(a.ring_start)
+                a.host_out = a.host_w = None
+            a.dev_out = a.dev_w = None
+        else:
+            a.seg = None
+
+    def _fill(self, rec, a: _Active, count: int):
+        r = a.req
+        n = len(r.masses)
+        rec["n"], rec["dtype"], rec["M"] = n, hp.F32, r.M
+        rec["masses"][:n] = r.masses
+        rec["seed"], rec["event_offset"] = r.seed, 0
+        rec["first"], rec["count"] = a.next_first, count
+        if r.kind == "generate":
+            rec["kind"] = hp.REQ_GENERATE
+            rec["out"], rec["ld"], rec["weights"] = a.dev_out.data_ptr(), a.dev_out.shape[-1], a.dev_w.data_ptr()
+        else:
+            rec["kind"], rec["me"] = hp.REQ_INTEGRATE, r.me
+            rec["params"][: len(r.params)] = r.params
+            rec["total"], rec["seg_partials"] = r.nevents, a.seg.data_ptr()
+
+    # ------------------------------------------------------------------ the loop
+    def run(self, requests, time_scale: float = 1.0, max_wall: float | None = None) -> dict:
+        """Serve `requests` (sorted by arrival, seconds from start); returns latencies and
+        throughput.  time_scale stretches the arrival times."""
+        torch = self.torch
+        t0 = time.perf_counter()
+        pending = deque(enumerate(requests))
+        queue: deque[_Active] = deque()
+        active: list[_Active] = []
+        inflight: deque = deque()  # (tick, event, runner index, [(slot, active)], [done actives])
+        latencies, done = {}, []
+        tick = 0
+        events_done = 0
+        while pending or queue or active or inflight:
+            now = time.perf_counter()
+            if max_wall is not None and now - t0 > max_wall:
+                break
+            while pending and t0 + pending[0][1].arrival * time_scale <= now:
+                rid, r = pending.popleft()
+                queue.append(_Active(rid, r, t0 + r.arrival * time_scale))
+            while queue and len(active) < self.max_slices:
+                if not self._admit(queue[0]):
+                    break
+                active.append(queue.popleft())
+            # harvest finished ticks (oldest first)
+            while inflight and (len(inflight) >= 2 or inflight[0][1].query()):
+                t_i, ev, ri, slots, finishing = inflight.popleft()
+                ev.synchronize()
+                tnow = time.perf_counter()
+                for slot, a in slots:
+                    if a.req.kind == "integrate" and a in finishing:
+                        a.result = self.runners[ri].result(slot)
+                for a in finishing:
+                    latencies[a.rid] = tnow - a.arrival
+                    events_done += a.req.nevents
+                    done.append(a)
+                    self._release(a)
+            launchable = [a for a in active if a.next_first < a.req.nevents]
+            if launchable and len(inflight) < 2:
+                ri = tick % 2
+                slots, finishing = [], []
+                for k, a in enumerate(launchable):
+                    if a.req.kind == "generate":
+                        count = a.req.nevents
+                    else:
+                        count = min(self.int_slice, a.req.nevents - a.next_first)
+                    self._fill(self.table[k], a, count)
+                    slots.append((k, a))
+                    a.next_first += count
+                    if a.next_first >= a.req.nevents:
+                        finishing.append(a)
+                self.runners[ri].run(self.table, len(launchable), use_graph=self.use_graph, stream=self.stream)
+                for a in finishing:
+                    if a.req.kind == "generate":
+                        a.host_out.copy_(a.dev_out, non_blocking=True)
+                        a.host_w.copy_(a.dev_w, non_blocking=True)
+                ev = torch.cuda.Event()
+                ev.record(self.stream)
+                inflight.append((tick, ev, ri, slots, finishing))
+                active = [a for a in active if a.next_first < a.req.nevents]
+                tick += 1
+            elif not inflight and not active and not queue and pending:
+                wait = t0 + pending[0][1].arrival * time_scale - time.perf_counter()
+                if wait > 0:
+                    time.sleep(min(wait, 2e-4))
+            elif inflight and not inflight[0][1].query():
+                time.sleep(2e-5)
+        wall = time.perf_counter() - t0
+        return _summary(latencies, events_done, wall, ticks=tick, done=done)
+
+    def close(self):
+        for r in self.runners:
+            r.close()
+
+
+class PlainServer:
+    """One request at a time, in arrival order, with the single-request entry points."""
+
+    def __init__(self, keep_outputs: bool = False):
+        import torch
+        self.torch = torch
+        self.keep_outputs = keep_outputs
+        self.stream = torch.cuda.current_stream()
+
+    def run(self, requests, time_scale: float = 1.0, max_wall: float | None = None) -> dict:
+        torch = self.torch
+        t0 = time.perf_counter()
+        latencies, done = {}, []
+        events_done = 0
+        pin = {}
+        for rid, r in enumerate(requests):
+            arr = t0 + r.arrival * time_scale
+            while time.perf_counter() < arr:
+                time.sleep(min(2e-4, max(0.0, arr - time.perf_counter())))
+            if max_wall is not None and time.perf_counter() - t0 > max_wall:
+                break
+            a = _Active(rid, r, arr)
+            if r.kind == "generate":
+                n = len(r.masses)
+                p, w = hp.generate(r.M, r.masses, r.nevents, r.seed, dtype="f32")
+                key = (n, p.shape[-1])
+                if key not in pin:
+                    pin[key] = (torch.empty(p.shape, dtype=torch.float32, pin_memory=True),
+                                torch.empty(p.shape[-1], dtype=torch.float32, pin_memory=True))
+                ho, hw = pin[key]
+                ho.copy_(p, non_blocking=True)
+                hw[: r.nevents].copy_(w, non_blocking=True)
+                self.stream.synchronize()
+                if self.keep_outputs:
+                    a.host_out, a.host_w = ho.clone(), hw.clone()
+            else:
+                a.result = hp.integrate(r.M, r.masses, r.nevents, r.seed, kin_dtype="f32", me=r.me,
+                                        params=r.params)
+            latencies[rid] = time.perf_counter() - arr
+            events_done += r.nevents
+            done.append(a)
+        wall = time.perf_counter() - t0
+        return _summary(latencies, events_done, wall, done=done)
+
+
+def _summary(latencies: dict, events: int, wall: float, ticks: int = 0, done=None) -> dict:
+    lat = np.array(sorted(latencies.values())) if latencies else np.zeros(1)
+    return {"completed": len(latencies), "events": events, "wall_s": wall,
+            "events_per_s": events / wall if wall > 0 else 0.0,
+            "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+            "max_ms": float(lat.max() * 1e3), "ticks": ticks, "done": done}

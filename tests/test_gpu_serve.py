@@ -1,0 +1,49 @@
+"""The continuous-batching server: every request's result is the same alone (single-request
+entry points) and in the mix, bit for bit, and latencies are recorded for all requests."""
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import paper_1711_05683_b300 as hp  # noqa: E402
+import workloads  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1711_05683_b300 import build as hp_build
+    hp_build.build()
+    torch.cuda.set_device(0)
+
+
+def test_served_results_equal_single_requests():
+    from paper_1711_05683_b300 import serve
+    reqs = workloads.serve_stream(rate_hz=2000, duration_s=0.15, gen_log_events=(2.0, 5.0),
+                                  int_log_events=(4.0, 7.4), rng_seed=99)
+    assert any(r.kind == "integrate" and r.nevents > 2 ** 21 for r in reqs)  # sliced over ticks
+    srv = serve.Server(max_slices=512, int_slice_segments=1, pinned_bytes=1 << 30, keep_outputs=True)
+    res = srv.run(reqs)
+    srv.close()
+    assert res["completed"] == len(reqs)
+    assert res["ticks"] > 1
+    for a in res["done"]:
+        r = a.req
+        if r.kind == "generate":
+            p, w = hp.generate(r.M, r.masses, r.nevents, r.seed, dtype="f32")
+            torch.cuda.synchronize()
+            assert torch.equal(a.host_out[:, :, : r.nevents], p[:, :, : r.nevents].cpu())
+            assert torch.equal(a.host_w[: r.nevents], w.cpu())
+        else:
+            ref = hp.integrate(r.M, r.masses, r.nevents, r.seed, kin_dtype="f32", me=r.me, params=r.params)
+            assert a.result == ref
+
+
+def test_plain_server_matches_too():
+    from paper_1711_05683_b300 import serve
+    reqs = workloads.serve_stream(rate_hz=500, duration_s=0.05, gen_log_events=(2.0, 4.0),
+                                  int_log_events=(4.0, 5.0), rng_seed=3)
+    res = serve.PlainServer(keep_outputs=True).run(reqs)
+    assert res["completed"] == len(reqs) and res["p99_ms"] >= res["p50_ms"]
