@@ -147,7 +147,8 @@ def run_ours(args) -> None:
     buf64 = torch.empty(max_elems, dtype=torch.float64, device="cuda")  # reused by every launch
     buf32 = buf64.view(torch.float32)
     stream = torch.cuda.current_stream()
-    base_offset = rank * (nev + int_events)  # disjoint counter-event ranges per rank
+    from paper_1711_05683_b300 import shard
+    base_offset = shard.rank_event_offset(rank, nev + int_events)  # disjoint counter-event ranges
 
     def views(n, dtype):
         ld = nev
@@ -202,11 +203,7 @@ def run_ours(args) -> None:
     t1.record(stream)
     barrier()
     clk = clocks.stop()
-    total_ms = t0.elapsed_time(t1)
-    if world > 1:
-        tt = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
+    total_ms = shard.max_over_ranks(t0.elapsed_time(t1), device="cuda")
     ms_per_step = total_ms / args.steps
     per_step_events = len(items) * nev + int_events
     value = per_step_events * world / (ms_per_step / 1e3)
@@ -247,11 +244,7 @@ def run_ours(args) -> None:
             e2e_step()
         b.record(stream)
         barrier()
-        e2e_ms = a.elapsed_time(b) / e2e_steps
-        if world > 1:
-            tt = torch.tensor([e2e_ms], device="cuda", dtype=torch.float64)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            e2e_ms = float(tt.item())
+        e2e_ms = shard.max_over_ranks(a.elapsed_time(b) / e2e_steps, device="cuda")
         e2e = {"value": per_step_events * world / (e2e_ms / 1e3), "unit": "events/s",
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": e2e_steps,
                "ms_per_step": e2e_ms}

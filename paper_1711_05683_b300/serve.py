@@ -80,7 +80,7 @@ class PinnedRing:
 
 class Server:
     def __init__(self, budget_bytes: int = 40 * 10 ** 9, max_slices: int = 4096,
-                 int_slice_segments: int = 8, pinned_bytes: int = 4 << 30,
+                 int_slice_segments: int = 4, pinned_bytes: int = 4 << 30,
                  keep_outputs: bool = False, use_graph: bool = True):
         import torch
         self.torch = torch
@@ -150,16 +150,22 @@ class Server:
             rec["total"], rec["seg_partials"] = r.nevents, a.seg.data_ptr()
 
     # ------------------------------------------------------------------ the loop
-    def run(self, requests, time_scale: float = 1.0, max_wall: float | None = None) -> dict:
+    def run(self, requests, time_scale: float = 1.0, max_wall: float | None = None,
+            cancel_after: dict | None = None) -> dict:
         """Serve `requests` (sorted by arrival, seconds from start); returns latencies and
-        throughput.  time_scale stretches the arrival times."""
+        throughput.  time_scale stretches the arrival times.  cancel_after maps a request
+        index to a time (seconds from start) after which the client withdraws it: the server
+        drops it at the next tick boundary and releases its memory (host-side fault
+        injection; work already on the GPU finishes and is discarded)."""
         torch = self.torch
+        cancel_after = dict(cancel_after or {})
+        cancelled = []
         t0 = time.perf_counter()
         pending = deque(enumerate(requests))
         queue: deque[_Active] = deque()
         active: list[_Active] = []
         inflight: deque = deque()  # (tick, event, runner index, [(slot, active)], [done actives])
-        latencies, done = {}, []
+        latencies, kinds, done = {}, {}, []
         tick = 0
         events_done = 0
         while pending or queue or active or inflight:
@@ -183,9 +189,20 @@ class Server:
                         a.result = self.runners[ri].result(slot)
                 for a in finishing:
                     latencies[a.rid] = tnow - a.arrival
+                    kinds[a.rid] = a.req.kind
                     events_done += a.req.nevents
                     done.append(a)
                     self._release(a)
+            if cancel_after:
+                keep = []
+                for a in active:
+                    t_c = cancel_after.get(a.rid)
+                    if t_c is not None and now - t0 >= t_c and a.next_first < a.req.nevents:
+                        cancelled.append(a.rid)
+                        self._release(a)
+                    else:
+                        keep.append(a)
+                active = keep
             launchable = [a for a in active if a.next_first < a.req.nevents]
             if launchable and len(inflight) < 2:
                 ri = tick % 2
@@ -217,7 +234,9 @@ class Server:
             elif inflight and not inflight[0][1].query():
                 time.sleep(2e-5)
         wall = time.perf_counter() - t0
-        return _summary(latencies, events_done, wall, ticks=tick, done=done)
+        out = _summary(latencies, events_done, wall, ticks=tick, done=done, kinds=kinds)
+        out["cancelled"] = cancelled
+        return out
 
     def close(self):
         for r in self.runners:
@@ -225,20 +244,21 @@ class Server:
 
 
 class PlainServer:
-    """One request at a time, in arrival order, with the single-request entry points."""
+    """One request at a time, in arrival order, with the single-request entry points; generated
+    events are copied to the same kind of pinned ring as the batched server uses."""
 
-    def __init__(self, keep_outputs: bool = False):
+    def __init__(self, keep_outputs: bool = False, pinned_bytes: int = 4 << 30):
         import torch
         self.torch = torch
         self.keep_outputs = keep_outputs
         self.stream = torch.cuda.current_stream()
+        self.ring = PinnedRing(pinned_bytes)
 
     def run(self, requests, time_scale: float = 1.0, max_wall: float | None = None) -> dict:
         torch = self.torch
         t0 = time.perf_counter()
-        latencies, done = {}, []
+        latencies, kinds, done = {}, {}, []
         events_done = 0
-        pin = {}
         for rid, r in enumerate(requests):
             arr = t0 + r.arrival * time_scale
             while time.perf_counter() < arr:
@@ -249,29 +269,40 @@ class PlainServer:
             if r.kind == "generate":
                 n = len(r.masses)
                 p, w = hp.generate(r.M, r.masses, r.nevents, r.seed, dtype="f32")
-                key = (n, p.shape[-1])
-                if key not in pin:
-                    pin[key] = (torch.empty(p.shape, dtype=torch.float32, pin_memory=True),
-                                torch.empty(p.shape[-1], dtype=torch.float32, pin_memory=True))
-                ho, hw = pin[key]
+                ld = p.shape[-1]
+                nbytes = (4 * n + 1) * ld * 4
+                start = self.ring.alloc(nbytes)
+                if start is None:  # ring full: everything before is finished (synchronous server)
+                    self.ring.live.clear()
+                    start = self.ring.alloc(nbytes)
+                hb = self.ring.buf[start: start + nbytes].view(torch.float32)
+                ho, hw = hb[: 4 * n * ld].view(n, 4, ld), hb[4 * n * ld:]
                 ho.copy_(p, non_blocking=True)
                 hw[: r.nevents].copy_(w, non_blocking=True)
                 self.stream.synchronize()
                 if self.keep_outputs:
                     a.host_out, a.host_w = ho.clone(), hw.clone()
+                self.ring.free(start)
             else:
                 a.result = hp.integrate(r.M, r.masses, r.nevents, r.seed, kin_dtype="f32", me=r.me,
                                         params=r.params)
             latencies[rid] = time.perf_counter() - arr
+            kinds[rid] = r.kind
             events_done += r.nevents
             done.append(a)
         wall = time.perf_counter() - t0
-        return _summary(latencies, events_done, wall, done=done)
+        return _summary(latencies, events_done, wall, done=done, kinds=kinds)
 
 
-def _summary(latencies: dict, events: int, wall: float, ticks: int = 0, done=None) -> dict:
+def _summary(latencies: dict, events: int, wall: float, ticks: int = 0, done=None, kinds=None) -> dict:
     lat = np.array(sorted(latencies.values())) if latencies else np.zeros(1)
-    return {"completed": len(latencies), "events": events, "wall_s": wall,
-            "events_per_s": events / wall if wall > 0 else 0.0,
-            "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
-            "max_ms": float(lat.max() * 1e3), "ticks": ticks, "done": done}
+    out = {"completed": len(latencies), "events": events, "wall_s": wall,
+           "events_per_s": events / wall if wall > 0 else 0.0,
+           "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+           "max_ms": float(lat.max() * 1e3), "ticks": ticks, "done": done}
+    for kind in ("generate", "integrate"):
+        v = np.array([latencies[k] for k in latencies if kinds and kinds.get(k) == kind])
+        if len(v):
+            out[kind] = {"n": int(len(v)), "p50_ms": float(np.percentile(v, 50) * 1e3),
+                         "p99_ms": float(np.percentile(v, 99) * 1e3)}
+    return out

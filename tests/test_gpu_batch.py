@@ -165,3 +165,30 @@ def test_batch_rejects_bad_slices():
     with pytest.raises(hp.HydraError):
         b.run(table)
     b.close()
+
+
+def test_integral_checkpoint_and_resume():
+    """An integral's whole running state is (seed, next event index, segment partials): copy
+    the partials to the host, drop every device object, restore into a new batch runner and
+    continue; the result equals one uninterrupted call bit for bit."""
+    d = workloads.D0_DALITZ
+    S = hp.SEGMENT_EVENTS
+    total = 5 * S + 777
+    ref = hp.integrate(d["M"], d["masses"], total, 17, kin_dtype="f32", me=hp.ME_DALITZ_2BW,
+                       params=d["params"])
+    seg = torch.zeros(8 * hp.segments(total), dtype=torch.float64, device="cuda")
+    b = hp.Batch(4)
+    t = np.zeros(1, dtype=hp.request_dtype())
+    int_record(t[0], d["M"], d["masses"], total, 17, "f32", hp.ME_DALITZ_2BW, d["params"], seg, 0, 3 * S)
+    b.run(t)
+    torch.cuda.synchronize()
+    checkpoint = {"next": 3 * S, "seg": seg.cpu().clone()}
+    b.close()
+    del seg
+    seg2 = checkpoint["seg"].cuda()
+    b2 = hp.Batch(4)
+    int_record(t[0], d["M"], d["masses"], total, 17, "f32", hp.ME_DALITZ_2BW, d["params"], seg2,
+               checkpoint["next"], total - checkpoint["next"])
+    b2.run(t)
+    assert b2.result(0) == ref
+    b2.close()

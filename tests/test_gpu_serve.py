@@ -47,3 +47,29 @@ def test_plain_server_matches_too():
                                   int_log_events=(4.0, 5.0), rng_seed=3)
     res = serve.PlainServer(keep_outputs=True).run(reqs)
     assert res["completed"] == len(reqs) and res["p99_ms"] >= res["p50_ms"]
+
+
+def test_cancelled_request_leaves_the_others_intact():
+    """Host-side fault injection: a client withdraws a long integral mid-flight; the server
+    drops it between ticks and every other request still gets its single-request result."""
+    from paper_1711_05683_b300 import serve
+    d = workloads.D0_DALITZ
+    reqs = workloads.serve_stream(rate_hz=1000, duration_s=0.05, gen_log_events=(2.0, 4.0),
+                                  int_log_events=(4.0, 5.0), rng_seed=11)
+    big = workloads.Request("integrate", d["M"], d["masses"], 60 * 2 ** 21, 123, me=1,
+                            params=d["params"], arrival=0.0)
+    reqs = [big] + list(reqs)
+    srv = serve.Server(max_slices=256, int_slice_segments=1, pinned_bytes=1 << 28, keep_outputs=True)
+    res = srv.run(reqs, cancel_after={0: 0.005})
+    srv.close()
+    assert res["cancelled"] == [0]
+    assert res["completed"] == len(reqs) - 1
+    for a in res["done"]:
+        r = a.req
+        assert a.rid != 0
+        if r.kind == "integrate":
+            assert a.result == hp.integrate(r.M, r.masses, r.nevents, r.seed, kin_dtype="f32", me=r.me,
+                                            params=r.params)
+        else:
+            p, w = hp.generate(r.M, r.masses, r.nevents, r.seed, dtype="f32")
+            assert torch.equal(a.host_w[: r.nevents], w.cpu())
