@@ -281,6 +281,23 @@ hydra_status hydra_batch_result(hydra_batch *batch, int i, hydra_integral *resul
 /* Wait for the latest run and release the batch runner. */
 hydra_status hydra_batch_destroy(hydra_batch *batch);
 
+/*
+ * Arithmetic of FP64 generation (HYDRA_F64 in hydra_phsp_generate, hydra_phsp_generate_host
+ * and batched generation).  B300's FP64 pipe is a small fraction of its FP32 pipe, so by
+ * default the kinematics run in double-float arithmetic (pairs of FP32 numbers, ~48
+ * significand bits, error-free sums and products plus Newton-corrected reciprocal, square
+ * root and sine/cosine) with FP64 weights and FP64 outputs; HYDRA_FP64_NATIVE uses FP64
+ * instructions throughout.  Both agree with an FP64 reference to ~1e-14 of the event scale.
+ * Process-wide.  Errors: INVALID_ARG.
+ */
+typedef enum hydra_fp64_arith {
+    HYDRA_FP64_NATIVE = 0,
+    HYDRA_FP64_DOUBLE_FLOAT = 1
+} hydra_fp64_arith;
+
+hydra_status hydra_set_fp64_arith(hydra_fp64_arith arith);
+hydra_fp64_arith hydra_get_fp64_arith(void);
+
 /* Release the per-device scratch memory of the library (all devices).  Not thread safe
  * with respect to calls in flight. */
 hydra_status hydra_shutdown(void);

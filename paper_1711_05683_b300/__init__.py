@@ -74,6 +74,8 @@ def lib() -> ctypes.CDLL:
         L.hydra_phsp_generate_host.argtypes = [d, i, dp, u64, u64, u64, i, vp, u64, vp, vp]
         L.hydra_phsp_integrate_noalloc.argtypes = L.hydra_phsp_integrate.argtypes
         L.hydra_set_launch_config.argtypes = [i, i, i, i, i]
+        L.hydra_set_fp64_arith.argtypes = [i]
+        L.hydra_get_fp64_arith.restype = i
         L.hydra_batch_create.argtypes = [i, u64, ctypes.POINTER(vp)]
         L.hydra_batch_run.argtypes = [vp, vp, i, i, vp]
         L.hydra_batch_result.argtypes = [vp, i, ctypes.POINTER(Integral)]
@@ -81,7 +83,8 @@ def lib() -> ctypes.CDLL:
         L.hydra_get_launch_config.argtypes = [i, i, i, ctypes.POINTER(i), ctypes.POINTER(i)]
         for name in ("hydra_phsp_volume_factor", "hydra_phsp_generate", "hydra_phsp_integrate",
                      "hydra_phsp_draws", "hydra_phsp_generate_host", "hydra_phsp_integrate_noalloc",
-                     "hydra_set_launch_config", "hydra_get_launch_config", "hydra_batch_create",
+                     "hydra_set_launch_config", "hydra_get_launch_config", "hydra_set_fp64_arith",
+                     "hydra_batch_create",
                      "hydra_batch_run", "hydra_batch_result", "hydra_batch_destroy", "hydra_shutdown"):
             getattr(L, name).restype = i
         _lib = L
@@ -201,6 +204,18 @@ def set_launch_config(kind: int, n: int, dtype, block: int, events_per_thread: i
     KERNEL_INTEGRATE) for n daughters in a precision; results do not depend on it."""
     _check(lib().hydra_set_launch_config(int(kind), int(n), _dtype_code(dtype), int(block),
                                          int(events_per_thread)))
+
+
+FP64_NATIVE, FP64_DOUBLE_FLOAT = 0, 1
+
+
+def set_fp64_arith(arith: int) -> None:
+    """Arithmetic of FP64 generation: FP64_DOUBLE_FLOAT (default) or FP64_NATIVE."""
+    _check(lib().hydra_set_fp64_arith(int(arith)))
+
+
+def get_fp64_arith() -> int:
+    return int(lib().hydra_get_fp64_arith())
 
 
 def get_launch_config(kind: int, n: int, dtype) -> tuple[int, int]:

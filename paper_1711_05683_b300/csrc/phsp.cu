@@ -21,6 +21,7 @@
 #include <cstdio>
 #include <cstring>
 #include <atomic>
+#include <type_traits>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -36,12 +37,18 @@ namespace hydra {
 // Generation
 // ------------------------------------------------------------------------------------
 // Thread t takes the group of EPT consecutive events g*EPT.. (grid-stride over groups); the
-// last nevents % EPT events are taken one each by the first threads of the grid.
+// last nevents % EPT events are taken one each by the first threads of the grid.  R is the
+// kinematic arithmetic (float, double, or df = pairs of floats for FP64 outputs).
 template <int N, typename R, int EPT>
 __global__ void __launch_bounds__(512) phsp_generate_kernel(const __grid_constant__ DecayConsts C,
                                                             uint64_t nevents, uint64_t event_offset,
-                                                            R* __restrict__ out, uint64_t ld,
-                                                            R* __restrict__ weights) {
+                                                            typename Prec<R>::Out* __restrict__ out,
+                                                            uint64_t ld,
+                                                            typename Prec<R>::Out* __restrict__ weights) {
+    if constexpr (std::is_same<R, df>::value) {
+        df_sincos_table_init();
+        __syncthreads();
+    }
     const uint64_t tid = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
     const uint64_t groups = nevents / EPT;
@@ -177,6 +184,18 @@ hydra_status make_consts(double M, int n, const double* masses, uint64_t seed,
     C->Tsf = static_cast<float>(C->Ts);
     C->Ts_halff = static_cast<float>(C->Ts_half);
     C->Cf = static_cast<float>(Cn);
+    auto split = [](double v, float* o) {
+        o[0] = static_cast<float>(v);
+        o[1] = static_cast<float>(v - static_cast<double>(o[0]));
+    };
+    split(M, C->Mdf);
+    split(C->Ts, C->Tsdf);
+    split(C->Ts_half, C->Ts_halfdf);
+    for (int i = 0; i < n; ++i) {
+        split(C->m[i], C->mdf[i]);
+        split(C->mu[i], C->mudf[i]);
+        split(C->m2[i], C->m2df[i]);
+    }
     for (int i = 0; i < n; ++i) {
         C->mf[i] = static_cast<float>(C->m[i]);
         C->muf[i] = static_cast<float>(C->mu[i]);
@@ -294,10 +313,15 @@ struct LaunchCfg {
 };
 static LaunchCfg g_cfg[2][2][kNMax + 1];
 
+std::atomic<int> g_fp64_arith{HYDRA_FP64_DOUBLE_FLOAT};
+
 static Launch select_generate(hydra_dtype dtype, int n) {
     LaunchCfg& c = g_cfg[HYDRA_KERNEL_GENERATE][dtype][n];
     const int ept = c.ept.load(std::memory_order_relaxed);
-    const void* k = dtype == HYDRA_F32 ? generate_kernel_for<float>(n, ept) : generate_kernel_for<double>(n, ept);
+    const void* k = nullptr;
+    if (dtype == HYDRA_F32) k = generate_kernel_for<float>(n, ept);
+    else if (g_fp64_arith.load(std::memory_order_relaxed) == HYDRA_FP64_NATIVE) k = generate_kernel_for<double>(n, ept);
+    else k = generate_kernel_for<df>(n, ept);
     return Launch{k, c.block.load(std::memory_order_relaxed), ept};
 }
 
@@ -732,6 +756,15 @@ hydra_status hydra_set_launch_config(hydra_kernel_kind kind, int n, hydra_dtype 
     c.ept.store(events_per_thread);
     return HYDRA_OK;
 }
+
+hydra_status hydra_set_fp64_arith(hydra_fp64_arith arith) {
+    if (arith != HYDRA_FP64_NATIVE && arith != HYDRA_FP64_DOUBLE_FLOAT)
+        return fail(HYDRA_ERR_INVALID_ARG, "unknown FP64 arithmetic %d", static_cast<int>(arith));
+    g_fp64_arith.store(arith);
+    return HYDRA_OK;
+}
+
+hydra_fp64_arith hydra_get_fp64_arith(void) { return static_cast<hydra_fp64_arith>(g_fp64_arith.load()); }
 
 hydra_status hydra_get_launch_config(hydra_kernel_kind kind, int n, hydra_dtype dtype, int* block,
                                      int* events_per_thread) {

@@ -15,6 +15,7 @@
 #include <cstdint>
 #include <cstring>
 #include <mutex>
+#include <type_traits>
 #include <vector>
 
 #include "hydra_phsp.h"
@@ -64,8 +65,9 @@ __device__ __forceinline__ int find_slot(const uint64_t* __restrict__ prefix, in
 
 template <int N, typename R>
 __device__ __forceinline__ void generate_tile(const DecayConsts& C, const BatchEntry& e, uint64_t lt, int lane) {
-    R* out = static_cast<R*>(e.out);
-    R* w = static_cast<R*>(e.weights);
+    using Out = typename Prec<R>::Out;
+    Out* out = static_cast<Out*>(e.out);
+    Out* w = static_cast<Out*>(e.weights);
     const uint64_t base = lt * kTileEvents;
 #pragma unroll 1
     for (int it = 0; it < kTileEvents / (32 * kBatchEPT); ++it) {
@@ -119,9 +121,14 @@ __device__ __forceinline__ TileSums integrate_tile_n(int n, int me, const DecayC
     }
 }
 
-template <typename R>
+// RG: arithmetic of generation tiles (float, double or df); RI: of integral tiles.
+template <typename RG, typename RI>
 __global__ void __launch_bounds__(kBatchBlock) phsp_batch_kernel(BatchHeader* __restrict__ hdr,
                                                                  TileSums* __restrict__ partials) {
+    if constexpr (std::is_same<RG, df>::value) {
+        df_sincos_table_init();
+        __syncthreads();
+    }
     __shared__ DecayConsts sC[kBatchWarps];
     __shared__ MEConsts sP[kBatchWarps];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -147,9 +154,9 @@ __global__ void __launch_bounds__(kBatchBlock) phsp_batch_kernel(BatchHeader* __
         __syncwarp();
         const uint64_t lt = t - prefix[r];
         if (e.kind == HYDRA_REQ_GENERATE) {
-            generate_tile_n<R>(e.n, sC[warp], e, lt, lane);
+            generate_tile_n<RG>(e.n, sC[warp], e, lt, lane);
         } else {
-            const TileSums ts = integrate_tile_n<R>(e.n, e.me, sC[warp], sP[warp], e, e.first / kTileEvents + lt, lane);
+            const TileSums ts = integrate_tile_n<RI>(e.n, e.me, sC[warp], sP[warp], e, e.first / kTileEvents + lt, lane);
             if (lane == 0) partials[e.partial_begin + lt] = ts;
         }
         __syncwarp();
@@ -205,8 +212,8 @@ struct hydra_batch {
     hydra_integral* h_results = nullptr;
     cudaEvent_t table_done = nullptr;  // the table copy of the latest run has completed
     cudaEvent_t run_done = nullptr;    // the latest run has completed
-    cudaGraphExec_t graph[2] = {nullptr, nullptr};  // per dtype
-    int grid_main[2] = {0, 0};
+    cudaGraphExec_t graph[3] = {nullptr, nullptr, nullptr};  // per variant (see run_variant)
+    int grid_main[3] = {0, 0, 0};
     int grid_aux = 0;
     std::vector<uint8_t> finalized;  // per slice of the latest run
     std::vector<int32_t> kinds;
@@ -227,27 +234,35 @@ size_t table_size(int nreq, int nfinal) {
     return align_up(off, 256);
 }
 
-void launch_run_kernels(hydra_batch* b, int dt, cudaStream_t s) {
+// Variant 0: FP32; 1: FP64 with native FP64 generation; 2: FP64 with double-float generation.
+int run_variant(int dtype) {
+    if (dtype == HYDRA_F32) return 0;
+    return g_fp64_arith.load(std::memory_order_relaxed) == HYDRA_FP64_NATIVE ? 1 : 2;
+}
+
+void launch_run_kernels(hydra_batch* b, int v, cudaStream_t s) {
     BatchHeader* hdr = reinterpret_cast<BatchHeader*>(b->d_table);
-    if (dt == HYDRA_F32)
-        phsp_batch_kernel<float><<<b->grid_main[dt], kBatchBlock, 0, s>>>(hdr, b->d_partials);
+    if (v == 0)
+        phsp_batch_kernel<float, float><<<b->grid_main[v], kBatchBlock, 0, s>>>(hdr, b->d_partials);
+    else if (v == 1)
+        phsp_batch_kernel<double, double><<<b->grid_main[v], kBatchBlock, 0, s>>>(hdr, b->d_partials);
     else
-        phsp_batch_kernel<double><<<b->grid_main[dt], kBatchBlock, 0, s>>>(hdr, b->d_partials);
+        phsp_batch_kernel<df, double><<<b->grid_main[v], kBatchBlock, 0, s>>>(hdr, b->d_partials);
     batch_reduce_segments<<<b->grid_aux, kBatchBlock, 0, s>>>(hdr, b->d_partials);
     batch_finalize<<<b->grid_aux, kBatchBlock, 0, s>>>(hdr, b->d_results);
 }
 
-hydra_status capture_graph(hydra_batch* b, int dt) {
+hydra_status capture_graph(hydra_batch* b, int v) {
     cudaStream_t cs;
     cudaError_t err = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
     if (err != cudaSuccess) return cuda_fail(err, "capture stream");
     cudaGraph_t g = nullptr;
     err = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (err == cudaSuccess) {
-        launch_run_kernels(b, dt, cs);
+        launch_run_kernels(b, v, cs);
         err = cudaStreamEndCapture(cs, &g);
     }
-    if (err == cudaSuccess) err = cudaGraphInstantiate(&b->graph[dt], g, 0);
+    if (err == cudaSuccess) err = cudaGraphInstantiate(&b->graph[v], g, 0);
     if (g) cudaGraphDestroy(g);
     cudaStreamDestroy(cs);
     if (err != cudaSuccess) return cuda_fail(err, "batch graph capture");
@@ -284,13 +299,15 @@ hydra_status hydra_batch_create(int max_requests, uint64_t max_integrate_tiles, 
     }
     int sms = 148, occ = 1;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, phsp_batch_kernel<float>, kBatchBlock, 0);
-    b->grid_main[HYDRA_F32] = sms * (occ > 0 ? occ : 1);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, phsp_batch_kernel<double>, kBatchBlock, 0);
-    b->grid_main[HYDRA_F64] = sms * (occ > 0 ? occ : 1);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, phsp_batch_kernel<float, float>, kBatchBlock, 0);
+    b->grid_main[0] = sms * (occ > 0 ? occ : 1);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, phsp_batch_kernel<double, double>, kBatchBlock, 0);
+    b->grid_main[1] = sms * (occ > 0 ? occ : 1);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, phsp_batch_kernel<df, double>, kBatchBlock, 0);
+    b->grid_main[2] = sms * (occ > 0 ? occ : 1);
     b->grid_aux = sms;
-    for (int dt = 0; dt < 2; ++dt) {
-        const hydra_status st = capture_graph(b, dt);
+    for (int v = 0; v < 3; ++v) {
+        const hydra_status st = capture_graph(b, v);
         if (st != HYDRA_OK) {
             hydra_batch_destroy(b);
             return st;
@@ -406,10 +423,11 @@ hydra_status hydra_batch_run(hydra_batch* b, const hydra_request* reqs, int nreq
     err = cudaMemcpyAsync(b->d_table, b->h_table, bytes, cudaMemcpyHostToDevice, s);
     if (err == cudaSuccess) err = cudaEventRecord(b->table_done, s);
     if (err != cudaSuccess) return cuda_fail(err, "batch table copy");
+    const int v = run_variant(dt);
     if (use_graph) {
-        err = cudaGraphLaunch(b->graph[dt], s);
+        err = cudaGraphLaunch(b->graph[v], s);
     } else {
-        launch_run_kernels(b, dt, s);
+        launch_run_kernels(b, v, s);
         err = cudaGetLastError();
     }
     if (err != cudaSuccess) return cuda_fail(err, "batch launch");
@@ -439,8 +457,8 @@ hydra_status hydra_batch_result(hydra_batch* b, int i, hydra_integral* result) {
 hydra_status hydra_batch_destroy(hydra_batch* b) {
     if (!b) return HYDRA_OK;
     if (b->run_done) cudaEventSynchronize(b->run_done);
-    for (int dt = 0; dt < 2; ++dt)
-        if (b->graph[dt]) cudaGraphExecDestroy(b->graph[dt]);
+    for (int v = 0; v < 3; ++v)
+        if (b->graph[v]) cudaGraphExecDestroy(b->graph[v]);
     if (b->d_table) cudaFree(b->d_table);
     if (b->h_table) cudaFreeHost(b->h_table);
     if (b->d_partials) cudaFree(b->d_partials);

@@ -11,6 +11,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "phsp_df.cuh"
+
 namespace hydra {
 
 constexpr int kNMax = 10;
@@ -28,6 +30,9 @@ struct DecayConsts {
     // FP32 copies (rounded from the FP64 values)
     float Mf, Tsf, Ts_halff, Cf;
     float mf[kNMax], muf[kNMax], m2f[kNMax];
+    // double-float copies (hi, lo) for the df kinematics of the FP64 generator
+    float Mdf[2], Tsdf[2], Ts_halfdf[2];
+    float mdf[kNMax][2], mudf[kNMax][2], m2df[kNMax][2];
     // Philox round keys: key + r * (W0, W1), r = 0..9
     uint32_t rk0[10], rk1[10];
 };
@@ -107,6 +112,11 @@ template <> struct Prec<float> {
         *s = -sn;
         *c = -cs;
     }
+    using W = float;    // weight accumulation type
+    using Out = float;  // stored type
+    __device__ static W w_mul(W w, float p) { return w * p; }
+    __device__ static W Cw(const DecayConsts& C) { return C.Cf; }
+    __device__ static Out out(float v) { return v; }
     __device__ static float M(const DecayConsts& C) { return C.Mf; }
     __device__ static float Ts(const DecayConsts& C) { return C.Tsf; }
     __device__ static float Ts_half(const DecayConsts& C) { return C.Ts_halff; }
@@ -127,6 +137,11 @@ template <> struct Prec<double> {
     __device__ static void sincos_2pi_u(uint32_t x, double* s, double* c) {
         sincospi(__fma_rn(__uint2double_rn(x), 4.656612873077392578125e-10, 2.3283064365386962890625e-10), s, c);
     }
+    using W = double;
+    using Out = double;
+    __device__ static W w_mul(W w, double p) { return w * p; }
+    __device__ static W Cw(const DecayConsts& C) { return C.C; }
+    __device__ static Out out(double v) { return v; }
     __device__ static double M(const DecayConsts& C) { return C.M; }
     __device__ static double Ts(const DecayConsts& C) { return C.Ts; }
     __device__ static double Ts_half(const DecayConsts& C) { return C.Ts_half; }
@@ -134,6 +149,29 @@ template <> struct Prec<double> {
     __device__ static double m(const DecayConsts& C, int i) { return C.m[i]; }
     __device__ static double mu(const DecayConsts& C, int i) { return C.mu[i]; }
     __device__ static double m2(const DecayConsts& C, int i) { return C.m2[i]; }
+};
+
+// Double-float kinematics for the FP64 generator: arithmetic on the FP32 pipe with ~48
+// significand bits (phsp_df.cuh); the weight product and the stored values are FP64.
+template <> struct Prec<df> {
+    using W = double;
+    using Out = double;
+    __device__ static df u32(uint32_t v) { return df_from_u32(v); }
+    __device__ static df i32(int32_t v) { return df_from_i32(v); }
+    __device__ static df sqrt_(df v) { return df_sqrt(v); }
+    __device__ static df rcp(df v) { return df_rcp(v); }
+    __device__ static df div(df a, df b) { return df_div(a, b); }
+    __device__ static df fma_(df a, df b, df c) { return a * b + c; }
+    __device__ static void sincos_2pi_u(uint32_t x, df* s, df* c) { df_sincos_2pi_u(x, s_sincos_table, s, c); }
+    __device__ static W w_mul(W w, df p) { return w * df_to_double(p); }
+    __device__ static W Cw(const DecayConsts& C) { return C.C; }
+    __device__ static Out out(df v) { return df_to_double(v); }
+    __device__ static df M(const DecayConsts& C) { return df{C.Mdf[0], C.Mdf[1]}; }
+    __device__ static df Ts(const DecayConsts& C) { return df{C.Tsdf[0], C.Tsdf[1]}; }
+    __device__ static df Ts_half(const DecayConsts& C) { return df{C.Ts_halfdf[0], C.Ts_halfdf[1]}; }
+    __device__ static df m(const DecayConsts& C, int i) { return df{C.mdf[i][0], C.mdf[i][1]}; }
+    __device__ static df mu(const DecayConsts& C, int i) { return df{C.mudf[i][0], C.mudf[i][1]}; }
+    __device__ static df m2(const DecayConsts& C, int i) { return df{C.m2df[i][0], C.m2df[i][1]}; }
 };
 
 // ------------------------------------------------------------------------------------
@@ -195,10 +233,12 @@ __device__ __forceinline__ void raubold_lynch_group(const DecayConsts& C, const 
     const R Ts = P::Ts(C);
     const R Ts_half = P::Ts_half(C);
 
-    R w[EPT], Q0[EPT], Qx[EPT], Qy[EPT], Qz[EPT], Mnext[EPT];
+    using W = typename P::W;
+    W w[EPT];
+    R Q0[EPT], Qx[EPT], Qy[EPT], Qz[EPT], Mnext[EPT];
 #pragma unroll
     for (int q = 0; q < EPT; ++q) {
-        w[q] = R(1);  // prod p_k; C_n is applied last so only the final product can leave the normal range
+        w[q] = W(1);  // prod p_k; C_n is applied last so only the final product can leave the normal range
         Q0[q] = M; Qx[q] = R(0); Qy[q] = R(0); Qz[q] = R(0);
         Mnext[q] = M;  // M_{k+1}
     }
@@ -253,7 +293,7 @@ __device__ __forceinline__ void raubold_lynch_group(const DecayConsts& C, const 
             const R lam = ((gap * (gap + twoMk)) * (gap + twom)) * ((gap + twoMk) + twom);
             const R invM = P::rcp(Mnext[q]);
             const R p = P::sqrt_(lam) * (R(0.5) * invM);
-            w[q] *= p;
+            w[q] = P::w_mul(w[q], p);
             // isotropic direction of subsystem k in the rest frame of subsystem k+1
             const uint32_t xc = xcs[q];
             const uint32_t xp = xps[q];
@@ -285,7 +325,7 @@ __device__ __forceinline__ void raubold_lynch_group(const DecayConsts& C, const 
     }
     sink.daughter(0, Q0, Qx, Qy, Qz);
 #pragma unroll
-    for (int q = 0; q < EPT; ++q) w[q] = w[q] * P::Cn(C);
+    for (int q = 0; q < EPT; ++q) w[q] = w[q] * P::Cw(C);
     sink.weight(w);
 }
 
@@ -310,19 +350,32 @@ __device__ __forceinline__ void store_group(R* __restrict__ p, const R (&v)[EPT]
 
 template <typename R, int EPT>
 struct StoreSink {
-    R* __restrict__ base;  // out + e0
-    R* __restrict__ wout;  // weights + e0
+    using Out = typename Prec<R>::Out;
+    using W = typename Prec<R>::W;
+    Out* __restrict__ base;  // out + e0
+    Out* __restrict__ wout;  // weights + e0
     uint64_t ld;
     __device__ __forceinline__ void subsystem_mass(int, const R (&)[EPT]) {}
+    __device__ __forceinline__ void put(Out* p, const R (&v)[EPT]) {
+        Out o[EPT];
+#pragma unroll
+        for (int q = 0; q < EPT; ++q) o[q] = Prec<R>::out(v[q]);
+        store_group<Out, EPT>(p, o);
+    }
     __device__ __forceinline__ void daughter(int i, const R (&E)[EPT], const R (&px)[EPT],
                                              const R (&py)[EPT], const R (&pz)[EPT]) {
-        R* p = base + static_cast<uint64_t>(4 * i) * ld;
-        store_group<R, EPT>(p, E);
-        store_group<R, EPT>(p + ld, px);
-        store_group<R, EPT>(p + 2 * ld, py);
-        store_group<R, EPT>(p + 3 * ld, pz);
+        Out* p = base + static_cast<uint64_t>(4 * i) * ld;
+        put(p, E);
+        put(p + ld, px);
+        put(p + 2 * ld, py);
+        put(p + 3 * ld, pz);
     }
-    __device__ __forceinline__ void weight(const R (&w)[EPT]) { store_group<R, EPT>(wout, w); }
+    __device__ __forceinline__ void weight(const W (&w)[EPT]) {
+        Out o[EPT];
+#pragma unroll
+        for (int q = 0; q < EPT; ++q) o[q] = static_cast<Out>(w[q]);
+        store_group<Out, EPT>(wout, o);
+    }
 };
 
 }  // namespace hydra

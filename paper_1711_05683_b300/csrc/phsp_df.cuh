@@ -1,0 +1,186 @@
+// phsp_df.cuh -- double-float ("df") arithmetic: a value is the unevaluated sum hi + lo of
+// two FP32 numbers with |lo| <= ulp(hi)/2, about 48 significand bits.  On B300 the FP32
+// pipe is ~64x wider than the FP64 pipe, so the FP64 generator computes its kinematics in
+// df and converts to double only when it stores.
+//
+// Building blocks (error-free transformations):
+//   TwoSum (Knuth):        s = fl(a+b), e = exact a + b - s                (6 FP32 ops)
+//   FastTwoSum (Dekker):   same when |a| >= |b|                            (3 ops)
+//   TwoProd (with FMA):    p = fl(a*b), e = fma(a, b, -p) exact            (2 ops)
+// Addition is the "sloppy" double-word sum (TwoSum of the high parts, low parts added,
+// renormalised): its error is bounded by ~2^-46 (|x| + |y|), i.e. relative to the operands,
+// which is the measure the generator's tolerance uses (error at the event scale).
+// Multiplication is the FMA-based double-word product (relative error ~2^-46).
+// Reciprocal, division and square root take an FP32 hardware approximation as the seed and
+// apply one Newton-Raphson correction evaluated in double-word arithmetic, which squares
+// the seed's ~2^-23 relative error to ~2^-46.
+//
+// Range: full ~48-bit precision needs |hi| >= ~2^-100 (the low part must stay a normal
+// FP32 number); values whose FP32 part underflows lose precision or flush to zero, an
+// absolute error below 2^-126 -- negligible at the event scale of GeV-range kinematics.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace hydra {
+
+struct df {
+    float hi, lo;
+    df() = default;
+    __host__ __device__ constexpr df(float h) : hi(h), lo(0.0f) {}
+    __host__ __device__ constexpr df(float h, float l) : hi(h), lo(l) {}
+};
+
+__device__ __forceinline__ df df_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return df{s, e};
+}
+
+__device__ __forceinline__ df df_fast_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float e = __fsub_rn(b, __fsub_rn(s, a));
+    return df{s, e};
+}
+
+__device__ __forceinline__ df df_from_float(float a) { return df{a, 0.0f}; }
+
+// x + y
+__device__ __forceinline__ df operator+(df x, df y) {
+    const df s = df_two_sum(x.hi, y.hi);
+    const float l = __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo));
+    return df_fast_two_sum(s.hi, l);
+}
+
+__device__ __forceinline__ df operator-(df x) { return df{-x.hi, -x.lo}; }
+__device__ __forceinline__ df operator-(df x, df y) { return x + (-y); }
+
+// x * y
+__device__ __forceinline__ df operator*(df x, df y) {
+    const float p = __fmul_rn(x.hi, y.hi);
+    float e = __fmaf_rn(x.hi, y.hi, -p);
+    e = __fmaf_rn(x.hi, y.lo, e);
+    e = __fmaf_rn(x.lo, y.hi, e);
+    return df_fast_two_sum(p, e);
+}
+
+// x * a for an FP32 a
+__device__ __forceinline__ df operator*(df x, float a) {
+    const float p = __fmul_rn(x.hi, a);
+    float e = __fmaf_rn(x.hi, a, -p);
+    e = __fmaf_rn(x.lo, a, e);
+    return df_fast_two_sum(p, e);
+}
+
+// 1/y: seed r = rcp.approx(hi); e = 1 - y r (exact to first order in df); r (1 + e)
+__device__ __forceinline__ df df_rcp(df y) {
+    float r;
+    asm("rcp.approx.f32 %0, %1;" : "=f"(r) : "f"(y.hi));
+    float e = __fmaf_rn(-y.hi, r, 1.0f);
+    e = __fmaf_rn(-y.lo, r, e);
+    return df_fast_two_sum(r, __fmul_rn(r, e));
+}
+
+__device__ __forceinline__ df df_div(df x, df y) { return x * df_rcp(y); }
+
+__device__ __forceinline__ df& operator*=(df& x, df y) {
+    x = x * y;
+    return x;
+}
+
+// sqrt(x), x >= 0: s0 = x.hi rsqrt(x.hi); s = s0 + (x - s0^2) / (2 s0), the residual formed
+// with an exact product; 0 for x = 0.
+__device__ __forceinline__ df df_sqrt(df x) {
+    if (!(x.hi > 0.0f)) return df{0.0f, 0.0f};
+    float r;
+    asm("rsqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x.hi));
+    const float s0 = __fmul_rn(x.hi, r);
+    const float p = __fmul_rn(s0, s0);
+    const float pe = __fmaf_rn(s0, s0, -p);
+    const float res = __fadd_rn(__fsub_rn(__fsub_rn(x.hi, p), pe), x.lo);
+    return df_fast_two_sum(s0, __fmul_rn(res, __fmul_rn(0.5f, r)));
+}
+
+// Exact conversion of a 32-bit unsigned / signed integer.
+__device__ __forceinline__ df df_from_u32(uint32_t v) {
+    return df_two_sum(__uint2float_rz(v & 0xFFFFFF00u), __uint2float_rz(v & 0xFFu));
+}
+
+__device__ __forceinline__ df df_from_i32(int32_t v) {
+    // v = (v & ~0xFF) + (v & 0xFF), both parts exact in FP32
+    const int32_t high = static_cast<int32_t>(static_cast<uint32_t>(v) & 0xFFFFFF00u);
+    return df_two_sum(__int2float_rz(high), __uint2float_rz(static_cast<uint32_t>(v) & 0xFFu));
+}
+
+__device__ __forceinline__ double df_to_double(df x) {
+    return __dadd_rn(static_cast<double>(x.hi), static_cast<double>(x.lo));
+}
+
+// ------------------------------------------------------------------------------------
+// sin and cos of phi = 2 pi u, u = (x + 1/2) 2^-32 for a 32-bit x, in df.
+//
+// Reduction is exact integer arithmetic: the top three bits of x give the octant; phi =
+// j pi/2 +- theta with theta = 2 pi t 2^-32 in [0, pi/4], t the (half-odd) distance to the
+// nearest multiple of pi/2 (t < 2^29).  theta = theta_k + delta with theta_k = k pi/256
+// (k = top 6 bits of t, table of sin/cos of theta_k in df) and 0 <= delta < pi/256; then
+//   sin(delta) = delta (1 - delta^2/6 + delta^4/120),  cos(delta) = 1 - delta^2/2 + delta^4/24,
+// (Taylor; the omitted terms are below 2^-48 relative), the delta^2 terms in df and the
+// delta^4 terms in FP32, and the angle-sum identities combine table and remainder.
+// ------------------------------------------------------------------------------------
+struct SinCosTable {
+    float sh[64], sl[64], ch[64], cl[64];  // sin/cos(k pi/256), k = 0..63, hi and lo parts
+};
+
+// The table lives in shared memory of the kernels that compute in df; each block fills it
+// once (sincospi in FP64 on 64 threads) before its first event.
+static __shared__ SinCosTable s_sincos_table;
+
+__device__ __forceinline__ void df_sincos_table_init() {
+    for (int k = threadIdx.x; k < 64; k += blockDim.x) {
+        double sv, cv;
+        sincospi(static_cast<double>(k) / 256.0, &sv, &cv);
+        const float sh = __double2float_rn(sv), ch = __double2float_rn(cv);
+        s_sincos_table.sh[k] = sh;
+        s_sincos_table.sl[k] = __double2float_rn(sv - static_cast<double>(sh));
+        s_sincos_table.ch[k] = ch;
+        s_sincos_table.cl[k] = __double2float_rn(cv - static_cast<double>(ch));
+    }
+}
+
+__device__ __forceinline__ void df_sincos_2pi_u(uint32_t x, const SinCosTable& T, df* s, df* c) {
+    const uint32_t oct = x >> 29;            // octant 0..7
+    const uint32_t r = x & 0x1FFFFFFFu;      // position inside the octant (29 bits)
+    // distance (in units of 2^-32 turns, times 2 to stay integral) to the nearest multiple of
+    // a quarter turn: even octants measure from the start, odd ones from the end
+    const bool odd = oct & 1u;
+    const uint32_t t2 = odd ? ((0x20000000u - r) << 1) - 1u : (r << 1) + 1u;  // 2 t, < 2^30
+    const uint32_t k = t2 >> 24;             // table index 0..63 (theta_k = k pi/256)
+    const uint32_t rem2 = t2 & 0xFFFFFFu;    // 2 (t - k 2^23), < 2^24: exact in FP32
+    // delta = 2 pi (t - k 2^23) 2^-32 = rem2 * (pi 2^-32)
+    const df pi_scaled{7.31459059988282e-10f, -2.035470133961082e-17f};  // pi 2^-32 (hi + lo)
+    const df minus_sixth{-0.1666666716337204f, 4.967053879312289e-09f};  // -1/6 (hi + lo)
+    const df d = pi_scaled * __uint2float_rn(rem2);
+    const df d2 = d * d;
+    const float d2f = d2.hi;
+    const float d4 = __fmul_rn(d2f, d2f);
+    // sin(delta) = delta - delta^3/6 + delta^5/120 ; cos(delta) = 1 - delta^2/2 + delta^4/24
+    const df sd = d + d * ((d2 * minus_sixth) + df_from_float(__fmul_rn(d4, 1.0f / 120.0f)));
+    const df cd = df_from_float(1.0f) + ((d2 * -0.5f) + df_from_float(__fmul_rn(d4, 1.0f / 24.0f)));
+    const df sk{T.sh[k], T.sl[k]}, ck{T.ch[k], T.cl[k]};
+    const df st = sk * cd + ck * sd;  // sin(theta)
+    const df ct = ck * cd - sk * sd;  // cos(theta)
+    // phi = j pi/2 + theta (even octant) or j pi/2 - theta (odd octant), j = quadrant index
+    const uint32_t j = ((oct + 1u) >> 1) & 3u;
+    const df sp = odd ? -st : st;     // sin(+-theta)
+    // sin(j pi/2 + a), cos(j pi/2 + a) for a = +-theta
+    switch (j) {
+        case 0: *s = sp; *c = ct; break;
+        case 1: *s = ct; *c = -sp; break;
+        case 2: *s = -sp; *c = -ct; break;
+        default: *s = -ct; *c = sp; break;
+    }
+}
+
+}  // namespace hydra

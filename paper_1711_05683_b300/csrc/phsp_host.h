@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 #include <string>
 
@@ -24,6 +25,9 @@ hydra_status make_consts(double M, int n, const double* masses, uint64_t seed, D
 
 // Validate a matrix element id and its parameters and fill both precisions.
 hydra_status make_me(hydra_me_id me, int n, const double* params, int nparams, MEConsts* P);
+
+// Arithmetic of FP64 generation (hydra_set_fp64_arith), shared by single and batched runs.
+extern std::atomic<int> g_fp64_arith;
 
 // Grid for a grid-stride kernel: min(blocks needed, resident blocks per SM x SMs).
 int grid_for(const void* kernel, int block, uint64_t work_items);

@@ -115,3 +115,10 @@ def test_launch_config_validation(L):
     assert L.hydra_set_launch_config(1, 5, 1, 128, 2) == 0
     assert L.hydra_get_launch_config(1, 5, 1, ctypes.byref(b), ctypes.byref(e)) == 0
     assert (b.value, e.value) == (128, 2)
+
+
+def test_fp64_arith_switch(L):
+    assert L.hydra_get_fp64_arith() == 1
+    assert hp.STATUS[L.hydra_set_fp64_arith(7)] == "HYDRA_ERR_INVALID_ARG"
+    assert L.hydra_set_fp64_arith(0) == 0 and L.hydra_get_fp64_arith() == 0
+    assert L.hydra_set_fp64_arith(1) == 0 and L.hydra_get_fp64_arith() == 1

@@ -337,3 +337,27 @@ def test_autotuner_picks_a_valid_shape():
         assert len(r["table"]) == len(autotune.BLOCKS) * len(autotune.EPTS)
     finally:
         hp.set_launch_config(hp.KERNEL_GENERATE, 4, "f32", *saved)
+
+
+# ----------------------------------------------------------------------------- FP64 arithmetics
+@pytest.mark.parametrize("arith", ["native", "double_float"])
+@pytest.mark.parametrize("n", [2, 3, 5, 8, 10])
+def test_fp64_arithmetics_against_oracle(arith, n):
+    """Both FP64 generation arithmetics (FP64 instructions, or double-float pairs on the FP32
+    pipe) stay within 1e-12 of the event scale of the FP64 oracle."""
+    saved = hp.get_fp64_arith()
+    hp.set_fp64_arith(hp.FP64_NATIVE if arith == "native" else hp.FP64_DOUBLE_FLOAT)
+    try:
+        for massive in (False, True):
+            err_p, err_w = compare_events(10.0, workloads.sweep_masses(n, massive), 5003, 77 + n, "f64",
+                                          offset=2 ** 35 + 11)
+            assert err_p <= 1e-12 and err_w <= 1e-12, (arith, n, massive, err_p, err_w)
+    finally:
+        hp.set_fp64_arith(saved)
+
+
+def test_double_float_directions_over_many_angles():
+    """2e5 two-body events (two angle draws each, all octants of the double-float sine and
+    cosine) against the oracle; the error is reported at ~1e-14 of the scale."""
+    err_p, err_w = compare_events(10.0, (0.0, 0.0), 200_000, 4242, "f64")
+    assert err_p <= 1e-13 and err_w <= 1e-13, (err_p, err_w)
