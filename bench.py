@@ -343,7 +343,7 @@ def batch_waves(reqs, arena_bytes=ARENA_BYTES):
     return waves
 
 
-def run_batch_workload(count: int = 4096, reps: int = 2) -> dict:
+def run_batch_workload(count: int = 4096, reps: int = 2, arena_bytes: int = ARENA_BYTES) -> dict:
     """Uneven generate requests (N 2..8, M 1..10 GeV, masses U[0, M/2N], events log-uniform
     1e3..1e7, per-request seeds): one persistent batch launch (graph) per wave against one
     plain launch per request, same waves, same 40 GB output arena (overwritten per wave)."""
@@ -351,8 +351,8 @@ def run_batch_workload(count: int = 4096, reps: int = 2) -> dict:
     import torch
     import paper_1711_05683_b300 as hp
     reqs = workloads.batch_requests(count)
-    waves = batch_waves(reqs)
-    arena = torch.empty(ARENA_BYTES // 4, dtype=torch.float32, device="cuda")
+    waves = batch_waves(reqs, arena_bytes)
+    arena = torch.empty(arena_bytes // 4, dtype=torch.float32, device="cuda")
     base = arena.data_ptr()
     tables = []
     for wave in waves:
@@ -413,7 +413,7 @@ def run_batch_workload(count: int = 4096, reps: int = 2) -> dict:
     del arena
     torch.cuda.empty_cache()
     return {"requests": count, "events": total, "output_bytes": out_bytes, "waves": len(waves),
-            "arena_bytes": ARENA_BYTES,
+            "arena_bytes": arena_bytes,
             "batched_graph": {"events_per_s": total / bw, "s": bw, "device_s": bd,
                               "hbm_gbs": out_bytes / bw / 1e9},
             "batched_no_graph": {"events_per_s": total / gw, "s": gw, "device_s": gd},
@@ -440,11 +440,18 @@ def run_serve_workload(duration_s: float = 30.0, rate_hz: float = 2000.0) -> dic
     plain = serve.PlainServer()
     plain.run(warm)
     res_p = plain.run(reqs, max_wall=duration_s * 3)
-    for r in (res_b, res_p):
+    # the same stream replayed 4x faster (8000 requests/s offered): behaviour under load
+    fast = [r for r in reqs if r.arrival < duration_s / 2]
+    srv = serve.Server()
+    res_b4 = srv.run(fast, time_scale=0.25)
+    srv.close()
+    res_p4 = serve.PlainServer().run(fast, time_scale=0.25, max_wall=duration_s * 2)
+    for r in (res_b, res_p, res_b4, res_p4):
         r.pop("done", None)
     return {"requests": len(reqs), "duration_s": duration_s, "rate_hz": rate_hz,
             "offered_events": sum(r.nevents for r in reqs), "batched": res_b, "plain": res_p,
-            "p99_ratio_plain_over_batched": res_p["p99_ms"] / res_b["p99_ms"] if res_b["p99_ms"] else None}
+            "p99_ratio_plain_over_batched": res_p["p99_ms"] / res_b["p99_ms"] if res_b["p99_ms"] else None,
+            "at_4x_rate": {"requests": len(fast), "rate_hz": 4 * rate_hz, "batched": res_b4, "plain": res_p4}}
 
 
 # ----------------------------------------------------------------------------- CPU oracle arm
@@ -526,6 +533,8 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--batch-count", type=int, default=4096)
+    ap.add_argument("--arena-gb", type=float, default=40.0)
     ap.add_argument("--workload", default="sweep", choices=["sweep", "batch", "serve"])
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     args = ap.parse_args()
@@ -538,7 +547,9 @@ def main():
         hp_build.build()
         torch.cuda.set_device(0)
         hp.lib()
-        print(json.dumps({"workload": "batch", **run_batch_workload()}), flush=True)
+        print(json.dumps({"workload": "batch", **run_batch_workload(args.batch_count, reps=args.steps,
+                                                                   arena_bytes=int(args.arena_gb * 1e9))}),
+              flush=True)
     elif args.workload == "serve":
         import torch
         import paper_1711_05683_b300 as hp

@@ -112,6 +112,11 @@ template <> struct Prec<float> {
         *s = -sn;
         *c = -cs;
     }
+    __device__ static float scale(float x, float pow2) { return x * pow2; }
+    // 1 + cos(theta), 1 - cos(theta), cos(theta) of a cos(theta) draw x (u = (x + 1/2) 2^-32)
+    __device__ static float one_plus_cos(uint32_t x) { return __fmaf_rn(__uint2float_rn(x), 4.656612873077392578125e-10f, 2.3283064365386962890625e-10f); }
+    __device__ static float one_minus_cos(uint32_t x) { return one_plus_cos(~x); }
+    __device__ static float cos_of(uint32_t x) { return __fmaf_rn(__int2float_rn(static_cast<int32_t>(x ^ 0x80000000u)), 4.656612873077392578125e-10f, 2.3283064365386962890625e-10f); }
     using W = float;    // weight accumulation type
     using Out = float;  // stored type
     __device__ static W w_mul(W w, float p) { return w * p; }
@@ -137,6 +142,10 @@ template <> struct Prec<double> {
     __device__ static void sincos_2pi_u(uint32_t x, double* s, double* c) {
         sincospi(__fma_rn(__uint2double_rn(x), 4.656612873077392578125e-10, 2.3283064365386962890625e-10), s, c);
     }
+    __device__ static double scale(double x, double pow2) { return x * pow2; }
+    __device__ static double one_plus_cos(uint32_t x) { return __fma_rn(__uint2double_rn(x), 4.656612873077392578125e-10, 2.3283064365386962890625e-10); }
+    __device__ static double one_minus_cos(uint32_t x) { return one_plus_cos(~x); }
+    __device__ static double cos_of(uint32_t x) { return __fma_rn(__int2double_rn(static_cast<int32_t>(x ^ 0x80000000u)), 4.656612873077392578125e-10, 2.3283064365386962890625e-10); }
     using W = double;
     using Out = double;
     __device__ static W w_mul(W w, double p) { return w * p; }
@@ -156,6 +165,10 @@ template <> struct Prec<double> {
 template <> struct Prec<df> {
     using W = double;
     using Out = double;
+    __device__ static df scale(df x, float pow2) { return df_scale(x, pow2); }
+    __device__ static df one_plus_cos(uint32_t x) { return df_half_odd_u32(x); }
+    __device__ static df one_minus_cos(uint32_t x) { return df_half_odd_u32(~x); }
+    __device__ static df cos_of(uint32_t x) { return df_half_odd_centered(x); }
     __device__ static df u32(uint32_t v) { return df_from_u32(v); }
     __device__ static df i32(int32_t v) { return df_from_i32(v); }
     __device__ static df sqrt_(df v) { return df_sqrt(v); }
@@ -208,8 +221,6 @@ __device__ __forceinline__ void raubold_lynch_group(const DecayConsts& C, const 
     constexpr int kMass = N - 2;
     constexpr int kMassBlocks = (kMass + 3) / 4;
     constexpr int kY = kMass > 0 ? kMass : 1;
-    constexpr R kTwoM31 = R(4.656612873077392578125e-10);  // 2^-31
-    constexpr R kTwoM32 = R(2.3283064365386962890625e-10); // 2^-32
 
     uint32_t y[EPT][kY];
     uint32_t blk[EPT][4];
@@ -288,18 +299,18 @@ __device__ __forceinline__ void raubold_lynch_group(const DecayConsts& C, const 
             Mk_out[q] = Mk;
             // two-body momentum
             const R mk1 = P::m(C, k);
-            const R twoMk = R(2) * Mk;
-            const R twom = R(2) * mk1;
+            const R twoMk = P::scale(Mk, 2.0f);
+            const R twom = P::scale(mk1, 2.0f);
             const R lam = ((gap * (gap + twoMk)) * (gap + twom)) * ((gap + twoMk) + twom);
             const R invM = P::rcp(Mnext[q]);
-            const R p = P::sqrt_(lam) * (R(0.5) * invM);
+            const R p = P::sqrt_(lam) * P::scale(invM, 0.5f);
             w[q] = P::w_mul(w[q], p);
             // isotropic direction of subsystem k in the rest frame of subsystem k+1
             const uint32_t xc = xcs[q];
             const uint32_t xp = xps[q];
-            const R cos_t = P::fma_(P::i32(static_cast<int32_t>(xc ^ 0x80000000u)), kTwoM31, kTwoM32);
-            const R one_m = P::fma_(P::u32(~xc), kTwoM31, kTwoM32);  // 1 - cos(theta)
-            const R one_p = P::fma_(P::u32(xc), kTwoM31, kTwoM32);   // 1 + cos(theta)
+            const R cos_t = P::cos_of(xc);         // 2u - 1
+            const R one_m = P::one_minus_cos(xc);  // 1 - cos(theta)
+            const R one_p = P::one_plus_cos(xc);   // 1 + cos(theta)
             const R sin_t = P::sqrt_(one_m * one_p);
             R sphi, cphi;
             P::sincos_2pi_u(xp, &sphi, &cphi);  // phi = 2 pi u

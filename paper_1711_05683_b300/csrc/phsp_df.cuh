@@ -114,8 +114,43 @@ __device__ __forceinline__ df df_from_i32(int32_t v) {
     return df_two_sum(__int2float_rz(high), __uint2float_rz(static_cast<uint32_t>(v) & 0xFFu));
 }
 
+// FP32 -> FP64 by bit manipulation on the integer pipe (exact for normal numbers; zero and
+// FP32 subnormals, below 2^-126, become a signed zero).  Keeps conversions off B300's narrow
+// FP64 pipe: a stored value costs one DADD instead of two conversions and a DADD.
+__device__ __forceinline__ double f32_to_f64_bits(float f) {
+    const uint32_t b = __float_as_uint(f);
+    const uint32_t sign = b & 0x80000000u;
+    uint32_t hi = (((b & 0x7FFFFFFFu) >> 3) + 0x38000000u) | sign;  // exponent rebias 127 -> 1023
+    uint32_t lo = b << 29;
+    if ((b & 0x7F800000u) == 0u) {
+        hi = sign;
+        lo = 0u;
+    }
+    return __hiloint2double(static_cast<int>(hi), static_cast<int>(lo));
+}
+
+// Nearest double to hi + lo.
 __device__ __forceinline__ double df_to_double(df x) {
-    return __dadd_rn(static_cast<double>(x.hi), static_cast<double>(x.lo));
+    return __dadd_rn(f32_to_f64_bits(x.hi), f32_to_f64_bits(x.lo));
+}
+
+// x * 2^k for an exact power of two (both parts scale exactly).
+__device__ __forceinline__ df df_scale(df x, float pow2) { return df{__fmul_rn(x.hi, pow2), __fmul_rn(x.lo, pow2)}; }
+
+// (x + 1/2) 2^-31 for a 32-bit unsigned x (= 1 + cos(theta) when x is a cos(theta) draw):
+// x + 1/2 = (x & ~0xFF) + ((x & 0xFF) + 1/2), both parts exact in FP32, then an exact scale.
+__device__ __forceinline__ df df_half_odd_u32(uint32_t x) {
+    const float a = __uint2float_rz(x & 0xFFFFFF00u);
+    const float b = __fadd_rn(__uint2float_rz(x & 0xFFu), 0.5f);
+    return df_scale(df_two_sum(a, b), 4.656612873077392578125e-10f);
+}
+
+// (x - 2^31 + 1/2) 2^-31 for a 32-bit unsigned x (= cos(theta) = 2u - 1 exactly)
+__device__ __forceinline__ df df_half_odd_centered(uint32_t x) {
+    const int32_t c = static_cast<int32_t>(x ^ 0x80000000u);
+    const float a = __int2float_rz(static_cast<int32_t>(static_cast<uint32_t>(c) & 0xFFFFFF00u));
+    const float b = __fadd_rn(__uint2float_rz(x & 0xFFu), 0.5f);
+    return df_scale(df_two_sum(a, b), 4.656612873077392578125e-10f);
 }
 
 // ------------------------------------------------------------------------------------
