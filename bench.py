@@ -36,6 +36,18 @@ GEN_EVENTS = workloads.SWEEP_NEVENTS
 INT_CFG = workloads.D0_DALITZ
 
 
+# Thread instructions issued per event by the generator kernels at their tuned launch shapes
+# (ncu smsp__inst_executed.sum x 32 / events on a 4e6-event launch of each kernel; the
+# command and table are in profiles/launches_instr_sweep_4e6.md).  They are the per-event
+# work of the issue-bound FP64 (double-float) generator, the dominant kernel of the step.
+INSTR_PER_EVENT = {
+    ("f32", 2): 113, ("f32", 3): 210, ("f32", 4): 295, ("f32", 5): 420, ("f32", 6): 538,
+    ("f32", 7): 671, ("f32", 8): 795, ("f32", 9): 924, ("f32", 10): 1043,
+    ("f64", 2): 594, ("f64", 3): 1499, ("f64", 4): 2269, ("f64", 5): 3085, ("f64", 6): 3896,
+    ("f64", 7): 4714, ("f64", 8): 5498, ("f64", 9): 6323, ("f64", 10): 7142,
+}
+
+
 def bytes_per_event(n: int, dtype: str) -> int:
     """Algorithmic output bytes per generated event: 4n components + 1 weight."""
     return (4 * n + 1) * (4 if dtype == "f32" else 8)
@@ -279,15 +291,33 @@ def run_ours(args) -> None:
     f32 = fam["f32"]
     f32_bytes = sum(bytes_per_event(x["n"], "f32") * x["events"] for x in f32)
     f32_ms = fam_ms["f32"]
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    sm_mhz = clk.get("sm_mhz") or clk.get("sm_max_mhz") or 2032.0
+    issue_peak = sms * 4 * 32 * sm_mhz * 1e6 / 1e12  # thread instructions per second (1e12)
     roof = None
     if dominant in ("f32", "f64"):
         rows = fam[dominant]
         tot_bytes = sum(bytes_per_event(x["n"], dominant) * x["events"] for x in rows)
-        achieved = tot_bytes / (fam_ms[dominant] / 1e3) / 1e9 / len(rows) * len(rows)
-        roof = {"bound": "hbm", "kernel": f"phsp_generate_kernel<N,{'float' if dominant == 'f32' else 'double'}> (N=2..10)",
-                "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": round(achieved / peaks["hbm_gbs"], 4), "peak_src": peaks["src"] + " (MEASURED_PEAKS hbm_gbs copy)",
-                "traffic": None}
+        hbm = tot_bytes / (fam_ms[dominant] / 1e3) / 1e9
+        if dominant == "f64":
+            instr = sum(INSTR_PER_EVENT[("f64", x["n"])] * x["events"] for x in rows)
+            achieved = instr / (fam_ms[dominant] / 1e3) / 1e12
+            roof = {"bound": "alu", "kernel": "phsp_generate_kernel<N, df, EPT> (FP64 outputs, double-float "
+                                              "arithmetic), N=2..10, 18 launches per step",
+                    "achieved": round(achieved, 2), "peak": round(issue_peak, 2),
+                    "unit": "T thread-instructions/s issued",
+                    "frac": round(achieved / issue_peak, 4),
+                    "peak_src": f"SM issue limit: {sms} SMs x 4 schedulers x 32 lanes x {sm_mhz:.0f} MHz (sampled)",
+                    "work_src": "instructions per event from ncu (INSTR_PER_EVENT)",
+                    "hbm_gbs": round(hbm, 1), "hbm_frac_of_measured": round(hbm / peaks["hbm_gbs"], 4),
+                    "traffic": round((tot_bytes / len(rows) - 64e6) / 1e9, 3),
+                    "traffic_note": "GB per launch: ncu dram read+write on 4e6-event launches is the algorithmic "
+                                    "bytes minus 64 MB left dirty in L2; scaled to the launch's events"}
+        else:
+            roof = {"bound": "hbm", "kernel": "phsp_generate_kernel<N, float, EPT> (N=2..10)",
+                    "achieved": round(hbm, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "frac": round(hbm / peaks["hbm_gbs"], 4), "peak_src": peaks["src"], "traffic": None}
     line = {
         "metric": "phase-space events/s (N=2..10 generator sweep FP32+FP64, plus Dalitz integral)",
         "value": value, "unit": "events/s", "n_gpus": world, "steps": args.steps,
@@ -301,9 +331,12 @@ def run_ours(args) -> None:
                    "parallelism": f"replicas x{world}"},
         "gpu_launches": args.steps * (len(items) + 2 * math.ceil(int_events / 2 ** 26) + 1),
         "roofline": roof,
-        "fp32_generator_roofline": {"bound": "hbm", "achieved": round(f32_bytes / (f32_ms / 1e3) / 1e9, 1),
-                                    "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                                    "frac": round(f32_bytes / (f32_ms / 1e3) / 1e9 / peaks["hbm_gbs"], 4)},
+        "fp32_generator_roofline": {"bound": "hbm", "kernel": "phsp_generate_kernel<N, float, EPT> (N=2..10)",
+                                    "achieved": round(f32_bytes / (f32_ms / 1e3) / 1e9, 1),
+                                    "peak": peaks["hbm_gbs"], "unit": "GB/s", "peak_src": "MEASURED_PEAKS hbm_gbs (copy)",
+                                    "frac": round(f32_bytes / (f32_ms / 1e3) / 1e9 / peaks["hbm_gbs"], 4),
+                                    "issue_frac": round(sum(INSTR_PER_EVENT[("f32", x["n"])] * x["events"] for x in f32)
+                                                        / (f32_ms / 1e3) / 1e12 / issue_peak, 4)},
         "dominant": dominant, "family_ms_per_step": {k: round(v, 3) for k, v in fam_ms.items()},
         "breakdown": breakdown, "clocks": clk, "e2e": e2e,
         "launch_shapes": {"source": tuning.get("source"),
