@@ -63,6 +63,15 @@ def _lib(kind: str = "f64") -> ctypes.CDLL:
                                                         ctypes.c_uint64, ctypes.c_int, dp,
                                                         ctypes.c_int, dp]
             getattr(lib, pfx + "integrate").restype = ctypes.c_int
+            getattr(lib, pfx + "generate_boosted").argtypes = [ctypes.c_double, ctypes.c_int, dp,
+                                                               ctypes.c_uint64, ctypes.c_uint64,
+                                                               ctypes.c_uint64, dp, dp, ctypes.c_uint64,
+                                                               rp, rp]
+            getattr(lib, pfx + "generate_boosted").restype = ctypes.c_int
+            getattr(lib, pfx + "unweight").argtypes = [ctypes.c_double, ctypes.c_int, dp, ctypes.c_uint64,
+                                                       ctypes.c_uint64, ctypes.c_uint64, ctypes.c_double,
+                                                       ctypes.POINTER(ctypes.c_ubyte)]
+            getattr(lib, pfx + "unweight").restype = ctypes.c_int
             getattr(lib, pfx + "me_dalitz_2bw").argtypes = [ctypes.c_double, ctypes.c_double, dp]
             getattr(lib, pfx + "me_dalitz_2bw").restype = ctypes.c_double
             _libs[kind] = lib
@@ -126,6 +135,41 @@ def generate(M: float, masses, nevents: int, seed: int, event_offset: int = 0,
     if rc != 0:
         raise OracleError("invalid decay")
     return out, w
+
+
+def generate_boosted(M: float, masses, nevents: int, seed: int, mother=None, mothers=None,
+                     event_offset: int = 0, kind: str = "f64") -> tuple[np.ndarray, np.ndarray]:
+    """Events of a moving parent: generated at rest, then every daughter boosted to the frame
+    where the parent has momentum `mother` (3 values) or mothers[:, e] (array [3, nevents])."""
+    n = len(masses)
+    dt = np.float64 if kind == "f64" else np.longdouble
+    out = np.empty((n, 4, nevents), dtype=dt)
+    w = np.empty(nevents, dtype=dt)
+    real = ctypes.c_double if kind == "f64" else ctypes.c_longdouble
+    rp, dp = ctypes.POINTER(real), ctypes.POINTER(ctypes.c_double)
+    if mothers is not None:
+        mo = np.ascontiguousarray(mothers, dtype=np.float64)
+        mp, mptr, mld = None, mo.ctypes.data_as(dp), mo.shape[1]
+    else:
+        mo = None
+        mp, mptr, mld = (ctypes.c_double * 3)(*[float(v) for v in mother]), None, 0
+    rc = getattr(_lib(kind), _pfx(kind) + "generate_boosted")(
+        float(M), n, _masses(masses), nevents, seed, event_offset, mp, mptr, mld,
+        out.ctypes.data_as(rp), w.ctypes.data_as(rp))
+    if rc != 0:
+        raise OracleError("invalid decay")
+    return out, w
+
+
+def unweight(M: float, masses, nevents: int, seed: int, w_max: float, event_offset: int = 0) -> np.ndarray:
+    """Accept flags of accept-reject unweighting: keep e when u_e w_max < w_e (u_e = draw 3n-4)."""
+    acc = np.zeros(nevents, dtype=np.uint8)
+    rc = getattr(_lib(), "oracle_unweight")(float(M), len(masses), _masses(masses), nevents, seed,
+                                             event_offset, float(w_max),
+                                             acc.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)))
+    if rc != 0:
+        raise OracleError("invalid arguments")
+    return acc.astype(bool)
 
 
 def integrate_sums(M: float, masses, nevents: int, seed: int, me: int = 0, params=(),

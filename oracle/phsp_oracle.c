@@ -307,3 +307,54 @@ int API(integrate)(double M, int n, const double *masses, uint64_t nevents, uint
     sums[0] = (double)sf; sums[1] = (double)sf2; sums[2] = (double)sw; sums[3] = (double)sw2;
     return 0;
 }
+
+/* ------------------------------------------------------------------------------------ */
+/* Moving mother (Listing 4, Generate(Mother, ...)): each event is generated in the parent */
+/* rest frame as above and every daughter is then taken to the frame in which the parent */
+/* has momentum (px, py, pz) and energy sqrt(M^2 + p^2) by the pure boost of boost().     */
+/* mothers: NULL -> one momentum mother_p[3] for all events; otherwise per-event momenta  */
+/* stored as mothers[c * mld + e], c = x, y, z.                                           */
+/* ------------------------------------------------------------------------------------ */
+int API(generate_boosted)(double M, int n, const double *masses, uint64_t nevents, uint64_t seed,
+                          uint64_t event_offset, const double *mother_p, const double *mothers,
+                          uint64_t mld, real *out, real *w)
+{
+    struct decay D;
+    int rc = setup_decay(&D, M, n, masses);
+    if (rc != 0) return rc;
+    real p[NMAX][4];
+    for (uint64_t e = 0; e < nevents; ++e) {
+        real we = one_event(&D, seed, event_offset + e, p);
+        real P[4];
+        for (int c = 0; c < 3; ++c) P[c + 1] = mothers ? (real)mothers[(uint64_t)c * mld + e] : (real)mother_p[c];
+        P[0] = sqrt(D.M * D.M + P[1] * P[1] + P[2] * P[2] + P[3] * P[3]);
+        for (int i = 0; i < n; ++i) {
+            real lab[4];
+            boost(P, D.M, p[i], lab);
+            for (int c = 0; c < 4; ++c) out[((uint64_t)i * 4 + (uint64_t)c) * nevents + e] = lab[c];
+        }
+        w[e] = we;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Unweighting by accept-reject (section 4.2, "unweighted samples"): event e is kept when */
+/* u_e w_max < w_e, u_e = (x + 1/2) 2^-32 with x the event's draw 3n-4 (the first draw    */
+/* after those of its kinematics).  accept[e] = 1 or 0.  The weights are the oracle's.     */
+/* ------------------------------------------------------------------------------------ */
+int API(unweight)(double M, int n, const double *masses, uint64_t nevents, uint64_t seed,
+                  uint64_t event_offset, double w_max, unsigned char *accept)
+{
+    struct decay D;
+    int rc = setup_decay(&D, M, n, masses);
+    if (rc != 0) return rc;
+    if (!(w_max > 0.0)) return -1;
+    real p[NMAX][4];
+    for (uint64_t e = 0; e < nevents; ++e) {
+        real we = one_event(&D, seed, event_offset + e, p);
+        real u = uniform_of(API(draw)(seed, event_offset + e, 3 * n - 4));
+        accept[e] = (unsigned char)(u * (real)w_max < we);
+    }
+    return 0;
+}

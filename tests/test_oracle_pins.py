@@ -282,3 +282,91 @@ def test_near_threshold_stays_physical():
         np.testing.assert_allclose(tot[0], M, atol=1e-13 * M)
         for i, m in enumerate(masses):
             np.testing.assert_allclose(minkowski2(p[i].T), m * m, rtol=0, atol=1e-12 * M * M)
+
+
+# ----------------------------------------------------------------------------- moving mother
+def lorentz_matrix(P, M):
+    """4x4 matrix of the pure boost that takes the rest frame of mass M to 4-momentum P
+    (Lambda^0_0 = gamma, Lambda^0_i = gamma beta_i, Lambda^i_j = delta_ij + (gamma-1) b_i b_j)."""
+    gamma = P[0] / M
+    beta = np.asarray(P[1:]) / P[0]
+    b2 = beta @ beta
+    L = np.eye(4)
+    L[0, 0] = gamma
+    L[0, 1:] = L[1:, 0] = gamma * beta
+    if b2 > 0:
+        L[1:, 1:] += (gamma - 1.0) * np.outer(beta, beta) / b2
+    return L
+
+
+@pytest.mark.parametrize("n", [2, 3, 6, 10])
+def test_boosted_events_are_the_rest_frame_events_boosted(n):
+    rng = np.random.default_rng(300 + n)
+    M, masses = workloads.random_decay(rng, n)
+    mother = (1.3 * M, -0.7 * M, 2.1 * M)
+    P = np.array([math.sqrt(M * M + sum(v * v for v in mother)), *mother])
+    lab, w_lab = oracle.generate_boosted(M, masses, 200, seed=5, mother=mother)
+    rest, w_rest = oracle.generate(M, masses, 200, seed=5)
+    assert np.array_equal(w_lab, w_rest)  # weights are Lorentz invariant
+    Linv = lorentz_matrix(np.array([P[0], *(-P[1:])]), M)  # inverse boost
+    back = np.einsum("ab,ibe->iae", Linv, lab)
+    np.testing.assert_allclose(back, rest, rtol=0, atol=1e-12 * P[0])
+    tot = lab.sum(axis=0)
+    np.testing.assert_allclose(tot, np.broadcast_to(P[:, None], tot.shape), rtol=0, atol=1e-12 * P[0])
+    for i in range(n):
+        np.testing.assert_allclose(minkowski2(lab[i].T), masses[i] ** 2, rtol=0, atol=1e-10 * P[0] ** 2)
+    s_lab = minkowski2((lab[0] + lab[-1]).T)
+    s_rest = minkowski2((rest[0] + rest[-1]).T)
+    np.testing.assert_allclose(s_lab, s_rest, rtol=0, atol=1e-10 * P[0] ** 2)
+
+
+def test_per_event_mothers():
+    M, masses = 3.0, (0.2, 0.3, 0.4, 0.5)
+    rng = np.random.default_rng(9)
+    moms = rng.normal(0.0, 5.0, size=(3, 300))
+    lab, _ = oracle.generate_boosted(M, masses, 300, seed=2, mothers=moms)
+    tot = lab.sum(axis=0)
+    E = np.sqrt(M * M + (moms ** 2).sum(axis=0))
+    np.testing.assert_allclose(tot[0], E, rtol=1e-13)
+    np.testing.assert_allclose(tot[1:], moms, rtol=0, atol=1e-12 * E.max())
+    # one event equals the uniform-mother call with that event's momentum
+    one, _ = oracle.generate_boosted(M, masses, 1, seed=2, mother=tuple(moms[:, 7]), event_offset=7)
+    np.testing.assert_allclose(one[:, :, 0], lab[:, :, 7], rtol=0, atol=1e-13 * E[7])
+
+
+# ----------------------------------------------------------------------------- unweighting
+def test_unweighting_acceptance_rate_and_flat_dalitz_density():
+    """Accept-reject against w_max keeps each event with probability w/w_max: the accepted
+    fraction is E[w]/w_max, and the accepted (unweighted) 3-body events are uniform in the
+    Dalitz plane (chi^2 of counts against bin area, bins inside the boundary)."""
+    cfg = workloads.B_TO_JPSI_K_PI
+    M, (m1, m2, m3) = cfg["M"], cfg["masses"]
+    nev = 600_000
+    p, w = oracle.generate(M, cfg["masses"], nev, seed=11)
+    w_max = float(w.max()) * 1.0001
+    acc = oracle.unweight(M, cfg["masses"], nev, seed=11, w_max=w_max)
+    rate = w.mean() / w_max
+    k = acc.sum()
+    assert abs(k - nev * rate) < 5 * math.sqrt(nev * rate * (1 - rate)), (k, nev * rate)
+    s12 = minkowski2((p[0] + p[1]).T)[acc]
+    s23 = minkowski2((p[1] + p[2]).T)[acc]
+    lo12, hi12 = (m1 + m2) ** 2, (M - m3) ** 2
+    lo23, hi23 = (m2 + m3) ** 2, (M - m1) ** 2
+    nb = 16
+    e12, e23 = np.linspace(lo12, hi12, nb + 1), np.linspace(lo23, hi23, nb + 1)
+    cnt, _, _ = np.histogram2d(s12, s23, bins=[e12, e23])
+    area_tot = R3_quad(M, cfg["masses"]) * 4 * M * M / math.pi ** 2
+    area = (e12[1] - e12[0]) * (e23[1] - e23[0])
+    expect = k * area / area_tot
+
+    def inside(a, b):
+        lo, hi = dalitz_s23_range(M, m1, m2, m3, a)
+        return lo12 < a < hi12 and lo < b < hi
+
+    chi2, dof = 0.0, 0
+    for i in range(nb):
+        for j in range(nb):
+            if all(inside(e12[i + a], e23[j + b]) for a in (0, 1) for b in (0, 1)):
+                chi2 += (cnt[i, j] - expect) ** 2 / expect
+                dof += 1
+    assert dof > 50 and stats.chi2.sf(chi2, dof) > 1e-3, (chi2, dof)
