@@ -138,6 +138,49 @@ hydra_status hydra_phsp_generate_host(double M, int n, const double *masses, uin
                                       hydra_stream_t stream);
 
 /*
+ * Events of a moving parent (Listing 4, Generate(Mother, ...)): each event is generated in
+ * the parent rest frame exactly as hydra_phsp_generate generates it, then every daughter is
+ * taken to the frame where the parent has momentum p (energy sqrt(M^2 + p^2)) by the pure
+ * boost E' = (P0 E + P.p)/M, p' = p + P (E' + E)/(P0 + M).  Weights are Lorentz invariant and
+ * unchanged.  Give exactly one of:
+ *   mother_p   host array of 3 doubles: one parent momentum for every event;
+ *   mothers    device array [3][mld] of dtype: the momentum of event e's parent at
+ *              mothers[c*mld + e] (c = x, y, z), mld >= nevents.
+ * Other arguments, layout and errors as hydra_phsp_generate.  Asynchronous.
+ */
+hydra_status hydra_phsp_generate_boosted(double M, int n, const double *masses, uint64_t nevents,
+                                         uint64_t seed, uint64_t event_offset, hydra_dtype dtype,
+                                         const double *mother_p, const void *mothers, uint64_t mld,
+                                         void *out, uint64_t ld, void *weights, hydra_stream_t stream);
+
+/*
+ * Unweighting by accept-reject (section 4.2, "unweighted samples"): event e (counter-event
+ * index event_offset + e, with n daughters and key `seed`) is kept when u_e w_max < w_e, where
+ * u_e = (x + 1/2) 2^-32 and x is the event's draw 3n-4, the first draw after those of its
+ * kinematics; the product and the comparison are in the weights' precision.
+ *   weights     device array of nevents dtype values (from hydra_phsp_generate)
+ *   w_max       the bound; <= 0 uses the largest weight of the sample
+ *   indices     device array with room for nevents int64: receives the kept event indices
+ *               in increasing order (deterministic)
+ *   naccepted   host: number of kept events; w_max_used (host, optional): the bound used
+ * Blocks until the count is on the host.  Errors: UNSUPPORTED_N, INVALID_ARG, OOM, CUDA.
+ */
+hydra_status hydra_phsp_unweight(int n, uint64_t nevents, uint64_t seed, uint64_t event_offset,
+                                 hydra_dtype dtype, const void *weights, double w_max,
+                                 int64_t *indices, uint64_t *naccepted, double *w_max_used,
+                                 hydra_stream_t stream);
+
+/*
+ * Copy selected events (e.g. the kept events of hydra_phsp_unweight) into a compact SoA
+ * buffer: dst[(i*4 + c)*dst_ld + j] = src[(i*4 + c)*src_ld + indices[j]] for j < count, and
+ * dst_weights[j] = src_weights[indices[j]] when both weight pointers are non-NULL.  Device
+ * buffers of dtype; dst_ld >= count.  Asynchronous.  Errors: UNSUPPORTED_N, INVALID_ARG, CUDA.
+ */
+hydra_status hydra_phsp_gather(int n, hydra_dtype dtype, const void *src, uint64_t src_ld,
+                               const void *src_weights, const int64_t *indices, uint64_t count,
+                               void *dst, uint64_t dst_ld, void *dst_weights, hydra_stream_t stream);
+
+/*
  * Phase-space integral of f = w |ME|^2 over nevents events (section 3, "phase-space Monte
  * Carlo integration"; the events are those hydra_phsp_generate would produce for the same
  * seed and event_offset, computed on the device and never stored).

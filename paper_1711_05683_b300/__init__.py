@@ -75,6 +75,9 @@ def lib() -> ctypes.CDLL:
         L.hydra_phsp_integrate_noalloc.argtypes = L.hydra_phsp_integrate.argtypes
         L.hydra_set_launch_config.argtypes = [i, i, i, i, i]
         L.hydra_set_fp64_arith.argtypes = [i]
+        L.hydra_phsp_generate_boosted.argtypes = [d, i, dp, u64, u64, u64, i, dp, vp, u64, vp, u64, vp, vp]
+        L.hydra_phsp_unweight.argtypes = [i, u64, u64, u64, i, vp, d, vp, ctypes.POINTER(u64), dp, vp]
+        L.hydra_phsp_gather.argtypes = [i, i, vp, u64, vp, vp, u64, vp, u64, vp, vp]
         L.hydra_get_fp64_arith.restype = i
         L.hydra_batch_create.argtypes = [i, u64, ctypes.POINTER(vp)]
         L.hydra_batch_run.argtypes = [vp, vp, i, i, vp]
@@ -84,6 +87,7 @@ def lib() -> ctypes.CDLL:
         for name in ("hydra_phsp_volume_factor", "hydra_phsp_generate", "hydra_phsp_integrate",
                      "hydra_phsp_draws", "hydra_phsp_generate_host", "hydra_phsp_integrate_noalloc",
                      "hydra_set_launch_config", "hydra_get_launch_config", "hydra_set_fp64_arith",
+                     "hydra_phsp_generate_boosted", "hydra_phsp_unweight", "hydra_phsp_gather",
                      "hydra_batch_create",
                      "hydra_batch_run", "hydra_batch_result", "hydra_batch_destroy", "hydra_shutdown"):
             getattr(L, name).restype = i
@@ -174,6 +178,57 @@ def generate(M: float, masses, nevents: int, seed: int, *, dtype="f32", event_of
     generate_into(M, masses, nevents, seed, out, w, dtype=dtype, event_offset=event_offset,
                   stream=stream)
     return out, w[:nevents]
+
+
+def generate_boosted(M: float, masses, nevents: int, seed: int, *, mother=None, mothers=None,
+                     dtype="f32", event_offset: int = 0, stream=None):
+    """Events of a moving parent (Listing 4, Generate(Mother, ...)): `mother` is one momentum
+    (px, py, pz) for all events, or `mothers` a device tensor [3, >= nevents] of per-event
+    momenta in the output dtype.  Returns (p, w) like generate()."""
+    import torch
+    code = _dtype_code(dtype)
+    tdt = torch.float32 if code == F32 else torch.float64
+    ld = padded_ld(nevents)
+    out = torch.empty((len(masses), 4, ld), dtype=tdt, device="cuda")
+    w = torch.empty((ld,), dtype=tdt, device="cuda")
+    mp = (ctypes.c_double * 3)(*[float(v) for v in mother]) if mother is not None else None
+    mptr = ctypes.c_void_p(mothers.data_ptr()) if mothers is not None else None
+    mld = int(mothers.shape[-1]) if mothers is not None else 0
+    _check(lib().hydra_phsp_generate_boosted(float(M), len(masses), _dbl(masses), int(nevents), int(seed),
+                                             int(event_offset), code, mp, mptr, mld,
+                                             ctypes.c_void_p(out.data_ptr()), ld,
+                                             ctypes.c_void_p(w.data_ptr()), _stream_handle(stream)))
+    return out, w[:nevents]
+
+
+def unweight(n: int, weights, seed: int, *, w_max: float = 0.0, dtype="f32", event_offset: int = 0,
+             stream=None):
+    """Accept-reject unweighting of the events whose weights are `weights` (device tensor):
+    returns (indices of kept events as an int64 device tensor, w_max used)."""
+    import torch
+    nev = int(weights.shape[0])
+    idx = torch.empty(max(1, nev), dtype=torch.int64, device="cuda")
+    cnt = ctypes.c_uint64()
+    used = ctypes.c_double()
+    _check(lib().hydra_phsp_unweight(int(n), nev, int(seed), int(event_offset), _dtype_code(dtype),
+                                     ctypes.c_void_p(weights.data_ptr()), float(w_max),
+                                     ctypes.c_void_p(idx.data_ptr()), ctypes.byref(cnt), ctypes.byref(used),
+                                     _stream_handle(stream)))
+    return idx[: cnt.value], used.value
+
+
+def gather(p, w, indices, *, dtype="f32", stream=None):
+    """Compact events p[:, :, indices] (and w[indices]) with the library's gather kernel."""
+    import torch
+    n, cnt = int(p.shape[0]), int(indices.shape[0])
+    ld = padded_ld(cnt)
+    dst = torch.empty((n, 4, ld), dtype=p.dtype, device="cuda")
+    dw = torch.empty(ld, dtype=p.dtype, device="cuda")
+    _check(lib().hydra_phsp_gather(n, _dtype_code(dtype), ctypes.c_void_p(p.data_ptr()), int(p.shape[-1]),
+                                   ctypes.c_void_p(w.data_ptr()), ctypes.c_void_p(indices.data_ptr()), cnt,
+                                   ctypes.c_void_p(dst.data_ptr()), ld, ctypes.c_void_p(dw.data_ptr()),
+                                   _stream_handle(stream)))
+    return dst[:, :, :cnt], dw[:cnt]
 
 
 def integrate(M: float, masses, nevents: int, seed: int, *, kin_dtype="f32", me: int = ME_FLAT,

@@ -11,7 +11,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "libhydra_phsp.so")
-SOURCES = [os.path.join(CSRC, "phsp.cu"), os.path.join(CSRC, "phsp_batch.cu")]
+SOURCES = [os.path.join(CSRC, "phsp.cu"), os.path.join(CSRC, "phsp_batch.cu"),
+           os.path.join(CSRC, "phsp_extras.cu")]
 DEPS = SOURCES + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))] + \
     [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE) if f.endswith(".h")]
 
@@ -23,13 +24,23 @@ def nvcc() -> str:
     raise RuntimeError("nvcc not found: the CUDA toolkit is required to build libhydra_phsp.so")
 
 
+OBJDIR = os.path.join(PKG, "_build")
+# -fmad=false: no implicit contraction; the kernels write every fused multiply-add out, so
+# each event's rounding is fixed by the source at every launch shape.
+CFLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-fmad=false",
+          "-std=c++17", "-Xcompiler", "-fPIC,-O2", "-I", INCLUDE]
+
+
 def command(out: str = LIB, extra: list[str] | None = None) -> list[str]:
-    # -fmad=false: no implicit contraction; the kernels write every fused multiply-add out,
-    # so each event's rounding is fixed by the source at every launch shape.
-    return [nvcc(), "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo",
-            "-fmad=false", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "-shared", "-cudart", "shared",
-            "-I", INCLUDE, "-Xlinker", "-rpath,/usr/local/cuda/lib64",
+    """One-step build command (all sources, one nvcc invocation)."""
+    return [nvcc(), *CFLAGS, "-shared", "-cudart", "shared", "-Xlinker", "-rpath,/usr/local/cuda/lib64",
             *(extra or []), "-o", out, *SOURCES]
+
+
+def _compile(src: str, extra) -> str:
+    obj = os.path.join(OBJDIR, os.path.basename(src) + ".o")
+    subprocess.check_call([nvcc(), *CFLAGS, *(extra or []), "-c", "-o", obj, src])
+    return obj
 
 
 def needs_build() -> bool:
@@ -40,10 +51,17 @@ def needs_build() -> bool:
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile the translation units in parallel, then link libhydra_phsp.so."""
     if force or needs_build():
+        from concurrent.futures import ThreadPoolExecutor
+        os.makedirs(OBJDIR, exist_ok=True)
+        extra = ["-Xptxas", "-v"] if verbose else None
+        with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
+            objs = list(ex.map(lambda src: _compile(src, extra), SOURCES))
         tmp = LIB + ".tmp"
-        cmd = command(tmp, ["-Xptxas", "-v"] if verbose else None)
-        subprocess.check_call(cmd)
+        subprocess.check_call([nvcc(), "-gencode", "arch=compute_103a,code=sm_103a", "-shared",
+                               "-cudart", "shared", "-Xlinker", "-rpath,/usr/local/cuda/lib64",
+                               "-o", tmp, *objs])
         os.replace(tmp, LIB)
     return LIB
 

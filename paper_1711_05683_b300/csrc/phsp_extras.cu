@@ -1,0 +1,474 @@
+// phsp_extras.cu -- moving parents, unweighted samples and event compaction (section 4.2:
+// Listing 4's Generate(Mother, ...) and "weighted and unweighted samples").
+//
+//   phsp_generate_boost_kernel<N, R, EPT>  the generator of phsp.cu whose sink takes every
+//                                          daughter from the parent rest frame to the lab by
+//                                          the pure boost to the parent's momentum (one for
+//                                          all events, or one per event read from HBM)
+//   unweight_max / unweight_count / unweight_scan / unweight_write
+//                                          accept-reject against w_max: event e is kept when
+//                                          u_e w_max < w_e (u_e its draw 3n-4); indices of the
+//                                          kept events are written in event order (stable,
+//                                          deterministic: counts per 4096-event tile, an
+//                                          exclusive scan, ranks by warp ballots)
+//   gather_events                          copies kept events into a compact SoA buffer
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <mutex>
+#include <type_traits>
+#include <vector>
+
+#include "hydra_phsp.h"
+#include "phsp_device.cuh"
+#include "phsp_host.h"
+
+namespace hydra {
+
+// ------------------------------------------------------------------------------------
+// Moving parent
+// ------------------------------------------------------------------------------------
+template <typename R> __device__ __forceinline__ R from_out(typename Prec<R>::Out v);
+template <> __device__ __forceinline__ float from_out<float>(float v) { return v; }
+template <> __device__ __forceinline__ double from_out<double>(double v) { return v; }
+template <> __device__ __forceinline__ df from_out<df>(double v) {
+    const float h = __double2float_rn(v);
+    return df{h, __double2float_rn(v - static_cast<double>(h))};
+}
+
+// Pure boost of each daughter from the parent rest frame to the frame where the parent has
+// 4-momentum (P0, P) and mass M:  E' = (P0 E + P.p)/M,  p' = p + P (E' + E)/(P0 + M).
+template <typename R, int EPT>
+struct BoostSink {
+    StoreSink<R, EPT> inner;
+    R P0[EPT], Px[EPT], Py[EPT], Pz[EPT], invPM[EPT];
+    R invM;
+    __device__ __forceinline__ void subsystem_mass(int, const R (&)[EPT]) {}
+    __device__ __forceinline__ void daughter(int i, const R (&E)[EPT], const R (&px)[EPT],
+                                             const R (&py)[EPT], const R (&pz)[EPT]) {
+        using P = Prec<R>;
+        R oE[EPT], ox[EPT], oy[EPT], oz[EPT];
+#pragma unroll
+        for (int q = 0; q < EPT; ++q) {
+            const R bp = P::fma_(Pz[q], pz[q], P::fma_(Py[q], py[q], Px[q] * px[q]));
+            const R E1 = P::fma_(P0[q], E[q], bp) * invM;
+            const R f = (E1 + E[q]) * invPM[q];
+            oE[q] = E1;
+            ox[q] = P::fma_(f, Px[q], px[q]);
+            oy[q] = P::fma_(f, Py[q], py[q]);
+            oz[q] = P::fma_(f, Pz[q], pz[q]);
+        }
+        inner.daughter(i, oE, ox, oy, oz);
+    }
+    __device__ __forceinline__ void weight(const typename Prec<R>::W (&w)[EPT]) { inner.weight(w); }
+};
+
+// Events e0 .. e0+E-1 of a moving parent: load (or take) each parent momentum, form
+// P0 = sqrt(M^2 + p^2) and 1/(P0 + M), run the event group with the boosting sink.
+template <int N, typename R, int E>
+__device__ __forceinline__ void boosted_group(const DecayConsts& C, uint64_t e0, uint64_t event_offset,
+                                              typename Prec<R>::Out* out, uint64_t ld, typename Prec<R>::Out* weights,
+                                              const typename Prec<R>::Out* mothers, uint64_t mld,
+                                              const R (&U)[3], R M, R M2, R invM) {
+    using P = Prec<R>;
+    BoostSink<R, E> sink{StoreSink<R, E>{out + e0, weights + e0, ld}};
+    sink.invM = invM;
+    uint64_t ev[E];
+#pragma unroll
+    for (int q = 0; q < E; ++q) {
+        ev[q] = event_offset + e0 + q;
+        R px = U[0], py = U[1], pz = U[2];
+        if (mothers) {
+            px = from_out<R>(mothers[e0 + q]);
+            py = from_out<R>(mothers[mld + e0 + q]);
+            pz = from_out<R>(mothers[2 * mld + e0 + q]);
+        }
+        const R P0 = P::sqrt_(P::fma_(pz, pz, P::fma_(py, py, P::fma_(px, px, M2))));
+        sink.P0[q] = P0;
+        sink.Px[q] = px;
+        sink.Py[q] = py;
+        sink.Pz[q] = pz;
+        sink.invPM[q] = P::rcp(P0 + M);
+    }
+    raubold_lynch_group<N, R, E>(C, ev, sink);
+}
+
+// mothers: per-event parent momenta [3][mld] of the output type, or NULL for the single
+// momentum (ux, uy, uz).  Groups of EPT consecutive events; the ragged tail one by one.
+template <int N, typename R, int EPT>
+__global__ void __launch_bounds__(512) phsp_generate_boost_kernel(
+    const __grid_constant__ DecayConsts C, uint64_t nevents, uint64_t event_offset,
+    typename Prec<R>::Out* __restrict__ out, uint64_t ld, typename Prec<R>::Out* __restrict__ weights,
+    const typename Prec<R>::Out* __restrict__ mothers, uint64_t mld, double ux, double uy, double uz) {
+    using P = Prec<R>;
+    using Out = typename P::Out;
+    if constexpr (std::is_same<R, df>::value) {
+        df_sincos_table_init();
+        __syncthreads();
+    }
+    const R M = P::M(C);
+    const R invM = P::rcp(M);
+    const R M2 = M * M;
+    const R U[3] = {from_out<R>(static_cast<Out>(ux)), from_out<R>(static_cast<Out>(uy)),
+                    from_out<R>(static_cast<Out>(uz))};
+    const uint64_t tid = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+    const uint64_t groups = nevents / EPT;
+    for (uint64_t g = tid; g < groups; g += stride)
+        boosted_group<N, R, EPT>(C, g * EPT, event_offset, out, ld, weights, mothers, mld, U, M, M2, invM);
+    if constexpr (EPT > 1) {
+        const uint64_t e = groups * EPT + tid;
+        if (e < nevents)
+            boosted_group<N, R, 1>(C, e, event_offset, out, ld, weights, mothers, mld, U, M, M2, invM);
+    }
+}
+
+template <typename R, int EPT>
+static const void* boost_kernel_n(int n) {
+    switch (n) {
+        case 2: return reinterpret_cast<const void*>(&phsp_generate_boost_kernel<2, R, EPT>);
+        case 3: return reinterpret_cast<const void*>(&phsp_generate_boost_kernel<3, R, EPT>);
+        case 4: return reinterpret_cast<const void*>(&phsp_generate_boost_kernel<4, R, EPT>);
+        case 5: return reinterpret_cast<const void*>(&phsp_generate_boost_kernel<5, R, EPT>);
+        case 6: return reinterpret_cast<const void*>(&phsp_generate_boost_kernel<6, R, EPT>);
+        case 7: return reinterpret_cast<const void*>(&phsp_generate_boost_kernel<7, R, EPT>);
+        case 8: return reinterpret_cast<const void*>(&phsp_generate_boost_kernel<8, R, EPT>);
+        case 9: return reinterpret_cast<const void*>(&phsp_generate_boost_kernel<9, R, EPT>);
+        case 10: return reinterpret_cast<const void*>(&phsp_generate_boost_kernel<10, R, EPT>);
+    }
+    return nullptr;
+}
+
+// ------------------------------------------------------------------------------------
+// Unweighting
+// ------------------------------------------------------------------------------------
+constexpr int kUwBlock = 256;
+constexpr int kUwPerThread = 16;
+constexpr int kUwTile = kUwBlock * kUwPerThread;  // 4096 events per block tile
+
+// Largest weight (order-preserving integer bits of non-negative FP32 / FP64 values).
+template <typename T>
+__global__ void __launch_bounds__(kUwBlock) unweight_max(const T* __restrict__ w, uint64_t nevents,
+                                                         unsigned long long* __restrict__ out_bits) {
+    unsigned long long best = 0;
+    for (uint64_t e = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < nevents;
+         e += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
+        unsigned long long b;
+        if constexpr (sizeof(T) == 4) b = __float_as_uint(fmaxf(w[e], 0.0f));
+        else b = static_cast<unsigned long long>(__double_as_longlong(fmax(w[e], 0.0)));
+        best = b > best ? b : best;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const unsigned long long o = __shfl_xor_sync(0xffffffffu, best, off);
+        best = o > best ? o : best;
+    }
+    if ((threadIdx.x & 31) == 0) atomicMax(out_bits, best);
+}
+
+// Accept decision of event e (kinematic draws 0..3n-5, the accept draw is 3n-4).
+template <typename T>
+__device__ __forceinline__ bool accept_event(const DecayConsts& C, int draw, uint64_t ev, T w, T w_max) {
+    uint32_t x[4];
+    philox4x32_10(static_cast<uint32_t>(ev), static_cast<uint32_t>(ev >> 32), draw / 4, 0u, C.rk0, C.rk1, x);
+    const uint32_t xd = x[draw % 4];
+    if constexpr (sizeof(T) == 4) {
+        const float u = __fmaf_rn(__uint2float_rn(xd), 2.3283064365386962890625e-10f, 1.16415321826934814453125e-10f);
+        return __fmul_rn(u, w_max) < w;
+    } else {
+        const double u = __fma_rn(__uint2double_rn(xd), 2.3283064365386962890625e-10, 1.16415321826934814453125e-10);
+        return __dmul_rn(u, w_max) < w;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ T bits_to_value(unsigned long long b) {
+    if constexpr (sizeof(T) == 4) return __uint_as_float(static_cast<uint32_t>(b));
+    else return __longlong_as_double(static_cast<long long>(b));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kUwBlock) unweight_count(const __grid_constant__ DecayConsts C, int draw,
+                                                           const T* __restrict__ w, uint64_t nevents,
+                                                           uint64_t event_offset,
+                                                           const unsigned long long* __restrict__ wmax_bits,
+                                                           uint32_t* __restrict__ tile_counts) {
+    __shared__ uint32_t warp_cnt[kUwBlock / 32];
+    const T w_max = bits_to_value<T>(*wmax_bits);
+    const uint64_t base = static_cast<uint64_t>(blockIdx.x) * kUwTile;
+    uint32_t cnt = 0;
+    for (int j = 0; j < kUwPerThread; ++j) {
+        const uint64_t e = base + static_cast<uint64_t>(j * kUwBlock + threadIdx.x);
+        if (e < nevents && accept_event<T>(C, draw, event_offset + e, w[e], w_max)) ++cnt;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, off);
+    if ((threadIdx.x & 31) == 0) warp_cnt[threadIdx.x >> 5] = cnt;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t s = 0;
+        for (int i = 0; i < kUwBlock / 32; ++i) s += warp_cnt[i];
+        tile_counts[blockIdx.x] = s;
+    }
+}
+
+// Exclusive scan of the tile counts by one block (each thread scans a contiguous range).
+__global__ void __launch_bounds__(1024) unweight_scan(const uint32_t* __restrict__ counts, uint64_t ntiles,
+                                                      uint64_t* __restrict__ offsets, uint64_t* __restrict__ total) {
+    __shared__ uint64_t part[1024];
+    const uint64_t per = (ntiles + blockDim.x - 1) / blockDim.x;
+    const uint64_t lo = threadIdx.x * per, hi = lo + per < ntiles ? lo + per : ntiles;
+    uint64_t s = 0;
+    for (uint64_t i = lo; i < hi; ++i) s += counts[i];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint64_t acc = 0;
+        for (unsigned i = 0; i < blockDim.x; ++i) {
+            const uint64_t v = part[i];
+            part[i] = acc;
+            acc += v;
+        }
+        *total = acc;
+    }
+    __syncthreads();
+    uint64_t acc = part[threadIdx.x];
+    for (uint64_t i = lo; i < hi; ++i) {
+        offsets[i] = acc;
+        acc += counts[i];
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kUwBlock) unweight_write(const __grid_constant__ DecayConsts C, int draw,
+                                                           const T* __restrict__ w, uint64_t nevents,
+                                                           uint64_t event_offset,
+                                                           const unsigned long long* __restrict__ wmax_bits,
+                                                           const uint64_t* __restrict__ offsets,
+                                                           int64_t* __restrict__ indices) {
+    __shared__ uint32_t warp_cnt[kUwBlock / 32];
+    const T w_max = bits_to_value<T>(*wmax_bits);
+    const uint64_t base = static_cast<uint64_t>(blockIdx.x) * kUwTile;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint64_t run = offsets[blockIdx.x];
+    for (int j = 0; j < kUwPerThread; ++j) {
+        const uint64_t e = base + static_cast<uint64_t>(j * kUwBlock + threadIdx.x);
+        const bool a = e < nevents && accept_event<T>(C, draw, event_offset + e, w[e], w_max);
+        const uint32_t ballot = __ballot_sync(0xffffffffu, a);
+        if (lane == 0) warp_cnt[warp] = __popc(ballot);
+        __syncthreads();
+        uint64_t before = 0, total = 0;
+        for (int i = 0; i < kUwBlock / 32; ++i) {
+            if (i < warp) before += warp_cnt[i];
+            total += warp_cnt[i];
+        }
+        if (a) indices[run + before + __popc(ballot & ((1u << lane) - 1u))] = static_cast<int64_t>(e);
+        run += total;
+        __syncthreads();
+    }
+}
+
+// dst[(i*4 + c)*dst_ld + j] = src[(i*4 + c)*src_ld + idx[j]], dst_w[j] = src_w[idx[j]].
+template <typename T>
+__global__ void __launch_bounds__(256) gather_events(int arrays, const T* __restrict__ src, uint64_t src_ld,
+                                                     const T* __restrict__ src_w, const int64_t* __restrict__ idx,
+                                                     uint64_t count, T* __restrict__ dst, uint64_t dst_ld,
+                                                     T* __restrict__ dst_w) {
+    for (uint64_t j = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; j < count;
+         j += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
+        const uint64_t s = static_cast<uint64_t>(idx[j]);
+        for (int a = 0; a < arrays; ++a) dst[a * dst_ld + j] = src[a * src_ld + s];
+        if (src_w && dst_w) dst_w[j] = src_w[s];
+    }
+}
+
+// Per-device scratch for unweighting: tile counts and offsets, the max and the total.
+struct UwScratch {
+    std::mutex mu;
+    uint32_t* counts = nullptr;
+    uint64_t* offsets = nullptr;
+    uint64_t cap = 0;
+    unsigned long long* wmax = nullptr;  // [0] max bits, [1] total
+    unsigned long long* h = nullptr;     // pinned copy of the two
+};
+static std::mutex g_uw_mu;
+static std::vector<UwScratch*> g_uw;
+
+static UwScratch* uw_scratch() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    std::lock_guard<std::mutex> lk(g_uw_mu);
+    if (static_cast<int>(g_uw.size()) <= dev) g_uw.resize(dev + 1, nullptr);
+    if (!g_uw[dev]) g_uw[dev] = new UwScratch();
+    return g_uw[dev];
+}
+
+}  // namespace hydra
+
+using namespace hydra;
+
+extern "C" {
+
+hydra_status hydra_phsp_generate_boosted(double M, int n, const double* masses, uint64_t nevents,
+                                         uint64_t seed, uint64_t event_offset, hydra_dtype dtype,
+                                         const double* mother_p, const void* mothers, uint64_t mld,
+                                         void* out, uint64_t ld, void* weights, hydra_stream_t stream) {
+    DecayConsts C;
+    hydra_status st = make_consts(M, n, masses, seed, &C);
+    if (st != HYDRA_OK) return st;
+    if (dtype != HYDRA_F32 && dtype != HYDRA_F64) return fail(HYDRA_ERR_INVALID_ARG, "unknown dtype %d", static_cast<int>(dtype));
+    if (event_offset + nevents < event_offset) return fail(HYDRA_ERR_INVALID_ARG, "event_offset + nevents overflows 64 bits");
+    if ((mother_p == nullptr) == (mothers == nullptr))
+        return fail(HYDRA_ERR_INVALID_ARG, "give exactly one of mother_p (one momentum) and mothers (per event)");
+    if (mother_p)
+        for (int c = 0; c < 3; ++c)
+            if (!std::isfinite(mother_p[c])) return fail(HYDRA_ERR_INVALID_ARG, "mother momentum is not finite");
+    if (nevents == 0) return HYDRA_OK;
+    if (!out || !weights) return fail(HYDRA_ERR_INVALID_ARG, "out and weights must not be NULL");
+    if (ld < nevents) return fail(HYDRA_ERR_INVALID_ARG, "ld < nevents");
+    if (mothers && mld < nevents) return fail(HYDRA_ERR_INVALID_ARG, "mld < nevents");
+    if ((reinterpret_cast<uintptr_t>(out) & 15u) || (reinterpret_cast<uintptr_t>(weights) & 15u) || ld % 4 != 0)
+        return fail(HYDRA_ERR_MISALIGNED, "out and weights must be 16-byte aligned and ld a multiple of 4");
+    int block = 256, ept = 1;
+    hydra_get_launch_config(HYDRA_KERNEL_GENERATE, n, dtype, &block, &ept);
+    ept = ept >= 2 ? 2 : 1;
+    const void* k = nullptr;
+    if (dtype == HYDRA_F32) k = ept == 2 ? boost_kernel_n<float, 2>(n) : boost_kernel_n<float, 1>(n);
+    else if (g_fp64_arith.load() == HYDRA_FP64_NATIVE) k = ept == 2 ? boost_kernel_n<double, 2>(n) : boost_kernel_n<double, 1>(n);
+    else k = ept == 2 ? boost_kernel_n<df, 2>(n) : boost_kernel_n<df, 1>(n);
+    double ux = mother_p ? mother_p[0] : 0.0, uy = mother_p ? mother_p[1] : 0.0, uz = mother_p ? mother_p[2] : 0.0;
+    const int grid = grid_for(k, block, (nevents + ept - 1) / ept);
+    void* args[] = {&C, &nevents, &event_offset, &out, &ld, &weights, const_cast<void**>(&mothers), &mld, &ux, &uy, &uz};
+    const cudaError_t err = cudaLaunchKernel(k, dim3(grid), dim3(block), args, 0, reinterpret_cast<cudaStream_t>(stream));
+    if (err != cudaSuccess) return cuda_fail(err, "boosted generate launch");
+    return HYDRA_OK;
+}
+
+hydra_status hydra_phsp_unweight(int n, uint64_t nevents, uint64_t seed, uint64_t event_offset, hydra_dtype dtype,
+                                 const void* weights, double w_max, int64_t* indices, uint64_t* naccepted,
+                                 double* w_max_used, hydra_stream_t stream) {
+    if (n < 2 || n > kNMax) return fail(HYDRA_ERR_UNSUPPORTED_N, "n = %d outside [2, %d]", n, kNMax);
+    if (dtype != HYDRA_F32 && dtype != HYDRA_F64) return fail(HYDRA_ERR_INVALID_ARG, "unknown dtype %d", static_cast<int>(dtype));
+    if (!naccepted) return fail(HYDRA_ERR_INVALID_ARG, "naccepted is NULL");
+    if (event_offset + nevents < event_offset) return fail(HYDRA_ERR_INVALID_ARG, "event_offset + nevents overflows 64 bits");
+    if (!std::isfinite(w_max)) return fail(HYDRA_ERR_INVALID_ARG, "w_max is not finite");
+    *naccepted = 0;
+    if (nevents == 0) return HYDRA_OK;
+    if (!weights || !indices) return fail(HYDRA_ERR_INVALID_ARG, "weights and indices must not be NULL");
+    DecayConsts C;
+    std::memset(&C, 0, sizeof C);
+    uint32_t k0 = static_cast<uint32_t>(seed), k1 = static_cast<uint32_t>(seed >> 32);
+    for (int r = 0; r < 10; ++r) {
+        C.rk0[r] = k0;
+        C.rk1[r] = k1;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    const int draw = 3 * n - 4;
+    UwScratch* s = uw_scratch();
+    if (!s) return fail(HYDRA_ERR_CUDA, "no current CUDA device");
+    std::lock_guard<std::mutex> lk(s->mu);
+    const uint64_t ntiles = (nevents + kUwTile - 1) / kUwTile;
+    cudaError_t err = cudaSuccess;
+    if (!s->wmax) {
+        if (cudaMalloc(&s->wmax, 2 * sizeof(unsigned long long)) != cudaSuccess ||
+            cudaMallocHost(&s->h, 2 * sizeof(unsigned long long)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(HYDRA_ERR_OOM, "unweighting scratch");
+        }
+    }
+    if (ntiles > s->cap) {
+        if (s->counts) cudaFree(s->counts);
+        if (s->offsets) cudaFree(s->offsets);
+        s->counts = nullptr;
+        s->offsets = nullptr;
+        s->cap = 0;
+        if (cudaMalloc(&s->counts, ntiles * sizeof(uint32_t)) != cudaSuccess ||
+            cudaMalloc(&s->offsets, ntiles * sizeof(uint64_t)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(HYDRA_ERR_OOM, "unweighting scratch for %llu tiles", static_cast<unsigned long long>(ntiles));
+        }
+        s->cap = ntiles;
+    }
+    cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+    unsigned long long bits = 0;
+    if (w_max > 0.0) {
+        if (dtype == HYDRA_F32) {
+            const float f = static_cast<float>(w_max);
+            std::memcpy(&bits, &f, 4);
+        } else {
+            std::memcpy(&bits, &w_max, 8);
+        }
+        err = cudaMemcpyAsync(s->wmax, &bits, sizeof bits, cudaMemcpyHostToDevice, cs);
+    } else {
+        err = cudaMemsetAsync(s->wmax, 0, sizeof(unsigned long long), cs);
+        if (err == cudaSuccess) {
+            int dev = 0, sms = 148;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            if (dtype == HYDRA_F32)
+                unweight_max<float><<<sms * 4, kUwBlock, 0, cs>>>(static_cast<const float*>(weights), nevents, s->wmax);
+            else
+                unweight_max<double><<<sms * 4, kUwBlock, 0, cs>>>(static_cast<const double*>(weights), nevents, s->wmax);
+            err = cudaGetLastError();
+        }
+    }
+    if (err != cudaSuccess) return cuda_fail(err, "unweighting max");
+    const unsigned grid = static_cast<unsigned>(ntiles);
+    if (dtype == HYDRA_F32) {
+        unweight_count<float><<<grid, kUwBlock, 0, cs>>>(C, draw, static_cast<const float*>(weights), nevents, event_offset, s->wmax, s->counts);
+    } else {
+        unweight_count<double><<<grid, kUwBlock, 0, cs>>>(C, draw, static_cast<const double*>(weights), nevents, event_offset, s->wmax, s->counts);
+    }
+    unweight_scan<<<1, 1024, 0, cs>>>(s->counts, ntiles, s->offsets, reinterpret_cast<uint64_t*>(s->wmax + 1));
+    if (dtype == HYDRA_F32) {
+        unweight_write<float><<<grid, kUwBlock, 0, cs>>>(C, draw, static_cast<const float*>(weights), nevents, event_offset, s->wmax, s->offsets, indices);
+    } else {
+        unweight_write<double><<<grid, kUwBlock, 0, cs>>>(C, draw, static_cast<const double*>(weights), nevents, event_offset, s->wmax, s->offsets, indices);
+    }
+    err = cudaGetLastError();
+    if (err == cudaSuccess) err = cudaMemcpyAsync(s->h, s->wmax, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, cs);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(cs);
+    if (err != cudaSuccess) return cuda_fail(err, "unweighting");
+    *naccepted = s->h[1];
+    if (w_max_used) {
+        if (dtype == HYDRA_F32) {
+            float f;
+            const uint32_t b32 = static_cast<uint32_t>(s->h[0]);
+            std::memcpy(&f, &b32, 4);
+            *w_max_used = f;
+        } else {
+            std::memcpy(w_max_used, &s->h[0], 8);
+        }
+    }
+    return HYDRA_OK;
+}
+
+hydra_status hydra_phsp_gather(int n, hydra_dtype dtype, const void* src, uint64_t src_ld, const void* src_weights,
+                               const int64_t* indices, uint64_t count, void* dst, uint64_t dst_ld, void* dst_weights,
+                               hydra_stream_t stream) {
+    if (n < 2 || n > kNMax) return fail(HYDRA_ERR_UNSUPPORTED_N, "n = %d outside [2, %d]", n, kNMax);
+    if (dtype != HYDRA_F32 && dtype != HYDRA_F64) return fail(HYDRA_ERR_INVALID_ARG, "unknown dtype %d", static_cast<int>(dtype));
+    if (count == 0) return HYDRA_OK;
+    if (!src || !indices || !dst) return fail(HYDRA_ERR_INVALID_ARG, "NULL buffer");
+    if (dst_ld < count) return fail(HYDRA_ERR_INVALID_ARG, "dst_ld < count");
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const uint64_t need = (count + 255) / 256;
+    const unsigned grid = static_cast<unsigned>(need < static_cast<uint64_t>(sms) * 8 ? need : static_cast<uint64_t>(sms) * 8);
+    cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+    if (dtype == HYDRA_F32)
+        gather_events<float><<<grid, 256, 0, cs>>>(4 * n, static_cast<const float*>(src), src_ld, static_cast<const float*>(src_weights),
+                                                   indices, count, static_cast<float*>(dst), dst_ld, static_cast<float*>(dst_weights));
+    else
+        gather_events<double><<<grid, 256, 0, cs>>>(4 * n, static_cast<const double*>(src), src_ld, static_cast<const double*>(src_weights),
+                                                    indices, count, static_cast<double*>(dst), dst_ld, static_cast<double*>(dst_weights));
+    const cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return cuda_fail(err, "gather launch");
+    return HYDRA_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,92 @@
+"""Moving parents, unweighting and gather (section 4.2: Generate(Mother, ...), "weighted and
+unweighted samples") against the oracle."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
+import paper_1711_05683_b300 as hp  # noqa: E402
+import workloads  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+TOL = {"f64": 1e-12, "f32": 2e-5}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1711_05683_b300 import build as hp_build
+    hp_build.build()
+    torch.cuda.set_device(0)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("n", [2, 3, 7, 10])
+def test_boosted_one_mother(n, dtype):
+    rng = np.random.default_rng(40 + n)
+    M, masses = workloads.random_decay(rng, n)
+    mother = (0.4 * M, -2.5 * M, 1.1 * M)
+    nev = 2001
+    p, w = hp.generate_boosted(M, masses, nev, 9, mother=mother, dtype=dtype, event_offset=5)
+    ref_p, ref_w = oracle.generate_boosted(M, masses, nev, 9, mother=mother, event_offset=5)
+    gp = p[:, :, :nev].double().cpu().numpy()
+    scale = np.maximum(ref_p[:, 0, :].max(axis=0), M)
+    assert (np.abs(gp - ref_p) / scale).max() <= TOL[dtype]
+    np.testing.assert_allclose(w.double().cpu().numpy(), ref_w, rtol=TOL[dtype])
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_boosted_per_event_mothers(dtype):
+    M, masses = 3.0, (0.2, 0.3, 0.4, 0.5, 0.1)
+    nev = 3003
+    rng = np.random.default_rng(3)
+    moms = rng.normal(0.0, 6.0, size=(3, nev))
+    tdt = torch.float32 if dtype == "f32" else torch.float64
+    dm = torch.as_tensor(moms, dtype=tdt, device="cuda").contiguous()
+    p, _ = hp.generate_boosted(M, masses, nev, 4, mothers=dm, dtype=dtype)
+    ref_p, _ = oracle.generate_boosted(M, masses, nev, 4, mothers=dm.double().cpu().numpy())
+    scale = np.maximum(ref_p[:, 0, :].max(axis=0), M)
+    assert (np.abs(p[:, :, :nev].double().cpu().numpy() - ref_p) / scale).max() <= TOL[dtype]
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_unweighting_matches_oracle(dtype):
+    """Kept events are those of the oracle's accept-reject, except where u w_max and w differ
+    by less than the weights' tolerance (there either decision is correct)."""
+    cfg = workloads.B_TO_JPSI_K_PI
+    M, masses, n = cfg["M"], cfg["masses"], 3
+    nev = 100_003
+    p, w = hp.generate(M, masses, nev, 21, dtype=dtype)
+    ref_p, ref_w = oracle.generate(M, masses, nev, 21)
+    w_max = float(ref_w.max()) * 1.0000001
+    idx, used = hp.unweight(n, w, 21, w_max=w_max, dtype=dtype)
+    got = np.zeros(nev, dtype=bool)
+    got[idx.cpu().numpy()] = True
+    acc = oracle.unweight(M, masses, nev, 21, w_max=w_max)
+    u = (np.array([oracle.draw(21, e, 3 * n - 4) for e in range(nev)], dtype=np.float64) + 0.5) / 2 ** 32
+    band = np.abs(u * w_max - ref_w) <= 4 * TOL[dtype] * ref_w + 1e-300
+    assert np.all((got == acc) | band)
+    assert np.all(np.diff(idx.cpu().numpy()) > 0)  # strictly increasing, stable order
+    # the sample's own maximum as the bound
+    idx2, used2 = hp.unweight(n, w, 21, dtype=dtype)
+    assert used2 == pytest.approx(float(w.max()), rel=0, abs=0)
+    assert 0 < len(idx2) < nev
+    # gather: the compacted events are the selected events
+    dst, dw = hp.gather(p, w, idx2, dtype=dtype)
+    assert torch.equal(dst, p[:, :, idx2]) and torch.equal(dw, w[idx2])
+
+
+def test_unweighting_is_deterministic_and_chunkable():
+    """Accept decisions depend only on (seed, event index, w, w_max): two halves with
+    event_offset give the indices of one call."""
+    M, masses = 10.0, workloads.sweep_masses(5, True)
+    nev = 50_000
+    p, w = hp.generate(M, masses, nev, 8, dtype="f64")
+    wm = float(w.max())
+    a, _ = hp.unweight(5, w, 8, w_max=wm, dtype="f64")
+    h = 20_000
+    b1, _ = hp.unweight(5, w[:h].contiguous(), 8, w_max=wm, dtype="f64")
+    b2, _ = hp.unweight(5, w[h:].contiguous(), 8, w_max=wm, dtype="f64", event_offset=h)
+    assert torch.equal(a, torch.cat([b1, b2 + h]))
