@@ -72,6 +72,9 @@ def _lib(kind: str = "f64") -> ctypes.CDLL:
                                                        ctypes.c_uint64, ctypes.c_uint64, ctypes.c_double,
                                                        ctypes.POINTER(ctypes.c_ubyte)]
             getattr(lib, pfx + "unweight").restype = ctypes.c_int
+            getattr(lib, pfx + "evaluate").argtypes = [ctypes.c_int, ctypes.c_uint64, dp, ctypes.c_uint64, dp,
+                                                       ctypes.c_int, dp, ctypes.c_int, dp, dp]
+            getattr(lib, pfx + "evaluate").restype = ctypes.c_int
             getattr(lib, pfx + "me_dalitz_2bw").argtypes = [ctypes.c_double, ctypes.c_double, dp]
             getattr(lib, pfx + "me_dalitz_2bw").restype = ctypes.c_double
             _libs[kind] = lib
@@ -196,6 +199,22 @@ def integrate(M: float, masses, nevents: int, seed: int, me: int = 0, params=(),
     var_mean = (s[1] / n - mean * mean) / (n - 1.0) if nevents > 1 else float("nan")
     return dict(mean=mean, var_mean=var_mean, sum_f=s[0], sum_f2=s[1], sum_w=s[2],
                 sum_w2=s[3], n=nevents)
+
+
+def evaluate(events: np.ndarray, weights: np.ndarray, me: int = 0, params=()) -> tuple[np.ndarray, np.ndarray]:
+    """f_e = w_e |ME|^2 on stored events events[n, 4, nevents] (FP64); returns (values, sums)."""
+    ev = np.ascontiguousarray(events, dtype=np.float64)
+    w = np.ascontiguousarray(weights, dtype=np.float64)
+    n, _, nev = ev.shape
+    vals = np.empty(nev, dtype=np.float64)
+    sums = (ctypes.c_double * 4)()
+    par = (ctypes.c_double * max(1, len(params)))(*[float(p) for p in params])
+    dp = ctypes.POINTER(ctypes.c_double)
+    rc = getattr(_lib(), "oracle_evaluate")(n, nev, ev.ctypes.data_as(dp), nev, w.ctypes.data_as(dp), me,
+                                            par, len(params), vals.ctypes.data_as(dp), sums)
+    if rc != 0:
+        raise OracleError("invalid arguments")
+    return vals, np.array(list(sums))
 
 
 def me_dalitz_2bw(s12: float, s23: float, params) -> float:

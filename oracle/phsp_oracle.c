@@ -358,3 +358,32 @@ int API(unweight)(double M, int n, const double *masses, uint64_t nevents, uint6
     }
     return 0;
 }
+
+/* ------------------------------------------------------------------------------------ */
+/* Model evaluation on stored events (section 4.2, "evaluation of model"; section 3,     */
+/* "parallel function evaluation"): f_e = w_e |ME|^2(p_e) for events given as the         */
+/* structure of arrays ev[(i*4 + c) * ld + e] and weights w[e].  values[e] = f_e (if not  */
+/* NULL); sums[0..3] = (sum f, sum f^2, sum w, sum w^2) in long double.  me as integrate.  */
+/* ------------------------------------------------------------------------------------ */
+int API(evaluate)(int n, uint64_t nevents, const double *ev, uint64_t ld, const double *w, int me,
+                  const double *params, int nparams, double *values, double sums[4])
+{
+    if (n < 2 || n > NMAX) return -1;
+    if (me == 1 && (n != 3 || nparams < 6)) return -1;
+    if (me != 0 && me != 1) return -1;
+    long double sf = 0, sf2 = 0, sw = 0, sw2 = 0;
+    for (uint64_t e = 0; e < nevents; ++e) {
+        real p[NMAX][4];
+        for (int i = 0; i < n; ++i)
+            for (int c = 0; c < 4; ++c) p[i][c] = (real)ev[((uint64_t)i * 4 + (uint64_t)c) * ld + e];
+        real me2 = 1;
+        if (me == 1) me2 = dalitz_2bw(invariant_mass2(p[0], p[1]), invariant_mass2(p[1], p[2]), params);
+        real we = (real)w[e];
+        real f = we * me2;
+        if (values) values[e] = (double)f;
+        sf += f; sf2 += (long double)f * f;
+        sw += we; sw2 += (long double)we * we;
+    }
+    sums[0] = (double)sf; sums[1] = (double)sf2; sums[2] = (double)sw; sums[3] = (double)sw2;
+    return 0;
+}

@@ -370,3 +370,36 @@ def test_unweighting_acceptance_rate_and_flat_dalitz_density():
                 chi2 += (cnt[i, j] - expect) ** 2 / expect
                 dof += 1
     assert dof > 50 and stats.chi2.sf(chi2, dof) > 1e-3, (chi2, dof)
+
+
+def test_evaluate_on_stored_events_equals_integrate():
+    """Evaluating the matrix element on stored events reproduces the integral over the same
+    generated events, and the flat matrix element returns the weights."""
+    d = workloads.D0_DALITZ
+    p, w = oracle.generate(d["M"], d["masses"], 20_000, seed=4)
+    vals, sums = oracle.evaluate(p, w, me=1, params=d["params"])
+    ref = oracle.integrate_sums(d["M"], d["masses"], 20_000, seed=4, me=1, params=d["params"])
+    np.testing.assert_allclose(sums, ref, rtol=1e-13)
+    flat, fs = oracle.evaluate(p, w)
+    assert np.array_equal(flat, w)
+    s12 = minkowski2((p[0] + p[1]).T)
+    s23 = minkowski2((p[1] + p[2]).T)
+    for e in (0, 17, 19_999):
+        assert vals[e] == pytest.approx(w[e] * oracle.me_dalitz_2bw(s12[e], s23[e], d["params"]), rel=1e-12)
+
+
+def test_sequential_decay_composition():
+    """A two-stage decay (daughter 2 of a 3-body decay decays to 2 bodies): the stage-2
+    particles are the decay of the stage-1 daughter in its own frame, so their total
+    4-momentum equals it, their invariant mass is its mass, and all final particles
+    conserve the parent's 4-momentum."""
+    M, m = 5.0, (0.5, 1.2, 0.3)
+    sub = (0.4, 0.6)
+    p1, _ = oracle.generate(M, m, 500, seed=1)
+    moms = p1[1, 1:4, :]  # daughter 2's momenta
+    p2, _ = oracle.generate_boosted(m[1], sub, 500, seed=2, mothers=moms)
+    np.testing.assert_allclose(p2.sum(axis=0), p1[1], rtol=0, atol=1e-12 * M)
+    np.testing.assert_allclose(np.sqrt(minkowski2(p2.sum(axis=0).T)), m[1], rtol=1e-12)
+    final = p1[0] + p1[2] + p2[0] + p2[1]
+    np.testing.assert_allclose(final[0], M, atol=1e-12 * M)
+    np.testing.assert_allclose(final[1:], 0.0, atol=1e-12 * M)
