@@ -345,6 +345,7 @@ def run_ours(args) -> None:
     }
     if not args.no_batch:
         line["batch"] = run_batch_workload()
+        line["extensions"] = run_extras()
     if not args.no_serve:
         line["serve"] = run_serve_workload(duration_s=args.serve_seconds)
     if not args.no_cpu_baseline:
@@ -453,6 +454,43 @@ def run_batch_workload(count: int = 4096, reps: int = 2, arena_bytes: int = AREN
             "plain_launches": {"events_per_s": total / pw, "s": pw, "device_s": pd,
                                "hbm_gbs": out_bytes / pw / 1e9},
             "speedup_vs_plain": pw / bw}
+
+
+# ----------------------------------------------------------------------------- extensions
+def run_extras(nev: int = 100_000_000, reps: int = 3) -> dict:
+    """Events/s of the moving-parent generator (per-event parent momenta read from HBM),
+    accept-reject unweighting and matrix-element evaluation on stored events (FP32, N=3,
+    Dalitz decay, 1e8 events; best of `reps` after one warm-up, CUDA events)."""
+    import torch
+    import paper_1711_05683_b300 as hp
+    d = INT_CFG
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        best = float("inf")
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            best = min(best, a.elapsed_time(b) / 1e3)
+        return best
+
+    moms = torch.randn((3, nev), dtype=torch.float32, device="cuda", generator=torch.Generator("cuda").manual_seed(1))
+    res = {}
+    t = timed(lambda: hp.generate_boosted(d["M"], d["masses"], nev, 3, mothers=moms, dtype="f32"))
+    res["boosted_generate_f32_n3"] = {"events_per_s": nev / t, "hbm_gbs": nev * (52 + 12) / t / 1e9}
+    p, w = hp.generate(d["M"], d["masses"], nev, 3, dtype="f32")
+    t = timed(lambda: hp.unweight(3, w, 3, dtype="f32"))
+    res["unweight_f32_n3"] = {"events_per_s": nev / t, "kept": len(hp.unweight(3, w, 3, dtype="f32")[0])}
+    t = timed(lambda: hp.evaluate(p, w, me=hp.ME_DALITZ_2BW, params=d["params"], dtype="f32"))
+    res["evaluate_dalitz_f32"] = {"events_per_s": nev / t, "hbm_gbs": nev * 52 / t / 1e9}
+    del p, w, moms
+    torch.cuda.empty_cache()
+    return res
 
 
 # ----------------------------------------------------------------------------- serving loop

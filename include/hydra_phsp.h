@@ -171,6 +171,22 @@ hydra_status hydra_phsp_unweight(int n, uint64_t nevents, uint64_t seed, uint64_
                                  hydra_stream_t stream);
 
 /*
+ * Evaluation of a matrix element on stored events (section 4.2, "evaluation of model";
+ * section 3, "parallel function evaluation on multidimensional data-sets"):
+ * f_e = w_e |ME|^2(p_e) with s_ij = (p_i + p_j)^2 formed from the stored 4-vectors.
+ *   events, ld   device SoA [n][4][ld] of dtype (may be NULL for HYDRA_ME_FLAT)
+ *   weights      device array of nevents dtype values
+ *   values       device array receiving f_e (dtype), or NULL
+ *   result       host: mean, variance of the mean and sums of f and w, reduced in the fixed
+ *                tile / segment order of hydra_phsp_integrate (deterministic)
+ * Blocking.  Errors: UNSUPPORTED_N, INVALID_ARG, OOM, CUDA.
+ */
+hydra_status hydra_phsp_evaluate(int n, uint64_t nevents, hydra_dtype dtype, hydra_me_id me,
+                                 const double *params, int nparams, const void *events, uint64_t ld,
+                                 const void *weights, void *values, hydra_integral *result,
+                                 hydra_stream_t stream);
+
+/*
  * Copy selected events (e.g. the kept events of hydra_phsp_unweight) into a compact SoA
  * buffer: dst[(i*4 + c)*dst_ld + j] = src[(i*4 + c)*src_ld + indices[j]] for j < count, and
  * dst_weights[j] = src_weights[indices[j]] when both weight pointers are non-NULL.  Device

@@ -78,6 +78,7 @@ def lib() -> ctypes.CDLL:
         L.hydra_phsp_generate_boosted.argtypes = [d, i, dp, u64, u64, u64, i, dp, vp, u64, vp, u64, vp, vp]
         L.hydra_phsp_unweight.argtypes = [i, u64, u64, u64, i, vp, d, vp, ctypes.POINTER(u64), dp, vp]
         L.hydra_phsp_gather.argtypes = [i, i, vp, u64, vp, vp, u64, vp, u64, vp, vp]
+        L.hydra_phsp_evaluate.argtypes = [i, u64, i, i, dp, i, vp, u64, vp, vp, ctypes.POINTER(Integral), vp]
         L.hydra_get_fp64_arith.restype = i
         L.hydra_batch_create.argtypes = [i, u64, ctypes.POINTER(vp)]
         L.hydra_batch_run.argtypes = [vp, vp, i, i, vp]
@@ -88,6 +89,7 @@ def lib() -> ctypes.CDLL:
                      "hydra_phsp_draws", "hydra_phsp_generate_host", "hydra_phsp_integrate_noalloc",
                      "hydra_set_launch_config", "hydra_get_launch_config", "hydra_set_fp64_arith",
                      "hydra_phsp_generate_boosted", "hydra_phsp_unweight", "hydra_phsp_gather",
+                     "hydra_phsp_evaluate",
                      "hydra_batch_create",
                      "hydra_batch_run", "hydra_batch_result", "hydra_batch_destroy", "hydra_shutdown"):
             getattr(L, name).restype = i
@@ -229,6 +231,36 @@ def gather(p, w, indices, *, dtype="f32", stream=None):
                                    ctypes.c_void_p(dst.data_ptr()), ld, ctypes.c_void_p(dw.data_ptr()),
                                    _stream_handle(stream)))
     return dst[:, :, :cnt], dw[:cnt]
+
+
+def evaluate(p, w, nevents: int | None = None, *, me: int = ME_FLAT, params=(), dtype="f32",
+             want_values: bool = False, stream=None):
+    """f = w |ME|^2 on stored events p [n, 4, ld] with weights w (device tensors); returns
+    (integral dict, values tensor or None)."""
+    import torch
+    nev = int(w.shape[0]) if nevents is None else int(nevents)
+    n = int(p.shape[0])
+    vals = torch.empty(nev, dtype=w.dtype, device="cuda") if want_values else None
+    res = Integral()
+    _check(lib().hydra_phsp_evaluate(n, nev, _dtype_code(dtype), int(me), _dbl(params), len(params),
+                                     ctypes.c_void_p(p.data_ptr()), int(p.shape[-1]),
+                                     ctypes.c_void_p(w.data_ptr()),
+                                     ctypes.c_void_p(vals.data_ptr()) if vals is not None else None,
+                                     ctypes.byref(res), _stream_handle(stream)))
+    return res.as_dict(), vals
+
+
+def generate_sequential(M: float, masses, i: int, sub_masses, nevents: int, seed: int, sub_seed: int, *,
+                        dtype="f32", stream=None):
+    """Sequential decay (section 4.2): the n-body decay of M, then daughter i (mass masses[i])
+    decays to len(sub_masses) bodies in its own frame.  Stage 2 uses the per-event parent
+    momenta read straight from stage 1's SoA rows (px, py, pz of daughter i) and its own key
+    `sub_seed`.  Returns (p1, w1, p2, w2); the event weight is w1 * w2."""
+    p1, w1 = generate(M, masses, nevents, seed, dtype=dtype, stream=stream)
+    moms = p1[i, 1:4]  # [3, ld] view: rows px, py, pz of daughter i, leading dimension ld
+    p2, w2 = generate_boosted(masses[i], sub_masses, nevents, sub_seed, mothers=moms, dtype=dtype,
+                              stream=stream)
+    return p1, w1, p2, w2
 
 
 def integrate(M: float, masses, nevents: int, seed: int, *, kin_dtype="f32", me: int = ME_FLAT,

@@ -24,6 +24,7 @@
 #include "hydra_phsp.h"
 #include "phsp_device.cuh"
 #include "phsp_host.h"
+#include "phsp_integral.cuh"
 
 namespace hydra {
 
@@ -305,6 +306,98 @@ static UwScratch* uw_scratch() {
     return g_uw[dev];
 }
 
+// ------------------------------------------------------------------------------------
+// Model evaluation on stored events: f_e = w_e |ME|^2(p_e), values and the deterministic
+// integral (the tile / segment / fold tree of the generated-event integral).
+// ------------------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ R pair_mass2(const R* __restrict__ ev, uint64_t ld, uint64_t e, int a, int b) {
+    using P = Prec<R>;
+    const R E = ev[(4 * a) * ld + e] + ev[(4 * b) * ld + e];
+    const R x = ev[(4 * a + 1) * ld + e] + ev[(4 * b + 1) * ld + e];
+    const R y = ev[(4 * a + 2) * ld + e] + ev[(4 * b + 2) * ld + e];
+    const R z = ev[(4 * a + 3) * ld + e] + ev[(4 * b + 3) * ld + e];
+    return P::fma_(E, E, -P::fma_(z, z, P::fma_(y, y, x * x)));
+}
+
+template <typename R, int ME>
+__global__ void __launch_bounds__(256) evaluate_tiles(uint64_t nevents, const R* __restrict__ ev, uint64_t ld,
+                                                      const R* __restrict__ w, const __grid_constant__ MEConsts P,
+                                                      R* __restrict__ values, uint64_t tile_begin, uint64_t ntiles,
+                                                      TileSums* __restrict__ partials) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t warp = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = (static_cast<uint64_t>(gridDim.x) * blockDim.x) >> 5;
+    for (uint64_t t = warp; t < ntiles; t += nwarps) {
+        const uint64_t base = (tile_begin + t) * kTileEvents;
+        double af = 0.0, af2 = 0.0, aw = 0.0, aw2 = 0.0;
+        for (int g = 0; g < kLaneIters / kGroupEvents; ++g) {
+            R sf = R(0), sf2 = R(0), sw = R(0), sw2 = R(0);
+            for (int i = 0; i < kGroupEvents; ++i) {
+                const uint64_t e = base + static_cast<uint64_t>(32 * (g * kGroupEvents + i) + lane);
+                if (e < nevents) {
+                    const R we = w[e];
+                    R f = we;
+                    if constexpr (ME == HYDRA_ME_DALITZ_2BW)
+                        f = we * dalitz_2bw<R>(P, pair_mass2<R>(ev, ld, e, 0, 1), pair_mass2<R>(ev, ld, e, 1, 2));
+                    if (values) values[e] = f;
+                    sf += f;
+                    sf2 = Prec<R>::fma_(f, f, sf2);
+                    sw += we;
+                    sw2 = Prec<R>::fma_(we, we, sw2);
+                }
+            }
+            af += static_cast<double>(sf);
+            af2 += static_cast<double>(sf2);
+            aw += static_cast<double>(sw);
+            aw2 += static_cast<double>(sw2);
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            af += __shfl_xor_sync(0xffffffffu, af, off);
+            af2 += __shfl_xor_sync(0xffffffffu, af2, off);
+            aw += __shfl_xor_sync(0xffffffffu, aw, off);
+            aw2 += __shfl_xor_sync(0xffffffffu, aw2, off);
+        }
+        if (lane == 0) partials[t] = TileSums{af, af2, aw, aw2};
+    }
+}
+
+__global__ void __launch_bounds__(128) eval_reduce_segments(const TileSums* __restrict__ partials, uint64_t ntiles,
+                                                            uint64_t seg_begin, double* __restrict__ seg_out) {
+    const uint64_t seg = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nseg = (ntiles + kSegTiles - 1) / kSegTiles;
+    if (seg >= nseg) return;
+    const uint64_t t0 = seg * kSegTiles;
+    const uint64_t nt = ntiles - t0 < kSegTiles ? ntiles - t0 : kSegTiles;
+    segment_sums(partials + t0, nt, threadIdx.x & 31, seg_out + (seg_begin + seg) * 8);
+}
+
+__global__ void __launch_bounds__(32) eval_finalize(const double* __restrict__ seg, uint64_t nseg, uint64_t nevents,
+                                                    hydra_integral* __restrict__ out) {
+    fold_segments(seg, nseg, nevents, threadIdx.x & 31, out);
+}
+
+struct EvalScratch {
+    std::mutex mu;
+    TileSums* tiles = nullptr;
+    double* segs = nullptr;
+    uint64_t seg_cap = 0;
+    hydra_integral* d_res = nullptr;
+    hydra_integral* h_res = nullptr;
+};
+static std::mutex g_ev_mu;
+static std::vector<EvalScratch*> g_ev;
+
+static EvalScratch* eval_scratch() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    std::lock_guard<std::mutex> lk(g_ev_mu);
+    if (static_cast<int>(g_ev.size()) <= dev) g_ev.resize(dev + 1, nullptr);
+    if (!g_ev[dev]) g_ev[dev] = new EvalScratch();
+    return g_ev[dev];
+}
+
 }  // namespace hydra
 
 using namespace hydra;
@@ -443,6 +536,76 @@ hydra_status hydra_phsp_unweight(int n, uint64_t nevents, uint64_t seed, uint64_
             std::memcpy(w_max_used, &s->h[0], 8);
         }
     }
+    return HYDRA_OK;
+}
+
+hydra_status hydra_phsp_evaluate(int n, uint64_t nevents, hydra_dtype dtype, hydra_me_id me, const double* params,
+                                 int nparams, const void* events, uint64_t ld, const void* weights, void* values,
+                                 hydra_integral* result, hydra_stream_t stream) {
+    if (n < 2 || n > kNMax) return fail(HYDRA_ERR_UNSUPPORTED_N, "n = %d outside [2, %d]", n, kNMax);
+    if (dtype != HYDRA_F32 && dtype != HYDRA_F64) return fail(HYDRA_ERR_INVALID_ARG, "unknown dtype %d", static_cast<int>(dtype));
+    if (!result) return fail(HYDRA_ERR_INVALID_ARG, "result is NULL");
+    if (nevents == 0) return fail(HYDRA_ERR_INVALID_ARG, "nevents must be > 0");
+    if (!weights || (me != HYDRA_ME_FLAT && !events)) return fail(HYDRA_ERR_INVALID_ARG, "NULL events or weights");
+    if (events && ld < nevents) return fail(HYDRA_ERR_INVALID_ARG, "ld < nevents");
+    MEConsts P;
+    hydra_status st = make_me(me, n, params, nparams, &P);
+    if (st != HYDRA_OK) return st;
+    EvalScratch* s = eval_scratch();
+    if (!s) return fail(HYDRA_ERR_CUDA, "no current CUDA device");
+    std::lock_guard<std::mutex> lk(s->mu);
+    const uint64_t ntiles = (nevents + kTileEvents - 1) / kTileEvents;
+    const uint64_t nseg = (ntiles + kSegTiles - 1) / kSegTiles;
+    if (!s->tiles) {
+        if (cudaMalloc(&s->tiles, kChunkTiles * sizeof(TileSums)) != cudaSuccess ||
+            cudaMalloc(&s->d_res, sizeof(hydra_integral)) != cudaSuccess ||
+            cudaMallocHost(&s->h_res, sizeof(hydra_integral)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(HYDRA_ERR_OOM, "evaluation scratch");
+        }
+    }
+    if (nseg > s->seg_cap) {
+        if (s->segs) cudaFree(s->segs);
+        s->segs = nullptr;
+        s->seg_cap = 0;
+        if (cudaMalloc(&s->segs, nseg * 8 * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(HYDRA_ERR_OOM, "evaluation segment scratch");
+        }
+        s->seg_cap = nseg;
+    }
+    cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    for (uint64_t t0 = 0; t0 < ntiles; t0 += kChunkTiles) {
+        const uint64_t nt = ntiles - t0 < kChunkTiles ? ntiles - t0 : kChunkTiles;
+        const uint64_t need = (nt * 32 + 255) / 256;
+        const unsigned grid = static_cast<unsigned>(need < static_cast<uint64_t>(sms) * 8 ? need : static_cast<uint64_t>(sms) * 8);
+        if (dtype == HYDRA_F32) {
+            if (me == HYDRA_ME_DALITZ_2BW)
+                evaluate_tiles<float, HYDRA_ME_DALITZ_2BW><<<grid, 256, 0, cs>>>(nevents, static_cast<const float*>(events), ld,
+                    static_cast<const float*>(weights), P, static_cast<float*>(values), t0, nt, s->tiles);
+            else
+                evaluate_tiles<float, HYDRA_ME_FLAT><<<grid, 256, 0, cs>>>(nevents, static_cast<const float*>(events), ld,
+                    static_cast<const float*>(weights), P, static_cast<float*>(values), t0, nt, s->tiles);
+        } else {
+            if (me == HYDRA_ME_DALITZ_2BW)
+                evaluate_tiles<double, HYDRA_ME_DALITZ_2BW><<<grid, 256, 0, cs>>>(nevents, static_cast<const double*>(events), ld,
+                    static_cast<const double*>(weights), P, static_cast<double*>(values), t0, nt, s->tiles);
+            else
+                evaluate_tiles<double, HYDRA_ME_FLAT><<<grid, 256, 0, cs>>>(nevents, static_cast<const double*>(events), ld,
+                    static_cast<const double*>(weights), P, static_cast<double*>(values), t0, nt, s->tiles);
+        }
+        const uint64_t ns = (nt + kSegTiles - 1) / kSegTiles;
+        eval_reduce_segments<<<static_cast<unsigned>((ns * 32 + 127) / 128), 128, 0, cs>>>(s->tiles, nt, t0 / kSegTiles, s->segs);
+    }
+    eval_finalize<<<1, 32, 0, cs>>>(s->segs, nseg, nevents, s->d_res);
+    cudaError_t err = cudaGetLastError();
+    if (err == cudaSuccess) err = cudaMemcpyAsync(s->h_res, s->d_res, sizeof(hydra_integral), cudaMemcpyDeviceToHost, cs);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(cs);
+    if (err != cudaSuccess) return cuda_fail(err, "evaluate");
+    *result = *s->h_res;
     return HYDRA_OK;
 }
 

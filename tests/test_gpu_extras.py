@@ -90,3 +90,50 @@ def test_unweighting_is_deterministic_and_chunkable():
     b1, _ = hp.unweight(5, w[:h].contiguous(), 8, w_max=wm, dtype="f64")
     b2, _ = hp.unweight(5, w[h:].contiguous(), 8, w_max=wm, dtype="f64", event_offset=h)
     assert torch.equal(a, torch.cat([b1, b2 + h]))
+
+
+def test_evaluate_on_oracle_events_fp64():
+    """The evaluation kernel on the oracle's own events (uploaded) reproduces the oracle's
+    values and sums; on GPU-generated events it reproduces the generated-event integral."""
+    d = workloads.D0_DALITZ
+    nev = 3 * 2048 * 5 + 77
+    p, w = oracle.generate(d["M"], d["masses"], nev, seed=12)
+    vals_ref, sums_ref = oracle.evaluate(p, w, me=1, params=d["params"])
+    dp = torch.as_tensor(p, device="cuda").contiguous()
+    dw = torch.as_tensor(w, device="cuda").contiguous()
+    res, vals = hp.evaluate(dp, dw, me=hp.ME_DALITZ_2BW, params=d["params"], dtype="f64", want_values=True)
+    np.testing.assert_allclose(vals.cpu().numpy(), vals_ref, rtol=1e-12)
+    np.testing.assert_allclose([res["sum_f"], res["sum_f2"], res["sum_w"], res["sum_w2"]], sums_ref, rtol=1e-12)
+    gp, gw = hp.generate(d["M"], d["masses"], nev, 12, dtype="f64")
+    res2, _ = hp.evaluate(gp, gw, me=hp.ME_DALITZ_2BW, params=d["params"], dtype="f64")
+    ref2 = hp.integrate(d["M"], d["masses"], nev, 12, kin_dtype="f64", me=hp.ME_DALITZ_2BW, params=d["params"])
+    assert res2["sum_f"] == pytest.approx(ref2["sum_f"], rel=1e-12)
+    assert res2["sum_w"] == pytest.approx(ref2["sum_w"], rel=1e-12)
+
+
+def test_evaluate_fp32_and_flat():
+    d = workloads.D0_DALITZ
+    nev = 50_001
+    gp, gw = hp.generate(d["M"], d["masses"], nev, 2, dtype="f32")
+    res, vals = hp.evaluate(gp, gw, me=hp.ME_DALITZ_2BW, params=d["params"], dtype="f32", want_values=True)
+    ref_vals, ref_sums = oracle.evaluate(gp[:, :, :nev].double().cpu().numpy(), gw.double().cpu().numpy(),
+                                         me=1, params=d["params"])
+    assert abs(res["sum_f"] - ref_sums[0]) <= 2e-4 * ref_sums[0]
+    np.testing.assert_allclose(vals.double().cpu().numpy(), ref_vals, rtol=2e-3)
+    flat, fv = hp.evaluate(gp, gw, dtype="f32", want_values=True)
+    assert torch.equal(fv, gw)
+    assert flat["sum_w"] == flat["sum_f"]
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_sequential_decay_matches_oracle_composition(dtype):
+    M, m, sub = 5.0, (0.5, 1.2, 0.3), (0.4, 0.6)
+    nev = 4001
+    p1, w1, p2, w2 = hp.generate_sequential(M, m, 1, sub, nev, 1, 2, dtype=dtype)
+    r1, rw1 = oracle.generate(M, m, nev, seed=1)
+    r2, rw2 = oracle.generate_boosted(m[1], sub, nev, seed=2, mothers=r1[1, 1:4, :])
+    scale = M
+    assert (np.abs(p1[:, :, :nev].double().cpu().numpy() - r1) / scale).max() <= TOL[dtype]
+    tol2 = TOL[dtype] if dtype == "f64" else 1e-4  # stage 2 inherits stage 1's FP32 momenta
+    assert (np.abs(p2[:, :, :nev].double().cpu().numpy() - r2) / scale).max() <= tol2
+    np.testing.assert_allclose((w1 * w2).double().cpu().numpy(), rw1 * rw2, rtol=max(TOL[dtype], 1e-12) * 4)
