@@ -81,6 +81,47 @@ def _lib(kind: str = "f64") -> ctypes.CDLL:
         return _libs[kind]
 
 
+class variant:
+    """Context manager that makes the f64 oracle functions use another build of the oracle
+    source (used by the tests that plant mistakes in a copy of the source)."""
+
+    def __init__(self, so_path: str):
+        self.path = so_path
+        self.saved = None
+
+    def __enter__(self):
+        lib = _lib("f64")  # ensure the normal library is set up, then swap
+        with _lock:
+            self.saved = _libs["f64"]
+            new = ctypes.CDLL(self.path)
+            for attr in ("philox4x32_10", "draw", "volume_factor", "generate", "integrate", "me_dalitz_2bw",
+                         "generate_boosted", "unweight", "evaluate"):
+                src = getattr(lib, "oracle_" + attr)
+                dst = getattr(new, "oracle_" + attr)
+                dst.argtypes, dst.restype = src.argtypes, src.restype
+            _libs["f64"] = new
+        return self
+
+    def __exit__(self, *exc):
+        with _lock:
+            _libs["f64"] = self.saved
+        return False
+
+
+def compile_variant(source_text: str, out_path: str) -> str:
+    """Compile oracle source text (FP64 build) to a shared library at out_path."""
+    src = out_path + ".c"
+    with open(src, "w") as fh:
+        fh.write(source_text)
+    subprocess.check_call(["gcc", *_CFLAGS, "-o", out_path, src, "-lm"])
+    return out_path
+
+
+def source() -> str:
+    with open(_SRC) as fh:
+        return fh.read()
+
+
 def _pfx(kind: str) -> str:
     return "oracle_" if kind == "f64" else "oracle_ld_"
 
