@@ -113,6 +113,7 @@ template <> struct Prec<float> {
         *c = -cs;
     }
     __device__ static float scale(float x, float pow2) { return x * pow2; }
+    __device__ static float half_odd(uint32_t y) { return __uint2float_rn(y) + 0.5f; }  // y + 1/2
     // 1 + cos(theta), 1 - cos(theta), cos(theta) of a cos(theta) draw x (u = (x + 1/2) 2^-32)
     __device__ static float one_plus_cos(uint32_t x) { return __fmaf_rn(__uint2float_rn(x), 4.656612873077392578125e-10f, 2.3283064365386962890625e-10f); }
     __device__ static float one_minus_cos(uint32_t x) { return one_plus_cos(~x); }
@@ -143,6 +144,7 @@ template <> struct Prec<double> {
         sincospi(__fma_rn(__uint2double_rn(x), 4.656612873077392578125e-10, 2.3283064365386962890625e-10), s, c);
     }
     __device__ static double scale(double x, double pow2) { return x * pow2; }
+    __device__ static double half_odd(uint32_t y) { return __uint2double_rn(y) + 0.5; }
     __device__ static double one_plus_cos(uint32_t x) { return __fma_rn(__uint2double_rn(x), 4.656612873077392578125e-10, 2.3283064365386962890625e-10); }
     __device__ static double one_minus_cos(uint32_t x) { return one_plus_cos(~x); }
     __device__ static double cos_of(uint32_t x) { return __fma_rn(__int2double_rn(static_cast<int32_t>(x ^ 0x80000000u)), 4.656612873077392578125e-10, 2.3283064365386962890625e-10); }
@@ -166,6 +168,7 @@ template <> struct Prec<df> {
     using W = double;
     using Out = double;
     __device__ static df scale(df x, float pow2) { return df_scale(x, pow2); }
+    __device__ static df half_odd(uint32_t y) { return df_scale(df_half_odd_u32(y), 2147483648.0f); }
     __device__ static df one_plus_cos(uint32_t x) { return df_half_odd_u32(x); }
     __device__ static df one_minus_cos(uint32_t x) { return df_half_odd_u32(~x); }
     __device__ static df cos_of(uint32_t x) { return df_half_odd_centered(x); }
@@ -242,7 +245,6 @@ __device__ __forceinline__ void raubold_lynch_group(const DecayConsts& C, const 
 
     const R M = P::M(C);
     const R Ts = P::Ts(C);
-    const R Ts_half = P::Ts_half(C);
 
     using W = typename P::W;
     W w[EPT];
@@ -284,15 +286,15 @@ __device__ __forceinline__ void raubold_lynch_group(const DecayConsts& C, const 
             // intermediate mass M_k
             R Mk;
             if (k == 1) Mk = P::m(C, 0);
-            else Mk = P::fma_(P::u32(y[q][k - 2]) + R(0.5), Ts, P::mu(C, k - 1));
+            else Mk = P::fma_(P::half_odd(y[q][k - 2]), Ts, P::mu(C, k - 1));
             // kinetic gap Delta_k = T (r_k - r_{k-1}) from integer differences
             R gap;
             if constexpr (N == 2) {
                 gap = Ts * R(4294967296.0);  // T exactly: Ts = T * 2^-32
             } else if (k == 1) {
-                gap = P::fma_(P::u32(y[q][0]), Ts, Ts_half);
+                gap = P::half_odd(y[q][0]) * Ts;
             } else if (k == N - 1) {
-                gap = P::fma_(P::u32(~y[q][kY - 1]), Ts, Ts_half);
+                gap = P::half_odd(~y[q][kY - 1]) * Ts;
             } else {
                 gap = P::u32(y[q][k - 1] - y[q][k - 2]) * Ts;
             }

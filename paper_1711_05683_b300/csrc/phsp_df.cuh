@@ -153,29 +153,38 @@ __device__ __forceinline__ df df_half_odd_centered(uint32_t x) {
     return df_scale(df_two_sum(a, b), 4.656612873077392578125e-10f);
 }
 
+// x + f for an FP32 f with |f| <= |x.hi| (a correction term): FastTwoSum and renormalise.
+__device__ __forceinline__ df df_add_small(df x, float f) {
+    const float s = __fadd_rn(x.hi, f);
+    const float e = __fadd_rn(__fsub_rn(f, __fsub_rn(s, x.hi)), x.lo);
+    return df_fast_two_sum(s, e);
+}
+
 // ------------------------------------------------------------------------------------
 // sin and cos of phi = 2 pi u, u = (x + 1/2) 2^-32 for a 32-bit x, in df.
 //
-// Reduction is exact integer arithmetic: the top three bits of x give the octant; phi =
-// j pi/2 +- theta with theta = 2 pi t 2^-32 in [0, pi/4], t the (half-odd) distance to the
-// nearest multiple of pi/2 (t < 2^29).  theta = theta_k + delta with theta_k = k pi/256
-// (k = top 6 bits of t, table of sin/cos of theta_k in df) and 0 <= delta < pi/256; then
-//   sin(delta) = delta (1 - delta^2/6 + delta^4/120),  cos(delta) = 1 - delta^2/2 + delta^4/24,
-// (Taylor; the omitted terms are below 2^-48 relative), the delta^2 terms in df and the
-// delta^4 terms in FP32, and the angle-sum identities combine table and remainder.
+// They multiply momenta bounded by the event scale, so the target is an absolute error of
+// ~1e-15.  Reduction is exact integer arithmetic: the top three bits of x give the octant;
+// phi = j pi/2 +- theta with theta = 2 pi t 2^-32 in [0, pi/4], t the (half-odd) distance to
+// the nearest multiple of pi/2.  theta = theta_k + delta with theta_k = k pi/1024 (k = top 8
+// bits of 2t; a 256-entry table of sin/cos(theta_k) in df) and 0 <= delta < pi/1024:
+//   sin(delta) = delta - delta^3/6 (1 - delta^2/20)      (the correction, <= 4.9e-9, in FP32:
+//                                                          absolute error < 1e-15)
+//   cos(delta) = 1 - delta^2/2 + delta^4/24             (delta^2 from an exact product)
+// then the angle-sum identities, and branch-free signs/swap for the quadrant.
 // ------------------------------------------------------------------------------------
 struct SinCosTable {
-    float sh[64], sl[64], ch[64], cl[64];  // sin/cos(k pi/256), k = 0..63, hi and lo parts
+    float sh[256], sl[256], ch[256], cl[256];  // sin/cos(k pi/1024), k = 0..255, hi and lo parts
 };
 
 // The table lives in shared memory of the kernels that compute in df; each block fills it
-// once (sincospi in FP64 on 64 threads) before its first event.
+// once (sincospi in FP64) before its first event.
 static __shared__ SinCosTable s_sincos_table;
 
 __device__ __forceinline__ void df_sincos_table_init() {
-    for (int k = threadIdx.x; k < 64; k += blockDim.x) {
+    for (int k = threadIdx.x; k < 256; k += blockDim.x) {
         double sv, cv;
-        sincospi(static_cast<double>(k) / 256.0, &sv, &cv);
+        sincospi(static_cast<double>(k) / 1024.0, &sv, &cv);
         const float sh = __double2float_rn(sv), ch = __double2float_rn(cv);
         s_sincos_table.sh[k] = sh;
         s_sincos_table.sl[k] = __double2float_rn(sv - static_cast<double>(sh));
@@ -187,35 +196,38 @@ __device__ __forceinline__ void df_sincos_table_init() {
 __device__ __forceinline__ void df_sincos_2pi_u(uint32_t x, const SinCosTable& T, df* s, df* c) {
     const uint32_t oct = x >> 29;            // octant 0..7
     const uint32_t r = x & 0x1FFFFFFFu;      // position inside the octant (29 bits)
-    // distance (in units of 2^-32 turns, times 2 to stay integral) to the nearest multiple of
-    // a quarter turn: even octants measure from the start, odd ones from the end
     const bool odd = oct & 1u;
     const uint32_t t2 = odd ? ((0x20000000u - r) << 1) - 1u : (r << 1) + 1u;  // 2 t, < 2^30
-    const uint32_t k = t2 >> 24;             // table index 0..63 (theta_k = k pi/256)
-    const uint32_t rem2 = t2 & 0xFFFFFFu;    // 2 (t - k 2^23), < 2^24: exact in FP32
-    // delta = 2 pi (t - k 2^23) 2^-32 = rem2 * (pi 2^-32)
+    const uint32_t k = t2 >> 22;             // table index 0..255 (theta_k = k pi/1024)
+    const uint32_t rem2 = t2 & 0x3FFFFFu;    // 2 (t - k 2^21), < 2^22: exact in FP32
     const df pi_scaled{7.31459059988282e-10f, -2.035470133961082e-17f};  // pi 2^-32 (hi + lo)
-    const df minus_sixth{-0.1666666716337204f, 4.967053879312289e-09f};  // -1/6 (hi + lo)
-    const df d = pi_scaled * __uint2float_rn(rem2);
-    const df d2 = d * d;
-    const float d2f = d2.hi;
-    const float d4 = __fmul_rn(d2f, d2f);
-    // sin(delta) = delta - delta^3/6 + delta^5/120 ; cos(delta) = 1 - delta^2/2 + delta^4/24
-    const df sd = d + d * ((d2 * minus_sixth) + df_from_float(__fmul_rn(d4, 1.0f / 120.0f)));
-    const df cd = df_from_float(1.0f) + ((d2 * -0.5f) + df_from_float(__fmul_rn(d4, 1.0f / 24.0f)));
+    const df d = pi_scaled * __uint2float_rn(rem2);                       // delta
+    const float d2f = __fmul_rn(d.hi, d.hi);
+    // sin(delta)
+    const float corr = __fmul_rn(__fmul_rn(d.hi, __fmul_rn(d2f, 0.16666667163372039795f)),
+                                 __fmaf_rn(d2f, -0.05f, 1.0f));
+    const df sd = df_add_small(d, -corr);
+    // cos(delta): delta^2 = p + e exactly (TwoProd) plus 2 hi lo
+    const float p2 = d2f;
+    const float e2 = __fmaf_rn(2.0f * d.hi, d.lo, __fmaf_rn(d.hi, d.hi, -p2));
+    const df one_minus = df_fast_two_sum(1.0f, -0.5f * p2);
+    const float tail = __fmaf_rn(__fmul_rn(p2, p2), 1.0f / 24.0f, -0.5f * e2);
+    const df cd = df_fast_two_sum(one_minus.hi, __fadd_rn(one_minus.lo, tail));
     const df sk{T.sh[k], T.sl[k]}, ck{T.ch[k], T.cl[k]};
     const df st = sk * cd + ck * sd;  // sin(theta)
     const df ct = ck * cd - sk * sd;  // cos(theta)
-    // phi = j pi/2 + theta (even octant) or j pi/2 - theta (odd octant), j = quadrant index
+    // phi = j pi/2 + a with a = +theta (even octant) or -theta (odd), j = quadrant index:
+    // sin(j pi/2 + a), cos(j pi/2 + a) = (sin a, cos a) rotated by j quarter turns
     const uint32_t j = ((oct + 1u) >> 1) & 3u;
-    const df sp = odd ? -st : st;     // sin(+-theta)
-    // sin(j pi/2 + a), cos(j pi/2 + a) for a = +-theta
-    switch (j) {
-        case 0: *s = sp; *c = ct; break;
-        case 1: *s = ct; *c = -sp; break;
-        case 2: *s = -sp; *c = -ct; break;
-        default: *s = -ct; *c = sp; break;
+    const df sa = odd ? -st : st;
+    const bool swap = j & 1u;
+    df so = swap ? ct : sa, co = swap ? -sa : ct;
+    if (j & 2u) {
+        so = -so;
+        co = -co;
     }
+    *s = so;
+    *c = co;
 }
 
 }  // namespace hydra
