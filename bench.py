@@ -31,6 +31,7 @@ sys.path.insert(0, ROOT)
 
 import workloads  # noqa: E402
 
+METRIC = "phase-space events/s (N=3..10, FP32/FP64) vs roofline; served p50/p99 latency"
 GEN_N = workloads.SWEEP_N
 GEN_EVENTS = workloads.SWEEP_NEVENTS
 INT_CFG = workloads.D0_DALITZ
@@ -149,8 +150,13 @@ def run_ours(args) -> None:
     hp.lib()
     # launch shapes: the autotuner's cached choice for this GPU, or a fresh tuning (untimed)
     from paper_1711_05683_b300 import autotune
-    tuning = autotune.load_or_tune(integrate_cases=[(3, "f32", INT_CFG["M"], INT_CFG["masses"],
-                                                     hp.ME_DALITZ_2BW, INT_CFG["params"])])
+    cases = [(3, "f32", INT_CFG["M"], INT_CFG["masses"], hp.ME_DALITZ_2BW, INT_CFG["params"])]
+    if rank == 0:  # rank 0 tunes (or loads) and writes the cache; the others then load it
+        tuning = autotune.load_or_tune(integrate_cases=cases)
+    if world > 1:
+        dist.barrier()
+    if rank != 0:
+        tuning = autotune.load_or_tune(integrate_cases=cases)
 
     nev = args.events
     int_events = args.int_events
@@ -319,7 +325,7 @@ def run_ours(args) -> None:
                     "achieved": round(hbm, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
                     "frac": round(hbm / peaks["hbm_gbs"], 4), "peak_src": peaks["src"], "traffic": None}
     line = {
-        "metric": "phase-space events/s (N=2..10 generator sweep FP32+FP64, plus Dalitz integral)",
+        "metric": METRIC,
         "value": value, "unit": "events/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32,f64", "data": "synthetic",
@@ -577,7 +583,7 @@ def run_reference(args) -> None:
                       args.events, args.int_events)
     wall = time.perf_counter() - t0
     per_step_events = len(sweep_items()) * args.events + args.int_events
-    line = {"impl": "reference", "metric": "phase-space events/s (N=2..10 generator sweep FP32+FP64, plus Dalitz integral)",
+    line = {"impl": "reference", "metric": METRIC,
             "value": cb["value"], "unit": "events/s", "n_gpus": int(os.environ.get("WORLD_SIZE", "1")),
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step_events / cb["value"] * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
