@@ -75,6 +75,10 @@ def _lib(kind: str = "f64") -> ctypes.CDLL:
             getattr(lib, pfx + "evaluate").argtypes = [ctypes.c_int, ctypes.c_uint64, dp, ctypes.c_uint64, dp,
                                                        ctypes.c_int, dp, ctypes.c_int, dp, dp]
             getattr(lib, pfx + "evaluate").restype = ctypes.c_int
+            getattr(lib, pfx + "vegas").argtypes = [ctypes.c_double, ctypes.c_int, dp, ctypes.c_uint64, ctypes.c_int,
+                                                    dp, ctypes.c_int, ctypes.c_uint64, ctypes.c_int, ctypes.c_int,
+                                                    ctypes.c_double, ctypes.c_int, dp, dp, dp, dp]
+            getattr(lib, pfx + "vegas").restype = ctypes.c_int
             getattr(lib, pfx + "me_dalitz_2bw").argtypes = [ctypes.c_double, ctypes.c_double, dp]
             getattr(lib, pfx + "me_dalitz_2bw").restype = ctypes.c_double
             _libs[kind] = lib
@@ -95,7 +99,7 @@ class variant:
             self.saved = _libs["f64"]
             new = ctypes.CDLL(self.path)
             for attr in ("philox4x32_10", "draw", "volume_factor", "generate", "integrate", "me_dalitz_2bw",
-                         "generate_boosted", "unweight", "evaluate"):
+                         "generate_boosted", "unweight", "evaluate", "vegas"):
                 src = getattr(lib, "oracle_" + attr)
                 dst = getattr(new, "oracle_" + attr)
                 dst.argtypes, dst.restype = src.argtypes, src.restype
@@ -256,6 +260,26 @@ def evaluate(events: np.ndarray, weights: np.ndarray, me: int = 0, params=()) ->
     if rc != 0:
         raise OracleError("invalid arguments")
     return vals, np.array(list(sums))
+
+
+def vegas(M: float, masses, seed: int, calls: int, iterations: int, bins: int = 50, alpha: float = 1.5,
+          skip: int = 1, me: int = 0, params=()) -> dict:
+    """VEGAS (importance sampling, GSL structure) of |ME|^2 over the Raubold-Lynch variables:
+    per-iteration estimates and variances, the combined result, sigma, chi2/dof, final grid."""
+    n = len(masses)
+    D = 3 * n - 4
+    est = np.zeros(iterations)
+    var = np.zeros(iterations)
+    res = np.zeros(3)
+    grid = np.zeros((D, bins + 1))
+    dp = ctypes.POINTER(ctypes.c_double)
+    par = (ctypes.c_double * max(1, len(params)))(*[float(p) for p in params])
+    rc = getattr(_lib(), "oracle_vegas")(float(M), n, _masses(masses), seed, me, par, len(params), calls,
+                                         iterations, bins, float(alpha), skip, est.ctypes.data_as(dp),
+                                         var.ctypes.data_as(dp), res.ctypes.data_as(dp), grid.ctypes.data_as(dp))
+    if rc != 0:
+        raise OracleError("invalid arguments")
+    return {"est": est, "var": var, "mean": res[0], "sigma": res[1], "chi2_dof": res[2], "grid": grid}
 
 
 def me_dalitz_2bw(s12: float, s23: float, params) -> float:

@@ -158,21 +158,18 @@ static void boost(const real q[4], real mq, const real v[4], real out[4])
 }
 
 /* ------------------------------------------------------------------------------------ */
-/* One event of the Raubold-Lynch generator.  Writes p[i][0..3] = (E, px, py, pz) of      */
-/* daughter i+1 and returns the weight.                                                   */
+/* One event of the Raubold-Lynch generator from its 3n-4 uniform variables u[0..3n-5]    */
+/* (u[0..n-3] the intermediate-mass uniforms, then cos(theta) and phi uniforms per step). */
+/* Writes p[i][0..3] = (E, px, py, pz) of daughter i+1 and returns the weight.            */
 /* ------------------------------------------------------------------------------------ */
-static real one_event(const struct decay *D, uint64_t seed, uint64_t event, real p[][4])
+static real event_from_uniforms(const struct decay *D, const real *u, real p[][4])
 {
     const int n = D->n;
 
-    /* Step 1 (R1): the 3n-4 draws of this event. */
-    uint32_t x[3 * NMAX];
-    for (int d = 0; d < 3 * n - 4; ++d) x[d] = API(draw)(seed, event, d);
-
-    /* Step 2: sort the n-2 mass draws into ascending order (insertion sort). */
-    uint32_t y[NMAX];
+    /* Step 2: sort the n-2 mass uniforms into ascending order (insertion sort). */
+    real y[NMAX];
     for (int j = 0; j < n - 2; ++j) {
-        uint32_t v = x[j];
+        real v = u[j];
         int i = j;
         while (i > 0 && y[i - 1] > v) { y[i] = y[i - 1]; --i; }
         y[i] = v;
@@ -185,7 +182,7 @@ static real one_event(const struct decay *D, uint64_t seed, uint64_t event, real
      * (Arrays are indexed by k: Mk[k], r[k], gap[k].) */
     real r[NMAX + 1], Mk[NMAX + 1], gap[NMAX + 1];
     r[0] = 0;
-    for (int j = 1; j <= n - 2; ++j) r[j] = uniform_of(y[j - 1]);
+    for (int j = 1; j <= n - 2; ++j) r[j] = y[j - 1];
     r[n - 1] = 1;
     Mk[1] = D->m[0];
     for (int k = 2; k <= n - 1; ++k) Mk[k] = D->mu[k - 1] + r[k - 1] * D->T;
@@ -213,9 +210,9 @@ static real one_event(const struct decay *D, uint64_t seed, uint64_t event, real
     real Q[4] = {D->M, 0, 0, 0};
     for (int k = n - 1; k >= 1; --k) {
         int j = n - 1 - k;
-        real c = (real)2 * uniform_of(x[n - 2 + 2 * j]) - (real)1;
+        real c = (real)2 * u[n - 2 + 2 * j] - (real)1;
         real s = sqrt(((real)1 - c) * ((real)1 + c));
-        real phi = (real)2 * PI_R * uniform_of(x[n - 1 + 2 * j]);
+        real phi = (real)2 * PI_R * u[n - 1 + 2 * j];
         real dir[3] = {s * cos(phi), s * sin(phi), c};
         real q = pk[k];
         /* In the rest frame of subsystem k+1: subsystem k along +dir, daughter k+1 along -dir. */
@@ -231,6 +228,14 @@ static real one_event(const struct decay *D, uint64_t seed, uint64_t event, real
     }
     for (int c4 = 0; c4 < 4; ++c4) p[0][c4] = Q[c4]; /* daughter 1 = subsystem 1 */
     return w;
+}
+
+/* One event from its Philox draws (R1): u_d = (x_d + 1/2) 2^-32 (R2), then the map above. */
+static real one_event(const struct decay *D, uint64_t seed, uint64_t event, real p[][4])
+{
+    real u[3 * NMAX];
+    for (int d = 0; d < 3 * D->n - 4; ++d) u[d] = uniform_of(API(draw)(seed, event, d));
+    return event_from_uniforms(D, u, p);
 }
 
 /* Generate events event_offset .. event_offset+nevents-1 into the structure of arrays
@@ -385,5 +390,125 @@ int API(evaluate)(int n, uint64_t nevents, const double *ev, uint64_t ld, const 
         sw += we; sw2 += (long double)we * we;
     }
     sums[0] = (double)sf; sums[1] = (double)sf2; sums[2] = (double)sw; sums[3] = (double)sw2;
+    return 0;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* VEGAS over the phase-space variables (section 3 "self-adaptive importance sampling",   */
+/* section 4.1; G. P. Lepage, J. Comput. Phys. 27 (1978) 192, with the iteration and      */
+/* grid refinement structure of GSL's vegas in importance-sampling mode).                  */
+/*                                                                                          */
+/* The integrand is F(u) = w(u) |ME|^2(event(u)) on the unit cube of the D = 3n-4 uniform  */
+/* variables of event_from_uniforms, so Int F du = Int |ME|^2 dR_n.  Each dimension has a  */
+/* grid of K bins (edges g[d][0] = 0 < ... < g[d][K] = 1).  Iteration i draws `calls`     */
+/* points: y_d = (x + 1/2) 2^-32 from Philox draw d of sample s under counter (s low, s    */
+/* high, d/4, i + 1) (stream i + 1; key = seed); bin b = floor(y K); u_d = g[b] + (y K - b) */
+/* (g[b+1] - g[b]); Jacobian J = prod_d K (g[b+1] - g[b]); f = F(u) J.  The iteration's    */
+/* estimate is the mean of f with variance (<f^2> - <f>^2)/(calls - 1); each bin collects  */
+/* the sum of f^2 of its points.  Refinement per dimension: smooth the bin sums with       */
+/* weights (1, 2, 1)/4 inside and (1, 1)/2 at the ends, turn each into the importance      */
+/* weight ((r - 1)/ln r)^alpha with r = d_i / sum d (0 for an empty bin), and move the     */
+/* edges so that every new bin holds an equal share of the total weight (linear within    */
+/* the old bins).  Iterations from `skip` on are combined with weights 1/var: result =     */
+/* sum(I_i/var_i)/sum(1/var_i), sigma = 1/sqrt(sum 1/var_i), chi2/dof over those          */
+/* iterations.  K = 1 is plain Monte Carlo.                                                */
+/* ------------------------------------------------------------------------------------ */
+#define VEGAS_MAXD (3 * NMAX - 4)
+#define VEGAS_MAXK 256
+
+static void vegas_refine(double *g, const double *dsum, int K, double alpha)
+{
+    double d[VEGAS_MAXK], w[VEGAS_MAXK], tot = 0.0;
+    if (K == 1) return;
+    d[0] = (dsum[0] + dsum[1]) / 2.0;
+    for (int i = 1; i < K - 1; ++i) d[i] = (dsum[i - 1] + 2.0 * dsum[i] + dsum[i + 1]) / 4.0;
+    d[K - 1] = (dsum[K - 2] + dsum[K - 1]) / 2.0;
+    for (int i = 0; i < K; ++i) tot += d[i];
+    if (!(tot > 0.0)) return;
+    double wtot = 0.0;
+    for (int i = 0; i < K; ++i) {
+        double r = d[i] / tot;
+        w[i] = (r > 0.0 && r < 1.0) ? pow((r - 1.0) / log(r), alpha) : (r >= 1.0 ? 1.0 : 0.0);
+        wtot += w[i];
+    }
+    if (!(wtot > 0.0)) return;
+    double per = wtot / K, acc = 0.0, newg[VEGAS_MAXK + 1];
+    int j = 0; /* old bin being consumed */
+    newg[0] = 0.0;
+    for (int i = 1; i < K; ++i) {
+        double need = per * i;
+        while (j < K - 1 && acc + w[j] < need) { acc += w[j]; ++j; }
+        double frac = w[j] > 0.0 ? (need - acc) / w[j] : 0.0;
+        if (frac > 1.0) frac = 1.0;
+        if (frac < 0.0) frac = 0.0;
+        newg[i] = g[j] + frac * (g[j + 1] - g[j]);
+    }
+    newg[K] = 1.0;
+    for (int i = 0; i <= K; ++i) g[i] = newg[i];
+}
+
+int API(vegas)(double M, int n, const double *masses, uint64_t seed, int me, const double *params,
+               int nparams, uint64_t calls, int iterations, int bins, double alpha, int skip,
+               double *est, double *var, double *result, double *grid_out)
+{
+    struct decay D;
+    int rc = setup_decay(&D, M, n, masses);
+    if (rc != 0) return rc;
+    if (me == 1 && (n != 3 || nparams < 6)) return -1;
+    if ((me != 0 && me != 1) || bins < 1 || bins > VEGAS_MAXK || iterations < 1 || calls < 2) return -1;
+    const int Dm = 3 * n - 4, K = bins;
+    static double g[VEGAS_MAXD][VEGAS_MAXK + 1], dsum[VEGAS_MAXD][VEGAS_MAXK];
+    for (int d = 0; d < Dm; ++d)
+        for (int b = 0; b <= K; ++b) g[d][b] = (double)b / K;
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    double sw = 0.0, swi = 0.0, swi2 = 0.0;
+    for (int it = 0; it < iterations; ++it) {
+        for (int d = 0; d < Dm; ++d)
+            for (int b = 0; b < K; ++b) dsum[d][b] = 0.0;
+        long double sf = 0, sf2 = 0;
+        for (uint64_t s = 0; s < calls; ++s) {
+            real u[3 * NMAX], p[NMAX][4];
+            int bin[3 * NMAX];
+            double jac = 1.0;
+            for (int d = 0; d < Dm; ++d) {
+                uint32_t ctr[4] = {(uint32_t)s, (uint32_t)(s >> 32), (uint32_t)(d / 4), (uint32_t)(it + 1)};
+                uint32_t out[4];
+                API(philox4x32_10)(ctr, key, out);
+                double y = ((double)out[d % 4] + 0.5) * (1.0 / 4294967296.0);
+                int b = (int)(y * K);
+                if (b >= K) b = K - 1;
+                double width = g[d][b + 1] - g[d][b];
+                u[d] = (real)(g[d][b] + (y * K - b) * width);
+                jac *= K * width;
+                bin[d] = b;
+            }
+            real w = event_from_uniforms(&D, u, p);
+            real me2 = 1;
+            if (me == 1) me2 = dalitz_2bw(invariant_mass2(p[0], p[1]), invariant_mass2(p[1], p[2]), params);
+            double f = (double)(w * me2) * jac;
+            sf += f;
+            sf2 += (long double)f * f;
+            for (int d = 0; d < Dm; ++d) dsum[d][bin[d]] += f * f;
+        }
+        double mean = (double)(sf / calls);
+        double v = (double)((sf2 / calls - (long double)mean * mean) / (calls - 1));
+        est[it] = mean;
+        var[it] = v;
+        if (it >= skip && v > 0.0) {
+            sw += 1.0 / v;
+            swi += mean / v;
+            swi2 += mean * mean / v;
+        }
+        if (it < iterations - 1)
+            for (int d = 0; d < Dm; ++d) vegas_refine(g[d], dsum[d], K, alpha);
+    }
+    double res = sw > 0.0 ? swi / sw : est[iterations - 1];
+    int used = iterations - skip;
+    result[0] = res;
+    result[1] = sw > 0.0 ? 1.0 / sqrt(sw) : sqrt(var[iterations - 1]);
+    result[2] = used > 1 ? (swi2 - res * res * sw) / (used - 1) : 0.0;
+    if (grid_out)
+        for (int d = 0; d < Dm; ++d)
+            for (int b = 0; b <= K; ++b) grid_out[d * (K + 1) + b] = g[d][b];
     return 0;
 }

@@ -29,8 +29,7 @@ MUTATIONS = {
     "philox_word": ("uint32_t n0 = hi1 ^ c[1] ^ k[0];", "uint32_t n0 = hi0 ^ c[1] ^ k[0];"),
     "sort_order": ("while (i > 0 && y[i - 1] > v)", "while (i > 0 && y[i - 1] < v)"),
     "two_body_mass": ("pk[k] = sqrt(lam) / ((real)2 * Mk[k + 1]);", "pk[k] = sqrt(lam) / ((real)2 * Mk[k]);"),
-    "cos_theta": ("real c = (real)2 * uniform_of(x[n - 2 + 2 * j]) - (real)1;",
-                  "real c = uniform_of(x[n - 2 + 2 * j]) - (real)1;"),
+    "cos_theta": ("real c = (real)2 * u[n - 2 + 2 * j] - (real)1;", "real c = u[n - 2 + 2 * j] - (real)1;"),
     "bw_width": ("real xb = m0b * m0b - s23, yb = m0b * Gb", "real xb = m0b * m0b - s23, yb = m0b * Ga"),
     "dalitz_pair": ("dalitz_2bw(invariant_mass2(p[0], p[1]), invariant_mass2(p[1], p[2]), params);\n        real f = w * me2;",
                     "dalitz_2bw(invariant_mass2(p[0], p[1]), invariant_mass2(p[0], p[2]), params);\n        real f = w * me2;"),

@@ -403,3 +403,39 @@ def test_sequential_decay_composition():
     final = p1[0] + p1[2] + p2[0] + p2[1]
     np.testing.assert_allclose(final[0], M, atol=1e-12 * M)
     np.testing.assert_allclose(final[1:], 0.0, atol=1e-12 * M)
+
+
+# ----------------------------------------------------------------------------- VEGAS
+def test_vegas_against_quadrature_and_plain():
+    """VEGAS (importance sampling over the 3n-4 phase-space variables) of the Dalitz matrix
+    element and of the flat one agrees with 2-D quadrature within 4 sigma; one bin per
+    dimension (plain MC) too; grids stay ordered from 0 to 1."""
+    d = workloads.D0_DALITZ
+    exact, _ = dalitz_me_integral_quad(d["M"], d["masses"], d["params"])
+    for bins in (50, 1):
+        r = oracle.vegas(d["M"], d["masses"], 3, 60_000, 6, bins=bins, me=1, params=d["params"])
+        assert abs(r["mean"] - exact) < 4 * r["sigma"], (bins, r["mean"], exact, r["sigma"])
+        assert r["chi2_dof"] < 4.0
+        g = r["grid"]
+        assert np.all(g[:, 0] == 0.0) and np.all(g[:, -1] == 1.0) and np.all(np.diff(g, axis=1) > 0)
+    flat = oracle.vegas(d["M"], d["masses"], 4, 40_000, 4, bins=20)
+    assert abs(flat["mean"] - R3_quad(d["M"], d["masses"])) < 4 * flat["sigma"]
+
+
+def test_vegas_adapts_to_a_separable_peak():
+    """With only the K*(892) term and a narrow width, the peak sits at a fixed value of the
+    intermediate-mass variable u0 = (0.892 - m1 - m2)/T: the refined grid puts its narrowest
+    bin there, the per-iteration error falls by more than 10x, and the result matches
+    quadrature."""
+    d = workloads.D0_DALITZ
+    par = (0.892, 0.005, 1.02, 0.004, 0.0, 1.2)
+    r = oracle.vegas(d["M"], d["masses"], 1, 60_000, 8, bins=50, me=1, params=par)
+    sig = np.sqrt(r["var"])
+    assert sig[-1] < sig[0] / 10
+    m1, m2, _ = d["masses"]
+    u0 = (0.892 - m1 - m2) / (d["M"] - sum(d["masses"]))
+    g0 = r["grid"][0]
+    k = int(np.argmin(np.diff(g0)))
+    assert g0[k] - 0.002 <= u0 <= g0[k + 1] + 0.002
+    exact, _ = dalitz_me_integral_quad(d["M"], d["masses"], par)
+    assert abs(r["mean"] - exact) < 4 * r["sigma"], (r["mean"], exact, r["sigma"])
