@@ -187,6 +187,37 @@ hydra_status hydra_phsp_evaluate(int n, uint64_t nevents, hydra_dtype dtype, hyd
                                  hydra_stream_t stream);
 
 /*
+ * VEGAS importance sampling over the phase-space variables (section 3, "self-adaptive
+ * importance sampling"; section 4.1; G. P. Lepage, J. Comput. Phys. 27 (1978) 192):
+ * Int |ME|^2 dR_n as the integral of F(u) = w(u) |ME|^2(event(u)) over the unit cube of the
+ * D = 3n-4 Raubold-Lynch variables (u_0..u_{n-3} intermediate-mass uniforms, then one
+ * (cos theta, phi) pair per top-down step), through a separable grid of `bins` bins per
+ * dimension, refined after every iteration.  Iteration i draws `calls` points: y_d =
+ * (x + 1/2) 2^-32 from Philox word d%4 of counter (s low, s high, d/4, i + 1) with key
+ * `seed`; bin b = floor(y_d K); u_d = g_d[b] + (y_d K - b)(g_d[b+1] - g_d[b]); f = F(u) J with
+ * J = prod_d K (g_d[b+1] - g_d[b]).  Estimate = mean of f, variance (<f^2> - <f>^2)/(calls-1)
+ * (both reduced in the deterministic tile / segment order of hydra_phsp_integrate).  Each bin
+ * collects sum f^2 (64-bit fixed point relative to the iteration's largest f^2, so the
+ * histogram is order independent); refinement smooths it (1,2,1)/4 inside and (1,1)/2 at the
+ * ends, weights each bin ((r - 1)/ln r)^alpha with r its share, and places the new edges at
+ * equal shares of the total weight.  Iterations skip.. are combined with weights 1/var.
+ * FP64 throughout.  bins = 1 is plain Monte Carlo.
+ *   me, params   as hydra_phsp_integrate
+ *   calls        points per iteration, 2 .. 2^36 (8 bytes of device scratch each)
+ *   iterations   >= 1; bins: 1..256 with (3n-4)(bins+1) <= 6144; alpha >= 0; 0 <= skip < iterations
+ *   est, var     host arrays of `iterations` doubles: each iteration's estimate and variance
+ *   result       host double[3]: combined estimate, its standard deviation, chi^2 per degree
+ *                of freedom of the combined iterations (0 for one)
+ *   grid_out     host double[(3n-4)(bins+1)] receiving the final grid edges, or NULL
+ * Blocking (one host synchronisation per iteration).  Errors: UNSUPPORTED_N, BELOW_THRESHOLD,
+ * INVALID_ARG, OOM, CUDA.
+ */
+hydra_status hydra_phsp_vegas(double M, int n, const double *masses, uint64_t seed, hydra_me_id me,
+                              const double *params, int nparams, uint64_t calls, int iterations,
+                              int bins, double alpha, int skip, double *est, double *var,
+                              double *result, double *grid_out, hydra_stream_t stream);
+
+/*
  * Copy selected events (e.g. the kept events of hydra_phsp_unweight) into a compact SoA
  * buffer: dst[(i*4 + c)*dst_ld + j] = src[(i*4 + c)*src_ld + indices[j]] for j < count, and
  * dst_weights[j] = src_weights[indices[j]] when both weight pointers are non-NULL.  Device

@@ -79,6 +79,7 @@ def lib() -> ctypes.CDLL:
         L.hydra_phsp_unweight.argtypes = [i, u64, u64, u64, i, vp, d, vp, ctypes.POINTER(u64), dp, vp]
         L.hydra_phsp_gather.argtypes = [i, i, vp, u64, vp, vp, u64, vp, u64, vp, vp]
         L.hydra_phsp_evaluate.argtypes = [i, u64, i, i, dp, i, vp, u64, vp, vp, ctypes.POINTER(Integral), vp]
+        L.hydra_phsp_vegas.argtypes = [d, i, dp, u64, i, dp, i, u64, i, i, d, i, dp, dp, dp, dp, vp]
         L.hydra_get_fp64_arith.restype = i
         L.hydra_batch_create.argtypes = [i, u64, ctypes.POINTER(vp)]
         L.hydra_batch_run.argtypes = [vp, vp, i, i, vp]
@@ -248,6 +249,28 @@ def evaluate(p, w, nevents: int | None = None, *, me: int = ME_FLAT, params=(), 
                                      ctypes.c_void_p(vals.data_ptr()) if vals is not None else None,
                                      ctypes.byref(res), _stream_handle(stream)))
     return res.as_dict(), vals
+
+
+def vegas(M: float, masses, seed: int, calls: int, iterations: int, *, bins: int = 50, alpha: float = 1.5,
+          skip: int = 1, me: int = ME_FLAT, params=(), stream=None):
+    """VEGAS estimate of Int |ME|^2 dR_n (section 3, self-adaptive importance sampling) over the
+    3n-4 Raubold-Lynch variables, all iterations on the GPU in FP64.  Returns a dict with the
+    per-iteration estimates ``est`` and variances ``var``, the combined ``mean``, ``sigma``,
+    ``chi2_dof`` and the final ``grid`` [(3n-4), bins+1]."""
+    import numpy as np
+    n = len(masses)
+    D = 3 * n - 4
+    est = np.zeros(iterations)
+    var = np.zeros(iterations)
+    res = np.zeros(3)
+    grid = np.zeros((D, bins + 1))
+    dp = ctypes.POINTER(ctypes.c_double)
+    _check(lib().hydra_phsp_vegas(float(M), n, _dbl(masses), int(seed), int(me), _dbl(params), len(params),
+                                  int(calls), int(iterations), int(bins), float(alpha), int(skip),
+                                  est.ctypes.data_as(dp), var.ctypes.data_as(dp), res.ctypes.data_as(dp),
+                                  grid.ctypes.data_as(dp), _stream_handle(stream)))
+    return {"est": est, "var": var, "mean": float(res[0]), "sigma": float(res[1]), "chi2_dof": float(res[2]),
+            "grid": grid}
 
 
 def generate_sequential(M: float, masses, i: int, sub_masses, nevents: int, seed: int, sub_seed: int, *,

@@ -68,8 +68,14 @@ __device__ __forceinline__ void compare_exchange(uint32_t& a, uint32_t& b) {
     b = hi;
 }
 
-template <int K>
-__device__ __forceinline__ void sort_mass_draws(uint32_t* x) {
+__device__ __forceinline__ void compare_exchange(double& a, double& b) {
+    const double lo = fmin(a, b), hi = fmax(a, b);
+    a = lo;
+    b = hi;
+}
+
+template <int K, typename T>
+__device__ __forceinline__ void sort_mass_draws(T* x) {
     constexpr int kPairs[19][2] = {{0, 1}, {2, 3}, {4, 5}, {6, 7}, {0, 2}, {1, 3}, {4, 6},
                                    {5, 7}, {1, 2}, {5, 6}, {0, 4}, {1, 5}, {2, 6}, {3, 7},
                                    {2, 4}, {3, 5}, {1, 2}, {3, 4}, {5, 6}};
