@@ -496,6 +496,15 @@ def run_extras(nev: int = 100_000_000, reps: int = 3) -> dict:
     res["evaluate_dalitz_f32"] = {"events_per_s": nev / t, "hbm_gbs": nev * 52 / t / 1e9}
     del p, w, moms
     torch.cuda.empty_cache()
+    # VEGAS (FP64): 10 iterations of 1e8 points, Dalitz matrix element; and N=10 flat
+    n10 = workloads.sweep_masses(10, True)
+    for key, M, m, me, par, calls in (("vegas_dalitz_f64", d["M"], d["masses"], 1, d["params"], nev),
+                                      ("vegas_flat_n10_f64", workloads.SWEEP_M, n10, 0, (), nev // 10)):
+        its = 10
+        t = timed(lambda: hp.vegas(M, m, 5, calls, its, bins=100, me=me, params=par))
+        r = hp.vegas(M, m, 5, calls, its, bins=100, me=me, params=par)
+        res[key] = {"points_per_s": calls * its / t, "calls": calls, "iterations": its, "bins": 100,
+                    "mean": r["mean"], "sigma": r["sigma"], "chi2_dof": r["chi2_dof"]}
     return res
 
 

@@ -68,8 +68,8 @@ __device__ __forceinline__ void compare_exchange(uint32_t& a, uint32_t& b) {
     b = hi;
 }
 
-__device__ __forceinline__ void compare_exchange(double& a, double& b) {
-    const double lo = fmin(a, b), hi = fmax(a, b);
+__device__ __forceinline__ void compare_exchange(uint64_t& a, uint64_t& b) {
+    const uint64_t lo = a < b ? a : b, hi = a < b ? b : a;
     a = lo;
     b = hi;
 }

@@ -398,254 +398,6 @@ static EvalScratch* eval_scratch() {
     return g_ev[dev];
 }
 
-// ------------------------------------------------------------------------------------
-// VEGAS over the Raubold-Lynch variables (section 4.1; Lepage 1978): importance sampling of
-// F(u) = w(u) |ME|^2(event(u)) on the unit cube of the D = 3n-4 variables, through a
-// separable grid of K bins per dimension refined after every iteration.  FP64.
-// ------------------------------------------------------------------------------------
-constexpr int kVegasMaxD = 3 * kNMax - 4;
-constexpr int kVegasSmemGrid = 6144;  // doubles of grid edges in shared memory (48 KB)
-
-// The Raubold-Lynch map from real uniforms u[0..3n-5] (u[0..n-3] intermediate-mass
-// uniforms, sorted here; then (cos theta, phi) uniforms per top-down step), FP64.
-// Returns the weight and the lab energy of daughter 1 and the mass M_2 (for s12, s23).
-template <int N>
-__device__ __forceinline__ double rl_event_from_uniforms(const DecayConsts& C, const double* u, double& E1, double& M2) {
-    using P = Prec<double>;
-    constexpr int kY = N > 2 ? N - 2 : 1;
-    double y[kY];
-#pragma unroll
-    for (int j = 0; j < N - 2; ++j) y[j] = u[j];
-    sort_mass_draws<N - 2>(y);
-    const double M = C.M, T = C.Ts * 4294967296.0;
-    double w = 1.0, Q0 = M, Qx = 0.0, Qy = 0.0, Qz = 0.0, Mnext = M;
-    M2 = M;
-#pragma unroll
-    for (int k = N - 1; k >= 1; --k) {
-        const int j = N - 1 - k;
-        const double rk = (k == N - 1) ? 1.0 : y[k - 1];
-        const double rkm = (k == 1) ? 0.0 : y[k - 2];
-        const double Mk = (k == 1) ? C.m[0] : __fma_rn(rkm, T, C.mu[k - 1]);
-        if (k == 2) M2 = Mk;
-        const double gap = T * (rk - rkm);
-        const double mk1 = C.m[k];
-        const double twoMk = 2.0 * Mk, twom = 2.0 * mk1;
-        const double lam = ((gap * (gap + twoMk)) * (gap + twom)) * ((gap + twoMk) + twom);
-        const double invM = 1.0 / Mnext;
-        const double p = sqrt(lam) * (0.5 * invM);
-        w *= p;
-        const double uc = u[N - 2 + 2 * j], up = u[N - 1 + 2 * j];
-        const double cos_t = 2.0 * uc - 1.0;
-        const double sin_t = sqrt((2.0 - 2.0 * uc) * (2.0 * uc));
-        double sphi, cphi;
-        sincospi(2.0 * up, &sphi, &cphi);
-        const double ps = p * sin_t;
-        const double px = ps * cphi, py = ps * sphi, pz = p * cos_t;
-        const double Es = sqrt(__fma_rn(p, p, Mk * Mk));
-        if (k == N - 1) {
-            Q0 = Es; Qx = px; Qy = py; Qz = pz;
-        } else {
-            const double qp = __fma_rn(Qz, pz, __fma_rn(Qy, py, Qx * px));
-            const double E1v = __fma_rn(Q0, Es, qp) * invM;
-            const double f = (E1v + Es) / (Q0 + Mnext);
-            Qx = __fma_rn(f, Qx, px);
-            Qy = __fma_rn(f, Qy, py);
-            Qz = __fma_rn(f, Qz, pz);
-            Q0 = E1v;
-        }
-        Mnext = Mk;
-    }
-    E1 = Q0;
-    return w * C.C;
-}
-
-// Bins of sample s: y_d = (x + 1/2) 2^-32 from Philox word d%4 of counter (s low, s high,
-// d/4, stream) and b = floor(y_d K); calls visit(d, b, y_d) for d = 0..D-1, one Philox block
-// per four dimensions.
-template <typename Visit>
-__device__ __forceinline__ void vegas_bins(const DecayConsts& C, uint64_t s, uint32_t stream, int D, int K,
-                                           Visit visit) {
-#pragma unroll
-    for (int q = 0; q < (D + 3) / 4; ++q) {
-        uint32_t x[4];
-        philox4x32_10(static_cast<uint32_t>(s), static_cast<uint32_t>(s >> 32), static_cast<uint32_t>(q), stream,
-                      C.rk0, C.rk1, x);
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int d = 4 * q + j;
-            if (d < D) {
-                const double y = __fma_rn(__uint2double_rn(x[j]), 2.3283064365386962890625e-10,
-                                          1.16415321826934814453125e-10);
-                const int b = static_cast<int>(y * K);
-                visit(d, b < K ? b : K - 1, y);
-            }
-        }
-    }
-}
-
-template <int N, int ME>
-__global__ void __launch_bounds__(256) vegas_eval(const __grid_constant__ DecayConsts C, const __grid_constant__ MEConsts P,
-                                                  const double* __restrict__ grid, int K, uint32_t stream,
-                                                  uint64_t calls, uint64_t tile_begin, uint64_t ntiles,
-                                                  TileSums* __restrict__ partials, double* __restrict__ fvals,
-                                                  unsigned long long* __restrict__ max_f2) {
-    constexpr int D = 3 * N - 4;
-    __shared__ double sg[kVegasSmemGrid];
-    for (int i = threadIdx.x; i < D * (K + 1); i += blockDim.x) sg[i] = grid[i];
-    __syncthreads();
-    const int lane = threadIdx.x & 31;
-    const uint64_t warp = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-    const uint64_t nwarps = (static_cast<uint64_t>(gridDim.x) * blockDim.x) >> 5;
-    unsigned long long mx = 0;
-    for (uint64_t t = warp; t < ntiles; t += nwarps) {
-        const uint64_t base = (tile_begin + t) * kTileEvents;
-        double af = 0.0, af2 = 0.0;
-        for (int g = 0; g < kLaneIters / kGroupEvents; ++g) {
-            double sf = 0.0, sf2 = 0.0;
-            for (int i = 0; i < kGroupEvents; ++i) {
-                const uint64_t s = base + static_cast<uint64_t>(32 * (g * kGroupEvents + i) + lane);
-                if (s < calls) {
-                    double u[D];
-                    double jac = 1.0;
-                    vegas_bins(C, s, stream, D, K, [&](int d, int b, double y) {
-                        // u_d = g[b] + (y K - b) (g[b+1] - g[b]); Jacobian factor K (g[b+1] - g[b])
-                        const double g0 = sg[d * (K + 1) + b], width = sg[d * (K + 1) + b + 1] - g0;
-                        u[d] = g0 + (y * K - b) * width;
-                        jac *= K * width;
-                    });
-                    double E1, M2;
-                    const double w = rl_event_from_uniforms<N>(C, u, E1, M2);
-                    double me2 = 1.0;
-                    if constexpr (ME == HYDRA_ME_DALITZ_2BW) {
-                        const double s12 = M2 * M2;
-                        const double s23 = __fma_rn(-2.0 * C.M, E1, __fma_rn(C.M, C.M, C.m2[0]));
-                        me2 = dalitz_2bw<double>(P, s12, s23);
-                    }
-                    const double f = (w * me2) * jac;
-                    fvals[s] = f;
-                    sf += f;
-                    sf2 = __fma_rn(f, f, sf2);
-                    const unsigned long long bits = static_cast<unsigned long long>(__double_as_longlong(f * f));
-                    mx = bits > mx ? bits : mx;
-                }
-            }
-            af += sf;
-            af2 += sf2;
-        }
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            af += __shfl_xor_sync(0xffffffffu, af, off);
-            af2 += __shfl_xor_sync(0xffffffffu, af2, off);
-        }
-        if (lane == 0) partials[t] = TileSums{af, af2, 0.0, 0.0};
-    }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        const unsigned long long o = __shfl_xor_sync(0xffffffffu, mx, off);
-        mx = o > mx ? o : mx;
-    }
-    if (lane == 0) atomicMax(max_f2, mx);
-}
-
-// Per-bin sums of f^2 in 64-bit fixed point, one unit = (largest f^2 of the iteration) / qnum
-// with qnum = 2^(62 - ceil(log2 calls)), so no bin can overflow: integer additions are order
-// independent, so the histogram and the refined grid are reproducible bit for bit.
-__global__ void __launch_bounds__(256) vegas_hist(const __grid_constant__ DecayConsts C, int D, int K, uint32_t stream,
-                                                  uint64_t calls, double qnum,
-                                                  const double* __restrict__ fvals,
-                                                  const unsigned long long* __restrict__ max_f2,
-                                                  unsigned long long* __restrict__ hist) {
-    extern __shared__ unsigned long long sh[];
-    for (int i = threadIdx.x; i < D * K; i += blockDim.x) sh[i] = 0ull;
-    __syncthreads();
-    const double mx = __longlong_as_double(static_cast<long long>(*max_f2));
-    const double scale = mx > 0.0 ? qnum / mx : 0.0;
-    for (uint64_t s = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; s < calls;
-         s += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
-        const double f = fvals[s];
-        const unsigned long long q = static_cast<unsigned long long>(f * f * scale);
-        if (q == 0ull) continue;
-        vegas_bins(C, s, stream, D, K, [&](int d, int b, double) { atomicAdd(&sh[d * K + b], q); });
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < D * K; i += blockDim.x)
-        if (sh[i]) atomicAdd(&hist[i], sh[i]);
-}
-
-template <int ME>
-static const void* vegas_eval_for(int n) {
-    switch (n) {
-        case 2: return reinterpret_cast<const void*>(&vegas_eval<2, ME>);
-        case 3: return reinterpret_cast<const void*>(&vegas_eval<3, ME>);
-        case 4: return reinterpret_cast<const void*>(&vegas_eval<4, ME>);
-        case 5: return reinterpret_cast<const void*>(&vegas_eval<5, ME>);
-        case 6: return reinterpret_cast<const void*>(&vegas_eval<6, ME>);
-        case 7: return reinterpret_cast<const void*>(&vegas_eval<7, ME>);
-        case 8: return reinterpret_cast<const void*>(&vegas_eval<8, ME>);
-        case 9: return reinterpret_cast<const void*>(&vegas_eval<9, ME>);
-        case 10: return reinterpret_cast<const void*>(&vegas_eval<10, ME>);
-    }
-    return nullptr;
-}
-
-// Grid refinement of one dimension (Lepage's rule): smooth the bin sums (1,2,1)/4 inside,
-// (1,1)/2 at the ends; importance weight ((r - 1)/ln r)^alpha of each bin's share r; move the
-// edges so that every new bin carries an equal share of the total weight.
-static void refine_dimension(double* g, const double* dsum, int K, double alpha) {
-    if (K == 1) return;
-    std::vector<double> sm(K), wt(K), ng(K + 1);
-    sm[0] = (dsum[0] + dsum[1]) / 2.0;
-    for (int i = 1; i < K - 1; ++i) sm[i] = (dsum[i - 1] + 2.0 * dsum[i] + dsum[i + 1]) / 4.0;
-    sm[K - 1] = (dsum[K - 2] + dsum[K - 1]) / 2.0;
-    double tot = 0.0;
-    for (int i = 0; i < K; ++i) tot += sm[i];
-    if (!(tot > 0.0)) return;
-    double wsum = 0.0;
-    for (int i = 0; i < K; ++i) {
-        const double r = sm[i] / tot;
-        wt[i] = (r > 0.0 && r < 1.0) ? std::pow((r - 1.0) / std::log(r), alpha) : (r >= 1.0 ? 1.0 : 0.0);
-        wsum += wt[i];
-    }
-    if (!(wsum > 0.0)) return;
-    const double share = wsum / K;
-    double acc = 0.0;
-    int j = 0;
-    ng[0] = 0.0;
-    for (int i = 1; i < K; ++i) {
-        const double need = share * i;
-        while (j < K - 1 && acc + wt[j] < need) acc += wt[j++];
-        double frac = wt[j] > 0.0 ? (need - acc) / wt[j] : 0.0;
-        frac = frac < 0.0 ? 0.0 : (frac > 1.0 ? 1.0 : frac);
-        ng[i] = g[j] + frac * (g[j + 1] - g[j]);
-    }
-    ng[K] = 1.0;
-    for (int i = 0; i <= K; ++i) g[i] = ng[i];
-}
-
-struct VegasScratch {
-    std::mutex mu;
-    TileSums* tiles = nullptr;
-    double* segs = nullptr;
-    uint64_t seg_cap = 0;
-    double* fvals = nullptr;
-    uint64_t fcap = 0;
-    double* grid = nullptr;
-    unsigned long long* hist = nullptr;   // [D*K] then max f^2 at [kVegasMaxD * 256]
-    hydra_integral* d_res = nullptr;
-    void* h_pin = nullptr;                 // pinned: result + hist
-};
-static std::mutex g_vg_mu;
-static std::vector<VegasScratch*> g_vg;
-
-static VegasScratch* vegas_scratch() {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
-    std::lock_guard<std::mutex> lk(g_vg_mu);
-    if (static_cast<int>(g_vg.size()) <= dev) g_vg.resize(dev + 1, nullptr);
-    if (!g_vg[dev]) g_vg[dev] = new VegasScratch();
-    return g_vg[dev];
-}
-
 }  // namespace hydra
 
 using namespace hydra;
@@ -854,130 +606,6 @@ hydra_status hydra_phsp_evaluate(int n, uint64_t nevents, hydra_dtype dtype, hyd
     if (err == cudaSuccess) err = cudaStreamSynchronize(cs);
     if (err != cudaSuccess) return cuda_fail(err, "evaluate");
     *result = *s->h_res;
-    return HYDRA_OK;
-}
-
-hydra_status hydra_phsp_vegas(double M, int n, const double* masses, uint64_t seed, hydra_me_id me, const double* params,
-                              int nparams, uint64_t calls, int iterations, int bins, double alpha, int skip,
-                              double* est, double* var, double* result, double* grid_out, hydra_stream_t stream) {
-    DecayConsts C;
-    hydra_status st = make_consts(M, n, masses, seed, &C);
-    if (st != HYDRA_OK) return st;
-    MEConsts P;
-    st = make_me(me, n, params, nparams, &P);
-    if (st != HYDRA_OK) return st;
-    const int D = 3 * n - 4, K = bins;
-    if (iterations < 1 || calls < 2 || calls > (uint64_t{1} << 36) || !est || !var || !result)
-        return fail(HYDRA_ERR_INVALID_ARG, "need iterations >= 1, 2 <= calls <= 2^36 and est/var/result arrays");
-    if (K < 1 || K > 256 || D * (K + 1) > kVegasSmemGrid)
-        return fail(HYDRA_ERR_INVALID_ARG, "bins = %d: need 1 <= bins <= 256 and (3n-4)(bins+1) <= %d", K, kVegasSmemGrid);
-    if (!(alpha >= 0.0) || skip < 0 || skip >= iterations) return fail(HYDRA_ERR_INVALID_ARG, "bad alpha or skip");
-    const void* kern = me == HYDRA_ME_FLAT ? vegas_eval_for<HYDRA_ME_FLAT>(n) : vegas_eval_for<HYDRA_ME_DALITZ_2BW>(n);
-    if (!kern) return fail(HYDRA_ERR_UNSUPPORTED_N, "no VEGAS kernel for n = %d", n);
-    VegasScratch* s = vegas_scratch();
-    if (!s) return fail(HYDRA_ERR_CUDA, "no current CUDA device");
-    std::lock_guard<std::mutex> lk(s->mu);
-    const uint64_t ntiles = (calls + kTileEvents - 1) / kTileEvents;
-    const uint64_t nseg = (ntiles + kSegTiles - 1) / kSegTiles;
-    const size_t hist_words = static_cast<size_t>(kVegasMaxD) * 256 + 1;
-    if (!s->tiles) {
-        if (cudaMalloc(&s->tiles, kChunkTiles * sizeof(TileSums)) != cudaSuccess ||
-            cudaMalloc(&s->grid, static_cast<size_t>(kVegasSmemGrid) * sizeof(double)) != cudaSuccess ||
-            cudaMalloc(&s->hist, hist_words * sizeof(unsigned long long)) != cudaSuccess ||
-            cudaMalloc(&s->d_res, sizeof(hydra_integral)) != cudaSuccess ||
-            cudaMallocHost(&s->h_pin, sizeof(hydra_integral) + hist_words * sizeof(unsigned long long)) != cudaSuccess) {
-            cudaGetLastError();
-            return fail(HYDRA_ERR_OOM, "VEGAS scratch");
-        }
-    }
-    if (nseg > s->seg_cap) {
-        if (s->segs) cudaFree(s->segs);
-        s->segs = nullptr;
-        s->seg_cap = 0;
-        if (cudaMalloc(&s->segs, nseg * 8 * sizeof(double)) != cudaSuccess) {
-            cudaGetLastError();
-            return fail(HYDRA_ERR_OOM, "VEGAS segment scratch");
-        }
-        s->seg_cap = nseg;
-    }
-    if (calls > s->fcap) {
-        if (s->fvals) cudaFree(s->fvals);
-        s->fvals = nullptr;
-        s->fcap = 0;
-        if (cudaMalloc(&s->fvals, calls * sizeof(double)) != cudaSuccess) {
-            cudaGetLastError();
-            return fail(HYDRA_ERR_OOM, "VEGAS sample values (%llu calls)", static_cast<unsigned long long>(calls));
-        }
-        s->fcap = calls;
-    }
-    std::vector<double> g(static_cast<size_t>(D) * (K + 1));
-    for (int d = 0; d < D; ++d)
-        for (int b = 0; b <= K; ++b) g[static_cast<size_t>(d) * (K + 1) + b] = static_cast<double>(b) / K;
-    cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
-    int dev = 0, sms = 148;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    hydra_integral* h_res = static_cast<hydra_integral*>(s->h_pin);
-    unsigned long long* h_hist = reinterpret_cast<unsigned long long*>(static_cast<char*>(s->h_pin) + sizeof(hydra_integral));
-    unsigned long long* d_max = s->hist + static_cast<size_t>(kVegasMaxD) * 256;
-    int lg = 0;
-    while ((uint64_t{1} << lg) < calls) ++lg;
-    const double qnum = std::ldexp(1.0, 62 - lg);
-    double sw = 0.0, swi = 0.0, swi2 = 0.0;
-    std::vector<double> dsum(K);
-    for (int it = 0; it < iterations; ++it) {
-        const uint32_t stream_id = static_cast<uint32_t>(it + 1);
-        cudaError_t err = cudaMemcpyAsync(s->grid, g.data(), g.size() * sizeof(double), cudaMemcpyHostToDevice, cs);
-        if (err == cudaSuccess) err = cudaMemsetAsync(s->hist, 0, hist_words * sizeof(unsigned long long), cs);
-        if (err != cudaSuccess) return cuda_fail(err, "VEGAS grid upload");
-        for (uint64_t t0 = 0; t0 < ntiles; t0 += kChunkTiles) {
-            const uint64_t nt = ntiles - t0 < kChunkTiles ? ntiles - t0 : kChunkTiles;
-            const uint64_t need = (nt * 32 + 255) / 256;
-            const unsigned grid = static_cast<unsigned>(need < static_cast<uint64_t>(sms) * 4 ? need : static_cast<uint64_t>(sms) * 4);
-            const double* gp = s->grid;
-            int Kv = K;
-            uint32_t sid = stream_id;
-            uint64_t cl = calls, tb = t0, ntv = nt;
-            TileSums* tp = s->tiles;
-            double* fv = s->fvals;
-            unsigned long long* mp = d_max;
-            void* args[] = {&C, &P, &gp, &Kv, &sid, &cl, &tb, &ntv, &tp, &fv, &mp};
-            err = cudaLaunchKernel(kern, dim3(grid), dim3(256), args, 0, cs);
-            if (err != cudaSuccess) return cuda_fail(err, "VEGAS evaluation launch");
-            const uint64_t ns = (nt + kSegTiles - 1) / kSegTiles;
-            eval_reduce_segments<<<static_cast<unsigned>((ns * 32 + 127) / 128), 128, 0, cs>>>(s->tiles, nt, t0 / kSegTiles, s->segs);
-        }
-        eval_finalize<<<1, 32, 0, cs>>>(s->segs, nseg, calls, s->d_res);
-        const uint64_t hneed = (calls + 255) / 256;
-        const unsigned hgrid = static_cast<unsigned>(hneed < static_cast<uint64_t>(sms) * 4 ? hneed : static_cast<uint64_t>(sms) * 4);
-        vegas_hist<<<hgrid, 256, static_cast<size_t>(D) * K * sizeof(unsigned long long), cs>>>(C, D, K, stream_id, calls, qnum,
-                                                                                                 s->fvals, d_max, s->hist);
-        err = cudaGetLastError();
-        if (err == cudaSuccess) err = cudaMemcpyAsync(h_res, s->d_res, sizeof(hydra_integral), cudaMemcpyDeviceToHost, cs);
-        if (err == cudaSuccess)
-            err = cudaMemcpyAsync(h_hist, s->hist, static_cast<size_t>(D) * K * sizeof(unsigned long long), cudaMemcpyDeviceToHost, cs);
-        if (err == cudaSuccess) err = cudaStreamSynchronize(cs);
-        if (err != cudaSuccess) return cuda_fail(err, "VEGAS iteration");
-        est[it] = h_res->mean;
-        var[it] = h_res->var_mean;
-        if (it >= skip && var[it] > 0.0) {
-            sw += 1.0 / var[it];
-            swi += est[it] / var[it];
-            swi2 += est[it] * est[it] / var[it];
-        }
-        if (it < iterations - 1) {
-            for (int d = 0; d < D; ++d) {
-                for (int b = 0; b < K; ++b) dsum[b] = static_cast<double>(h_hist[static_cast<size_t>(d) * K + b]);
-                refine_dimension(&g[static_cast<size_t>(d) * (K + 1)], dsum.data(), K, alpha);
-            }
-        }
-    }
-    const double res = sw > 0.0 ? swi / sw : est[iterations - 1];
-    const int used = iterations - skip;
-    result[0] = res;
-    result[1] = sw > 0.0 ? 1.0 / std::sqrt(sw) : std::sqrt(var[iterations - 1]);
-    result[2] = used > 1 ? (swi2 - res * res * sw) / (used - 1) : 0.0;
-    if (grid_out) std::memcpy(grid_out, g.data(), g.size() * sizeof(double));
     return HYDRA_OK;
 }
 

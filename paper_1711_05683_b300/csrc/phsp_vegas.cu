@@ -1,0 +1,548 @@
+// phsp_vegas.cu -- VEGAS importance sampling over the Raubold-Lynch variables (section 3,
+// "self-adaptive importance sampling"; section 4.1; G. P. Lepage, J. Comput. Phys. 27 (1978)
+// 192).  The integrand is F(u) = w(u) |ME|^2(event(u)) on the unit cube of the D = 3n-4
+// variables of one event (n-2 intermediate-mass uniforms, then one (cos theta, phi) pair per
+// top-down two-body step), so that Int F du = Int |ME|^2 dR_n.  Each dimension has a grid of
+// K bins refined after every iteration; all sampling, kinematics and sums run on the GPU in
+// FP64 (native or double-float, hydra_set_fp64_arith), the refinement on the host.
+//
+// Per iteration i (Philox stream i + 1):
+//   vegas_eval  point s: y_d = (x + 1/2) 2^-32 from Philox word d%4 of counter (s low, s high,
+//               d/4, i + 1); bin and position from exact integers (below); the event's
+//               weight and |ME|^2; f = F(u) J stored per point; the deterministic tile sums
+//               of f and f^2 (the integral's tile / segment order); the largest f^2.
+//   vegas_hist  per-bin sums of f^2 in 64-bit fixed point (order-independent integer adds).
+//   host        estimate and variance; refinement of every dimension.
+//
+// Grid arithmetic.  With P = (2x + 1) K (< 2^41), the bin is b = floor(y K) = P >> 33 and the
+// position inside it is y K - b = rho 2^-33 with rho = P mod 2^33, both exact (y K has at
+// most 42 significant bits, so these are also what an FP64 evaluation of floor(y K) and
+// y K - b gives).  Edges are held as 64-bit fixed point G_b = g_b 2^64 and widths
+// W_b = G_{b+1} - G_b, so u 2^64 = G_b + floor(rho W_b 2^-33) to within one unit of 2^-64;
+// the Jacobian factor K (g_{b+1} - g_b) is the host's FP64 value.  Sorting the mass
+// variables and forming the kinetic gaps T (r_k - r_{k-1}) then work on exact integers, as in
+// the generator.
+#include <cuda_runtime.h>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <mutex>
+#include <type_traits>
+#include <vector>
+#include "hydra_phsp.h"
+#include "phsp_device.cuh"
+#include "phsp_df.cuh"
+#include "phsp_host.h"
+#include "phsp_integral.cuh"
+
+namespace hydra {
+
+__global__ void eval_reduce_segments(const TileSums* __restrict__ partials, uint64_t ntiles, uint64_t seg_begin,
+                                     double* __restrict__ seg_out);
+__global__ void eval_finalize(const double* __restrict__ seg, uint64_t nseg, uint64_t nevents,
+                              hydra_integral* __restrict__ out);
+
+constexpr int kVegasMaxCells = 6144;  // D * K grid cells held in shared memory (24 B each)
+constexpr int kVegasBlock = 256;
+
+struct VegasCell {
+    uint64_t G;  // left edge g_b 2^64
+    uint64_t W;  // width (g_{b+1} - g_b) 2^64 (2^64 - 1 for a single bin)
+    double J;    // Jacobian factor K (g_{b+1} - g_b)
+};
+
+// Matrix-element constants (m0a^2, m0a Ga, m0b^2, m0b Gb, Re c, Im c) in FP64 and as
+// double-float pairs.
+struct VegasME {
+    double v[6];
+    float hi[6], lo[6];
+};
+
+template <typename R> struct VegasArith;
+
+// Native FP64: u = U 2^-64 rounded to double.
+template <> struct VegasArith<double> {
+    __device__ static double frac(uint64_t v) { return __ull2double_rn(v) * 5.42101086242752217003726400434970855712890625e-20; }
+    __device__ static double comp(uint64_t v) { return v == 0 ? 1.0 : frac(0 - v); }  // 1 - v 2^-64
+    __device__ static void sincos(uint64_t v, double* s, double* c) { sincospi(2.0 * frac(v), s, c); }
+    __device__ static double T(const DecayConsts& C) { return C.Ts * 4294967296.0; }
+    __device__ static double me(const VegasME& P, int i) { return P.v[i]; }
+    __device__ static double to_double(double x) { return x; }
+};
+
+// v 2^-64 as a double-float: the top 48 significant bits of v (the rest truncated, relative
+// error < 2^-47), hi built from the bits directly; 0 for v = 0.
+__device__ __forceinline__ df df_frac_u64(uint64_t v) {
+    if (v == 0) return df{0.0f, 0.0f};
+    const int lz = __clzll(static_cast<long long>(v));
+    const uint64_t m = v << lz;                                            // bit 63 set
+    const uint32_t t1 = static_cast<uint32_t>(m >> 40);                    // bits 63..40
+    const uint32_t t2 = static_cast<uint32_t>(m >> 16) & 0xFFFFFFu;        // bits 39..16
+    const float hi = __int_as_float(((126 - lz) << 23) | static_cast<int>(t1 & 0x7FFFFFu));  // t1 2^(-24-lz)
+    const float lo = __fmul_rn(__uint2float_rz(t2), __int_as_float((79 - lz) << 23));         // t2 2^(-48-lz)
+    return df_fast_two_sum(hi, lo);
+}
+
+// x + f for any FP32 f (TwoSum, then the low parts).
+__device__ __forceinline__ df df_add_f(df x, float f) {
+    const df s = df_two_sum(x.hi, f);
+    return df_fast_two_sum(s.hi, __fadd_rn(s.lo, x.lo));
+}
+
+template <> struct VegasArith<df> {
+    __device__ static df frac(uint64_t v) { return df_frac_u64(v); }
+    __device__ static df comp(uint64_t v) { return v == 0 ? df{1.0f, 0.0f} : df_frac_u64(0 - v); }
+    // phi = 2 pi v 2^-64 = 2 pi (X + 1/2) 2^-32 + delta, X = v >> 32, delta = 2 pi 2^-64 (L - 2^31)
+    // with L the low 32 bits (|delta| <= pi 2^-32): the table sin/cos of the first angle, then
+    // sin(a + delta) = s + c delta, cos(a + delta) = c - s delta (the delta^2 terms are below
+    // 3e-19).
+    __device__ static void sincos(uint64_t v, df* s, df* c) {
+        df s0, c0;
+        df_sincos_2pi_u(static_cast<uint32_t>(v >> 32), s_sincos_table, &s0, &c0);
+        const float delta = __fmul_rn(__int2float_rn(static_cast<int32_t>(static_cast<uint32_t>(v) ^ 0x80000000u)),
+                                      3.40612158008655459e-19f);
+        *s = df_add_f(s0, __fmul_rn(c0.hi, delta));
+        *c = df_add_f(c0, -__fmul_rn(s0.hi, delta));
+    }
+    __device__ static df T(const DecayConsts& C) { return df_scale(Prec<df>::Ts(C), 4294967296.0f); }
+    __device__ static df me(const VegasME& P, int i) { return df{P.hi[i], P.lo[i]}; }
+    __device__ static double to_double(df x) { return df_to_double(x); }
+};
+
+// Raubold-Lynch event of fixed-point uniforms U[0..3n-5] in arithmetic R (the generator's
+// construction: sorted mass variables, exact integer gaps, factorised Kallen lambda, top-down
+// pure boosts).  Returns the weight (FP64, C_n included); E1 = lab energy of daughter 1 and
+// M2 = mass of the (1, 2) subsystem, which fix s12 and s23.
+template <int N, typename R>
+__device__ __forceinline__ double vegas_event(const DecayConsts& C, const uint64_t (&U)[3 * N - 4], R& E1, R& M2) {
+    using P = Prec<R>;
+    using A = VegasArith<R>;
+    constexpr int kY = N > 2 ? N - 2 : 1;
+    uint64_t y[kY];
+#pragma unroll
+    for (int j = 0; j < N - 2; ++j) y[j] = U[j];
+    if constexpr (N > 3) sort_mass_draws<N - 2>(y);
+    const R M = P::M(C);
+    const R T = A::T(C);
+    double w = 1.0;
+    R Q0 = M, Qx = R(0.0f), Qy = R(0.0f), Qz = R(0.0f), Mnext = M;
+    M2 = M;
+#pragma unroll
+    for (int k = N - 1; k >= 1; --k) {
+        const int j = N - 1 - k;
+        R Mk;
+        if (k == 1) Mk = P::m(C, 0);
+        else Mk = P::fma_(A::frac(y[k - 2]), T, P::mu(C, k - 1));
+        if (k == 2) M2 = Mk;
+        R gap;
+        if constexpr (N == 2) gap = T;
+        else if (k == 1) gap = A::frac(y[0]) * T;
+        else if (k == N - 1) gap = A::comp(y[kY - 1]) * T;
+        else gap = A::frac(y[k - 1] - y[k - 2]) * T;
+        const R mk1 = P::m(C, k);
+        const R twoMk = P::scale(Mk, 2.0f), twom = P::scale(mk1, 2.0f);
+        const R lam = ((gap * (gap + twoMk)) * (gap + twom)) * ((gap + twoMk) + twom);
+        const R invM = P::rcp(Mnext);
+        const R p = P::sqrt_(lam) * P::scale(invM, 0.5f);
+        w = P::w_mul(w, p);
+        const uint64_t uc = U[N - 2 + 2 * j], up = U[N - 1 + 2 * j];
+        const R one_p = P::scale(A::frac(uc), 2.0f);  // 1 + cos(theta) = 2u
+        const R one_m = P::scale(A::comp(uc), 2.0f);  // 1 - cos(theta) = 2(1 - u)
+        const R cos_t = A::frac(uc) - A::comp(uc);            // 2u - 1
+        const R sin_t = P::sqrt_(one_m * one_p);
+        R sphi, cphi;
+        A::sincos(up, &sphi, &cphi);
+        const R ps = p * sin_t;
+        const R px = ps * cphi, py = ps * sphi, pz = p * cos_t;
+        const R Es = P::sqrt_(P::fma_(p, p, Mk * Mk));
+        if (k == N - 1) {
+            Q0 = Es; Qx = px; Qy = py; Qz = pz;
+        } else {
+            const R qp = P::fma_(Qz, pz, P::fma_(Qy, py, Qx * px));
+            const R E1v = P::fma_(Q0, Es, qp) * invM;
+            const R f = P::div(E1v + Es, Q0 + Mnext);
+            Qx = P::fma_(f, Qx, px);
+            Qy = P::fma_(f, Qy, py);
+            Qz = P::fma_(f, Qz, pz);
+            Q0 = E1v;
+        }
+        Mnext = Mk;
+    }
+    E1 = Q0;
+    return w * P::Cw(C);
+}
+
+// |BW(s12; a) + c BW(s23; b)|^2 in arithmetic R (the integral's formula).
+template <typename R>
+__device__ __forceinline__ R vegas_dalitz(const VegasME& PM, R s12, R s23) {
+    using A = VegasArith<R>;
+    using Q = Prec<R>;
+    const R xa = A::me(PM, 0) - s12, ya = A::me(PM, 1);
+    const R xb = A::me(PM, 2) - s23, yb = A::me(PM, 3);
+    const R ia = Q::rcp(Q::fma_(xa, xa, ya * ya));
+    const R ib = Q::rcp(Q::fma_(xb, xb, yb * yb));
+    const R cr = A::me(PM, 4), ci = A::me(PM, 5);
+    const R re = Q::fma_(xa, ia, Q::fma_(cr, xb, -(ci * yb)) * ib);
+    const R im = Q::fma_(ya, ia, Q::fma_(cr, yb, ci * xb) * ib);
+    return Q::fma_(re, re, im * im);
+}
+
+// Bins of point s: calls visit(d, b, rho) for d = 0..D-1 (one Philox block per four
+// dimensions), b = P >> 33 and rho = P mod 2^33 with P = (2x + 1) K.
+template <typename Visit>
+__device__ __forceinline__ void vegas_bins(const DecayConsts& C, uint64_t s, uint32_t stream, int D, int K,
+                                           Visit visit) {
+#pragma unroll
+    for (int q = 0; q < (D + 3) / 4; ++q) {
+        uint32_t x[4];
+        philox4x32_10(static_cast<uint32_t>(s), static_cast<uint32_t>(s >> 32), static_cast<uint32_t>(q), stream,
+                      C.rk0, C.rk1, x);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int d = 4 * q + j;
+            if (d < D) {
+                const uint64_t Pv = (2ull * x[j] + 1ull) * static_cast<uint64_t>(K);
+                visit(d, static_cast<int>(Pv >> 33), Pv & 0x1FFFFFFFFull);
+            }
+        }
+    }
+}
+
+template <int N, typename R, int ME>
+__global__ void __launch_bounds__(kVegasBlock) vegas_eval(const __grid_constant__ DecayConsts C,
+                                                          const __grid_constant__ VegasME PM,
+                                                          const VegasCell* __restrict__ grid, int K, uint32_t stream,
+                                                          uint64_t calls, uint64_t tile_begin, uint64_t ntiles,
+                                                          TileSums* __restrict__ partials, double* __restrict__ fvals,
+                                                          unsigned long long* __restrict__ max_f2) {
+    constexpr int D = 3 * N - 4;
+    extern __shared__ VegasCell cells[];
+    if constexpr (std::is_same_v<R, df>) df_sincos_table_init();
+    for (int i = threadIdx.x; i < D * K; i += blockDim.x) cells[i] = grid[i];
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const uint64_t warp = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = (static_cast<uint64_t>(gridDim.x) * blockDim.x) >> 5;
+    unsigned long long mx = 0;
+    for (uint64_t t = warp; t < ntiles; t += nwarps) {
+        const uint64_t base = (tile_begin + t) * kTileEvents;
+        double af = 0.0, af2 = 0.0;
+        for (int g = 0; g < kLaneIters / kGroupEvents; ++g) {
+            double sf = 0.0, sf2 = 0.0;
+            for (int i = 0; i < kGroupEvents; ++i) {
+                const uint64_t s = base + static_cast<uint64_t>(32 * (g * kGroupEvents + i) + lane);
+                if (s < calls) {
+                    uint64_t U[D];
+                    double jac = 1.0;
+                    vegas_bins(C, s, stream, D, K, [&](int d, int b, uint64_t rho) {
+                        const VegasCell c = cells[d * K + b];
+                        U[d] = c.G + ((__umul64hi(rho, c.W) << 31) | ((rho * c.W) >> 33));
+                        jac *= c.J;
+                    });
+                    R E1, M2;
+                    const double w = vegas_event<N, R>(C, U, E1, M2);
+                    double me2 = 1.0;
+                    if constexpr (ME == HYDRA_ME_DALITZ_2BW) {
+                        // s12 = M_2^2; s23 = (P - p1)^2 = M^2 + m1^2 - 2 M E1
+                        const R M = Prec<R>::M(C);
+                        const R s12 = M2 * M2;
+                        const R s23 = Prec<R>::fma_(Prec<R>::scale(M, -2.0f), E1,
+                                                    Prec<R>::fma_(M, M, Prec<R>::m2(C, 0)));
+                        me2 = VegasArith<R>::to_double(vegas_dalitz<R>(PM, s12, s23));
+                    }
+                    const double f = (w * me2) * jac;
+                    fvals[s] = f;
+                    sf += f;
+                    sf2 = __fma_rn(f, f, sf2);
+                    const unsigned long long bits = static_cast<unsigned long long>(__double_as_longlong(f * f));
+                    mx = bits > mx ? bits : mx;
+                }
+            }
+            af += sf;
+            af2 += sf2;
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            af += __shfl_xor_sync(0xffffffffu, af, off);
+            af2 += __shfl_xor_sync(0xffffffffu, af2, off);
+        }
+        if (lane == 0) partials[t] = TileSums{af, af2, 0.0, 0.0};
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const unsigned long long o = __shfl_xor_sync(0xffffffffu, mx, off);
+        mx = o > mx ? o : mx;
+    }
+    if (lane == 0) atomicMax(max_f2, mx);
+}
+
+// Per-bin sums of f^2 in 64-bit fixed point, one unit = (largest f^2 of the iteration) / qnum
+// with qnum = 2^(62 - ceil(log2 calls)), so no bin can overflow: integer additions are order
+// independent, so the histogram and the refined grid are reproducible bit for bit.
+__global__ void __launch_bounds__(kVegasBlock) vegas_hist(const __grid_constant__ DecayConsts C, int D, int K,
+                                                          uint32_t stream, uint64_t calls, double qnum,
+                                                          const double* __restrict__ fvals,
+                                                          const unsigned long long* __restrict__ max_f2,
+                                                          unsigned long long* __restrict__ hist) {
+    extern __shared__ unsigned long long sh[];
+    for (int i = threadIdx.x; i < D * K; i += blockDim.x) sh[i] = 0ull;
+    __syncthreads();
+    const double mx = __longlong_as_double(static_cast<long long>(*max_f2));
+    const double scale = mx > 0.0 ? qnum / mx : 0.0;
+    for (uint64_t s = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; s < calls;
+         s += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
+        const double f = fvals[s];
+        const unsigned long long q = static_cast<unsigned long long>(f * f * scale);
+        if (q == 0ull) continue;
+        vegas_bins(C, s, stream, D, K, [&](int d, int b, uint64_t) { atomicAdd(&sh[d * K + b], q); });
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < D * K; i += blockDim.x)
+        if (sh[i]) atomicAdd(&hist[i], sh[i]);
+}
+
+template <typename R, int ME>
+static const void* vegas_eval_for(int n) {
+    if constexpr (ME == HYDRA_ME_DALITZ_2BW) {
+        return n == 3 ? reinterpret_cast<const void*>(&vegas_eval<3, R, ME>) : nullptr;
+    } else {
+        switch (n) {
+            case 2: return reinterpret_cast<const void*>(&vegas_eval<2, R, ME>);
+            case 3: return reinterpret_cast<const void*>(&vegas_eval<3, R, ME>);
+            case 4: return reinterpret_cast<const void*>(&vegas_eval<4, R, ME>);
+            case 5: return reinterpret_cast<const void*>(&vegas_eval<5, R, ME>);
+            case 6: return reinterpret_cast<const void*>(&vegas_eval<6, R, ME>);
+            case 7: return reinterpret_cast<const void*>(&vegas_eval<7, R, ME>);
+            case 8: return reinterpret_cast<const void*>(&vegas_eval<8, R, ME>);
+            case 9: return reinterpret_cast<const void*>(&vegas_eval<9, R, ME>);
+            case 10: return reinterpret_cast<const void*>(&vegas_eval<10, R, ME>);
+        }
+        return nullptr;
+    }
+}
+
+// Grid refinement of one dimension (Lepage's rule): smooth the bin sums (1,2,1)/4 inside,
+// (1,1)/2 at the ends; importance weight ((r - 1)/ln r)^alpha of each bin's share r; move the
+// edges so that every new bin carries an equal share of the total weight.
+static void refine_dimension(double* g, const double* dsum, int K, double alpha) {
+    if (K == 1) return;
+    std::vector<double> sm(K), wt(K), ng(K + 1);
+    sm[0] = (dsum[0] + dsum[1]) / 2.0;
+    for (int i = 1; i < K - 1; ++i) sm[i] = (dsum[i - 1] + 2.0 * dsum[i] + dsum[i + 1]) / 4.0;
+    sm[K - 1] = (dsum[K - 2] + dsum[K - 1]) / 2.0;
+    double tot = 0.0;
+    for (int i = 0; i < K; ++i) tot += sm[i];
+    if (!(tot > 0.0)) return;
+    double wsum = 0.0;
+    for (int i = 0; i < K; ++i) {
+        const double r = sm[i] / tot;
+        wt[i] = (r > 0.0 && r < 1.0) ? std::pow((r - 1.0) / std::log(r), alpha) : (r >= 1.0 ? 1.0 : 0.0);
+        wsum += wt[i];
+    }
+    if (!(wsum > 0.0)) return;
+    const double share = wsum / K;
+    double acc = 0.0;
+    int j = 0;
+    ng[0] = 0.0;
+    for (int i = 1; i < K; ++i) {
+        const double need = share * i;
+        while (j < K - 1 && acc + wt[j] < need) acc += wt[j++];
+        double frac = wt[j] > 0.0 ? (need - acc) / wt[j] : 0.0;
+        frac = frac < 0.0 ? 0.0 : (frac > 1.0 ? 1.0 : frac);
+        ng[i] = g[j] + frac * (g[j + 1] - g[j]);
+    }
+    ng[K] = 1.0;
+    for (int i = 0; i <= K; ++i) g[i] = ng[i];
+}
+
+// Fixed-point cells of one dimension's edges g[0..K].
+static void grid_cells(const double* g, int K, VegasCell* out) {
+    std::vector<uint64_t> G(K);
+    for (int b = 0; b < K; ++b)
+        G[b] = g[b] < 1.0 ? static_cast<uint64_t>(std::ldexp(g[b], 64)) : ~uint64_t{0};  // exact below 2^64
+    for (int b = 0; b < K; ++b) {
+        out[b].G = G[b];
+        out[b].W = (K == 1) ? ~uint64_t{0} : (b + 1 < K ? G[b + 1] : uint64_t{0}) - G[b];  // G_K = 2^64 (mod 2^64)
+        out[b].J = K * (g[b + 1] - g[b]);
+    }
+}
+
+struct VegasScratch {
+    std::mutex mu;
+    TileSums* tiles = nullptr;
+    double* segs = nullptr;
+    uint64_t seg_cap = 0;
+    double* fvals = nullptr;
+    uint64_t fcap = 0;
+    VegasCell* cells = nullptr;
+    unsigned long long* hist = nullptr;  // [D*K] bin sums, then the largest f^2 (as bits)
+    hydra_integral* d_res = nullptr;
+    void* h_pin = nullptr;               // pinned: result, histogram, cells
+};
+static std::mutex g_vg_mu;
+static std::vector<VegasScratch*> g_vg;
+
+static VegasScratch* vegas_scratch() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    std::lock_guard<std::mutex> lk(g_vg_mu);
+    if (static_cast<int>(g_vg.size()) <= dev) g_vg.resize(dev + 1, nullptr);
+    if (!g_vg[dev]) g_vg[dev] = new VegasScratch();
+    return g_vg[dev];
+}
+
+}  // namespace hydra
+
+using namespace hydra;
+
+extern "C" {
+
+hydra_status hydra_phsp_vegas(double M, int n, const double* masses, uint64_t seed, hydra_me_id me, const double* params,
+                              int nparams, uint64_t calls, int iterations, int bins, double alpha, int skip,
+                              double* est, double* var, double* result, double* grid_out, hydra_stream_t stream) {
+    DecayConsts C;
+    hydra_status st = make_consts(M, n, masses, seed, &C);
+    if (st != HYDRA_OK) return st;
+    MEConsts P;
+    st = make_me(me, n, params, nparams, &P);
+    if (st != HYDRA_OK) return st;
+    const int D = 3 * n - 4, K = bins;
+    if (iterations < 1 || calls < 2 || calls > (uint64_t{1} << 36) || !est || !var || !result)
+        return fail(HYDRA_ERR_INVALID_ARG, "need iterations >= 1, 2 <= calls <= 2^36 and est/var/result arrays");
+    if (K < 1 || K > 256 || D * K > kVegasMaxCells)
+        return fail(HYDRA_ERR_INVALID_ARG, "bins = %d: need 1 <= bins <= 256 and (3n-4) bins <= %d", K, kVegasMaxCells);
+    if (!(alpha >= 0.0) || skip < 0 || skip >= iterations) return fail(HYDRA_ERR_INVALID_ARG, "bad alpha or skip");
+    const bool use_df = g_fp64_arith.load() == HYDRA_FP64_DOUBLE_FLOAT;
+    const void* kern = use_df ? (me == HYDRA_ME_FLAT ? vegas_eval_for<df, HYDRA_ME_FLAT>(n)
+                                                     : vegas_eval_for<df, HYDRA_ME_DALITZ_2BW>(n))
+                              : (me == HYDRA_ME_FLAT ? vegas_eval_for<double, HYDRA_ME_FLAT>(n)
+                                                     : vegas_eval_for<double, HYDRA_ME_DALITZ_2BW>(n));
+    if (!kern) return fail(HYDRA_ERR_UNSUPPORTED_N, "no VEGAS kernel for n = %d", n);
+    VegasME PM;
+    const double pv[6] = {P.a_m2, P.a_mg, P.b_m2, P.b_mg, P.c_re, P.c_im};
+    for (int i = 0; i < 6; ++i) {
+        PM.v[i] = pv[i];
+        PM.hi[i] = static_cast<float>(pv[i]);
+        PM.lo[i] = static_cast<float>(pv[i] - static_cast<double>(PM.hi[i]));
+    }
+    VegasScratch* s = vegas_scratch();
+    if (!s) return fail(HYDRA_ERR_CUDA, "no current CUDA device");
+    std::lock_guard<std::mutex> lk(s->mu);
+    const uint64_t ntiles = (calls + kTileEvents - 1) / kTileEvents;
+    const uint64_t nseg = (ntiles + kSegTiles - 1) / kSegTiles;
+    const size_t hist_words = static_cast<size_t>(kVegasMaxCells) + 1;
+    const size_t cell_bytes = static_cast<size_t>(kVegasMaxCells) * sizeof(VegasCell);
+    if (!s->tiles) {
+        if (cudaMalloc(&s->tiles, kChunkTiles * sizeof(TileSums)) != cudaSuccess ||
+            cudaMalloc(&s->cells, cell_bytes) != cudaSuccess ||
+            cudaMalloc(&s->hist, hist_words * sizeof(unsigned long long)) != cudaSuccess ||
+            cudaMalloc(&s->d_res, sizeof(hydra_integral)) != cudaSuccess ||
+            cudaMallocHost(&s->h_pin, sizeof(hydra_integral) + hist_words * sizeof(unsigned long long) + cell_bytes) !=
+                cudaSuccess) {
+            cudaGetLastError();
+            return fail(HYDRA_ERR_OOM, "VEGAS scratch");
+        }
+    }
+    if (nseg > s->seg_cap) {
+        if (s->segs) cudaFree(s->segs);
+        s->segs = nullptr;
+        s->seg_cap = 0;
+        if (cudaMalloc(&s->segs, nseg * 8 * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(HYDRA_ERR_OOM, "VEGAS segment scratch");
+        }
+        s->seg_cap = nseg;
+    }
+    if (calls > s->fcap) {
+        if (s->fvals) cudaFree(s->fvals);
+        s->fvals = nullptr;
+        s->fcap = 0;
+        if (cudaMalloc(&s->fvals, calls * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(HYDRA_ERR_OOM, "VEGAS point values (%llu calls)", static_cast<unsigned long long>(calls));
+        }
+        s->fcap = calls;
+    }
+    const size_t smem = static_cast<size_t>(D) * K * sizeof(VegasCell);
+    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(cell_bytes));
+    if (err != cudaSuccess) return cuda_fail(err, "VEGAS shared-memory limit");
+    int dev = 0, sms = 148, per_sm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kVegasBlock, smem);
+    per_sm = per_sm < 1 ? 1 : per_sm;
+    std::vector<double> g(static_cast<size_t>(D) * (K + 1));
+    for (int d = 0; d < D; ++d)
+        for (int b = 0; b <= K; ++b) g[static_cast<size_t>(d) * (K + 1) + b] = static_cast<double>(b) / K;
+    cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+    hydra_integral* h_res = static_cast<hydra_integral*>(s->h_pin);
+    unsigned long long* h_hist = reinterpret_cast<unsigned long long*>(static_cast<char*>(s->h_pin) + sizeof(hydra_integral));
+    VegasCell* h_cells = reinterpret_cast<VegasCell*>(h_hist + hist_words);
+    unsigned long long* d_max = s->hist + kVegasMaxCells;
+    int lg = 0;
+    while ((uint64_t{1} << lg) < calls) ++lg;
+    const double qnum = std::ldexp(1.0, 62 - lg);
+    double sw = 0.0, swi = 0.0, swi2 = 0.0;
+    std::vector<double> dsum(K);
+    for (int it = 0; it < iterations; ++it) {
+        const uint32_t stream_id = static_cast<uint32_t>(it + 1);
+        for (int d = 0; d < D; ++d) grid_cells(&g[static_cast<size_t>(d) * (K + 1)], K, h_cells + static_cast<size_t>(d) * K);
+        err = cudaMemcpyAsync(s->cells, h_cells, smem, cudaMemcpyHostToDevice, cs);
+        if (err == cudaSuccess) err = cudaMemsetAsync(s->hist, 0, hist_words * sizeof(unsigned long long), cs);
+        if (err != cudaSuccess) return cuda_fail(err, "VEGAS grid upload");
+        for (uint64_t t0 = 0; t0 < ntiles; t0 += kChunkTiles) {
+            const uint64_t nt = ntiles - t0 < kChunkTiles ? ntiles - t0 : kChunkTiles;
+            const uint64_t need = (nt * 32 + kVegasBlock - 1) / kVegasBlock;
+            const uint64_t cap = static_cast<uint64_t>(sms) * per_sm;
+            const unsigned grid = static_cast<unsigned>(need < cap ? need : cap);
+            const VegasCell* gp = s->cells;
+            int Kv = K;
+            uint32_t sid = stream_id;
+            uint64_t cl = calls, tb = t0, ntv = nt;
+            TileSums* tp = s->tiles;
+            double* fv = s->fvals;
+            unsigned long long* mp = d_max;
+            void* args[] = {&C, &PM, &gp, &Kv, &sid, &cl, &tb, &ntv, &tp, &fv, &mp};
+            err = cudaLaunchKernel(kern, dim3(grid), dim3(kVegasBlock), args, smem, cs);
+            if (err != cudaSuccess) return cuda_fail(err, "VEGAS evaluation launch");
+            const uint64_t ns = (nt + kSegTiles - 1) / kSegTiles;
+            eval_reduce_segments<<<static_cast<unsigned>((ns * 32 + 127) / 128), 128, 0, cs>>>(s->tiles, nt, t0 / kSegTiles, s->segs);
+        }
+        eval_finalize<<<1, 32, 0, cs>>>(s->segs, nseg, calls, s->d_res);
+        if (it < iterations - 1) {
+            const uint64_t hneed = (calls + kVegasBlock - 1) / kVegasBlock;
+            const uint64_t hcap = static_cast<uint64_t>(sms) * 4;
+            const unsigned hgrid = static_cast<unsigned>(hneed < hcap ? hneed : hcap);
+            vegas_hist<<<hgrid, kVegasBlock, static_cast<size_t>(D) * K * sizeof(unsigned long long), cs>>>(
+                C, D, K, stream_id, calls, qnum, s->fvals, d_max, s->hist);
+        }
+        err = cudaGetLastError();
+        if (err == cudaSuccess) err = cudaMemcpyAsync(h_res, s->d_res, sizeof(hydra_integral), cudaMemcpyDeviceToHost, cs);
+        if (err == cudaSuccess && it < iterations - 1)
+            err = cudaMemcpyAsync(h_hist, s->hist, static_cast<size_t>(D) * K * sizeof(unsigned long long), cudaMemcpyDeviceToHost, cs);
+        if (err == cudaSuccess) err = cudaStreamSynchronize(cs);
+        if (err != cudaSuccess) return cuda_fail(err, "VEGAS iteration");
+        est[it] = h_res->mean;
+        var[it] = h_res->var_mean;
+        if (it >= skip && var[it] > 0.0) {
+            sw += 1.0 / var[it];
+            swi += est[it] / var[it];
+            swi2 += est[it] * est[it] / var[it];
+        }
+        if (it < iterations - 1) {
+            for (int d = 0; d < D; ++d) {
+                for (int b = 0; b < K; ++b) dsum[b] = static_cast<double>(h_hist[static_cast<size_t>(d) * K + b]);
+                refine_dimension(&g[static_cast<size_t>(d) * (K + 1)], dsum.data(), K, alpha);
+            }
+        }
+    }
+    const double res = sw > 0.0 ? swi / sw : est[iterations - 1];
+    const int used = iterations - skip;
+    result[0] = res;
+    result[1] = sw > 0.0 ? 1.0 / std::sqrt(sw) : std::sqrt(var[iterations - 1]);
+    result[2] = used > 1 ? (swi2 - res * res * sw) / (used - 1) : 0.0;
+    if (grid_out) std::memcpy(grid_out, g.data(), g.size() * sizeof(double));
+    return HYDRA_OK;
+}
+
+}  // extern "C"

@@ -1,5 +1,6 @@
 """VEGAS over the Raubold-Lynch variables (section 3, self-adaptive importance sampling;
-section 4.1) on the GPU against the oracle's VEGAS, same seeds, same draws.
+section 4.1) on the GPU against the oracle's VEGAS, same seeds, same draws, in both FP64
+arithmetics of the library (double-float, the default, and native FP64).
 
 The first iteration uses the uniform grid on both sides, so its estimate and variance agree to
 FP64 reduction-order rounding.  Later iterations sample through refined grids; the GPU's bin
@@ -49,8 +50,16 @@ def _case(name):
     raise KeyError(name)
 
 
+@pytest.fixture(params=["df", "native"])
+def arith(request):
+    saved = hp.get_fp64_arith()
+    hp.set_fp64_arith(hp.FP64_NATIVE if request.param == "native" else hp.FP64_DOUBLE_FLOAT)
+    yield request.param
+    hp.set_fp64_arith(saved)
+
+
 @pytest.mark.parametrize("name", ["dalitz", "narrow_peak", "plain_mc", "flat_n5", "flat_n10"])
-def test_vegas_matches_oracle(name):
+def test_vegas_matches_oracle(name, arith):
     M, m, me, calls, iters, bins, tol = _case(name)
     g = hp.vegas(M, m, 11, calls, iters, bins=bins, **me)
     r = oracle.vegas(M, m, 11, calls, iters, bins=bins, **me)
@@ -65,7 +74,7 @@ def test_vegas_matches_oracle(name):
     assert np.all(np.diff(g["grid"], axis=1) > 0)
 
 
-def test_vegas_two_body_is_exact():
+def test_vegas_two_body_is_exact(arith):
     """n = 2: F is the constant R_2 = pi p*/M on the (cos theta, phi) square.  With one bin
     (J = 1) every iteration returns it to rounding; with a grid the first (uniform) one does,
     and the later ones average J = prod K (g[b+1] - g[b]), whose mean is 1."""
@@ -79,14 +88,14 @@ def test_vegas_two_body_is_exact():
     np.testing.assert_allclose(g["est"], r["est"], rtol=1e-8)
 
 
-def test_vegas_is_deterministic():
+def test_vegas_is_deterministic(arith):
     a = hp.vegas(D0["M"], D0["masses"], 3, 50_000, 3, bins=40, me=1, params=D0["params"])
     b = hp.vegas(D0["M"], D0["masses"], 3, 50_000, 3, bins=40, me=1, params=D0["params"])
     assert np.array_equal(a["est"], b["est"]) and np.array_equal(a["var"], b["var"])
     assert np.array_equal(a["grid"], b["grid"])
 
 
-def test_vegas_large_sample_against_quadrature():
+def test_vegas_large_sample_against_quadrature(arith):
     """2^24 + 3 points per iteration (8193 warp tiles, 9 segments): the first iteration equals
     the oracle's on the same draws; the combined result matches quadrature of the Dalitz
     integral within 5 sigma and the narrow peak's per-iteration error drops by 10x."""
