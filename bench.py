@@ -496,16 +496,54 @@ def run_extras(nev: int = 100_000_000, reps: int = 3) -> dict:
     res["evaluate_dalitz_f32"] = {"events_per_s": nev / t, "hbm_gbs": nev * 52 / t / 1e9}
     del p, w, moms
     torch.cuda.empty_cache()
-    # VEGAS (FP64): 10 iterations of 1e8 points, Dalitz matrix element; and N=10 flat
-    n10 = workloads.sweep_masses(10, True)
-    for key, M, m, me, par, calls in (("vegas_dalitz_f64", d["M"], d["masses"], 1, d["params"], nev),
-                                      ("vegas_flat_n10_f64", workloads.SWEEP_M, n10, 0, (), nev // 10)):
-        its = 10
-        t = timed(lambda: hp.vegas(M, m, 5, calls, its, bins=100, me=me, params=par))
-        r = hp.vegas(M, m, 5, calls, its, bins=100, me=me, params=par)
-        res[key] = {"points_per_s": calls * its / t, "calls": calls, "iterations": its, "bins": 100,
-                    "mean": r["mean"], "sigma": r["sigma"], "chi2_dof": r["chi2_dof"]}
+    res.update(run_vegas(nev, 10, reps=reps))
     return res
+
+
+# ----------------------------------------------------------------------------- VEGAS
+# Thread instructions per point of the double-float VEGAS kernels (ncu smsp__inst_executed.sum
+# x 32 / points on 4e6-point iterations, 100 bins; profiles/vegas_eval_df_dalitz_4e6.md).
+VEGAS_INSTR_PER_POINT = {("dalitz", "eval"): 1452, ("dalitz", "hist"): 320,
+                         ("flat10", "eval"): 2565, ("flat10", "hist"): 1200}
+
+
+def run_vegas(calls: int = 100_000_000, iterations: int = 10, reps: int = 3,
+              cases=("dalitz", "flat10")) -> dict:
+    """Points/s of hp.vegas (FP64, double-float arithmetic, 100 bins per dimension): the
+    Dalitz matrix element (N=3, `calls` points per iteration) and the flat N=10 integrand
+    (calls/10 points); the whole call timed (all iterations, host refinement included), best
+    of `reps` after one warm-up, with the issue-limit fraction of its kernels."""
+    import torch
+    import paper_1711_05683_b300 as hp
+    d = INT_CFG
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    out = {}
+    for case in cases:
+        if case == "dalitz":
+            M, m, me, par, c = d["M"], d["masses"], hp.ME_DALITZ_2BW, d["params"], calls
+        else:
+            M, m, me, par, c = workloads.SWEEP_M, workloads.sweep_masses(10, True), hp.ME_FLAT, (), max(2, calls // 10)
+        hp.vegas(M, m, 5, c, iterations, bins=100, me=me, params=par)
+        torch.cuda.synchronize()
+        best = float("inf")
+        clocks = ClockSampler(torch.cuda.current_device())
+        clocks.start()
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            r = hp.vegas(M, m, 5, c, iterations, bins=100, me=me, params=par)
+            best = min(best, time.perf_counter() - t0)
+        ck = clocks.stop()
+        pps = c * iterations / best
+        instr = VEGAS_INSTR_PER_POINT[(case, "eval")] + VEGAS_INSTR_PER_POINT[(case, "hist")] * (iterations - 1) / iterations
+        sm_mhz = ck.get("sm_mhz") or ck.get("sm_max_mhz") or 2032.0
+        issue_peak = sms * 4 * 32 * sm_mhz * 1e6
+        out[f"vegas_{case}_f64"] = {
+            "points_per_s": pps, "calls": c, "iterations": iterations, "bins": 100, "seconds": best,
+            "mean": r["mean"], "sigma": r["sigma"], "chi2_dof": r["chi2_dof"], "clocks": ck,
+            "roofline": {"bound": "alu", "achieved": round(instr * pps / 1e12, 2), "peak": round(issue_peak / 1e12, 2),
+                         "unit": "T thread-instructions/s issued", "frac": round(instr * pps / issue_peak, 4),
+                         "peak_src": f"SM issue limit: {sms} SMs x 4 schedulers x 32 lanes x {sm_mhz:.0f} MHz"}}
+    return out
 
 
 # ----------------------------------------------------------------------------- serving loop
@@ -621,7 +659,10 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--batch-count", type=int, default=4096)
     ap.add_argument("--arena-gb", type=float, default=40.0)
-    ap.add_argument("--workload", default="sweep", choices=["sweep", "batch", "serve"])
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "batch", "serve", "vegas"])
+    ap.add_argument("--vegas-calls", type=int, default=100_000_000)
+    ap.add_argument("--vegas-iterations", type=int, default=10)
+    ap.add_argument("--vegas-case", default="both", choices=["both", "dalitz", "flat10"])
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     args = ap.parse_args()
     if args.impl == "reference":
@@ -644,6 +685,16 @@ def main():
         torch.cuda.set_device(0)
         hp.lib()
         print(json.dumps({"workload": "serve", **run_serve_workload(duration_s=args.serve_seconds)}), flush=True)
+    elif args.workload == "vegas":
+        import torch
+        import paper_1711_05683_b300 as hp
+        from paper_1711_05683_b300 import build as hp_build
+        hp_build.build()
+        torch.cuda.set_device(0)
+        hp.lib()
+        cases = ("dalitz", "flat10") if args.vegas_case == "both" else (args.vegas_case,)
+        print(json.dumps({"workload": "vegas", **run_vegas(args.vegas_calls, args.vegas_iterations,
+                                                           reps=args.steps, cases=cases)}), flush=True)
     else:
         run_ours(args)
 

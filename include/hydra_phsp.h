@@ -203,7 +203,7 @@ hydra_status hydra_phsp_evaluate(int n, uint64_t nevents, hydra_dtype dtype, hyd
  * equal shares of the total weight.  Iterations skip.. are combined with weights 1/var.
  * FP64 throughout.  bins = 1 is plain Monte Carlo.
  *   me, params   as hydra_phsp_integrate
- *   calls        points per iteration, 2 .. 2^36 (8 bytes of device scratch each)
+ *   calls        points per iteration, 2 .. 2^36 (8 + 4 ceil((3n-4)/4) bytes of device scratch each)
  *   iterations   >= 1; bins: 1..256 with (3n-4) bins <= 6144; alpha >= 0; 0 <= skip < iterations
  *   est, var     host arrays of `iterations` doubles: each iteration's estimate and variance
  *   result       host double[3]: combined estimate, its standard deviation, chi^2 per degree

@@ -9,19 +9,24 @@
 // Per iteration i (Philox stream i + 1):
 //   vegas_eval  point s: y_d = (x + 1/2) 2^-32 from Philox word d%4 of counter (s low, s high,
 //               d/4, i + 1); bin and position from exact integers (below); the event's
-//               weight and |ME|^2; f = F(u) J stored per point; the deterministic tile sums
-//               of f and f^2 (the integral's tile / segment order); the largest f^2.
-//   vegas_hist  per-bin sums of f^2 in 64-bit fixed point (order-independent integer adds).
+//               weight and |ME|^2; f = F(u) J and the point's D bins (one byte each, four
+//               to a word: word q of point s at [q][calls]) stored;
+//               the deterministic tile sums of f and f^2 (the integral's tile / segment
+//               order); the largest f^2.
+//   vegas_hist  per-bin sums of f^2 in 64-bit fixed point (order-independent integer adds)
+//               from the stored values and bins.
 //   host        estimate and variance; refinement of every dimension.
 //
 // Grid arithmetic.  With P = (2x + 1) K (< 2^41), the bin is b = floor(y K) = P >> 33 and the
 // position inside it is y K - b = rho 2^-33 with rho = P mod 2^33, both exact (y K has at
 // most 42 significant bits, so these are also what an FP64 evaluation of floor(y K) and
 // y K - b gives).  Edges are held as 64-bit fixed point G_b = g_b 2^64 and widths
-// W_b = G_{b+1} - G_b, so u 2^64 = G_b + floor(rho W_b 2^-33) to within one unit of 2^-64;
-// the Jacobian factor K (g_{b+1} - g_b) is the host's FP64 value.  Sorting the mass
-// variables and forming the kinetic gaps T (r_k - r_{k-1}) then work on exact integers, as in
-// the generator.
+// W_b = G_{b+1} - G_b, so u 2^64 = G_b + floor(rho W_b 2^-33) to within one unit of 2^-64.
+// The Jacobian factor K (g_{b+1} - g_b) is the host's FP64 value, held as a double-float
+// mantissa in [1, 2) and a binary exponent: the product over the D dimensions multiplies the
+// mantissas in double-float and adds the exponents, one FP64 rounding at the end instead of D
+// FP64 multiplications on B300's narrow FP64 pipe.  Sorting the mass variables and forming the
+// kinetic gaps T (r_k - r_{k-1}) work on exact integers, as in the generator.
 #include <cuda_runtime.h>
 #include <cmath>
 #include <cstdint>
@@ -42,14 +47,30 @@ __global__ void eval_reduce_segments(const TileSums* __restrict__ partials, uint
 __global__ void eval_finalize(const double* __restrict__ seg, uint64_t nseg, uint64_t nevents,
                               hydra_integral* __restrict__ out);
 
-constexpr int kVegasMaxCells = 6144;  // D * K grid cells held in shared memory (24 B each)
+constexpr int kVegasMaxCells = 6144;  // D * K grid cells held in shared memory (32 B each)
 constexpr int kVegasBlock = 256;
+constexpr int kVegasMaxChunks = 1 << 11;  // 2^36 points / (kChunkTiles tiles of 2048), as 64-bit words
 
 struct VegasCell {
-    uint64_t G;  // left edge g_b 2^64
-    uint64_t W;  // width (g_{b+1} - g_b) 2^64 (2^64 - 1 for a single bin)
-    double J;    // Jacobian factor K (g_{b+1} - g_b)
+    uint64_t G;     // left edge g_b 2^64
+    uint64_t W;     // width (g_{b+1} - g_b) 2^64 (2^64 - 1 for a single bin)
+    float jh, jl;   // Jacobian factor K (g_{b+1} - g_b) = (jh + jl) 2^je, 1 <= jh + jl < 2
+    int32_t je;
+    int32_t pad;
 };
+static_assert(sizeof(VegasCell) == 32, "cells are 32 bytes");
+
+// (m_hi + m_lo) 2^e as the nearest double, for a double-float mantissa in [1, 2^D) and any
+// integer e: the power of two is built from its bits in two factors (each a normal double),
+// so results below the double range round to a subnormal or zero as a plain product would.
+__device__ __forceinline__ double df_ldexp(df m, int e) {
+    const int e1 = e < -1022 ? -1022 : (e > 1023 ? 1023 : e);
+    int e2 = e - e1;
+    e2 = e2 < -1022 ? -1022 : (e2 > 1023 ? 1023 : e2);
+    const double p1 = __longlong_as_double(static_cast<long long>(e1 + 1023) << 52);
+    const double p2 = __longlong_as_double(static_cast<long long>(e2 + 1023) << 52);
+    return (df_to_double(m) * p1) * p2;
+}
 
 // Matrix-element constants (m0a^2, m0a Ga, m0b^2, m0b Gb, Re c, Im c) in FP64 and as
 // double-float pairs.
@@ -214,17 +235,24 @@ __global__ void __launch_bounds__(kVegasBlock) vegas_eval(const __grid_constant_
                                                           const VegasCell* __restrict__ grid, int K, uint32_t stream,
                                                           uint64_t calls, uint64_t tile_begin, uint64_t ntiles,
                                                           TileSums* __restrict__ partials, double* __restrict__ fvals,
-                                                          unsigned long long* __restrict__ max_f2) {
+                                                          uint32_t* __restrict__ bins,
+                                                          unsigned long long* __restrict__ max_f2,
+                                                          unsigned int* __restrict__ next_tile) {
     constexpr int D = 3 * N - 4;
     extern __shared__ VegasCell cells[];
     if constexpr (std::is_same_v<R, df>) df_sincos_table_init();
     for (int i = threadIdx.x; i < D * K; i += blockDim.x) cells[i] = grid[i];
     __syncthreads();
     const int lane = threadIdx.x & 31;
-    const uint64_t warp = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-    const uint64_t nwarps = (static_cast<uint64_t>(gridDim.x) * blockDim.x) >> 5;
     unsigned long long mx = 0;
-    for (uint64_t t = warp; t < ntiles; t += nwarps) {
+    // Tiles are taken from a counter (a persistent grid stays balanced across SMs whatever
+    // the tile count); each tile's sums land at its own index, so the result does not depend
+    // on which warp took it.
+    for (;;) {
+        unsigned int tn = 0;
+        if (lane == 0) tn = atomicAdd(next_tile, 1u);
+        const uint64_t t = __shfl_sync(0xffffffffu, tn, 0);
+        if (t >= ntiles) break;
         const uint64_t base = (tile_begin + t) * kTileEvents;
         double af = 0.0, af2 = 0.0;
         for (int g = 0; g < kLaneIters / kGroupEvents; ++g) {
@@ -233,12 +261,19 @@ __global__ void __launch_bounds__(kVegasBlock) vegas_eval(const __grid_constant_
                 const uint64_t s = base + static_cast<uint64_t>(32 * (g * kGroupEvents + i) + lane);
                 if (s < calls) {
                     uint64_t U[D];
-                    double jac = 1.0;
+                    uint32_t packed[(D + 3) / 4] = {};
+                    df jm{1.0f, 0.0f};
+                    int je = 0;
                     vegas_bins(C, s, stream, D, K, [&](int d, int b, uint64_t rho) {
+                        packed[d / 4] |= static_cast<uint32_t>(b) << (8 * (d % 4));
                         const VegasCell c = cells[d * K + b];
                         U[d] = c.G + ((__umul64hi(rho, c.W) << 31) | ((rho * c.W) >> 33));
-                        jac *= c.J;
+                        jm = jm * df{c.jh, c.jl};
+                        je += c.je;
                     });
+                    const double jac = df_ldexp(jm, je);
+#pragma unroll
+                    for (int q = 0; q < (D + 3) / 4; ++q) bins[static_cast<uint64_t>(q) * calls + s] = packed[q];
                     R E1, M2;
                     const double w = vegas_event<N, R>(C, U, E1, M2);
                     double me2 = 1.0;
@@ -279,11 +314,13 @@ __global__ void __launch_bounds__(kVegasBlock) vegas_eval(const __grid_constant_
 // Per-bin sums of f^2 in 64-bit fixed point, one unit = (largest f^2 of the iteration) / qnum
 // with qnum = 2^(62 - ceil(log2 calls)), so no bin can overflow: integer additions are order
 // independent, so the histogram and the refined grid are reproducible bit for bit.
-__global__ void __launch_bounds__(kVegasBlock) vegas_hist(const __grid_constant__ DecayConsts C, int D, int K,
-                                                          uint32_t stream, uint64_t calls, double qnum,
+template <int D>
+__global__ void __launch_bounds__(kVegasBlock) vegas_hist(int K, uint64_t calls, double qnum,
                                                           const double* __restrict__ fvals,
+                                                          const uint32_t* __restrict__ bins,
                                                           const unsigned long long* __restrict__ max_f2,
                                                           unsigned long long* __restrict__ hist) {
+    constexpr int kWords = (D + 3) / 4;
     extern __shared__ unsigned long long sh[];
     for (int i = threadIdx.x; i < D * K; i += blockDim.x) sh[i] = 0ull;
     __syncthreads();
@@ -292,13 +329,32 @@ __global__ void __launch_bounds__(kVegasBlock) vegas_hist(const __grid_constant_
     for (uint64_t s = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; s < calls;
          s += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
         const double f = fvals[s];
-        const unsigned long long q = static_cast<unsigned long long>(f * f * scale);
-        if (q == 0ull) continue;
-        vegas_bins(C, s, stream, D, K, [&](int d, int b, uint64_t) { atomicAdd(&sh[d * K + b], q); });
+        uint32_t wd[kWords];
+#pragma unroll
+        for (int q = 0; q < kWords; ++q) wd[q] = bins[static_cast<uint64_t>(q) * calls + s];
+        const unsigned long long qf = static_cast<unsigned long long>(f * f * scale);
+        if (qf == 0ull) continue;
+#pragma unroll
+        for (int d = 0; d < D; ++d) atomicAdd(&sh[d * K + ((wd[d / 4] >> (8 * (d % 4))) & 0xFFu)], qf);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < D * K; i += blockDim.x)
         if (sh[i]) atomicAdd(&hist[i], sh[i]);
+}
+
+static const void* vegas_hist_for(int n) {
+    switch (n) {
+        case 2: return reinterpret_cast<const void*>(&vegas_hist<2>);
+        case 3: return reinterpret_cast<const void*>(&vegas_hist<5>);
+        case 4: return reinterpret_cast<const void*>(&vegas_hist<8>);
+        case 5: return reinterpret_cast<const void*>(&vegas_hist<11>);
+        case 6: return reinterpret_cast<const void*>(&vegas_hist<14>);
+        case 7: return reinterpret_cast<const void*>(&vegas_hist<17>);
+        case 8: return reinterpret_cast<const void*>(&vegas_hist<20>);
+        case 9: return reinterpret_cast<const void*>(&vegas_hist<23>);
+        case 10: return reinterpret_cast<const void*>(&vegas_hist<26>);
+    }
+    return nullptr;
 }
 
 template <typename R, int ME>
@@ -363,7 +419,18 @@ static void grid_cells(const double* g, int K, VegasCell* out) {
     for (int b = 0; b < K; ++b) {
         out[b].G = G[b];
         out[b].W = (K == 1) ? ~uint64_t{0} : (b + 1 < K ? G[b + 1] : uint64_t{0}) - G[b];  // G_K = 2^64 (mod 2^64)
-        out[b].J = K * (g[b + 1] - g[b]);
+        const double J = K * (g[b + 1] - g[b]);
+        int e = 0;
+        const double m = 2.0 * std::frexp(J, &e);  // J = m 2^(e-1), 1 <= m < 2 (J > 0)
+        out[b].jh = static_cast<float>(m);
+        out[b].jl = static_cast<float>(m - static_cast<double>(out[b].jh));
+        out[b].je = e - 1;
+        out[b].pad = 0;
+        if (!(J > 0.0)) {  // a zero-width bin: J = 0, as in the plain product
+            out[b].jh = 0.0f;
+            out[b].jl = 0.0f;
+            out[b].je = 0;
+        }
     }
 }
 
@@ -373,9 +440,11 @@ struct VegasScratch {
     double* segs = nullptr;
     uint64_t seg_cap = 0;
     double* fvals = nullptr;
+    uint32_t* bins = nullptr;  // [ceil(D/4)][calls]
     uint64_t fcap = 0;
+    int bins_d = 0;
     VegasCell* cells = nullptr;
-    unsigned long long* hist = nullptr;  // [D*K] bin sums, then the largest f^2 (as bits)
+    unsigned long long* hist = nullptr;  // [D*K] bin sums, the largest f^2 (as bits), tile counters
     hydra_integral* d_res = nullptr;
     void* h_pin = nullptr;               // pinned: result, histogram, cells
 };
@@ -430,7 +499,7 @@ hydra_status hydra_phsp_vegas(double M, int n, const double* masses, uint64_t se
     std::lock_guard<std::mutex> lk(s->mu);
     const uint64_t ntiles = (calls + kTileEvents - 1) / kTileEvents;
     const uint64_t nseg = (ntiles + kSegTiles - 1) / kSegTiles;
-    const size_t hist_words = static_cast<size_t>(kVegasMaxCells) + 1;
+    const size_t hist_words = static_cast<size_t>(kVegasMaxCells) + 1 + kVegasMaxChunks;
     const size_t cell_bytes = static_cast<size_t>(kVegasMaxCells) * sizeof(VegasCell);
     if (!s->tiles) {
         if (cudaMalloc(&s->tiles, kChunkTiles * sizeof(TileSums)) != cudaSuccess ||
@@ -453,15 +522,23 @@ hydra_status hydra_phsp_vegas(double M, int n, const double* masses, uint64_t se
         }
         s->seg_cap = nseg;
     }
-    if (calls > s->fcap) {
+    if (calls > s->fcap || D > s->bins_d) {
+        const uint64_t cap = calls > s->fcap ? calls : s->fcap;
+        const int dcap = D > s->bins_d ? D : s->bins_d;
         if (s->fvals) cudaFree(s->fvals);
+        if (s->bins) cudaFree(s->bins);
         s->fvals = nullptr;
+        s->bins = nullptr;
         s->fcap = 0;
-        if (cudaMalloc(&s->fvals, calls * sizeof(double)) != cudaSuccess) {
+        s->bins_d = 0;
+        if (cudaMalloc(&s->fvals, cap * sizeof(double)) != cudaSuccess ||
+            cudaMalloc(&s->bins, cap * static_cast<uint64_t>((dcap + 3) / 4) * sizeof(uint32_t)) != cudaSuccess) {
             cudaGetLastError();
-            return fail(HYDRA_ERR_OOM, "VEGAS point values (%llu calls)", static_cast<unsigned long long>(calls));
+            return fail(HYDRA_ERR_OOM, "VEGAS point values and bins (%llu calls, %d dimensions)",
+                        static_cast<unsigned long long>(calls), D);
         }
-        s->fcap = calls;
+        s->fcap = cap;
+        s->bins_d = dcap;
     }
     const size_t smem = static_cast<size_t>(D) * K * sizeof(VegasCell);
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(cell_bytes));
@@ -493,7 +570,7 @@ hydra_status hydra_phsp_vegas(double M, int n, const double* masses, uint64_t se
         for (uint64_t t0 = 0; t0 < ntiles; t0 += kChunkTiles) {
             const uint64_t nt = ntiles - t0 < kChunkTiles ? ntiles - t0 : kChunkTiles;
             const uint64_t need = (nt * 32 + kVegasBlock - 1) / kVegasBlock;
-            const uint64_t cap = static_cast<uint64_t>(sms) * per_sm;
+            const uint64_t cap = static_cast<uint64_t>(sms) * per_sm;  // one persistent wave
             const unsigned grid = static_cast<unsigned>(need < cap ? need : cap);
             const VegasCell* gp = s->cells;
             int Kv = K;
@@ -501,8 +578,10 @@ hydra_status hydra_phsp_vegas(double M, int n, const double* masses, uint64_t se
             uint64_t cl = calls, tb = t0, ntv = nt;
             TileSums* tp = s->tiles;
             double* fv = s->fvals;
+            uint32_t* bp = s->bins;
             unsigned long long* mp = d_max;
-            void* args[] = {&C, &PM, &gp, &Kv, &sid, &cl, &tb, &ntv, &tp, &fv, &mp};
+            unsigned int* ctr = reinterpret_cast<unsigned int*>(d_max + 1 + t0 / kChunkTiles);
+            void* args[] = {&C, &PM, &gp, &Kv, &sid, &cl, &tb, &ntv, &tp, &fv, &bp, &mp, &ctr};
             err = cudaLaunchKernel(kern, dim3(grid), dim3(kVegasBlock), args, smem, cs);
             if (err != cudaSuccess) return cuda_fail(err, "VEGAS evaluation launch");
             const uint64_t ns = (nt + kSegTiles - 1) / kSegTiles;
@@ -513,8 +592,17 @@ hydra_status hydra_phsp_vegas(double M, int n, const double* masses, uint64_t se
             const uint64_t hneed = (calls + kVegasBlock - 1) / kVegasBlock;
             const uint64_t hcap = static_cast<uint64_t>(sms) * 4;
             const unsigned hgrid = static_cast<unsigned>(hneed < hcap ? hneed : hcap);
-            vegas_hist<<<hgrid, kVegasBlock, static_cast<size_t>(D) * K * sizeof(unsigned long long), cs>>>(
-                C, D, K, stream_id, calls, qnum, s->fvals, d_max, s->hist);
+            const double* fv = s->fvals;
+            const uint32_t* bp = s->bins;
+            const unsigned long long* mp = d_max;
+            unsigned long long* hp = s->hist;
+            int Kv = K;
+            uint64_t cl = calls;
+            double qn = qnum;
+            void* hargs[] = {&Kv, &cl, &qn, &fv, &bp, &mp, &hp};
+            err = cudaLaunchKernel(vegas_hist_for(n), dim3(hgrid), dim3(kVegasBlock), hargs,
+                                   static_cast<size_t>(D) * K * sizeof(unsigned long long), cs);
+            if (err != cudaSuccess) return cuda_fail(err, "VEGAS histogram launch");
         }
         err = cudaGetLastError();
         if (err == cudaSuccess) err = cudaMemcpyAsync(h_res, s->d_res, sizeof(hydra_integral), cudaMemcpyDeviceToHost, cs);
