@@ -503,8 +503,8 @@ def run_extras(nev: int = 100_000_000, reps: int = 3) -> dict:
 # ----------------------------------------------------------------------------- VEGAS
 # Thread instructions per point of the double-float VEGAS kernels (ncu smsp__inst_executed.sum
 # x 32 / points on 4e6-point iterations, 100 bins; profiles/vegas_eval_df_dalitz_4e6.md).
-VEGAS_INSTR_PER_POINT = {("dalitz", "eval"): 1452, ("dalitz", "hist"): 320,
-                         ("flat10", "eval"): 2565, ("flat10", "hist"): 1200}
+VEGAS_INSTR_PER_POINT = {("dalitz", "eval"): 1536, ("dalitz", "hist"): 140,
+                         ("flat10", "eval"): 2785, ("flat10", "hist"): 557}
 
 
 def run_vegas(calls: int = 100_000_000, iterations: int = 10, reps: int = 3,
