@@ -42,10 +42,10 @@ INT_CFG = workloads.D0_DALITZ
 # command and table are in profiles/launches_instr_sweep_4e6.md).  They are the per-event
 # work of the issue-bound FP64 (double-float) generator, the dominant kernel of the step.
 INSTR_PER_EVENT = {
-    ("f32", 2): 81, ("f32", 3): 211, ("f32", 4): 296, ("f32", 5): 421, ("f32", 6): 539,
+    ("f32", 2): 91, ("f32", 3): 211, ("f32", 4): 296, ("f32", 5): 421, ("f32", 6): 539,
     ("f32", 7): 668, ("f32", 8): 794, ("f32", 9): 924, ("f32", 10): 1044,
-    ("f64", 2): 535, ("f64", 3): 1341, ("f64", 4): 2064, ("f64", 5): 2783, ("f64", 6): 3528,
-    ("f64", 7): 4276, ("f64", 8): 4987, ("f64", 9): 5744, ("f64", 10): 6492,
+    ("f64", 2): 498, ("f64", 3): 1215, ("f64", 4): 1850, ("f64", 5): 2496, ("f64", 6): 3159,
+    ("f64", 7): 3822, ("f64", 8): 4457, ("f64", 9): 5130, ("f64", 10): 5802,
 }
 
 

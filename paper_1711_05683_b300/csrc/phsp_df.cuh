@@ -57,21 +57,24 @@ __device__ __forceinline__ df operator+(df x, df y) {
 __device__ __forceinline__ df operator-(df x) { return df{-x.hi, -x.lo}; }
 __device__ __forceinline__ df operator-(df x, df y) { return x + (-y); }
 
-// x * y
+// x * y.  The result (p, e) is left unnormalised: p = fl(x.hi y.hi) and |e| is a few ulp(p)
+// (the exact rounding error of p plus the cross terms).  Every consumer takes such pairs:
+// additions renormalise, products fold e into their own cross terms, and reciprocal and
+// square root form their residual from both parts; the error stays ~2^-46 relative.
 __device__ __forceinline__ df operator*(df x, df y) {
     const float p = __fmul_rn(x.hi, y.hi);
     float e = __fmaf_rn(x.hi, y.hi, -p);
     e = __fmaf_rn(x.hi, y.lo, e);
     e = __fmaf_rn(x.lo, y.hi, e);
-    return df_fast_two_sum(p, e);
+    return df{p, e};
 }
 
-// x * a for an FP32 a
+// x * a for an FP32 a (unnormalised like the product above)
 __device__ __forceinline__ df operator*(df x, float a) {
     const float p = __fmul_rn(x.hi, a);
     float e = __fmaf_rn(x.hi, a, -p);
     e = __fmaf_rn(x.lo, a, e);
-    return df_fast_two_sum(p, e);
+    return df{p, e};
 }
 
 // 1/y: seed r = rcp.approx(hi); e = 1 - y r (exact to first order in df); r (1 + e)

@@ -269,6 +269,7 @@ __global__ void __launch_bounds__(kVegasBlock) vegas_eval(const __grid_constant_
                         const VegasCell c = cells[d * K + b];
                         U[d] = c.G + ((__umul64hi(rho, c.W) << 31) | ((rho * c.W) >> 33));
                         jm = jm * df{c.jh, c.jl};
+                        jm = df_fast_two_sum(jm.hi, jm.lo);  // renormalise along the D-long chain
                         je += c.je;
                     });
                     const double jac = df_ldexp(jm, je);
