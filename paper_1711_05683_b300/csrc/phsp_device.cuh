@@ -174,7 +174,7 @@ template <> struct Prec<df> {
     using W = double;
     using Out = double;
     __device__ static df scale(df x, float pow2) { return df_scale(x, pow2); }
-    __device__ static df half_odd(uint32_t y) { return df_scale(df_half_odd_u32(y), 2147483648.0f); }
+    __device__ static df half_odd(uint32_t y) { return df_half_odd_raw(y); }
     __device__ static df one_plus_cos(uint32_t x) { return df_half_odd_u32(x); }
     __device__ static df one_minus_cos(uint32_t x) { return df_half_odd_u32(~x); }
     __device__ static df cos_of(uint32_t x) { return df_half_odd_centered(x); }

@@ -106,15 +106,16 @@ __device__ __forceinline__ df df_sqrt(df x) {
     return df_fast_two_sum(s0, __fmul_rn(res, __fmul_rn(0.5f, r)));
 }
 
-// Exact conversion of a 32-bit unsigned / signed integer.
+// Exact conversion of a 32-bit unsigned / signed integer: v = (v & ~0xFF) + (v & 0xFF), both
+// parts exact in FP32.  The high part is 0 or at least 256 in magnitude and the low part below
+// 256, so Dekker's FastTwoSum gives the same exact pair as TwoSum.
 __device__ __forceinline__ df df_from_u32(uint32_t v) {
-    return df_two_sum(__uint2float_rz(v & 0xFFFFFF00u), __uint2float_rz(v & 0xFFu));
+    return df_fast_two_sum(__uint2float_rz(v & 0xFFFFFF00u), __uint2float_rz(v & 0xFFu));
 }
 
 __device__ __forceinline__ df df_from_i32(int32_t v) {
-    // v = (v & ~0xFF) + (v & 0xFF), both parts exact in FP32
     const int32_t high = static_cast<int32_t>(static_cast<uint32_t>(v) & 0xFFFFFF00u);
-    return df_two_sum(__int2float_rz(high), __uint2float_rz(static_cast<uint32_t>(v) & 0xFFu));
+    return df_fast_two_sum(__int2float_rz(high), __uint2float_rz(static_cast<uint32_t>(v) & 0xFFu));
 }
 
 // FP32 -> FP64 by bit manipulation on the integer pipe (exact for normal numbers; zero and
@@ -132,20 +133,34 @@ __device__ __forceinline__ double f32_to_f64_bits(float f) {
     return __hiloint2double(static_cast<int>(hi), static_cast<int>(lo));
 }
 
-// Nearest double to hi + lo.
+// The same rebias without the zero / subnormal case: exact for normal numbers; zero and FP32
+// subnormals map to a value below 2^-126 in magnitude.  Used for the low part of a
+// double-float, whose contribution below 2^-126 is far under the ulp of any result.
+__device__ __forceinline__ double f32_to_f64_bits_lo(float f) {
+    const uint32_t b = __float_as_uint(f);
+    const uint32_t hi = (((b & 0x7FFFFFFFu) >> 3) + 0x38000000u) | (b & 0x80000000u);
+    return __hiloint2double(static_cast<int>(hi), static_cast<int>(b << 29));
+}
+
+// Nearest double to hi + lo (to within 2^-126 absolute when lo is zero or subnormal).
 __device__ __forceinline__ double df_to_double(df x) {
-    return __dadd_rn(f32_to_f64_bits(x.hi), f32_to_f64_bits(x.lo));
+    return __dadd_rn(f32_to_f64_bits(x.hi), f32_to_f64_bits_lo(x.lo));
 }
 
 // x * 2^k for an exact power of two (both parts scale exactly).
 __device__ __forceinline__ df df_scale(df x, float pow2) { return df{__fmul_rn(x.hi, pow2), __fmul_rn(x.lo, pow2)}; }
 
 // (x + 1/2) 2^-31 for a 32-bit unsigned x (= 1 + cos(theta) when x is a cos(theta) draw):
-// x + 1/2 = (x & ~0xFF) + ((x & 0xFF) + 1/2), both parts exact in FP32, then an exact scale.
-__device__ __forceinline__ df df_half_odd_u32(uint32_t x) {
+// x + 1/2 = (x & ~0xFF) + ((x & 0xFF) + 1/2), both parts exact in FP32 (the first 0 or >= 256,
+// the second in (0, 256): FastTwoSum is exact), then an exact scale.
+__device__ __forceinline__ df df_half_odd_raw(uint32_t x) {  // x + 1/2, unscaled
     const float a = __uint2float_rz(x & 0xFFFFFF00u);
     const float b = __fadd_rn(__uint2float_rz(x & 0xFFu), 0.5f);
-    return df_scale(df_two_sum(a, b), 4.656612873077392578125e-10f);
+    return df_fast_two_sum(a, b);
+}
+
+__device__ __forceinline__ df df_half_odd_u32(uint32_t x) {
+    return df_scale(df_half_odd_raw(x), 4.656612873077392578125e-10f);
 }
 
 // (x - 2^31 + 1/2) 2^-31 for a 32-bit unsigned x (= cos(theta) = 2u - 1 exactly)
@@ -153,7 +168,7 @@ __device__ __forceinline__ df df_half_odd_centered(uint32_t x) {
     const int32_t c = static_cast<int32_t>(x ^ 0x80000000u);
     const float a = __int2float_rz(static_cast<int32_t>(static_cast<uint32_t>(c) & 0xFFFFFF00u));
     const float b = __fadd_rn(__uint2float_rz(x & 0xFFu), 0.5f);
-    return df_scale(df_two_sum(a, b), 4.656612873077392578125e-10f);
+    return df_scale(df_fast_two_sum(a, b), 4.656612873077392578125e-10f);
 }
 
 // x + f for an FP32 f with |f| <= |x.hi| (a correction term): FastTwoSum and renormalise.
