@@ -202,6 +202,19 @@ def run_ours(args) -> None:
             dist.barrier()
         torch.cuda.synchronize()
 
+    # Measured device ceilings (outside the timed region): FP32 / FP64 FMA rates and the
+    # write-only HBM bandwidth of 16-byte stores over 4 GB.
+    probe_buf = torch.empty(1 << 32, dtype=torch.uint8, device="cuda")
+    fma32 = hp.probe_fma_rate("f32", 200_000)
+    fma64 = hp.probe_fma_rate("f64", 4_000)
+    measured = {"fp32_fma_per_s": fma32, "fp32_tflops": round(2 * fma32 / 1e12, 2),
+                "fp64_fma_per_s": fma64, "fp64_tflops": round(2 * fma64 / 1e12, 3),
+                "hbm_write_gbs": round(hp.probe_write_bandwidth(probe_buf, 5), 1),
+                "src": "hydra_probe_fma_rate (8 independent FMA chains per thread, all SMs) and "
+                       "hydra_probe_write_bandwidth (16-byte stores over 4 GB), this run"}
+    del probe_buf
+    torch.cuda.empty_cache()
+
     for _ in range(args.warmup):
         step(False)
     barrier()
@@ -274,14 +287,23 @@ def run_ours(args) -> None:
         return
 
     peaks = load_peaks()
+    n_sms = torch.cuda.get_device_properties(0).multi_processor_count
+    issue_limit = n_sms * 4 * 32 * (clk.get("sm_mhz") or clk.get("sm_max_mhz") or 2032.0) * 1e6
     breakdown = []
     for k, (dtype, massive, n) in enumerate(items):
         ms = per_launch_ms[k] / args.steps
         gbs = bytes_per_event(n, dtype) * nev / (ms / 1e3) / 1e9
+        # per-kernel roofline: the slower of the output bytes at the measured HBM peak and the
+        # instructions at the SM issue limit
+        by_hbm = peaks["hbm_gbs"] * 1e9 / bytes_per_event(n, dtype)
+        by_issue = issue_limit / INSTR_PER_EVENT[(dtype, n)]
+        roof_ev = min(by_hbm, by_issue)
         breakdown.append({"kernel": f"phsp_generate_kernel<{n},{'float' if dtype == 'f32' else 'double'}>",
                           "n": n, "dtype": dtype, "massive": massive, "events": nev,
                           "ms": round(ms, 4), "events_per_s": nev / (ms / 1e3),
-                          "hbm_gbs": round(gbs, 1), "hbm_frac": round(gbs / peaks["hbm_gbs"], 4)})
+                          "hbm_gbs": round(gbs, 1), "hbm_frac": round(gbs / peaks["hbm_gbs"], 4),
+                          "roofline_events_per_s": roof_ev, "roofline_bound": "hbm" if by_hbm <= by_issue else "issue",
+                          "roofline_frac": round(nev / (ms / 1e3) / roof_ev, 4)})
     int_ms = per_launch_ms[-1] / args.steps
     breakdown.append({"kernel": "phsp_integrate_tiles<3,float,DALITZ_2BW>+reduce", "events": int_events,
                       "ms": round(int_ms, 4), "events_per_s": int_events / (int_ms / 1e3),
@@ -316,6 +338,8 @@ def run_ours(args) -> None:
                     "frac": round(achieved / issue_peak, 4),
                     "peak_src": f"SM issue limit: {sms} SMs x 4 schedulers x 32 lanes x {sm_mhz:.0f} MHz (sampled)",
                     "work_src": "instructions per event from ncu (INSTR_PER_EVENT)",
+                    "measured_issue_peak": round(measured["fp32_fma_per_s"] / 1e12, 2),
+                    "frac_of_measured_issue_peak": round(achieved / (measured["fp32_fma_per_s"] / 1e12), 4),
                     "hbm_gbs": round(hbm, 1), "hbm_frac_of_measured": round(hbm / peaks["hbm_gbs"], 4),
                     "traffic": round((tot_bytes / len(rows) - 64e6) / 1e9, 3),
                     "traffic_note": "GB per launch: ncu dram read+write on 4e6-event launches is the algorithmic "
@@ -342,7 +366,12 @@ def run_ours(args) -> None:
                                     "peak": peaks["hbm_gbs"], "unit": "GB/s", "peak_src": "MEASURED_PEAKS hbm_gbs (copy)",
                                     "frac": round(f32_bytes / (f32_ms / 1e3) / 1e9 / peaks["hbm_gbs"], 4),
                                     "issue_frac": round(sum(INSTR_PER_EVENT[("f32", x["n"])] * x["events"] for x in f32)
-                                                        / (f32_ms / 1e3) / 1e12 / issue_peak, 4)},
+                                                        / (f32_ms / 1e3) / 1e12 / issue_peak, 4),
+                                    "frac_of_write_peak": round(f32_bytes / (f32_ms / 1e3) / 1e9 / measured["hbm_write_gbs"], 4),
+                                    "write_peak_gbs": measured["hbm_write_gbs"],
+                                    "frac_of_per_kernel_roofline": round(
+                                        sum(x["events"] / x["roofline_events_per_s"] for x in f32) / (f32_ms / 1e3), 4)},
+        "measured_peaks": measured,
         "dominant": dominant, "family_ms_per_step": {k: round(v, 3) for k, v in fam_ms.items()},
         "breakdown": breakdown, "clocks": clk, "e2e": e2e,
         "launch_shapes": {"source": tuning.get("source"),

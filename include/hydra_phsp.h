@@ -388,6 +388,22 @@ typedef enum hydra_fp64_arith {
 hydra_status hydra_set_fp64_arith(hydra_fp64_arith arith);
 hydra_fp64_arith hydra_get_fp64_arith(void);
 
+/*
+ * Device ceilings for rooflines (no counterpart in the paper: these measure the GPU the
+ * library runs on).  hydra_probe_fma_rate runs independent chains of FP32 or FP64 fused
+ * multiply-adds in registers on every SM and returns the rate in FMA instructions per second
+ * (FLOP/s = 2x; for FP32 this is also the SM instruction-issue limit, one warp instruction per
+ * scheduler per clock).  hydra_probe_write_bandwidth writes the caller's device buffer with
+ * 16-byte stores `reps` times at each of eight launch shapes (4..32 blocks of 256 threads per
+ * SM, one or four stores in flight per thread) and returns the best write-only rate in GB/s
+ * (use a buffer far larger than L2).  Both block until done; iterations scale the FMA probe's
+ * duration.
+ * Errors: INVALID_ARG, MISALIGNED (buffer not 16-byte aligned), OOM, CUDA.
+ */
+hydra_status hydra_probe_fma_rate(hydra_dtype dtype, int iterations, double *fma_per_s, hydra_stream_t stream);
+hydra_status hydra_probe_write_bandwidth(void *buffer, uint64_t bytes, int reps, double *gb_per_s,
+                                         hydra_stream_t stream);
+
 /* Release the per-device scratch memory of the library (all devices).  Not thread safe
  * with respect to calls in flight. */
 hydra_status hydra_shutdown(void);

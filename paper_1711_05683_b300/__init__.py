@@ -80,6 +80,8 @@ def lib() -> ctypes.CDLL:
         L.hydra_phsp_gather.argtypes = [i, i, vp, u64, vp, vp, u64, vp, u64, vp, vp]
         L.hydra_phsp_evaluate.argtypes = [i, u64, i, i, dp, i, vp, u64, vp, vp, ctypes.POINTER(Integral), vp]
         L.hydra_phsp_vegas.argtypes = [d, i, dp, u64, i, dp, i, u64, i, i, d, i, dp, dp, dp, dp, vp]
+        L.hydra_probe_fma_rate.argtypes = [i, i, dp, vp]
+        L.hydra_probe_write_bandwidth.argtypes = [vp, u64, i, dp, vp]
         L.hydra_get_fp64_arith.restype = i
         L.hydra_batch_create.argtypes = [i, u64, ctypes.POINTER(vp)]
         L.hydra_batch_run.argtypes = [vp, vp, i, i, vp]
@@ -271,6 +273,22 @@ def vegas(M: float, masses, seed: int, calls: int, iterations: int, *, bins: int
                                   grid.ctypes.data_as(dp), _stream_handle(stream)))
     return {"est": est, "var": var, "mean": float(res[0]), "sigma": float(res[1]), "chi2_dof": float(res[2]),
             "grid": grid}
+
+
+def probe_fma_rate(dtype="f32", iterations: int = 100_000, stream=None) -> float:
+    """Measured fused multiply-add rate of the device (FMA instructions per second)."""
+    r = ctypes.c_double()
+    _check(lib().hydra_probe_fma_rate(_dtype_code(dtype), int(iterations), ctypes.byref(r), _stream_handle(stream)))
+    return r.value
+
+
+def probe_write_bandwidth(buffer, reps: int = 5, stream=None) -> float:
+    """Measured write-only bandwidth (GB/s) over a device tensor (16-byte stores)."""
+    r = ctypes.c_double()
+    nbytes = buffer.numel() * buffer.element_size()
+    _check(lib().hydra_probe_write_bandwidth(ctypes.c_void_p(buffer.data_ptr()), int(nbytes), int(reps),
+                                             ctypes.byref(r), _stream_handle(stream)))
+    return r.value
 
 
 def generate_sequential(M: float, masses, i: int, sub_masses, nevents: int, seed: int, sub_seed: int, *,
