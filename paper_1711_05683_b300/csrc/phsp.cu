@@ -780,9 +780,15 @@ hydra_status hydra_get_launch_config(hydra_kernel_kind kind, int n, hydra_dtype 
 }
 
 hydra_status hydra_shutdown(void) {
+    release_extras_scratch();
+    release_vegas_scratch();
     std::lock_guard<std::mutex> lk(g_scratch_mu);
-    for (DeviceScratch*& s : g_scratch) {
+    int cur = 0;
+    cudaGetDevice(&cur);
+    for (size_t d = 0; d < g_scratch.size(); ++d) {
+        DeviceScratch*& s = g_scratch[d];
         if (!s) continue;
+        cudaSetDevice(static_cast<int>(d));
         if (s->tiles) cudaFree(s->tiles);
         if (s->segs) cudaFree(s->segs);
         if (s->d_result) cudaFree(s->d_result);
@@ -796,6 +802,7 @@ hydra_status hydra_shutdown(void) {
         delete s;
         s = nullptr;
     }
+    cudaSetDevice(cur);
     return HYDRA_OK;
 }
 

@@ -398,6 +398,41 @@ static EvalScratch* eval_scratch() {
     return g_ev[dev];
 }
 
+// Frees the moving-parent / unweighting / evaluation scratch of every device (hydra_shutdown).
+void release_extras_scratch() {
+    int cur = 0;
+    cudaGetDevice(&cur);
+    {
+        std::lock_guard<std::mutex> lk(g_uw_mu);
+        for (size_t d = 0; d < g_uw.size(); ++d) {
+            UwScratch* s = g_uw[d];
+            if (!s) continue;
+            cudaSetDevice(static_cast<int>(d));
+            if (s->counts) cudaFree(s->counts);
+            if (s->offsets) cudaFree(s->offsets);
+            if (s->wmax) cudaFree(s->wmax);
+            if (s->h) cudaFreeHost(s->h);
+            delete s;
+            g_uw[d] = nullptr;
+        }
+    }
+    {
+        std::lock_guard<std::mutex> lk(g_ev_mu);
+        for (size_t d = 0; d < g_ev.size(); ++d) {
+            EvalScratch* s = g_ev[d];
+            if (!s) continue;
+            cudaSetDevice(static_cast<int>(d));
+            if (s->tiles) cudaFree(s->tiles);
+            if (s->segs) cudaFree(s->segs);
+            if (s->d_res) cudaFree(s->d_res);
+            if (s->h_res) cudaFreeHost(s->h_res);
+            delete s;
+            g_ev[d] = nullptr;
+        }
+    }
+    cudaSetDevice(cur);
+}
+
 }  // namespace hydra
 
 using namespace hydra;

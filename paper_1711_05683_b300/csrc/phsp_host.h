@@ -32,4 +32,8 @@ extern std::atomic<int> g_fp64_arith;
 // Grid for a grid-stride kernel: min(blocks needed, resident blocks per SM x SMs).
 int grid_for(const void* kernel, int block, uint64_t work_items);
 
+// Release of the scratch owned by the other translation units (called by hydra_shutdown).
+void release_extras_scratch();
+void release_vegas_scratch();
+
 }  // namespace hydra

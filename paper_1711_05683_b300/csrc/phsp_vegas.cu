@@ -461,6 +461,29 @@ static VegasScratch* vegas_scratch() {
     return g_vg[dev];
 }
 
+// Frees the VEGAS scratch of every device (hydra_shutdown).
+void release_vegas_scratch() {
+    int cur = 0;
+    cudaGetDevice(&cur);
+    std::lock_guard<std::mutex> lk(g_vg_mu);
+    for (size_t d = 0; d < g_vg.size(); ++d) {
+        VegasScratch* s = g_vg[d];
+        if (!s) continue;
+        cudaSetDevice(static_cast<int>(d));
+        if (s->tiles) cudaFree(s->tiles);
+        if (s->segs) cudaFree(s->segs);
+        if (s->fvals) cudaFree(s->fvals);
+        if (s->bins) cudaFree(s->bins);
+        if (s->cells) cudaFree(s->cells);
+        if (s->hist) cudaFree(s->hist);
+        if (s->d_res) cudaFree(s->d_res);
+        if (s->h_pin) cudaFreeHost(s->h_pin);
+        delete s;
+        g_vg[d] = nullptr;
+    }
+    cudaSetDevice(cur);
+}
+
 }  // namespace hydra
 
 using namespace hydra;

@@ -137,3 +137,53 @@ def test_sequential_decay_matches_oracle_composition(dtype):
     tol2 = TOL[dtype] if dtype == "f64" else 1e-4  # stage 2 inherits stage 1's FP32 momenta
     assert (np.abs(p2[:, :, :nev].double().cpu().numpy() - r2) / scale).max() <= tol2
     np.testing.assert_allclose((w1 * w2).double().cpu().numpy(), rw1 * rw2, rtol=max(TOL[dtype], 1e-12) * 4)
+
+
+def test_shutdown_releases_scratch_and_calls_recover():
+    """hydra_shutdown frees the scratch of every entry point (integral, evaluation,
+    unweighting, VEGAS); later calls allocate again and give the same bits."""
+    d = workloads.D0_DALITZ
+
+    def calls():
+        r = hp.integrate(d["M"], d["masses"], 1 << 22, 7, me=hp.ME_DALITZ_2BW, params=d["params"])
+        p, w = hp.generate(d["M"], d["masses"], 1 << 20, 3, dtype="f64")
+        e, _ = hp.evaluate(p, w, me=hp.ME_DALITZ_2BW, params=d["params"], dtype="f64")
+        k, _ = hp.unweight(3, w, 3, dtype="f64")
+        v = hp.vegas(d["M"], d["masses"], 5, 1 << 24, 2, bins=20, me=hp.ME_DALITZ_2BW, params=d["params"])
+        torch.cuda.synchronize()
+        return r, e, k.cpu(), v
+
+    def free_after_shutdown():
+        hp.shutdown()
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        return torch.cuda.mem_get_info()[0]
+
+    calls()  # loads every kernel once, so module memory is not counted below
+    free0 = free_after_shutdown()
+    r1, e1, k1, v1 = calls()
+    free1 = torch.cuda.mem_get_info()[0]
+    assert free0 - free1 > 150e6  # VEGAS alone holds 2^24 x 12 bytes of point scratch
+    free2 = free_after_shutdown()
+    assert free2 >= free0 - 8e6
+    r2, e2, k2, v2 = calls()
+    assert r1 == r2 and e1 == e2
+    assert torch.equal(k1, k2)
+    assert np.array_equal(v1["est"], v2["est"]) and np.array_equal(v1["grid"], v2["grid"])
+
+
+def test_probes_measure_plausible_ceilings():
+    """The roofline probes: FP32 FMA rate within the SM issue limit, FP64 far below it, a
+    write bandwidth between 1 TB/s and the HBM3e nominal 7.7 TB/s; bad arguments refused."""
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    f32 = hp.probe_fma_rate("f32", 20_000)
+    f64 = hp.probe_fma_rate("f64", 500)
+    assert 0.3 * sms * 128 * 1.0e9 < f32 < sms * 128 * 2.2e9
+    assert 0 < f64 < f32 / 8
+    buf = torch.empty(1 << 30, dtype=torch.uint8, device="cuda")
+    gbs = hp.probe_write_bandwidth(buf, 2)
+    assert 1000 < gbs < 7700
+    with pytest.raises(hp.HydraError, match="MISALIGNED"):
+        hp.probe_write_bandwidth(buf[1:], 1)
+    with pytest.raises(hp.HydraError, match="INVALID_ARG"):
+        hp.probe_fma_rate("f32", 0)
