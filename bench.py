@@ -44,8 +44,8 @@ INT_CFG = workloads.D0_DALITZ
 INSTR_PER_EVENT = {
     ("f32", 2): 91, ("f32", 3): 211, ("f32", 4): 296, ("f32", 5): 421, ("f32", 6): 539,
     ("f32", 7): 668, ("f32", 8): 794, ("f32", 9): 924, ("f32", 10): 1044,
-    ("f64", 2): 464, ("f64", 3): 1143, ("f64", 4): 1742, ("f64", 5): 2355, ("f64", 6): 2981,
-    ("f64", 7): 3614, ("f64", 8): 4215, ("f64", 9): 4850, ("f64", 10): 5488,
+    ("f64", 2): 460, ("f64", 3): 1136, ("f64", 4): 1732, ("f64", 5): 2346, ("f64", 6): 2966,
+    ("f64", 7): 3596, ("f64", 8): 4194, ("f64", 9): 4829, ("f64", 10): 5464,
 }
 
 

@@ -192,7 +192,7 @@ __device__ __forceinline__ df df_add_small(df x, float f) {
 // then the angle-sum identities, and branch-free signs/swap for the quadrant.
 // ------------------------------------------------------------------------------------
 struct SinCosTable {
-    float sh[256], sl[256], ch[256], cl[256];  // sin/cos(k pi/1024), k = 0..255, hi and lo parts
+    float4 e[256];  // (sin hi, sin lo, cos hi, cos lo) of k pi/1024, k = 0..255: one 16-byte load
 };
 
 // The table lives in shared memory of the kernels that compute in df; each block fills it
@@ -204,10 +204,8 @@ __device__ __forceinline__ void df_sincos_table_init() {
         double sv, cv;
         sincospi(static_cast<double>(k) / 1024.0, &sv, &cv);
         const float sh = __double2float_rn(sv), ch = __double2float_rn(cv);
-        s_sincos_table.sh[k] = sh;
-        s_sincos_table.sl[k] = __double2float_rn(sv - static_cast<double>(sh));
-        s_sincos_table.ch[k] = ch;
-        s_sincos_table.cl[k] = __double2float_rn(cv - static_cast<double>(ch));
+        s_sincos_table.e[k] = make_float4(sh, __double2float_rn(sv - static_cast<double>(sh)), ch,
+                                          __double2float_rn(cv - static_cast<double>(ch)));
     }
 }
 
@@ -231,7 +229,8 @@ __device__ __forceinline__ void df_sincos_2pi_u(uint32_t x, const SinCosTable& T
     const df one_minus = df_fast_two_sum(1.0f, -0.5f * p2);
     const float tail = __fmaf_rn(__fmul_rn(p2, p2), 1.0f / 24.0f, -0.5f * e2);
     const df cd = df_fast_two_sum(one_minus.hi, __fadd_rn(one_minus.lo, tail));
-    const df sk{T.sh[k], T.sl[k]}, ck{T.ch[k], T.cl[k]};
+    const float4 t = T.e[k];
+    const df sk{t.x, t.y}, ck{t.z, t.w};
     const df st = sk * cd + ck * sd;  // sin(theta)
     const df ct = ck * cd - sk * sd;  // cos(theta)
     // phi = j pi/2 + a with a = +theta (even octant) or -theta (odd), j = quadrant index:
