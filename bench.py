@@ -276,9 +276,26 @@ def run_ours(args) -> None:
         b.record(stream)
         barrier()
         e2e_ms = shard.max_over_ranks(a.elapsed_time(b) / e2e_steps, device="cuda")
+        # the host link's own D2H rate (one device-to-pinned copy of up to 4 GB, outside the timed region)
+        nb = min(1 << 32, hbuf64.numel() * 8)
+        probe = torch.empty(nb, dtype=torch.uint8, device="cuda")
+        hprobe = hbuf64.view(torch.uint8)[:nb]
+        hprobe.copy_(probe, non_blocking=True)
+        torch.cuda.synchronize()
+        c0 = torch.cuda.Event(enable_timing=True)
+        c1 = torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        hprobe.copy_(probe, non_blocking=True)
+        c1.record(stream)
+        c1.synchronize()
+        link_gbs = nb / (c0.elapsed_time(c1) / 1e3) / 1e9
+        del probe, hprobe
+        achieved_link = d2h / (e2e_ms / 1e3) / 1e9
         e2e = {"value": per_step_events * world / (e2e_ms / 1e3), "unit": "events/s",
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": e2e_steps,
-               "ms_per_step": e2e_ms}
+               "ms_per_step": e2e_ms, "d2h_gbs": round(achieved_link, 1),
+               "d2h_link_gbs_measured": round(link_gbs, 1), "link_frac": round(achieved_link / link_gbs, 4),
+               "bound": "host link (every generated event is copied to pinned host memory)"}
         del hbuf64, hbuf32
 
     if rank != 0:
