@@ -44,8 +44,8 @@ INT_CFG = workloads.D0_DALITZ
 INSTR_PER_EVENT = {
     ("f32", 2): 91, ("f32", 3): 211, ("f32", 4): 296, ("f32", 5): 421, ("f32", 6): 539,
     ("f32", 7): 668, ("f32", 8): 794, ("f32", 9): 924, ("f32", 10): 1044,
-    ("f64", 2): 460, ("f64", 3): 1136, ("f64", 4): 1732, ("f64", 5): 2346, ("f64", 6): 2966,
-    ("f64", 7): 3596, ("f64", 8): 4194, ("f64", 9): 4829, ("f64", 10): 5464,
+    ("f64", 2): 457, ("f64", 3): 1111, ("f64", 4): 1692, ("f64", 5): 2288, ("f64", 6): 2892,
+    ("f64", 7): 3509, ("f64", 8): 4095, ("f64", 9): 4714, ("f64", 10): 5334,
 }
 
 
@@ -549,8 +549,8 @@ def run_extras(nev: int = 100_000_000, reps: int = 3) -> dict:
 # ----------------------------------------------------------------------------- VEGAS
 # Thread instructions per point of the double-float VEGAS kernels (ncu smsp__inst_executed.sum
 # x 32 / points on 4e6-point iterations, 100 bins; profiles/vegas_eval_df_dalitz_4e6.md).
-VEGAS_INSTR_PER_POINT = {("dalitz", "eval"): 1536, ("dalitz", "hist"): 140,
-                         ("flat10", "eval"): 2785, ("flat10", "hist"): 557}
+VEGAS_INSTR_PER_POINT = {("dalitz", "eval"): 1314, ("dalitz", "hist"): 140,
+                         ("flat10", "eval"): 2502, ("flat10", "hist"): 557}
 
 
 def run_vegas(calls: int = 100_000_000, iterations: int = 10, reps: int = 3,

@@ -182,40 +182,49 @@ __device__ __forceinline__ df df_add_small(df x, float f) {
 // sin and cos of phi = 2 pi u, u = (x + 1/2) 2^-32 for a 32-bit x, in df.
 //
 // They multiply momenta bounded by the event scale, so the target is an absolute error of
-// ~1e-15.  Reduction is exact integer arithmetic: the top three bits of x give the octant;
-// phi = j pi/2 +- theta with theta = 2 pi t 2^-32 in [0, pi/4], t the (half-odd) distance to
-// the nearest multiple of pi/2.  theta = theta_k + delta with theta_k = k pi/1024 (k = top 8
-// bits of 2t; a 256-entry table of sin/cos(theta_k) in df) and 0 <= delta < pi/1024:
+// ~1e-15.  Reduction is exact integer arithmetic: phi = theta_k + delta with theta_k = k pi/1024,
+// k = the top 11 bits of x (a 2048-entry table of sin/cos(theta_k) in df over the whole
+// circle), and delta = pi (2r + 1) 2^-32 in (0, pi/1024), r = the low 21 bits:
 //   sin(delta) = delta - delta^3/6 (1 - delta^2/20)      (the correction, <= 4.9e-9, in FP32:
 //                                                          absolute error < 1e-15)
 //   cos(delta) = 1 - delta^2/2 + delta^4/24             (delta^2 from an exact product)
-// then the angle-sum identities, and branch-free signs/swap for the quadrant.
+// then the angle-sum identities.
 // ------------------------------------------------------------------------------------
 struct SinCosTable {
-    float4 e[256];  // (sin hi, sin lo, cos hi, cos lo) of k pi/1024, k = 0..255: one 16-byte load
+    float4 e[2048];  // (sin hi, sin lo, cos hi, cos lo) of k pi/1024: one 16-byte load
 };
 
-// The table lives in shared memory of the kernels that compute in df; each block fills it
-// once (sincospi in FP64) before its first event.
+// The table lives in shared memory (32 KB) of the kernels that compute in df.  Each block
+// fills it before its first event: entries 0..256 (angles 0..pi/4) from FP64 sincospi, the
+// rest from those by the exact symmetries sin(pi/2 - b) = cos b and quarter-turn rotations.
+// Every thread of the block must call it (it synchronises the block).
 static __shared__ SinCosTable s_sincos_table;
 
 __device__ __forceinline__ void df_sincos_table_init() {
-    for (int k = threadIdx.x; k < 256; k += blockDim.x) {
+    for (int k = threadIdx.x; k <= 256; k += blockDim.x) {
         double sv, cv;
         sincospi(static_cast<double>(k) / 1024.0, &sv, &cv);
         const float sh = __double2float_rn(sv), ch = __double2float_rn(cv);
         s_sincos_table.e[k] = make_float4(sh, __double2float_rn(sv - static_cast<double>(sh)), ch,
                                           __double2float_rn(cv - static_cast<double>(ch)));
     }
+    __syncthreads();
+    for (int k = 257 + threadIdx.x; k < 2048; k += blockDim.x) {
+        const int j = k >> 9, m = k & 511;  // k pi/1024 = j pi/2 + m pi/1024
+        float4 b = s_sincos_table.e[m <= 256 ? m : 512 - m];
+        if (m > 256) b = make_float4(b.z, b.w, b.x, b.y);  // sin(pi/2 - a) = cos a, cos(pi/2 - a) = sin a
+        float4 r;
+        if (j == 0) r = b;
+        else if (j == 1) r = make_float4(b.z, b.w, -b.x, -b.y);   // (cos, -sin)
+        else if (j == 2) r = make_float4(-b.x, -b.y, -b.z, -b.w); // (-sin, -cos)
+        else r = make_float4(-b.z, -b.w, b.x, b.y);               // (-cos, sin)
+        s_sincos_table.e[k] = r;
+    }
 }
 
 __device__ __forceinline__ void df_sincos_2pi_u(uint32_t x, const SinCosTable& T, df* s, df* c) {
-    const uint32_t oct = x >> 29;            // octant 0..7
-    const uint32_t r = x & 0x1FFFFFFFu;      // position inside the octant (29 bits)
-    const bool odd = oct & 1u;
-    const uint32_t t2 = odd ? ((0x20000000u - r) << 1) - 1u : (r << 1) + 1u;  // 2 t, < 2^30
-    const uint32_t k = t2 >> 22;             // table index 0..255 (theta_k = k pi/1024)
-    const uint32_t rem2 = t2 & 0x3FFFFFu;    // 2 (t - k 2^21), < 2^22: exact in FP32
+    const uint32_t k = x >> 21;                              // table index 0..2047
+    const uint32_t rem2 = ((x & 0x1FFFFFu) << 1) | 1u;      // 2r + 1 < 2^22: exact in FP32
     const df pi_scaled{7.31459059988282e-10f, -2.035470133961082e-17f};  // pi 2^-32 (hi + lo)
     const df d = pi_scaled * __uint2float_rn(rem2);                       // delta
     const float d2f = __fmul_rn(d.hi, d.hi);
@@ -231,20 +240,8 @@ __device__ __forceinline__ void df_sincos_2pi_u(uint32_t x, const SinCosTable& T
     const df cd = df_fast_two_sum(one_minus.hi, __fadd_rn(one_minus.lo, tail));
     const float4 t = T.e[k];
     const df sk{t.x, t.y}, ck{t.z, t.w};
-    const df st = sk * cd + ck * sd;  // sin(theta)
-    const df ct = ck * cd - sk * sd;  // cos(theta)
-    // phi = j pi/2 + a with a = +theta (even octant) or -theta (odd), j = quadrant index:
-    // sin(j pi/2 + a), cos(j pi/2 + a) = (sin a, cos a) rotated by j quarter turns
-    const uint32_t j = ((oct + 1u) >> 1) & 3u;
-    const df sa = odd ? -st : st;
-    const bool swap = j & 1u;
-    df so = swap ? ct : sa, co = swap ? -sa : ct;
-    if (j & 2u) {
-        so = -so;
-        co = -co;
-    }
-    *s = so;
-    *c = co;
+    *s = sk * cd + ck * sd;  // sin(theta_k + delta)
+    *c = ck * cd - sk * sd;  // cos(theta_k + delta)
 }
 
 }  // namespace hydra

@@ -20,13 +20,11 @@
 // Grid arithmetic.  With P = (2x + 1) K (< 2^41), the bin is b = floor(y K) = P >> 33 and the
 // position inside it is y K - b = rho 2^-33 with rho = P mod 2^33, both exact (y K has at
 // most 42 significant bits, so these are also what an FP64 evaluation of floor(y K) and
-// y K - b gives).  Edges are held as 64-bit fixed point G_b = g_b 2^64 and widths
-// W_b = G_{b+1} - G_b, so u 2^64 = G_b + floor(rho W_b 2^-33) to within one unit of 2^-64.
-// The Jacobian factor K (g_{b+1} - g_b) is the host's FP64 value, held as a double-float
-// mantissa in [1, 2) and a binary exponent: the product over the D dimensions multiplies the
-// mantissas in double-float and adds the exponents, one FP64 rounding at the end instead of D
-// FP64 multiplications on B300's narrow FP64 pipe.  Sorting the mass variables and forming the
-// kinetic gaps T (r_k - r_{k-1}) work on exact integers, as in the generator.
+// y K - b gives).  Edges are held as 64-bit fixed point G_b = g_b 2^64 (G_K = 2^64 - 1) and
+// widths W_b = G_{b+1} - G_b, so u 2^64 = G_b + floor(rho W_b 2^-33) to within one unit of
+// 2^-64; the Jacobian factor K (g_{b+1} - g_b) is the host's FP64 value.  A cell is 16 bytes
+// (K + 1 per dimension in shared memory).  Sorting the mass variables and forming the kinetic
+// gaps T (r_k - r_{k-1}) work on exact integers, as in the generator.
 #include <cuda_runtime.h>
 #include <cmath>
 #include <cstdint>
@@ -47,30 +45,16 @@ __global__ void eval_reduce_segments(const TileSums* __restrict__ partials, uint
 __global__ void eval_finalize(const double* __restrict__ seg, uint64_t nseg, uint64_t nevents,
                               hydra_integral* __restrict__ out);
 
-constexpr int kVegasMaxCells = 6144;  // D * K grid cells held in shared memory (32 B each)
+constexpr int kVegasMaxCells = 6144;  // D * K bins (D * (K + 1) cells of 16 B in shared memory)
+constexpr int kVegasMaxD = 3 * kNMax - 4;
 constexpr int kVegasBlock = 256;
 constexpr int kVegasMaxChunks = 1 << 11;  // 2^36 points / (kChunkTiles tiles of 2048), as 64-bit words
 
 struct VegasCell {
-    uint64_t G;     // left edge g_b 2^64
-    uint64_t W;     // width (g_{b+1} - g_b) 2^64 (2^64 - 1 for a single bin)
-    float jh, jl;   // Jacobian factor K (g_{b+1} - g_b) = (jh + jl) 2^je, 1 <= jh + jl < 2
-    int32_t je;
-    int32_t pad;
+    uint64_t G;  // left edge g_b 2^64 (the cell after the last bin holds 2^64 - 1)
+    double J;    // Jacobian factor K (g_{b+1} - g_b)
 };
-static_assert(sizeof(VegasCell) == 32, "cells are 32 bytes");
-
-// (m_hi + m_lo) 2^e as the nearest double, for a double-float mantissa in [1, 2^D) and any
-// integer e: the power of two is built from its bits in two factors (each a normal double),
-// so results below the double range round to a subnormal or zero as a plain product would.
-__device__ __forceinline__ double df_ldexp(df m, int e) {
-    const int e1 = e < -1022 ? -1022 : (e > 1023 ? 1023 : e);
-    int e2 = e - e1;
-    e2 = e2 < -1022 ? -1022 : (e2 > 1023 ? 1023 : e2);
-    const double p1 = __longlong_as_double(static_cast<long long>(e1 + 1023) << 52);
-    const double p2 = __longlong_as_double(static_cast<long long>(e2 + 1023) << 52);
-    return (df_to_double(m) * p1) * p2;
-}
+static_assert(sizeof(VegasCell) == 16, "cells are 16 bytes");
 
 // Matrix-element constants (m0a^2, m0a Ga, m0b^2, m0b Gb, Re c, Im c) in FP64 and as
 // double-float pairs.
@@ -241,7 +225,7 @@ __global__ void __launch_bounds__(kVegasBlock) vegas_eval(const __grid_constant_
     constexpr int D = 3 * N - 4;
     extern __shared__ VegasCell cells[];
     if constexpr (std::is_same_v<R, df>) df_sincos_table_init();
-    for (int i = threadIdx.x; i < D * K; i += blockDim.x) cells[i] = grid[i];
+    for (int i = threadIdx.x; i < D * (K + 1); i += blockDim.x) cells[i] = grid[i];
     __syncthreads();
     const int lane = threadIdx.x & 31;
     unsigned long long mx = 0;
@@ -262,17 +246,14 @@ __global__ void __launch_bounds__(kVegasBlock) vegas_eval(const __grid_constant_
                 if (s < calls) {
                     uint64_t U[D];
                     uint32_t packed[(D + 3) / 4] = {};
-                    df jm{1.0f, 0.0f};
-                    int je = 0;
+                    double jac = 1.0;
                     vegas_bins(C, s, stream, D, K, [&](int d, int b, uint64_t rho) {
                         packed[d / 4] |= static_cast<uint32_t>(b) << (8 * (d % 4));
-                        const VegasCell c = cells[d * K + b];
-                        U[d] = c.G + ((__umul64hi(rho, c.W) << 31) | ((rho * c.W) >> 33));
-                        jm = jm * df{c.jh, c.jl};
-                        jm = df_fast_two_sum(jm.hi, jm.lo);  // renormalise along the D-long chain
-                        je += c.je;
+                        const VegasCell c = cells[d * (K + 1) + b];
+                        const uint64_t W = cells[d * (K + 1) + b + 1].G - c.G;
+                        U[d] = c.G + ((__umul64hi(rho, W) << 31) | ((rho * W) >> 33));
+                        jac *= c.J;
                     });
-                    const double jac = df_ldexp(jm, je);
 #pragma unroll
                     for (int q = 0; q < (D + 3) / 4; ++q) bins[static_cast<uint64_t>(q) * calls + s] = packed[q];
                     R E1, M2;
@@ -412,27 +393,14 @@ static void refine_dimension(double* g, const double* dsum, int K, double alpha)
     for (int i = 0; i <= K; ++i) g[i] = ng[i];
 }
 
-// Fixed-point cells of one dimension's edges g[0..K].
+// Fixed-point cells of one dimension's edges g[0..K] (K + 1 cells).
 static void grid_cells(const double* g, int K, VegasCell* out) {
-    std::vector<uint64_t> G(K);
-    for (int b = 0; b < K; ++b)
-        G[b] = g[b] < 1.0 ? static_cast<uint64_t>(std::ldexp(g[b], 64)) : ~uint64_t{0};  // exact below 2^64
     for (int b = 0; b < K; ++b) {
-        out[b].G = G[b];
-        out[b].W = (K == 1) ? ~uint64_t{0} : (b + 1 < K ? G[b + 1] : uint64_t{0}) - G[b];  // G_K = 2^64 (mod 2^64)
-        const double J = K * (g[b + 1] - g[b]);
-        int e = 0;
-        const double m = 2.0 * std::frexp(J, &e);  // J = m 2^(e-1), 1 <= m < 2 (J > 0)
-        out[b].jh = static_cast<float>(m);
-        out[b].jl = static_cast<float>(m - static_cast<double>(out[b].jh));
-        out[b].je = e - 1;
-        out[b].pad = 0;
-        if (!(J > 0.0)) {  // a zero-width bin: J = 0, as in the plain product
-            out[b].jh = 0.0f;
-            out[b].jl = 0.0f;
-            out[b].je = 0;
-        }
+        out[b].G = g[b] < 1.0 ? static_cast<uint64_t>(std::ldexp(g[b], 64)) : ~uint64_t{0};  // exact below 2^64
+        out[b].J = K * (g[b + 1] - g[b]);
     }
+    out[K].G = ~uint64_t{0};  // 2^64 - 1: the last width is short by 2^-64
+    out[K].J = 0.0;
 }
 
 struct VegasScratch {
@@ -524,7 +492,7 @@ hydra_status hydra_phsp_vegas(double M, int n, const double* masses, uint64_t se
     const uint64_t ntiles = (calls + kTileEvents - 1) / kTileEvents;
     const uint64_t nseg = (ntiles + kSegTiles - 1) / kSegTiles;
     const size_t hist_words = static_cast<size_t>(kVegasMaxCells) + 1 + kVegasMaxChunks;
-    const size_t cell_bytes = static_cast<size_t>(kVegasMaxCells) * sizeof(VegasCell);
+    const size_t cell_bytes = static_cast<size_t>(kVegasMaxCells + kVegasMaxD) * sizeof(VegasCell);
     if (!s->tiles) {
         if (cudaMalloc(&s->tiles, kChunkTiles * sizeof(TileSums)) != cudaSuccess ||
             cudaMalloc(&s->cells, cell_bytes) != cudaSuccess ||
@@ -564,7 +532,7 @@ hydra_status hydra_phsp_vegas(double M, int n, const double* masses, uint64_t se
         s->fcap = cap;
         s->bins_d = dcap;
     }
-    const size_t smem = static_cast<size_t>(D) * K * sizeof(VegasCell);
+    const size_t smem = static_cast<size_t>(D) * (K + 1) * sizeof(VegasCell);
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(cell_bytes));
     if (err != cudaSuccess) return cuda_fail(err, "VEGAS shared-memory limit");
     int dev = 0, sms = 148, per_sm = 1;
@@ -587,7 +555,8 @@ hydra_status hydra_phsp_vegas(double M, int n, const double* masses, uint64_t se
     std::vector<double> dsum(K);
     for (int it = 0; it < iterations; ++it) {
         const uint32_t stream_id = static_cast<uint32_t>(it + 1);
-        for (int d = 0; d < D; ++d) grid_cells(&g[static_cast<size_t>(d) * (K + 1)], K, h_cells + static_cast<size_t>(d) * K);
+        for (int d = 0; d < D; ++d)
+            grid_cells(&g[static_cast<size_t>(d) * (K + 1)], K, h_cells + static_cast<size_t>(d) * (K + 1));
         err = cudaMemcpyAsync(s->cells, h_cells, smem, cudaMemcpyHostToDevice, cs);
         if (err == cudaSuccess) err = cudaMemsetAsync(s->hist, 0, hist_words * sizeof(unsigned long long), cs);
         if (err != cudaSuccess) return cuda_fail(err, "VEGAS grid upload");
