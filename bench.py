@@ -602,6 +602,8 @@ def run_serve_workload(duration_s: float = 30.0, rate_hz: float = 2000.0) -> dic
     from paper_1711_05683_b300 import serve
     reqs = workloads.serve_stream(rate_hz=rate_hz, duration_s=duration_s)
     warm = workloads.serve_stream(rate_hz=rate_hz, duration_s=0.5, rng_seed=1)
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()  # return what earlier phases cached, before the servers reserve theirs
     srv = serve.Server()
     srv.run(warm)
     res_b = srv.run(reqs)

@@ -1,8 +1,10 @@
 """Continuous-batching server for phase-space requests (generate and integrate).
 
 Requests arrive over time.  Each tick the server admits arrived requests while their
-device memory fits the HBM budget, then packs one slice of every active request into one
-batch run (hydra_batch_run: one persistent launch, replayed CUDA graph):
+device memory fits the HBM budget, then packs one slice of each active request, oldest first
+and up to `max_tick_events` events per tick (so that under overload requests still finish
+close to arrival order), into one batch run (hydra_batch_run: one persistent launch,
+replayed CUDA graph):
   * a generate request is one slice (its whole event count); its events land in a device
     staging buffer and are copied to pinned host memory right after the run;
   * an integrate request advances by up to `int_slice_segments` segments of 2^21 events per
@@ -14,6 +16,12 @@ Two batch runners alternate so that tick i+1 is packed and enqueued while tick i
 request completes when the host observes the event recorded after its last slice (and, for
 generation, after its copy to host memory); latency = completion time - arrival time.
 
+The HBM budget is reserved when the server starts, as two device rings (staging outputs, and
+integral partials in a small ring of their own); requests take blocks of them and return them
+when harvested, so the serving loop never allocates device memory (an allocation can
+synchronise the device and stall every request in flight).  Pinned host memory is a ring in
+the same way.
+
 Every slice computes exactly the events of the single-request entry points, so a request's
 result is the same alone and in the mix (tests check this bit for bit).
 
@@ -22,13 +30,30 @@ single-request entry points (generate + copy to host, or integrate).
 """
 from __future__ import annotations
 
+import contextlib
 import dataclasses
+import gc
 import time
 from collections import deque
 
 import numpy as np
 
 import paper_1711_05683_b300 as hp
+
+
+@contextlib.contextmanager
+def _no_gc_pauses():
+    """The serving loops run with Python's cyclic garbage collector off: a full collection
+    over the tens of thousands of request records alive in a run pauses the loop for tens of
+    milliseconds, which lands directly in the latency tail.  Reference counting still frees
+    everything the loops drop; the collector is restored afterwards."""
+    was = gc.isenabled()
+    gc.disable()
+    try:
+        yield
+    finally:
+        if was:
+            gc.enable()
 
 
 @dataclasses.dataclass
@@ -45,16 +70,18 @@ class _Active:
     seg: object = None              # integrate: device segment partials
     result: dict | None = None
     done_tick: int = -1
+    ring_start: int = -1            # block of the pinned host ring (generate)
+    dev_start: int = -1             # block of the device arena (staging or partials)
 
 
-class PinnedRing:
-    """Pinned host memory handed out in arrival order (a ring); blocks are released when
-    their request is harvested."""
+class Ring:
+    """A byte buffer (pinned host or device memory) handed out in arrival order as a ring of
+    256-byte-aligned blocks; blocks may be released in any order (when their request is
+    harvested) and a block is only handed out where it overlaps no live one."""
 
-    def __init__(self, nbytes: int):
-        import torch
-        self.buf = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
-        self.size = nbytes
+    def __init__(self, buf):
+        self.buf = buf
+        self.size = buf.numel()
         self.head = 0
         self.live = deque()  # (start, end) in allocation order
 
@@ -77,11 +104,24 @@ class PinnedRing:
                 del self.live[i]
                 return
 
+    def view(self, start: int, nbytes: int, dtype):
+        return self.buf[start: start + nbytes].view(dtype)
+
+
+def PinnedRing(nbytes: int) -> Ring:
+    import torch
+    return Ring(torch.empty(nbytes, dtype=torch.uint8, pin_memory=True))
+
+
+def DeviceRing(nbytes: int) -> Ring:
+    import torch
+    return Ring(torch.empty(nbytes, dtype=torch.uint8, device="cuda"))
+
 
 class Server:
     def __init__(self, budget_bytes: int = 40 * 10 ** 9, max_slices: int = 4096,
                  int_slice_segments: int = 4, pinned_bytes: int = 4 << 30,
-                 keep_outputs: bool = False, use_graph: bool = True):
+                 keep_outputs: bool = False, use_graph: bool = True, max_tick_events: int = 1 << 27):
         import torch
         self.torch = torch
         self.budget = budget_bytes
@@ -92,8 +132,13 @@ class Server:
         self.table = np.zeros(max_slices, dtype=hp.request_dtype())
         self.max_slices = max_slices
         self.ring = PinnedRing(pinned_bytes)
+        # staging outputs and (in a small ring of their own, so that long integrals do not
+        # split the large one) integral partials; together they are the HBM budget
+        self.seg_ring = DeviceRing(min(256 << 20, budget_bytes // 16))
+        self.dev_ring = DeviceRing(budget_bytes - self.seg_ring.size)
         self.keep_outputs = keep_outputs
         self.use_graph = use_graph
+        self.max_tick_events = max_tick_events
         self.stream = torch.cuda.current_stream()
 
     # ------------------------------------------------------------------ state per request
@@ -104,28 +149,34 @@ class Server:
         if r.kind == "generate":
             ld = hp.padded_ld(r.nevents)
             nbytes = (4 * n + 1) * ld * 4
-            if self.used + nbytes > self.budget:
+            dev = self.dev_ring.alloc(nbytes)
+            if dev is None:
                 return False
             host = self.ring.alloc(nbytes)
             if host is None:
+                self.dev_ring.free(dev)
                 return False
-            a.ring_start = host
-            hb = self.ring.buf[host: host + (4 * n + 1) * ld * 4].view(torch.float32)
+            a.ring_start, a.dev_start = host, dev
+            hb = self.ring.view(host, nbytes, torch.float32)
             a.host_out = hb[: 4 * n * ld].view(n, 4, ld)
             a.host_w = hb[4 * n * ld:]
-            a.dev_out = torch.empty((n, 4, ld), dtype=torch.float32, device="cuda")
-            a.dev_w = torch.empty(ld, dtype=torch.float32, device="cuda")
+            db = self.dev_ring.view(dev, nbytes, torch.float32)
+            a.dev_out = db[: 4 * n * ld].view(n, 4, ld)
+            a.dev_w = db[4 * n * ld:]
         else:
             nbytes = 64 * hp.segments(r.nevents)
-            if self.used + nbytes > self.budget:
+            dev = self.seg_ring.alloc(nbytes)
+            if dev is None:
                 return False
-            a.seg = torch.empty(8 * hp.segments(r.nevents), dtype=torch.float64, device="cuda")
+            a.dev_start = dev
+            a.seg = self.seg_ring.view(dev, nbytes, torch.float64)
         a.nbytes = nbytes
         self.used += nbytes
         return True
 
     def _release(self, a: _Active):
         self.used -= a.nbytes
+        (self.dev_ring if a.req.kind == "generate" else self.seg_ring).free(a.dev_start)
         if a.req.kind == "generate":
             if not self.keep_outputs:
                 self.ring.free(a.ring_start)
@@ -157,6 +208,10 @@ class Server:
         index to a time (seconds from start) after which the client withdraws it: the server
         drops it at the next tick boundary and releases its memory (host-side fault
         injection; work already on the GPU finishes and is discarded)."""
+        with _no_gc_pauses():
+            return self._run(requests, time_scale, max_wall, cancel_after)
+
+    def _run(self, requests, time_scale, max_wall, cancel_after) -> dict:
         torch = self.torch
         cancel_after = dict(cancel_after or {})
         cancelled = []
@@ -207,17 +262,22 @@ class Server:
             if launchable and len(inflight) < 2:
                 ri = tick % 2
                 slots, finishing = [], []
-                for k, a in enumerate(launchable):
+                room = self.max_tick_events  # oldest first, up to this many events per tick
+                for a in launchable:
                     if a.req.kind == "generate":
                         count = a.req.nevents
                     else:
                         count = min(self.int_slice, a.req.nevents - a.next_first)
+                    if slots and count > room:
+                        break
+                    room -= count
+                    k = len(slots)
                     self._fill(self.table[k], a, count)
                     slots.append((k, a))
                     a.next_first += count
                     if a.next_first >= a.req.nevents:
                         finishing.append(a)
-                self.runners[ri].run(self.table, len(launchable), use_graph=self.use_graph, stream=self.stream)
+                self.runners[ri].run(self.table, len(slots), use_graph=self.use_graph, stream=self.stream)
                 for a in finishing:
                     if a.req.kind == "generate":
                         a.host_out.copy_(a.dev_out, non_blocking=True)
@@ -241,6 +301,7 @@ class Server:
     def close(self):
         for r in self.runners:
             r.close()
+        self.dev_ring = self.seg_ring = None
 
 
 class PlainServer:
@@ -253,8 +314,18 @@ class PlainServer:
         self.keep_outputs = keep_outputs
         self.stream = torch.cuda.current_stream()
         self.ring = PinnedRing(pinned_bytes)
+        self.dev = torch.empty(0, dtype=torch.uint8, device="cuda")  # staging, grown on demand
+
+    def _staging(self, nbytes: int):
+        if self.dev.numel() < nbytes:
+            self.dev = self.torch.empty(max(nbytes, 2 * self.dev.numel()), dtype=self.torch.uint8, device="cuda")
+        return self.dev[:nbytes]
 
     def run(self, requests, time_scale: float = 1.0, max_wall: float | None = None) -> dict:
+        with _no_gc_pauses():
+            return self._run(requests, time_scale, max_wall)
+
+    def _run(self, requests, time_scale, max_wall) -> dict:
         torch = self.torch
         t0 = time.perf_counter()
         latencies, kinds, done = {}, {}, []
@@ -268,9 +339,11 @@ class PlainServer:
             a = _Active(rid, r, arr)
             if r.kind == "generate":
                 n = len(r.masses)
-                p, w = hp.generate(r.M, r.masses, r.nevents, r.seed, dtype="f32")
-                ld = p.shape[-1]
+                ld = hp.padded_ld(r.nevents)
                 nbytes = (4 * n + 1) * ld * 4
+                db = self._staging(nbytes).view(torch.float32)
+                p, w = db[: 4 * n * ld].view(n, 4, ld), db[4 * n * ld:]
+                hp.generate_into(r.M, r.masses, r.nevents, r.seed, p, w, dtype="f32")
                 start = self.ring.alloc(nbytes)
                 if start is None:  # ring full: everything before is finished (synchronous server)
                     self.ring.live.clear()
@@ -278,7 +351,7 @@ class PlainServer:
                 hb = self.ring.buf[start: start + nbytes].view(torch.float32)
                 ho, hw = hb[: 4 * n * ld].view(n, 4, ld), hb[4 * n * ld:]
                 ho.copy_(p, non_blocking=True)
-                hw[: r.nevents].copy_(w, non_blocking=True)
+                hw.copy_(w, non_blocking=True)
                 self.stream.synchronize()
                 if self.keep_outputs:
                     a.host_out, a.host_w = ho.clone(), hw.clone()
