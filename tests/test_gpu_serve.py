@@ -19,12 +19,16 @@ def _cuda():
     torch.cuda.set_device(0)
 
 
-def test_served_results_equal_single_requests():
+@pytest.mark.parametrize("tick_cap", [1 << 27, 1 << 18])
+def test_served_results_equal_single_requests(tick_cap):
+    """Every request's result alone equals its result in the mix; with a small per-tick event
+    cap the same stream runs as many short oldest-first ticks and still gives the same bits."""
     from paper_1711_05683_b300 import serve
     reqs = workloads.serve_stream(rate_hz=2000, duration_s=0.15, gen_log_events=(2.0, 5.0),
                                   int_log_events=(4.0, 7.4), rng_seed=99)
     assert any(r.kind == "integrate" and r.nevents > 2 ** 21 for r in reqs)  # sliced over ticks
-    srv = serve.Server(max_slices=512, int_slice_segments=1, pinned_bytes=1 << 30, keep_outputs=True)
+    srv = serve.Server(max_slices=512, int_slice_segments=1, pinned_bytes=1 << 30, keep_outputs=True,
+                       budget_bytes=8 * 10 ** 9, max_tick_events=tick_cap)
     res = srv.run(reqs)
     srv.close()
     assert res["completed"] == len(reqs)
