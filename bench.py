@@ -403,6 +403,7 @@ def run_ours(args) -> None:
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds, nev, int_events)
         line["cpu_baseline"]["value_ratio_note"] = "oracle, single thread, FP64; not a tuning target"
+        line["cpu_all_cores"] = cpu_all_cores(line["cpu_baseline"]["sample_events"], nev, int_events)
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -667,6 +668,52 @@ def cpu_baseline(seconds: float, nev_full: int, int_full: int) -> dict:
                       "about %.1f s), time scaled to the item's full count; FP64 oracle stands in for both "
                       "precisions" % (budget / 4), "sample_events": sample,
             "host_cores_available": os.cpu_count()}
+
+
+def _oracle_range(job):
+    """One worker's share of an all-cores oracle run (spawned process; the oracle's C library
+    is loaded in the worker)."""
+    import oracle
+    kind, M, masses, count, seed, offset = job
+    if kind == "generate":
+        oracle.generate(M, masses, count, seed, event_offset=offset)
+    else:
+        oracle.integrate_sums(M, masses, count, seed, me=1, params=INT_CFG["params"], event_offset=offset)
+    return count
+
+
+def cpu_all_cores(sample: dict, nev_full: int, int_full: int) -> dict:
+    """Context only: the same oracle on every host core, each item's sample (4x the
+    single-thread sample) split into equal event ranges over a spawned process pool; wall time
+    scaled to the item's full count."""
+    import multiprocessing as mp
+    import oracle
+    oracle.build()
+    procs = os.cpu_count() or 1
+    total_t = 0.0
+    total_ev = 0
+    with mp.get_context("spawn").Pool(procs) as pool:
+        pool.map(_oracle_range, [("generate", 10.0, (0.0, 0.0), 64, 1, 0)] * procs)  # warm the workers
+        for dtype, massive, n in sweep_items():
+            m = 4 * sample[f"{dtype}/{'massive' if massive else 'massless'}/N{n}"]
+            part = (m + procs - 1) // procs
+            jobs = [("generate", workloads.SWEEP_M, workloads.sweep_masses(n, massive), part, 1000 + n, i * part)
+                    for i in range(procs)]
+            t0 = time.perf_counter()
+            pool.map(_oracle_range, jobs)
+            total_t += (time.perf_counter() - t0) * nev_full / (part * procs)
+            total_ev += nev_full
+        m = 4 * sample["integrate"]
+        part = (m + procs - 1) // procs
+        jobs = [("integrate", INT_CFG["M"], INT_CFG["masses"], part, INT_CFG["seed"], i * part) for i in range(procs)]
+        t0 = time.perf_counter()
+        pool.map(_oracle_range, jobs)
+        total_t += (time.perf_counter() - t0) * int_full / (part * procs)
+        total_ev += int_full
+    return {"value": total_ev / total_t, "unit": "events/s", "cores": procs, "kind": "oracle",
+            "sample": "every item of the step on all host cores: 4x the single-thread sample split "
+                      "into equal event ranges over a spawned process pool, wall time scaled to the "
+                      "full count; context, not a baseline"}
 
 
 def run_reference(args) -> None:
