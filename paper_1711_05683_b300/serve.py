@@ -8,7 +8,7 @@ replayed CUDA graph):
   * a generate request is one slice (its whole event count); its events land in a device
     staging buffer and are copied to pinned host memory right after the run;
   * an integrate request advances by up to `int_slice_segments` segments of 2^21 events per
-    tick; its running state is device resident: the next counter-event index (the Philox
+    tick (16 by default: a 1e8-event integral takes 3 ticks); its running state is device resident: the next counter-event index (the Philox
     counter, kept on the host as an integer) and its compensated segment partial sums
     (a caller-owned device array the batch kernels update in place).  A long integral
     therefore shares the GPU with requests that arrive while it runs.
@@ -72,6 +72,8 @@ class _Active:
     done_tick: int = -1
     ring_start: int = -1            # block of the pinned host ring (generate)
     dev_start: int = -1             # block of the device arena (staging or partials)
+    latency: float = -1.0           # seconds from arrival to completion
+    rec: object = None              # the request's hydra_request record (static fields)
 
 
 class Ring:
@@ -120,7 +122,7 @@ def DeviceRing(nbytes: int) -> Ring:
 
 class Server:
     def __init__(self, budget_bytes: int = 40 * 10 ** 9, max_slices: int = 4096,
-                 int_slice_segments: int = 4, pinned_bytes: int = 4 << 30,
+                 int_slice_segments: int = 16, pinned_bytes: int = 4 << 30,
                  keep_outputs: bool = False, use_graph: bool = True, max_tick_events: int = 1 << 27):
         import torch
         self.torch = torch
@@ -172,6 +174,8 @@ class Server:
             a.seg = self.seg_ring.view(dev, nbytes, torch.float64)
         a.nbytes = nbytes
         self.used += nbytes
+        a.rec = np.zeros(1, dtype=self.table.dtype)[0]
+        self._fill(a.rec, a)
         return True
 
     def _release(self, a: _Active):
@@ -185,13 +189,13 @@ class Server:
         else:
             a.seg = None
 
-    def _fill(self, rec, a: _Active, count: int):
+    def _fill(self, rec, a: _Active):
+        """The request's static fields (the slice start and count are set per tick)."""
         r = a.req
         n = len(r.masses)
         rec["n"], rec["dtype"], rec["M"] = n, hp.F32, r.M
         rec["masses"][:n] = r.masses
         rec["seed"], rec["event_offset"] = r.seed, 0
-        rec["first"], rec["count"] = a.next_first, count
         if r.kind == "generate":
             rec["kind"] = hp.REQ_GENERATE
             rec["out"], rec["ld"], rec["weights"] = a.dev_out.data_ptr(), a.dev_out.shape[-1], a.dev_w.data_ptr()
@@ -243,7 +247,7 @@ class Server:
                     if a.req.kind == "integrate" and a in finishing:
                         a.result = self.runners[ri].result(slot)
                 for a in finishing:
-                    latencies[a.rid] = tnow - a.arrival
+                    a.latency = latencies[a.rid] = tnow - a.arrival
                     kinds[a.rid] = a.req.kind
                     events_done += a.req.nevents
                     done.append(a)
@@ -272,7 +276,9 @@ class Server:
                         break
                     room -= count
                     k = len(slots)
-                    self._fill(self.table[k], a, count)
+                    self.table[k] = a.rec
+                    self.table[k]["first"] = a.next_first
+                    self.table[k]["count"] = count
                     slots.append((k, a))
                     a.next_first += count
                     if a.next_first >= a.req.nevents:
@@ -359,7 +365,7 @@ class PlainServer:
             else:
                 a.result = hp.integrate(r.M, r.masses, r.nevents, r.seed, kin_dtype="f32", me=r.me,
                                         params=r.params)
-            latencies[rid] = time.perf_counter() - arr
+            a.latency = latencies[rid] = time.perf_counter() - arr
             kinds[rid] = r.kind
             events_done += r.nevents
             done.append(a)
