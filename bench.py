@@ -44,8 +44,8 @@ INT_CFG = workloads.D0_DALITZ
 INSTR_PER_EVENT = {
     ("f32", 2): 91, ("f32", 3): 211, ("f32", 4): 296, ("f32", 5): 421, ("f32", 6): 539,
     ("f32", 7): 668, ("f32", 8): 794, ("f32", 9): 924, ("f32", 10): 1044,
-    ("f64", 2): 457, ("f64", 3): 1111, ("f64", 4): 1692, ("f64", 5): 2288, ("f64", 6): 2892,
-    ("f64", 7): 3509, ("f64", 8): 4095, ("f64", 9): 4714, ("f64", 10): 5334,
+    ("f64", 2): 474, ("f64", 3): 1123, ("f64", 4): 1707, ("f64", 5): 2288, ("f64", 6): 2895,
+    ("f64", 7): 3501, ("f64", 8): 4085, ("f64", 9): 4713, ("f64", 10): 5332,
 }
 
 

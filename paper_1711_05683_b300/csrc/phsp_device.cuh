@@ -124,10 +124,12 @@ template <> struct Prec<float> {
     __device__ static float one_plus_cos(uint32_t x) { return __fmaf_rn(__uint2float_rn(x), 4.656612873077392578125e-10f, 2.3283064365386962890625e-10f); }
     __device__ static float one_minus_cos(uint32_t x) { return one_plus_cos(~x); }
     __device__ static float cos_of(uint32_t x) { return __fmaf_rn(__int2float_rn(static_cast<int32_t>(x ^ 0x80000000u)), 4.656612873077392578125e-10f, 2.3283064365386962890625e-10f); }
-    using W = float;    // weight accumulation type
+    using W = float;    // weight type
     using Out = float;  // stored type
-    __device__ static W w_mul(W w, float p) { return w * p; }
-    __device__ static W Cw(const DecayConsts& C) { return C.Cf; }
+    using Wacc = float;  // weight product while it accumulates
+    __device__ static Wacc w_one() { return 1.0f; }
+    __device__ static Wacc w_mul(Wacc w, float p) { return w * p; }
+    __device__ static W w_final(Wacc w, const DecayConsts& C) { return w * C.Cf; }
     __device__ static Out out(float v) { return v; }
     __device__ static float M(const DecayConsts& C) { return C.Mf; }
     __device__ static float Ts(const DecayConsts& C) { return C.Tsf; }
@@ -156,8 +158,10 @@ template <> struct Prec<double> {
     __device__ static double cos_of(uint32_t x) { return __fma_rn(__int2double_rn(static_cast<int32_t>(x ^ 0x80000000u)), 4.656612873077392578125e-10, 2.3283064365386962890625e-10); }
     using W = double;
     using Out = double;
-    __device__ static W w_mul(W w, double p) { return w * p; }
-    __device__ static W Cw(const DecayConsts& C) { return C.C; }
+    using Wacc = double;
+    __device__ static Wacc w_one() { return 1.0; }
+    __device__ static Wacc w_mul(Wacc w, double p) { return w * p; }
+    __device__ static W w_final(Wacc w, const DecayConsts& C) { return w * C.C; }
     __device__ static Out out(double v) { return v; }
     __device__ static double M(const DecayConsts& C) { return C.M; }
     __device__ static double Ts(const DecayConsts& C) { return C.Ts; }
@@ -185,8 +189,10 @@ template <> struct Prec<df> {
     __device__ static df div(df a, df b) { return df_div(a, b); }
     __device__ static df fma_(df a, df b, df c) { return a * b + c; }
     __device__ static void sincos_2pi_u(uint32_t x, df* s, df* c) { df_sincos_2pi_u(x, s_sincos_table, s, c); }
-    __device__ static W w_mul(W w, df p) { return w * df_to_double(p); }
-    __device__ static W Cw(const DecayConsts& C) { return C.C; }
+    using Wacc = DfWeight;  // double-float mantissa and binary exponent: no FP64 until the end
+    __device__ static Wacc w_one() { return df_weight_one(); }
+    __device__ static Wacc w_mul(Wacc w, df p) { return df_weight_mul(w, p); }
+    __device__ static W w_final(Wacc w, const DecayConsts& C) { return df_weight_final(w, C.C); }
     __device__ static Out out(df v) { return df_to_double(v); }
     __device__ static df M(const DecayConsts& C) { return df{C.Mdf[0], C.Mdf[1]}; }
     __device__ static df Ts(const DecayConsts& C) { return df{C.Tsdf[0], C.Tsdf[1]}; }
@@ -253,11 +259,11 @@ __device__ __forceinline__ void raubold_lynch_group(const DecayConsts& C, const 
     const R Ts = P::Ts(C);
 
     using W = typename P::W;
-    W w[EPT];
+    typename P::Wacc w[EPT];
     R Q0[EPT], Qx[EPT], Qy[EPT], Qz[EPT], Mnext[EPT];
 #pragma unroll
     for (int q = 0; q < EPT; ++q) {
-        w[q] = W(1);  // prod p_k; C_n is applied last so only the final product can leave the normal range
+        w[q] = P::w_one();  // prod p_k; C_n is applied last so only the final product can leave the normal range
         Q0[q] = M; Qx[q] = R(0); Qy[q] = R(0); Qz[q] = R(0);
         Mnext[q] = M;  // M_{k+1}
     }
@@ -343,9 +349,10 @@ __device__ __forceinline__ void raubold_lynch_group(const DecayConsts& C, const 
         sink.daughter(k, dE, dx, dy, dz);
     }
     sink.daughter(0, Q0, Qx, Qy, Qz);
+    W wout[EPT];
 #pragma unroll
-    for (int q = 0; q < EPT; ++q) w[q] = w[q] * P::Cw(C);
-    sink.weight(w);
+    for (int q = 0; q < EPT; ++q) wout[q] = P::w_final(w[q], C);
+    sink.weight(wout);
 }
 
 // ------------------------------------------------------------------------------------

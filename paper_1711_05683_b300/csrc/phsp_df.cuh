@@ -179,6 +179,39 @@ __device__ __forceinline__ df df_add_small(df x, float f) {
 }
 
 // ------------------------------------------------------------------------------------
+// Weight product prod_k p_k without the FP64 pipe: a double-float mantissa times 2^e.  Each
+// factor is scaled by an exact power of two into [1, 2) (its exponent read from the bits of
+// its high part) before the double-float product, so the mantissa stays below 2^(n-1) and the
+// range is the integer exponent's; one conversion to double at the end.
+// ------------------------------------------------------------------------------------
+struct DfWeight {
+    df m;
+    int e;
+};
+
+__device__ __forceinline__ DfWeight df_weight_one() { return DfWeight{df{1.0f, 0.0f}, 0}; }
+
+__device__ __forceinline__ DfWeight df_weight_mul(DfWeight w, df p) {
+    // p >= 0; 0 and FP32 subnormals read as exponent -127 (a zero stays zero, a subnormal is
+    // scaled into the normal range)
+    const int ep = static_cast<int>((__float_as_uint(p.hi) >> 23) & 0xFFu) - 127;
+    const float s = __uint_as_float(static_cast<uint32_t>(127 - ep) << 23);  // 2^-ep
+    return DfWeight{w.m * df{__fmul_rn(p.hi, s), __fmul_rn(p.lo, s)}, w.e + ep};
+}
+
+// w 2^0 as the nearest double, times an FP64 factor c: the power of two is built from its bits
+// in two factors (each a normal double), so a product below the double range rounds to a
+// subnormal or zero as a plain product would.
+__device__ __forceinline__ double df_weight_final(DfWeight w, double c) {
+    const int e1 = w.e < -1022 ? -1022 : (w.e > 1023 ? 1023 : w.e);
+    int e2 = w.e - e1;
+    e2 = e2 < -1022 ? -1022 : (e2 > 1023 ? 1023 : e2);
+    const double p1 = __longlong_as_double(static_cast<long long>(e1 + 1023) << 52);
+    const double p2 = __longlong_as_double(static_cast<long long>(e2 + 1023) << 52);
+    return ((df_to_double(w.m) * c) * p1) * p2;
+}
+
+// ------------------------------------------------------------------------------------
 // sin and cos of phi = 2 pi u, u = (x + 1/2) 2^-32 for a 32-bit x, in df.
 //
 // They multiply momenta bounded by the event scale, so the target is an absolute error of

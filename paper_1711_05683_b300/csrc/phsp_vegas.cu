@@ -129,7 +129,7 @@ __device__ __forceinline__ double vegas_event(const DecayConsts& C, const uint64
     if constexpr (N > 3) sort_mass_draws<N - 2>(y);
     const R M = P::M(C);
     const R T = A::T(C);
-    double w = 1.0;
+    typename P::Wacc w = P::w_one();
     R Q0 = M, Qx = R(0.0f), Qy = R(0.0f), Qz = R(0.0f), Mnext = M;
     M2 = M;
 #pragma unroll
@@ -174,7 +174,7 @@ __device__ __forceinline__ double vegas_event(const DecayConsts& C, const uint64
         Mnext = Mk;
     }
     E1 = Q0;
-    return w * P::Cw(C);
+    return P::w_final(w, C);
 }
 
 // |BW(s12; a) + c BW(s23; b)|^2 in arithmetic R (the integral's formula).
