@@ -142,9 +142,15 @@ __device__ __forceinline__ double f32_to_f64_bits_lo(float f) {
     return __hiloint2double(static_cast<int>(hi), static_cast<int>(b << 29));
 }
 
-// Nearest double to hi + lo (to within 2^-126 absolute when lo is zero or subnormal).
+// Nearest double to hi + lo (to within 2^-126 absolute when lo is zero or subnormal: an exact
+// zero is stored as 2^-127, far below any output's precision).
 __device__ __forceinline__ double df_to_double(df x) {
     return __dadd_rn(f32_to_f64_bits(x.hi), f32_to_f64_bits_lo(x.lo));
+}
+
+// Nearest double to hi + lo with zeros exact (for values whose zero has a meaning).
+__device__ __forceinline__ double df_to_double_exact(df x) {
+    return __dadd_rn(f32_to_f64_bits(x.hi), f32_to_f64_bits(x.lo));
 }
 
 // x * 2^k for an exact power of two (both parts scale exactly).
@@ -178,6 +184,25 @@ __device__ __forceinline__ df df_add_small(df x, float f) {
     return df_fast_two_sum(s, e);
 }
 
+// v 2^-64 as a double-float: the top 48 significant bits of v (the rest truncated, relative
+// error < 2^-47), hi built from the bits directly; 0 for v = 0.
+__device__ __forceinline__ df df_frac_u64(uint64_t v) {
+    if (v == 0) return df{0.0f, 0.0f};
+    const int lz = __clzll(static_cast<long long>(v));
+    const uint64_t m = v << lz;                                            // bit 63 set
+    const uint32_t t1 = static_cast<uint32_t>(m >> 40);                    // bits 63..40
+    const uint32_t t2 = static_cast<uint32_t>(m >> 16) & 0xFFFFFFu;        // bits 39..16
+    const float hi = __int_as_float(((126 - lz) << 23) | static_cast<int>(t1 & 0x7FFFFFu));  // t1 2^(-24-lz)
+    const float lo = __fmul_rn(__uint2float_rz(t2), __int_as_float((79 - lz) << 23));         // t2 2^(-48-lz)
+    return df_fast_two_sum(hi, lo);
+}
+
+// x + f for any FP32 f (TwoSum, then the low parts).
+__device__ __forceinline__ df df_add_f(df x, float f) {
+    const df s = df_two_sum(x.hi, f);
+    return df_fast_two_sum(s.hi, __fadd_rn(s.lo, x.lo));
+}
+
 // ------------------------------------------------------------------------------------
 // Weight product prod_k p_k without the FP64 pipe: a double-float mantissa times 2^e.  Each
 // factor is scaled by an exact power of two into [1, 2) (its exponent read from the bits of
@@ -208,7 +233,7 @@ __device__ __forceinline__ double df_weight_final(DfWeight w, double c) {
     e2 = e2 < -1022 ? -1022 : (e2 > 1023 ? 1023 : e2);
     const double p1 = __longlong_as_double(static_cast<long long>(e1 + 1023) << 52);
     const double p2 = __longlong_as_double(static_cast<long long>(e2 + 1023) << 52);
-    return ((df_to_double(w.m) * c) * p1) * p2;
+    return ((df_to_double_exact(w.m) * c) * p1) * p2;  // a zero factor (a tie) gives w = 0 exactly
 }
 
 // ------------------------------------------------------------------------------------

@@ -75,25 +75,6 @@ template <> struct VegasArith<double> {
     __device__ static double to_double(double x) { return x; }
 };
 
-// v 2^-64 as a double-float: the top 48 significant bits of v (the rest truncated, relative
-// error < 2^-47), hi built from the bits directly; 0 for v = 0.
-__device__ __forceinline__ df df_frac_u64(uint64_t v) {
-    if (v == 0) return df{0.0f, 0.0f};
-    const int lz = __clzll(static_cast<long long>(v));
-    const uint64_t m = v << lz;                                            // bit 63 set
-    const uint32_t t1 = static_cast<uint32_t>(m >> 40);                    // bits 63..40
-    const uint32_t t2 = static_cast<uint32_t>(m >> 16) & 0xFFFFFFu;        // bits 39..16
-    const float hi = __int_as_float(((126 - lz) << 23) | static_cast<int>(t1 & 0x7FFFFFu));  // t1 2^(-24-lz)
-    const float lo = __fmul_rn(__uint2float_rz(t2), __int_as_float((79 - lz) << 23));         // t2 2^(-48-lz)
-    return df_fast_two_sum(hi, lo);
-}
-
-// x + f for any FP32 f (TwoSum, then the low parts).
-__device__ __forceinline__ df df_add_f(df x, float f) {
-    const df s = df_two_sum(x.hi, f);
-    return df_fast_two_sum(s.hi, __fadd_rn(s.lo, x.lo));
-}
-
 template <> struct VegasArith<df> {
     __device__ static df frac(uint64_t v) { return df_frac_u64(v); }
     __device__ static df comp(uint64_t v) { return v == 0 ? df{1.0f, 0.0f} : df_frac_u64(0 - v); }

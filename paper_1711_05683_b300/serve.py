@@ -23,7 +23,11 @@ synchronise the device and stall every request in flight).  Pinned host memory i
 the same way.
 
 Every slice computes exactly the events of the single-request entry points, so a request's
-result is the same alone and in the mix (tests check this bit for bit).
+result is the same alone and in the mix (tests check this bit for bit).  A request that would
+not fit the budget even with nothing else admitted, or that cannot be admitted while nothing
+is active or in flight (so nothing would ever release memory, e.g. when kept outputs have
+filled the pinned ring), is refused (listed in the result's "refused") instead of blocking
+the queue.
 
 `PlainServer` is the comparison: one request at a time in arrival order with the
 single-request entry points (generate + copy to host, or integrate).
@@ -144,6 +148,14 @@ class Server:
         self.stream = torch.cuda.current_stream()
 
     # ------------------------------------------------------------------ state per request
+    def _fits_ever(self, a: _Active) -> bool:
+        """Whether the request could be admitted into empty rings (else it is refused)."""
+        r = a.req
+        if r.kind == "generate":
+            nbytes = (4 * len(r.masses) + 1) * hp.padded_ld(r.nevents) * 4
+            return nbytes <= self.dev_ring.size and nbytes <= self.ring.size
+        return 64 * hp.segments(r.nevents) <= self.seg_ring.size
+
     def _admit(self, a: _Active) -> bool:
         torch = self.torch
         r = a.req
@@ -218,7 +230,7 @@ class Server:
     def _run(self, requests, time_scale, max_wall, cancel_after) -> dict:
         torch = self.torch
         cancel_after = dict(cancel_after or {})
-        cancelled = []
+        cancelled, refused = [], []
         t0 = time.perf_counter()
         pending = deque(enumerate(requests))
         queue: deque[_Active] = deque()
@@ -235,7 +247,14 @@ class Server:
                 rid, r = pending.popleft()
                 queue.append(_Active(rid, r, t0 + r.arrival * time_scale))
             while queue and len(active) < self.max_slices:
+                if not self._fits_ever(queue[0]):  # larger than the budget: refused, not queued forever
+                    refused.append(queue.popleft().rid)
+                    continue
                 if not self._admit(queue[0]):
+                    if not active and not inflight:
+                        # nothing will release memory (kept outputs fill the pinned ring): refuse
+                        refused.append(queue.popleft().rid)
+                        continue
                     break
                 active.append(queue.popleft())
             # harvest finished ticks (oldest first)
@@ -302,6 +321,7 @@ class Server:
         wall = time.perf_counter() - t0
         out = _summary(latencies, events_done, wall, ticks=tick, done=done, kinds=kinds)
         out["cancelled"] = cancelled
+        out["refused"] = refused
         return out
 
     def close(self):

@@ -77,3 +77,48 @@ def test_cancelled_request_leaves_the_others_intact():
         else:
             p, w = hp.generate(r.M, r.masses, r.nevents, r.seed, dtype="f32")
             assert torch.equal(a.host_w[: r.nevents], w.cpu())
+
+
+def test_tight_budget_waits_for_space_and_refuses_what_never_fits():
+    """Admission by budget: with a 96 MB budget the requests are admitted as earlier ones free
+    their blocks, every result still equals the single-request one, and a request larger than
+    the whole budget is refused instead of blocking the queue."""
+    from paper_1711_05683_b300 import serve
+    reqs = workloads.serve_stream(rate_hz=4000, duration_s=0.05, gen_log_events=(5.0, 5.6),
+                                  int_log_events=(4.0, 5.0), rng_seed=21)
+    huge = workloads.Request("generate", 5.0, (0.1, 0.2, 0.3, 0.4, 0.5, 0.6, 0.7, 0.8), 2_000_000, 77,
+                             arrival=0.01)
+    reqs = sorted(list(reqs) + [huge], key=lambda r: r.arrival)
+    big_rid = reqs.index(huge)
+    gen_bytes = sum((4 * len(r.masses) + 1) * hp.padded_ld(r.nevents) * 4 for r in reqs
+                    if r.kind == "generate" and r is not huge)
+    srv = serve.Server(max_slices=64, int_slice_segments=1, pinned_bytes=4 << 30, keep_outputs=True,
+                       budget_bytes=96 * 10 ** 6)
+    assert srv.dev_ring.size < gen_bytes < srv.ring.size  # the device budget is the tight one
+    res = srv.run(reqs, max_wall=60.0)
+    srv.close()
+    assert res["refused"] == [big_rid]
+    assert res["completed"] == len(reqs) - 1
+    for a in res["done"]:
+        r = a.req
+        if r.kind == "generate":
+            p, w = hp.generate(r.M, r.masses, r.nevents, r.seed, dtype="f32")
+            assert torch.equal(a.host_w[: r.nevents], w.cpu())
+        else:
+            assert a.result == hp.integrate(r.M, r.masses, r.nevents, r.seed, kin_dtype="f32", me=r.me,
+                                            params=r.params)
+
+
+def test_kept_outputs_filling_the_pinned_ring_are_refused_not_waited_for():
+    """With keep_outputs the pinned ring is never released; once it is full, later generate
+    requests are refused (nothing could ever free space) and the run ends."""
+    from paper_1711_05683_b300 import serve
+    reqs = workloads.serve_stream(rate_hz=2000, duration_s=0.05, gen_log_events=(5.0, 5.3),
+                                  int_log_events=(4.0, 4.5), rng_seed=5)
+    srv = serve.Server(max_slices=64, int_slice_segments=1, pinned_bytes=64 << 20, keep_outputs=True,
+                       budget_bytes=2 * 10 ** 9)
+    res = srv.run(reqs, max_wall=60.0)
+    srv.close()
+    gens = [i for i, r in enumerate(reqs) if r.kind == "generate"]
+    assert res["refused"] and set(res["refused"]) <= set(gens)
+    assert res["completed"] + len(res["refused"]) == len(reqs)
