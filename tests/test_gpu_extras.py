@@ -187,3 +187,32 @@ def test_probes_measure_plausible_ceilings():
         hp.probe_write_bandwidth(buf[1:], 1)
     with pytest.raises(hp.HydraError, match="INVALID_ARG"):
         hp.probe_fma_rate("f32", 0)
+
+
+def test_compensated_reduction_against_fsum():
+    """The integral's tile / segment reduction (FP64: plain sums inside a 2048-event tile, at
+    most ~16 additions deep; Neumaier-compensated across tiles and segments) against
+    math.fsum, the correctly rounded sum, of the very per-event values it reduces: 3e7 Dalitz
+    f values (about 15 segments) and an adversarial mix of magnitudes 1e-8..1e8 with
+    alternating signs.  Bound: 16 roundings of 2^-53 relative to the sum of magnitudes (a
+    sequential sum of 3e7 terms can lose ~1e-9)."""
+    import math
+    d = workloads.D0_DALITZ
+    nev = 30_000_001
+    p, w = hp.generate(d["M"], d["masses"], nev, 13, dtype="f64")
+    res, vals = hp.evaluate(p, w, me=hp.ME_DALITZ_2BW, params=d["params"], dtype="f64", want_values=True)
+    v = vals[:nev].cpu().numpy()
+    exact = math.fsum(v)
+    assert abs(res["sum_f"] - exact) <= 2e-15 * abs(exact), (res["sum_f"], exact)
+    exact2 = math.fsum(v * v)
+    assert abs(res["sum_f2"] - exact2) <= 2e-15 * abs(exact2)
+    # adversarial: weights alternating in sign over 16 decades, flat matrix element (f = w)
+    rng = np.random.default_rng(8)
+    m = 5_000_003
+    ww = rng.uniform(1, 10, m) * 10.0 ** rng.integers(-8, 9, m) * np.where(np.arange(m) % 2, -1.0, 1.0)
+    wt = torch.from_numpy(ww).cuda()
+    pp = torch.zeros((3, 4, m), dtype=torch.float64, device="cuda")
+    r2, _ = hp.evaluate(pp, wt, me=hp.ME_FLAT, dtype="f64")
+    exact3 = math.fsum(ww)
+    scale = math.fsum(np.abs(ww))
+    assert abs(r2["sum_f"] - exact3) <= 2e-15 * scale, (r2["sum_f"], exact3, scale)
