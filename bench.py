@@ -44,8 +44,8 @@ INT_CFG = workloads.D0_DALITZ
 INSTR_PER_EVENT = {
     ("f32", 2): 91, ("f32", 3): 211, ("f32", 4): 296, ("f32", 5): 421, ("f32", 6): 539,
     ("f32", 7): 668, ("f32", 8): 794, ("f32", 9): 924, ("f32", 10): 1044,
-    ("f64", 2): 474, ("f64", 3): 1123, ("f64", 4): 1707, ("f64", 5): 2288, ("f64", 6): 2895,
-    ("f64", 7): 3501, ("f64", 8): 4085, ("f64", 9): 4713, ("f64", 10): 5332,
+    ("f64", 2): 477, ("f64", 3): 1125, ("f64", 4): 1710, ("f64", 5): 2291, ("f64", 6): 2991,
+    ("f64", 7): 3625, ("f64", 8): 4229, ("f64", 9): 4890, ("f64", 10): 5545,
 }
 
 

@@ -327,7 +327,10 @@ __device__ __forceinline__ void raubold_lynch_group(const DecayConsts& C, const 
             const R one_p = P::one_plus_cos(xc);   // 1 + cos(theta)
             const R sin_t = P::sqrt_(one_m * one_p);
             R sphi, cphi;
-            P::sincos_2pi_u(xp, &sphi, &cphi);  // phi = 2 pi u
+            if constexpr (std::is_same<R, df>::value && N >= 6)
+                df_sincos_2pi_u_outlined(xp, &sphi, &cphi);  // phi = 2 pi u (one copy of the code)
+            else
+                P::sincos_2pi_u(xp, &sphi, &cphi);  // phi = 2 pi u
             const R ps = p * sin_t;
             const R px = ps * cphi, py = ps * sphi, pz = p * cos_t;
             const R Es = P::sqrt_(P::fma_(p, p, Mk * Mk));
