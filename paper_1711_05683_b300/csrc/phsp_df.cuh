@@ -224,16 +224,24 @@ __device__ __forceinline__ DfWeight df_weight_mul(DfWeight w, df p) {
     return DfWeight{w.m * df{__fmul_rn(p.hi, s), __fmul_rn(p.lo, s)}, w.e + ep};
 }
 
-// w 2^0 as the nearest double, times an FP64 factor c: the power of two is built from its bits
-// in two factors (each a normal double), so a product below the double range rounds to a
-// subnormal or zero as a plain product would.
+// w as the nearest double, times an FP64 factor c.  The power 2^e is applied to the bits of
+// the product's exponent when the result stays a normal double (two FP64 instructions in all);
+// otherwise by two FP64 multiplications with normal powers of two, so that a result below the
+// double range rounds to a subnormal or zero as a plain product would.  A zero factor (a tie
+// in the mass draws) gives exactly 0.
 __device__ __forceinline__ double df_weight_final(DfWeight w, double c) {
+    const double v = df_to_double_exact(w.m) * c;
+    const long long bits = __double_as_longlong(v);
+    const int ev = static_cast<int>((bits >> 52) & 0x7FF);  // biased exponent of v
+    if (ev != 0 && ev + w.e > 0 && ev + w.e < 0x7FF)          // v normal and v 2^e normal
+        return __longlong_as_double(bits + (static_cast<long long>(w.e) << 52));
+    if (ev == 0 && v == 0.0) return v;
     const int e1 = w.e < -1022 ? -1022 : (w.e > 1023 ? 1023 : w.e);
     int e2 = w.e - e1;
     e2 = e2 < -1022 ? -1022 : (e2 > 1023 ? 1023 : e2);
     const double p1 = __longlong_as_double(static_cast<long long>(e1 + 1023) << 52);
     const double p2 = __longlong_as_double(static_cast<long long>(e2 + 1023) << 52);
-    return ((df_to_double_exact(w.m) * c) * p1) * p2;  // a zero factor (a tie) gives w = 0 exactly
+    return (v * p1) * p2;
 }
 
 // ------------------------------------------------------------------------------------
