@@ -550,8 +550,8 @@ def run_extras(nev: int = 100_000_000, reps: int = 3) -> dict:
 # ----------------------------------------------------------------------------- VEGAS
 # Thread instructions per point of the double-float VEGAS kernels (ncu smsp__inst_executed.sum
 # x 32 / points on 4e6-point iterations, 100 bins; profiles/vegas_eval_df_dalitz_4e6.md).
-VEGAS_INSTR_PER_POINT = {("dalitz", "eval"): 1314, ("dalitz", "hist"): 140,
-                         ("flat10", "eval"): 2502, ("flat10", "hist"): 557}
+VEGAS_INSTR_PER_POINT = {("dalitz", "eval"): 1331, ("dalitz", "hist"): 108,
+                         ("flat10", "eval"): 2482, ("flat10", "hist"): 457}
 
 
 def run_vegas(calls: int = 100_000_000, iterations: int = 10, reps: int = 3,

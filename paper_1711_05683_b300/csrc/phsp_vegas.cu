@@ -284,8 +284,13 @@ __global__ void __launch_bounds__(kVegasBlock) vegas_hist(int K, uint64_t calls,
                                                           const unsigned long long* __restrict__ max_f2,
                                                           unsigned long long* __restrict__ hist) {
     constexpr int kWords = (D + 3) / 4;
-    extern __shared__ unsigned long long sh[];
-    for (int i = threadIdx.x; i < D * K; i += blockDim.x) sh[i] = 0ull;
+    // each bin's 64-bit sum as two 32-bit words: the low word's atomic returns the old value,
+    // from which the carry into the high word follows (exact modulo 2^64, so the same integer
+    // sums as 64-bit atomics, mostly with one 32-bit atomic per update)
+    extern __shared__ uint32_t sh32[];
+    uint32_t* lo = sh32;
+    uint32_t* hi = sh32 + D * K;
+    for (int i = threadIdx.x; i < 2 * D * K; i += blockDim.x) sh32[i] = 0u;
     __syncthreads();
     const double mx = __longlong_as_double(static_cast<long long>(*max_f2));
     const double scale = mx > 0.0 ? qnum / mx : 0.0;
@@ -297,12 +302,20 @@ __global__ void __launch_bounds__(kVegasBlock) vegas_hist(int K, uint64_t calls,
         for (int q = 0; q < kWords; ++q) wd[q] = bins[static_cast<uint64_t>(q) * calls + s];
         const unsigned long long qf = static_cast<unsigned long long>(f * f * scale);
         if (qf == 0ull) continue;
+        const uint32_t ql = static_cast<uint32_t>(qf), qh = static_cast<uint32_t>(qf >> 32);
 #pragma unroll
-        for (int d = 0; d < D; ++d) atomicAdd(&sh[d * K + ((wd[d / 4] >> (8 * (d % 4))) & 0xFFu)], qf);
+        for (int d = 0; d < D; ++d) {
+            const int i = d * K + static_cast<int>((wd[d / 4] >> (8 * (d % 4))) & 0xFFu);
+            const uint32_t old = atomicAdd(&lo[i], ql);
+            const uint32_t up = qh + (old + ql < old ? 1u : 0u);
+            if (up) atomicAdd(&hi[i], up);
+        }
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < D * K; i += blockDim.x)
-        if (sh[i]) atomicAdd(&hist[i], sh[i]);
+    for (int i = threadIdx.x; i < D * K; i += blockDim.x) {
+        const unsigned long long v = (static_cast<unsigned long long>(hi[i]) << 32) | lo[i];
+        if (v) atomicAdd(&hist[i], v);
+    }
 }
 
 static const void* vegas_hist_for(int n) {
