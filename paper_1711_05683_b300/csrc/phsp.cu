@@ -111,17 +111,14 @@ __global__ void __launch_bounds__(512) phsp_integrate_tiles(const __grid_constan
 }
 
 // Segment partials: 8 doubles per segment, (s, c) for f, f^2, w, w^2.
-// One warp per segment of kSegTiles tiles (segment_sums in phsp_integral.cuh).
-__global__ void __launch_bounds__(128) reduce_segments(const TileSums* __restrict__ partials,
-                                                       uint64_t ntiles, uint64_t seg_begin,
-                                                       double* __restrict__ seg_out) {
-    const int lane = threadIdx.x & 31;
-    const uint64_t seg = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-    const uint64_t nseg = (ntiles + kSegTiles - 1) / kSegTiles;
-    if (seg >= nseg) return;
+// One block per segment of kSegTiles tiles (segment_sums_block in phsp_integral.cuh).
+__global__ void __launch_bounds__(kSegBlock) reduce_segments(const TileSums* __restrict__ partials,
+                                                             uint64_t ntiles, uint64_t seg_begin,
+                                                             double* __restrict__ seg_out) {
+    const uint64_t seg = blockIdx.x;
     const uint64_t t0 = seg * kSegTiles;
     const uint64_t nt = ntiles - t0 < kSegTiles ? ntiles - t0 : kSegTiles;
-    segment_sums(partials + t0, nt, lane, seg_out + (seg_begin + seg) * 8);
+    segment_sums_block(partials + t0, nt, seg_out + (seg_begin + seg) * 8);
 }
 
 // One warp folds all segments and writes the result.
@@ -474,8 +471,7 @@ static hydra_status launch_integrate_chunks(const Launch& L, const DecayConsts& 
         if (err != cudaSuccess) return cuda_fail(err, "integrate launch");
         const uint64_t nseg = (nt + kSegTiles - 1) / kSegTiles;
         const uint64_t seg_begin = t0 / kSegTiles;
-        const int rgrid = static_cast<int>((nseg * 32 + 127) / 128);
-        reduce_segments<<<rgrid, 128, 0, st>>>(s->tiles, nt, seg_begin, s->segs);
+        reduce_segments<<<static_cast<unsigned>(nseg), kSegBlock, 0, st>>>(s->tiles, nt, seg_begin, s->segs);
         err = cudaGetLastError();
         if (err != cudaSuccess) return cuda_fail(err, "segment reduction launch");
     }

@@ -165,20 +165,17 @@ __global__ void __launch_bounds__(kBatchBlock) phsp_batch_kernel(BatchHeader* __
 
 // One warp per (integral slice, segment): the slice's tile partials -> the request's
 // segment storage, with the same segment_sums as the single-request path.
-__global__ void __launch_bounds__(kBatchBlock) batch_reduce_segments(const BatchHeader* __restrict__ hdr,
-                                                                     const TileSums* __restrict__ partials) {
-    const int lane = threadIdx.x & 31;
-    const uint64_t gw = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-    const uint64_t nw = (static_cast<uint64_t>(gridDim.x) * blockDim.x) >> 5;
+__global__ void __launch_bounds__(kSegBlock) batch_reduce_segments(const BatchHeader* __restrict__ hdr,
+                                                                   const TileSums* __restrict__ partials) {
     const uint64_t njobs = hdr->nsegjobs;
-    for (uint64_t job = gw; job < njobs; job += nw) {
+    for (uint64_t job = blockIdx.x; job < njobs; job += gridDim.x) {  // one block per segment job
         const int r = find_slot(hdr->seg_prefix, hdr->nreq, job);
         const BatchEntry& e = hdr->entries[r];
         const uint64_t s = job - hdr->seg_prefix[r];
         const uint64_t slice_tiles = (e.count + kTileEvents - 1) / kTileEvents;
         const uint64_t t0 = s * kSegTiles;
         const uint64_t nt = slice_tiles - t0 < kSegTiles ? slice_tiles - t0 : kSegTiles;
-        segment_sums(partials + e.partial_begin + t0, nt, lane, e.seg + (e.first / kSegEvents + s) * 8);
+        segment_sums_block(partials + e.partial_begin + t0, nt, e.seg + (e.first / kSegEvents + s) * 8);
     }
 }
 
@@ -248,7 +245,7 @@ void launch_run_kernels(hydra_batch* b, int v, cudaStream_t s) {
         phsp_batch_kernel<double, double><<<b->grid_main[v], kBatchBlock, 0, s>>>(hdr, b->d_partials);
     else
         phsp_batch_kernel<df, double><<<b->grid_main[v], kBatchBlock, 0, s>>>(hdr, b->d_partials);
-    batch_reduce_segments<<<b->grid_aux, kBatchBlock, 0, s>>>(hdr, b->d_partials);
+    batch_reduce_segments<<<b->grid_aux, kSegBlock, 0, s>>>(hdr, b->d_partials);
     batch_finalize<<<b->grid_aux, kBatchBlock, 0, s>>>(hdr, b->d_results);
 }
 

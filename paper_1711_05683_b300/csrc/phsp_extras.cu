@@ -363,14 +363,12 @@ __global__ void __launch_bounds__(256) evaluate_tiles(uint64_t nevents, const R*
     }
 }
 
-__global__ void __launch_bounds__(128) eval_reduce_segments(const TileSums* __restrict__ partials, uint64_t ntiles,
-                                                            uint64_t seg_begin, double* __restrict__ seg_out) {
-    const uint64_t seg = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-    const uint64_t nseg = (ntiles + kSegTiles - 1) / kSegTiles;
-    if (seg >= nseg) return;
+__global__ void __launch_bounds__(kSegBlock) eval_reduce_segments(const TileSums* __restrict__ partials, uint64_t ntiles,
+                                                                  uint64_t seg_begin, double* __restrict__ seg_out) {
+    const uint64_t seg = blockIdx.x;  // one block per segment
     const uint64_t t0 = seg * kSegTiles;
     const uint64_t nt = ntiles - t0 < kSegTiles ? ntiles - t0 : kSegTiles;
-    segment_sums(partials + t0, nt, threadIdx.x & 31, seg_out + (seg_begin + seg) * 8);
+    segment_sums_block(partials + t0, nt, seg_out + (seg_begin + seg) * 8);
 }
 
 __global__ void __launch_bounds__(32) eval_finalize(const double* __restrict__ seg, uint64_t nseg, uint64_t nevents,
@@ -633,7 +631,7 @@ hydra_status hydra_phsp_evaluate(int n, uint64_t nevents, hydra_dtype dtype, hyd
                     static_cast<const double*>(weights), P, static_cast<double*>(values), t0, nt, s->tiles);
         }
         const uint64_t ns = (nt + kSegTiles - 1) / kSegTiles;
-        eval_reduce_segments<<<static_cast<unsigned>((ns * 32 + 127) / 128), 128, 0, cs>>>(s->tiles, nt, t0 / kSegTiles, s->segs);
+        eval_reduce_segments<<<static_cast<unsigned>(ns), kSegBlock, 0, cs>>>(s->tiles, nt, t0 / kSegTiles, s->segs);
     }
     eval_finalize<<<1, 32, 0, cs>>>(s->segs, nseg, nevents, s->d_res);
     cudaError_t err = cudaGetLastError();

@@ -175,20 +175,35 @@ __device__ __forceinline__ void warp_merge(Comp& a) {
     }
 }
 
-// Compensated sums of nt (<= kSegTiles) consecutive tile partials: lane l takes tiles
-// l, l+32, ... in order, then a fixed TwoSum butterfly; lane 0 writes 8 doubles (s, c) for
-// f, f^2, w, w^2 to out.
-__device__ __forceinline__ void segment_sums(const TileSums* __restrict__ partials, uint64_t nt, int lane,
-                                             double* __restrict__ out) {
+// Compensated sums of nt (<= kSegTiles) consecutive tile partials by one block of kSegWarps
+// warps (every thread of the block calls it): warp v takes tiles [v 128, (v + 1) 128), its
+// lane l tiles v 128 + l + 32 i (i = 0..3) in order; a fixed TwoSum butterfly merges the
+// lanes, thread 0 merges the warps in order v = 0..7 and writes 8 doubles (s, c) for f, f^2,
+// w, w^2 to out.  (One warp per segment left a 2^26-event chunk on 8 SMs, each lane with 128
+// dependent compensated FP64 additions on B300's narrow FP64 pipe.)
+constexpr int kSegWarps = 8;
+constexpr int kSegBlock = 32 * kSegWarps;
+
+__device__ __forceinline__ void segment_sums_block(const TileSums* __restrict__ partials, uint64_t nt,
+                                                   double* __restrict__ out) {
+    constexpr int kPerWarp = kSegTiles / kSegWarps;
+    constexpr int kPerLane = kPerWarp / 32;
+    __shared__ double part[kSegWarps][8];
+    const int lane = threadIdx.x & 31, v = threadIdx.x >> 5;
+    TileSums p[kPerLane];
+#pragma unroll
+    for (int i = 0; i < kPerLane; ++i) {
+        const uint64_t t = static_cast<uint64_t>(v * kPerWarp + i * 32 + lane);
+        p[i] = t < nt ? partials[t] : TileSums{0.0, 0.0, 0.0, 0.0};
+    }
     Comp f, f2, w, w2;
-    for (int j = 0; j < kSegTiles / 32; ++j) {
-        const uint64_t t = static_cast<uint64_t>(j * 32 + lane);
-        if (t < nt) {
-            const TileSums p = partials[t];
-            f.add(p.f);
-            f2.add(p.f2);
-            w.add(p.w);
-            w2.add(p.w2);
+#pragma unroll
+    for (int i = 0; i < kPerLane; ++i) {
+        if (static_cast<uint64_t>(v * kPerWarp + i * 32 + lane) < nt) {
+            f.add(p[i].f);
+            f2.add(p[i].f2);
+            w.add(p[i].w);
+            w2.add(p[i].w2);
         }
     }
     warp_merge(f);
@@ -196,9 +211,24 @@ __device__ __forceinline__ void segment_sums(const TileSums* __restrict__ partia
     warp_merge(w);
     warp_merge(w2);
     if (lane == 0) {
-        out[0] = f.s; out[1] = f.c; out[2] = f2.s; out[3] = f2.c;
-        out[4] = w.s; out[5] = w.c; out[6] = w2.s; out[7] = w2.c;
+        part[v][0] = f.s; part[v][1] = f.c; part[v][2] = f2.s; part[v][3] = f2.c;
+        part[v][4] = w.s; part[v][5] = w.c; part[v][6] = w2.s; part[v][7] = w2.c;
     }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        Comp q[4];
+        for (int k = 0; k < 4; ++k) {
+            q[k].s = part[0][2 * k];
+            q[k].c = part[0][2 * k + 1];
+        }
+        for (int u = 1; u < kSegWarps; ++u)
+            for (int k = 0; k < 4; ++k) q[k].merge(part[u][2 * k], part[u][2 * k + 1]);
+        for (int k = 0; k < 4; ++k) {
+            out[2 * k] = q[k].s;
+            out[2 * k + 1] = q[k].c;
+        }
+    }
+    __syncthreads();  // part is reused by the block's next segment
 }
 
 // One warp folds nseg segment partials (lane l: segments l, l+32, ...), merges lanes and

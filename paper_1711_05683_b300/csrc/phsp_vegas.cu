@@ -572,7 +572,7 @@ hydra_status hydra_phsp_vegas(double M, int n, const double* masses, uint64_t se
             err = cudaLaunchKernel(kern, dim3(grid), dim3(kVegasBlock), args, smem, cs);
             if (err != cudaSuccess) return cuda_fail(err, "VEGAS evaluation launch");
             const uint64_t ns = (nt + kSegTiles - 1) / kSegTiles;
-            eval_reduce_segments<<<static_cast<unsigned>((ns * 32 + 127) / 128), 128, 0, cs>>>(s->tiles, nt, t0 / kSegTiles, s->segs);
+            eval_reduce_segments<<<static_cast<unsigned>(ns), kSegBlock, 0, cs>>>(s->tiles, nt, t0 / kSegTiles, s->segs);
         }
         eval_finalize<<<1, 32, 0, cs>>>(s->segs, nseg, calls, s->d_res);
         if (it < iterations - 1) {
