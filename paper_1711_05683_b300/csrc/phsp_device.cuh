@@ -118,6 +118,10 @@ template <> struct Prec<float> {
         *s = -sn;
         *c = -cs;
     }
+    // cos(2 pi (xa - xb) 2^-32): the difference of two phi draws, exact modulo 2^32, in (-pi, pi]
+    __device__ static float cos_2pi_diff(uint32_t xa, uint32_t xb) {
+        return __cosf(__int2float_rn(static_cast<int32_t>(xa - xb)) * 1.46291807926715968e-09f);
+    }
     __device__ static float scale(float x, float pow2) { return x * pow2; }
     __device__ static float half_odd(uint32_t y) { return __uint2float_rn(y) + 0.5f; }  // y + 1/2
     // 1 + cos(theta), 1 - cos(theta), cos(theta) of a cos(theta) draw x (u = (x + 1/2) 2^-32)
@@ -150,6 +154,9 @@ template <> struct Prec<double> {
     // sin and cos of phi = 2 pi u with u = (x + 1/2) 2^-32: sincospi(2u), argument exact.
     __device__ static void sincos_2pi_u(uint32_t x, double* s, double* c) {
         sincospi(__fma_rn(__uint2double_rn(x), 4.656612873077392578125e-10, 2.3283064365386962890625e-10), s, c);
+    }
+    __device__ static double cos_2pi_diff(uint32_t xa, uint32_t xb) {
+        return cospi(__int2double_rn(static_cast<int32_t>(xa - xb)) * 4.656612873077392578125e-10);
     }
     __device__ static double scale(double x, double pow2) { return x * pow2; }
     __device__ static double half_odd(uint32_t y) { return __uint2double_rn(y) + 0.5; }

@@ -72,9 +72,56 @@ __device__ __forceinline__ R dalitz_2bw(const MEConsts& P, R s12, R s23) {
     return Q::fma_(re, re, im * im);
 }
 
+// The N = 3 integrand from the event's five draws without its 4-vectors.  Same event as
+// raubold_lynch_group<3>: draw 0 gives M_2 = mu_2 + r T, the gaps T (1 - r) and T r, the
+// momenta p2 (parent -> (12) + 3) and p1 ((12) -> 1 + 2) and the weight (p2 p1) C_3; draws
+// (1, 2) and (3, 4) are the directions n_a of subsystem (12) in the parent frame and n_b of
+// daughter 1 in the (12) frame, both in the parent's axes (pure boosts), so the boost gives
+//   E1 = (Q0 E1* + p2 p1 cos alpha) / M_2,  Q0 = sqrt(p2^2 + M_2^2),  E1* = sqrt(p1^2 + m1^2),
+//   cos alpha = n_a . n_b = c_a c_b + s_a s_b cos(phi_a - phi_b),
+// with phi_a - phi_b from the integer difference of the two phi draws.  Then s12 = M_2^2 and
+// s23 = M^2 + m1^2 - 2 M E1 as in the general path; one cosine instead of two sin/cos pairs
+// and no 3-vectors.
+template <typename R>
+__device__ __forceinline__ void dalitz3_point(const DecayConsts& C, const MEConsts& P, uint64_t e, R& f,
+                                              R& wout) {
+    using Q = Prec<R>;
+    uint32_t b0[4], b1[4];
+    philox4x32_10(static_cast<uint32_t>(e), static_cast<uint32_t>(e >> 32), 0u, 0u, C.rk0, C.rk1, b0);
+    philox4x32_10(static_cast<uint32_t>(e), static_cast<uint32_t>(e >> 32), 1u, 0u, C.rk0, C.rk1, b1);
+    const uint32_t y = b0[0], xca = b0[1], xpa = b0[2], xcb = b0[3], xpb = b1[0];
+    const R M = Q::M(C), Ts = Q::Ts(C);
+    const R m1 = Q::m(C, 0), m2 = Q::m(C, 1), m3 = Q::m(C, 2);
+    const R M2 = Q::fma_(Q::half_odd(y), Ts, Q::mu(C, 1));
+    const R gap2 = Q::half_odd(~y) * Ts;  // T (1 - r)
+    const R gap1 = Q::half_odd(y) * Ts;   // T r
+    const R twoM2 = Q::scale(M2, 2.0f), twom3 = Q::scale(m3, 2.0f);
+    const R lam2 = ((gap2 * (gap2 + twoM2)) * (gap2 + twom3)) * ((gap2 + twoM2) + twom3);
+    const R twom1 = Q::scale(m1, 2.0f), twom2 = Q::scale(m2, 2.0f);
+    const R lam1 = ((gap1 * (gap1 + twom1)) * (gap1 + twom2)) * ((gap1 + twom1) + twom2);
+    const R invM2 = Q::rcp(M2);
+    const R p2 = Q::sqrt_(lam2) * Q::scale(Q::rcp(M), 0.5f);
+    const R p1 = Q::sqrt_(lam1) * Q::scale(invM2, 0.5f);
+    const R w = Q::w_final(Q::w_mul(Q::w_mul(Q::w_one(), p2), p1), C);
+    const R ssq = (Q::one_minus_cos(xca) * Q::one_plus_cos(xca)) * (Q::one_minus_cos(xcb) * Q::one_plus_cos(xcb));
+    const R cos_alpha = Q::fma_(Q::cos_of(xca), Q::cos_of(xcb), Q::sqrt_(ssq) * Q::cos_2pi_diff(xpa, xpb));
+    const R Q0 = Q::sqrt_(Q::fma_(p2, p2, M2 * M2));
+    const R E1s = Q::sqrt_(Q::fma_(p1, p1, m1 * m1));
+    const R E1 = Q::fma_(Q0, E1s, (p2 * p1) * cos_alpha) * invM2;
+    const R s12 = M2 * M2;
+    const R s23 = Q::fma_(R(-2) * M, E1, Q::fma_(M, M, Q::m2(C, 0)));
+    wout = w;
+    f = w * dalitz_2bw<R>(P, s12, s23);
+}
+
 template <int N, typename R, int ME, int EPT>
 __device__ __forceinline__ void integrand_group(const DecayConsts& C, const MEConsts& P,
                                                 const uint64_t (&ev)[EPT], R (&f)[EPT], R (&w)[EPT]) {
+    if constexpr (ME == HYDRA_ME_DALITZ_2BW && N == 3) {
+#pragma unroll
+        for (int q = 0; q < EPT; ++q) dalitz3_point<R>(C, P, ev[q], f[q], w[q]);
+        return;
+    }
     IntegrandSink<R, EPT> s;
     raubold_lynch_group<N, R, EPT>(C, ev, s);
 #pragma unroll
