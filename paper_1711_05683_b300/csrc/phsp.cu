@@ -39,7 +39,7 @@ namespace hydra {
 // Thread t takes the group of EPT consecutive events g*EPT.. (grid-stride over groups); the
 // last nevents % EPT events are taken one each by the first threads of the grid.  R is the
 // kinematic arithmetic (float, double, or df = pairs of floats for FP64 outputs).
-template <int N, typename R, int EPT>
+template <int N, typename R, int EPT, bool kMassless = false>
 __global__ void __launch_bounds__(512) phsp_generate_kernel(const __grid_constant__ DecayConsts C,
                                                             uint64_t nevents, uint64_t event_offset,
                                                             typename Prec<R>::Out* __restrict__ out,
@@ -58,14 +58,14 @@ __global__ void __launch_bounds__(512) phsp_generate_kernel(const __grid_constan
 #pragma unroll
         for (int q = 0; q < EPT; ++q) ev[q] = event_offset + e0 + q;
         StoreSink<R, EPT> sink{out + e0, weights + e0, ld};
-        raubold_lynch_group<N, R, EPT>(C, ev, sink);
+        raubold_lynch_group<N, R, EPT, kMassless>(C, ev, sink);
     }
     if constexpr (EPT > 1) {
         const uint64_t e = groups * EPT + tid;
         if (e < nevents) {
             uint64_t ev[1] = {event_offset + e};
             StoreSink<R, 1> sink{out + e, weights + e, ld};
-            raubold_lynch_group<N, R, 1>(C, ev, sink);
+            raubold_lynch_group<N, R, 1, kMassless>(C, ev, sink);
         }
     }
 }
@@ -163,6 +163,7 @@ hydra_status make_consts(double M, int n, const double* masses, uint64_t seed,
         C->m[i] = m;
         C->mu[i] = sum;
         C->m2[i] = m * m;
+        if (m == 0.0) C->massless |= 1u << i;
     }
     const double T = M - sum;
     if (!(T > 0.0))
@@ -230,28 +231,39 @@ struct Launch {
     int ept;
 };
 
-template <typename R, int EPT>
+template <typename R, int EPT, bool M0>
 static const void* generate_kernel_n(int n) {
     switch (n) {
-        case 2: return reinterpret_cast<const void*>(&phsp_generate_kernel<2, R, EPT>);
-        case 3: return reinterpret_cast<const void*>(&phsp_generate_kernel<3, R, EPT>);
-        case 4: return reinterpret_cast<const void*>(&phsp_generate_kernel<4, R, EPT>);
-        case 5: return reinterpret_cast<const void*>(&phsp_generate_kernel<5, R, EPT>);
-        case 6: return reinterpret_cast<const void*>(&phsp_generate_kernel<6, R, EPT>);
-        case 7: return reinterpret_cast<const void*>(&phsp_generate_kernel<7, R, EPT>);
-        case 8: return reinterpret_cast<const void*>(&phsp_generate_kernel<8, R, EPT>);
-        case 9: return reinterpret_cast<const void*>(&phsp_generate_kernel<9, R, EPT>);
-        case 10: return reinterpret_cast<const void*>(&phsp_generate_kernel<10, R, EPT>);
+        case 2: return reinterpret_cast<const void*>(&phsp_generate_kernel<2, R, EPT, M0>);
+        case 3: return reinterpret_cast<const void*>(&phsp_generate_kernel<3, R, EPT, M0>);
+        case 4: return reinterpret_cast<const void*>(&phsp_generate_kernel<4, R, EPT, M0>);
+        case 5: return reinterpret_cast<const void*>(&phsp_generate_kernel<5, R, EPT, M0>);
+        case 6: return reinterpret_cast<const void*>(&phsp_generate_kernel<6, R, EPT, M0>);
+        case 7: return reinterpret_cast<const void*>(&phsp_generate_kernel<7, R, EPT, M0>);
+        case 8: return reinterpret_cast<const void*>(&phsp_generate_kernel<8, R, EPT, M0>);
+        case 9: return reinterpret_cast<const void*>(&phsp_generate_kernel<9, R, EPT, M0>);
+        case 10: return reinterpret_cast<const void*>(&phsp_generate_kernel<10, R, EPT, M0>);
     }
     return nullptr;
 }
 
+// massless: every daughter has mass 0 (the double-float generator has a variant for that case;
+// it saves the square root of every two-body momentum, 7-10% of its time)
 template <typename R>
-static const void* generate_kernel_for(int n, int ept) {
+static const void* generate_kernel_for(int n, int ept, bool massless) {
+    constexpr bool kHasMassless = std::is_same<R, df>::value;
+    if (kHasMassless && massless) {
+        switch (ept) {
+            case 1: return generate_kernel_n<R, 1, kHasMassless>(n);
+            case 2: return generate_kernel_n<R, 2, kHasMassless>(n);
+            case 4: return generate_kernel_n<R, 4, kHasMassless>(n);
+        }
+        return nullptr;
+    }
     switch (ept) {
-        case 1: return generate_kernel_n<R, 1>(n);
-        case 2: return generate_kernel_n<R, 2>(n);
-        case 4: return generate_kernel_n<R, 4>(n);
+        case 1: return generate_kernel_n<R, 1, false>(n);
+        case 2: return generate_kernel_n<R, 2, false>(n);
+        case 4: return generate_kernel_n<R, 4, false>(n);
     }
     return nullptr;
 }
@@ -312,13 +324,14 @@ static LaunchCfg g_cfg[2][2][kNMax + 1];
 
 std::atomic<int> g_fp64_arith{HYDRA_FP64_DOUBLE_FLOAT};
 
-static Launch select_generate(hydra_dtype dtype, int n) {
+static Launch select_generate(hydra_dtype dtype, int n, const DecayConsts& C) {
     LaunchCfg& c = g_cfg[HYDRA_KERNEL_GENERATE][dtype][n];
     const int ept = c.ept.load(std::memory_order_relaxed);
+    const bool massless = C.massless == (1u << n) - 1u;
     const void* k = nullptr;
-    if (dtype == HYDRA_F32) k = generate_kernel_for<float>(n, ept);
-    else if (g_fp64_arith.load(std::memory_order_relaxed) == HYDRA_FP64_NATIVE) k = generate_kernel_for<double>(n, ept);
-    else k = generate_kernel_for<df>(n, ept);
+    if (dtype == HYDRA_F32) k = generate_kernel_for<float>(n, ept, massless);
+    else if (g_fp64_arith.load(std::memory_order_relaxed) == HYDRA_FP64_NATIVE) k = generate_kernel_for<double>(n, ept, massless);
+    else k = generate_kernel_for<df>(n, ept, massless);
     return Launch{k, c.block.load(std::memory_order_relaxed), ept};
 }
 
@@ -560,7 +573,7 @@ hydra_status hydra_phsp_generate(double M, int n, const double* masses, uint64_t
         return fail(HYDRA_ERR_MISALIGNED, "out and weights must be 16-byte aligned");
     if (ld % 4 != 0) return fail(HYDRA_ERR_MISALIGNED, "ld = %llu must be a multiple of 4", static_cast<unsigned long long>(ld));
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    const Launch L = select_generate(dtype, n);
+    const Launch L = select_generate(dtype, n, C);
     const int grid = grid_for(L.kern, L.block, (nevents + L.ept - 1) / L.ept);
     void* args[] = {&C, &nevents, &event_offset, &out, &ld, &weights};
     const cudaError_t err = cudaLaunchKernel(L.kern, dim3(grid), dim3(L.block), args, 0, s);
@@ -589,7 +602,7 @@ hydra_status hydra_phsp_generate_host(double M, int n, const double* masses, uin
     st = ensure_staging(s, arrays * chunk * elem);
     if (st != HYDRA_OK) return st;
     cudaStream_t gs = reinterpret_cast<cudaStream_t>(stream);
-    const Launch L = select_generate(dtype, n);
+    const Launch L = select_generate(dtype, n, C);
     cudaError_t err = cudaSuccess;
     // the copy stream must not run ahead of work already queued on the caller's stream
     err = cudaEventRecord(s->gen_done[1], gs);

@@ -35,6 +35,7 @@ struct DecayConsts {
     float mdf[kNMax][2], mudf[kNMax][2], m2df[kNMax][2];
     // Philox round keys: key + r * (W0, W1), r = 0..9
     uint32_t rk0[10], rk1[10];
+    uint32_t massless;  // bit i set when daughter i+1 has mass 0
 };
 
 // ------------------------------------------------------------------------------------
@@ -235,8 +236,10 @@ template <> struct Prec<df> {
 //   sink.daughter(i, E, px, py, pz)  daughter index i = 0..n-1 (daughter i+1)
 //   sink.subsystem_mass(k, Mk)       M_k for k = 1..n-1
 //   sink.weight(w)
+// kMassless: a variant for decays whose daughters are all massless (chosen by the host), where
+// lambda(M_{k+1}^2, M_k^2, 0) = (Delta (Delta + 2 M_k))^2 and the momentum needs no square root.
 // ------------------------------------------------------------------------------------
-template <int N, typename R, int EPT, typename Sink>
+template <int N, typename R, int EPT, bool kMassless = false, typename Sink>
 __device__ __forceinline__ void raubold_lynch_group(const DecayConsts& C, const uint64_t (&ev)[EPT],
                                                     Sink& sink) {
     using P = Prec<R>;
@@ -319,12 +322,17 @@ __device__ __forceinline__ void raubold_lynch_group(const DecayConsts& C, const 
             }
             Mk_out[q] = Mk;
             // two-body momentum
-            const R mk1 = P::m(C, k);
             const R twoMk = P::scale(Mk, 2.0f);
-            const R twom = P::scale(mk1, 2.0f);
-            const R lam = ((gap * (gap + twoMk)) * (gap + twom)) * ((gap + twoMk) + twom);
             const R invM = P::rcp(Mnext[q]);
-            const R p = P::sqrt_(lam) * P::scale(invM, 0.5f);
+            R p;
+            if constexpr (kMassless) {
+                // every daughter massless: lambda = (Delta (Delta + 2 M_k))^2, no square root
+                p = (gap * (gap + twoMk)) * P::scale(invM, 0.5f);
+            } else {
+                const R twom = P::scale(P::m(C, k), 2.0f);
+                const R lam = ((gap * (gap + twoMk)) * (gap + twom)) * ((gap + twoMk) + twom);
+                p = P::sqrt_(lam) * P::scale(invM, 0.5f);
+            }
             w[q] = P::w_mul(w[q], p);
             // isotropic direction of subsystem k in the rest frame of subsystem k+1
             const uint32_t xc = xcs[q];
