@@ -43,10 +43,19 @@ INT_CFG = workloads.D0_DALITZ
 # work of the issue-bound FP64 (double-float) generator, the dominant kernel of the step.
 INSTR_PER_EVENT = {
     ("f32", 2): 91, ("f32", 3): 211, ("f32", 4): 296, ("f32", 5): 421, ("f32", 6): 539,
-    ("f32", 7): 668, ("f32", 8): 794, ("f32", 9): 924, ("f32", 10): 1044,
-    ("f64", 2): 477, ("f64", 3): 1125, ("f64", 4): 1710, ("f64", 5): 2291, ("f64", 6): 2991,
-    ("f64", 7): 3625, ("f64", 8): 4229, ("f64", 9): 4890, ("f64", 10): 5545,
+    ("f32", 7): 700, ("f32", 8): 794, ("f32", 9): 924, ("f32", 10): 1044,
+    ("f64", 2): 476, ("f64", 3): 1129, ("f64", 4): 1714, ("f64", 5): 2298, ("f64", 6): 3000,
+    ("f64", 7): 3633, ("f64", 8): 4235, ("f64", 9): 4887, ("f64", 10): 5540,
+    # the double-float variant for all-massless decays (no square root per two-body momentum)
+    ("f64", 2, "massless"): 419, ("f64", 3, "massless"): 1020, ("f64", 4, "massless"): 1554,
+    ("f64", 5, "massless"): 2088, ("f64", 6, "massless"): 2742, ("f64", 7, "massless"): 3318,
+    ("f64", 8, "massless"): 3849, ("f64", 9, "massless"): 4452, ("f64", 10, "massless"): 5032,
 }
+
+
+def instr_per_event(dtype: str, n: int, massive: bool) -> int:
+    """Thread instructions per event of the generator kernel a launch runs."""
+    return INSTR_PER_EVENT.get((dtype, n) if massive else (dtype, n, "massless"), INSTR_PER_EVENT[(dtype, n)])
 
 
 def bytes_per_event(n: int, dtype: str) -> int:
@@ -313,7 +322,7 @@ def run_ours(args) -> None:
         # per-kernel roofline: the slower of the output bytes at the measured HBM peak and the
         # instructions at the SM issue limit
         by_hbm = peaks["hbm_gbs"] * 1e9 / bytes_per_event(n, dtype)
-        by_issue = issue_limit / INSTR_PER_EVENT[(dtype, n)]
+        by_issue = issue_limit / instr_per_event(dtype, n, massive)
         roof_ev = min(by_hbm, by_issue)
         breakdown.append({"kernel": f"phsp_generate_kernel<{n},{'float' if dtype == 'f32' else 'double'}>",
                           "n": n, "dtype": dtype, "massive": massive, "events": nev,
@@ -346,7 +355,7 @@ def run_ours(args) -> None:
         tot_bytes = sum(bytes_per_event(x["n"], dominant) * x["events"] for x in rows)
         hbm = tot_bytes / (fam_ms[dominant] / 1e3) / 1e9
         if dominant == "f64":
-            instr = sum(INSTR_PER_EVENT[("f64", x["n"])] * x["events"] for x in rows)
+            instr = sum(instr_per_event("f64", x["n"], x["massive"]) * x["events"] for x in rows)
             achieved = instr / (fam_ms[dominant] / 1e3) / 1e12
             roof = {"bound": "alu", "kernel": "phsp_generate_kernel<N, df, EPT> (FP64 outputs, double-float "
                                               "arithmetic), N=2..10, 18 launches per step",
@@ -382,7 +391,7 @@ def run_ours(args) -> None:
                                     "achieved": round(f32_bytes / (f32_ms / 1e3) / 1e9, 1),
                                     "peak": peaks["hbm_gbs"], "unit": "GB/s", "peak_src": "MEASURED_PEAKS hbm_gbs (copy)",
                                     "frac": round(f32_bytes / (f32_ms / 1e3) / 1e9 / peaks["hbm_gbs"], 4),
-                                    "issue_frac": round(sum(INSTR_PER_EVENT[("f32", x["n"])] * x["events"] for x in f32)
+                                    "issue_frac": round(sum(instr_per_event("f32", x["n"], x["massive"]) * x["events"] for x in f32)
                                                         / (f32_ms / 1e3) / 1e12 / issue_peak, 4),
                                     "frac_of_write_peak": round(f32_bytes / (f32_ms / 1e3) / 1e9 / measured["hbm_write_gbs"], 4),
                                     "write_peak_gbs": measured["hbm_write_gbs"],
