@@ -53,6 +53,17 @@ INSTR_PER_EVENT = {
 }
 
 
+def fp_ops_per_event(n: int) -> int:
+    """Algorithmic floating-point operations of one Raubold-Lynch event (a multiply, add or
+    fused multiply-add counts 1; sqrt, reciprocal, division and a sin/cos pair count 1 each):
+    per boosted two-body step 51 -- the intermediate mass (2), gap (1), lambda's factors (8),
+    1/M and p (4), the weight factor (1), cos, 1 +- cos and sin theta (5), sin/cos phi (1), the
+    3-momentum (4), the energy (4), Q.p (5), the boosted energy (3), the boost factor (3),
+    the boosted 3-momentum (6) and the daughter by subtraction (4) -- and 34 for the parent's
+    own decay (no boost), plus the constant C_n."""
+    return 51 * (n - 2) + 34 + 1
+
+
 def instr_per_event(dtype: str, n: int, massive: bool) -> int:
     """Thread instructions per event of the generator kernel a launch runs."""
     return INSTR_PER_EVENT.get((dtype, n) if massive else (dtype, n, "massless"), INSTR_PER_EVENT[(dtype, n)])
@@ -366,6 +377,15 @@ def run_ours(args) -> None:
                     "work_src": "instructions per event from ncu (INSTR_PER_EVENT)",
                     "measured_issue_peak": round(measured["fp32_fma_per_s"] / 1e12, 2),
                     "frac_of_measured_issue_peak": round(achieved / (measured["fp32_fma_per_s"] / 1e12), 4),
+                    "algorithmic": {
+                        "fp64_ops_per_s": round(sum(fp_ops_per_event(x["n"]) * x["events"] for x in rows)
+                                                / (fam_ms[dominant] / 1e3) / 1e12, 3),
+                        "unit": "T FP64 operations/s (fp_ops_per_event: 51 per boosted two-body step)",
+                        "native_fp64_peak": round(measured["fp64_fma_per_s"] / 1e12, 3),
+                        "frac_of_native_fp64_peak": round(sum(fp_ops_per_event(x["n"]) * x["events"] for x in rows)
+                                                          / (fam_ms[dominant] / 1e3) / measured["fp64_fma_per_s"], 3),
+                        "note": "FP64-accurate arithmetic done on the FP32 pipes in double-float; the "
+                                "native FP64 pipe's peak is the ceiling a native FP64 kernel would have"},
                     "hbm_gbs": round(hbm, 1), "hbm_frac_of_measured": round(hbm / peaks["hbm_gbs"], 4),
                     "traffic": round((tot_bytes / len(rows) - 64e6) / 1e9, 3),
                     "traffic_note": "GB per launch: ncu dram read+write on 4e6-event launches is the algorithmic "
