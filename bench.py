@@ -42,26 +42,27 @@ INT_CFG = workloads.D0_DALITZ
 # command and table are in profiles/launches_instr_sweep_4e6.md).  They are the per-event
 # work of the issue-bound FP64 (double-float) generator, the dominant kernel of the step.
 INSTR_PER_EVENT = {
-    ("f32", 2): 91, ("f32", 3): 211, ("f32", 4): 296, ("f32", 5): 421, ("f32", 6): 539,
-    ("f32", 7): 700, ("f32", 8): 794, ("f32", 9): 924, ("f32", 10): 1044,
-    ("f64", 2): 476, ("f64", 3): 1129, ("f64", 4): 1714, ("f64", 5): 2298, ("f64", 6): 3000,
-    ("f64", 7): 3633, ("f64", 8): 4235, ("f64", 9): 4887, ("f64", 10): 5540,
+    ("f32", 2): 90, ("f32", 3): 199, ("f32", 4): 282, ("f32", 5): 400, ("f32", 6): 515,
+    ("f32", 7): 671, ("f32", 8): 762, ("f32", 9): 885, ("f32", 10): 999,
+    ("f64", 2): 374, ("f64", 3): 1014, ("f64", 4): 1575, ("f64", 5): 2142, ("f64", 6): 2827,
+    ("f64", 7): 3420, ("f64", 8): 4008, ("f64", 9): 4594, ("f64", 10): 5197,
     # the double-float variant for all-massless decays (no square root per two-body momentum)
-    ("f64", 2, "massless"): 419, ("f64", 3, "massless"): 1020, ("f64", 4, "massless"): 1554,
-    ("f64", 5, "massless"): 2088, ("f64", 6, "massless"): 2742, ("f64", 7, "massless"): 3318,
-    ("f64", 8, "massless"): 3849, ("f64", 9, "massless"): 4452, ("f64", 10, "massless"): 5032,
+    ("f64", 2, "massless"): 319, ("f64", 3, "massless"): 911, ("f64", 4, "massless"): 1441,
+    ("f64", 5, "massless"): 1951, ("f64", 6, "massless"): 2579, ("f64", 7, "massless"): 3128,
+    ("f64", 8, "massless"): 3637, ("f64", 9, "massless"): 4203, ("f64", 10, "massless"): 4773,
 }
 
 
 def fp_ops_per_event(n: int) -> int:
     """Algorithmic floating-point operations of one Raubold-Lynch event (a multiply, add or
     fused multiply-add counts 1; sqrt, reciprocal, division and a sin/cos pair count 1 each):
-    per boosted two-body step 51 -- the intermediate mass (2), gap (1), lambda's factors (8),
+    per boosted two-body step 48 -- the intermediate mass (2), gap (1), lambda's factors (8),
     1/M and p (4), the weight factor (1), cos, 1 +- cos and sin theta (5), sin/cos phi (1), the
-    3-momentum (4), the energy (4), Q.p (5), the boosted energy (3), the boost factor (3),
-    the boosted 3-momentum (6) and the daughter by subtraction (4) -- and 34 for the parent's
-    own decay (no boost), plus the constant C_n."""
-    return 51 * (n - 2) + 34 + 1
+    3-momentum (4), the energy M_k + Delta (Delta + 2 m) / (2 M_{k+1}) from a factor of lambda
+    (1), Q.p (5), the boosted energy (3), the boost factor (3), the boosted 3-momentum (6) and
+    the daughter by subtraction (4) -- and 31 for the parent's own decay (no boost), plus the
+    constant C_n."""
+    return 48 * (n - 2) + 31 + 1
 
 
 def instr_per_event(dtype: str, n: int, massive: bool) -> int:
@@ -380,7 +381,7 @@ def run_ours(args) -> None:
                     "algorithmic": {
                         "fp64_ops_per_s": round(sum(fp_ops_per_event(x["n"]) * x["events"] for x in rows)
                                                 / (fam_ms[dominant] / 1e3) / 1e12, 3),
-                        "unit": "T FP64 operations/s (fp_ops_per_event: 51 per boosted two-body step)",
+                        "unit": "T FP64 operations/s (fp_ops_per_event: 48 per boosted two-body step)",
                         "native_fp64_peak": round(measured["fp64_fma_per_s"] / 1e12, 3),
                         "frac_of_native_fp64_peak": round(sum(fp_ops_per_event(x["n"]) * x["events"] for x in rows)
                                                           / (fam_ms[dominant] / 1e3) / measured["fp64_fma_per_s"], 3),
@@ -579,8 +580,8 @@ def run_extras(nev: int = 100_000_000, reps: int = 3) -> dict:
 # ----------------------------------------------------------------------------- VEGAS
 # Thread instructions per point of the double-float VEGAS kernels (ncu smsp__inst_executed.sum
 # x 32 / points on 4e6-point iterations, 100 bins; profiles/vegas_eval_df_dalitz_4e6.md).
-VEGAS_INSTR_PER_POINT = {("dalitz", "eval"): 1331, ("dalitz", "hist"): 108,
-                         ("flat10", "eval"): 2482, ("flat10", "hist"): 457}
+VEGAS_INSTR_PER_POINT = {("dalitz", "eval"): 1283, ("dalitz", "hist"): 108,
+                         ("flat10", "eval"): 2479, ("flat10", "hist"): 457}
 
 
 def run_vegas(calls: int = 100_000_000, iterations: int = 10, reps: int = 3,

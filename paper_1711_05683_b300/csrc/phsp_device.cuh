@@ -226,6 +226,9 @@ template <> struct Prec<df> {
 // Delta_k = T (r_k - r_{k-1}) are formed from exact 32-bit integer differences.
 // p_k = sqrt(Delta (Delta + 2 M_k)(Delta + 2 m_{k+1})(Delta + 2 M_k + 2 m_{k+1})) / (2 M_{k+1})
 // (Kallen's lambda, factorised; no cancellation near threshold).  w = (prod p_k) C_n.
+// Subsystem k's energy in the rest frame of k+1 is M_k + Delta (Delta + 2 m_{k+1}) / (2 M_{k+1})
+// (the two-body energy (M_{k+1}^2 + M_k^2 - m_{k+1}^2) / (2 M_{k+1}) rewritten with the gap),
+// which reuses a factor of lambda instead of a square root of p^2 + M_k^2.
 //
 // Top-down: Q = lab 4-momentum of subsystem k+1 (daughters 1..k+1), Q = (M, 0) for k = n-1.
 // In its rest frame subsystem k moves along +p_k n and daughter k+1 along -p_k n.  The
@@ -324,14 +327,18 @@ __device__ __forceinline__ void raubold_lynch_group(const DecayConsts& C, const 
             // two-body momentum
             const R twoMk = P::scale(Mk, 2.0f);
             const R invM = P::rcp(Mnext[q]);
-            R p;
+            const R halfInvM = P::scale(invM, 0.5f);
+            R p, gm;  // gm = Delta (Delta + 2 m_{k+1})
             if constexpr (kMassless) {
                 // every daughter massless: lambda = (Delta (Delta + 2 M_k))^2, no square root
-                p = (gap * (gap + twoMk)) * P::scale(invM, 0.5f);
+                gm = gap * gap;
+                p = (gap * (gap + twoMk)) * halfInvM;
             } else {
                 const R twom = P::scale(P::m(C, k), 2.0f);
-                const R lam = ((gap * (gap + twoMk)) * (gap + twom)) * ((gap + twoMk) + twom);
-                p = P::sqrt_(lam) * P::scale(invM, 0.5f);
+                const R a = gap + twoMk;
+                gm = gap * (gap + twom);
+                const R lam = (gm * a) * (a + twom);
+                p = P::sqrt_(lam) * halfInvM;
             }
             w[q] = P::w_mul(w[q], p);
             // isotropic direction of subsystem k in the rest frame of subsystem k+1
@@ -348,7 +355,9 @@ __device__ __forceinline__ void raubold_lynch_group(const DecayConsts& C, const 
                 P::sincos_2pi_u(xp, &sphi, &cphi);  // phi = 2 pi u
             const R ps = p * sin_t;
             const R px = ps * cphi, py = ps * sphi, pz = p * cos_t;
-            const R Es = P::sqrt_(P::fma_(p, p, Mk * Mk));
+            // energy of subsystem k in the rest frame of k+1: (M_{k+1}^2 + M_k^2 - m_{k+1}^2) / (2 M_{k+1})
+            // = M_k + Delta (Delta + 2 m_{k+1}) / (2 M_{k+1}), a sum of positive terms
+            const R Es = P::fma_(gm, halfInvM, Mk);
             if (k == N - 1) {
                 // parent at rest: no boost
                 dE[q] = M - Es; dx[q] = -px; dy[q] = -py; dz[q] = -pz;

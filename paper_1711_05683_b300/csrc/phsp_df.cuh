@@ -133,19 +133,21 @@ __device__ __forceinline__ double f32_to_f64_bits(float f) {
     return __hiloint2double(static_cast<int>(hi), static_cast<int>(lo));
 }
 
-// The same rebias without the zero / subnormal case: exact for normal numbers; zero and FP32
-// subnormals map to a value below 2^-126 in magnitude.  Used for the low part of a
-// double-float, whose contribution below 2^-126 is far under the ulp of any result.
-__device__ __forceinline__ double f32_to_f64_bits_lo(float f) {
+// The same rebias without the zero / subnormal case: exact for normal numbers; a zero or an
+// FP32 subnormal maps to a value of magnitude in [2^-127, 2^-126) with its sign.
+__device__ __forceinline__ double f32_to_f64_bits_fast(float f) {
     const uint32_t b = __float_as_uint(f);
     const uint32_t hi = (((b & 0x7FFFFFFFu) >> 3) + 0x38000000u) | (b & 0x80000000u);
     return __hiloint2double(static_cast<int>(hi), static_cast<int>(b << 29));
 }
 
-// Nearest double to hi + lo (to within 2^-126 absolute when lo is zero or subnormal: an exact
-// zero is stored as 2^-127, far below any output's precision).
+// Nearest double to hi + lo for the stored kinematics, to within 2^-125 absolute: parts below
+// 2^-126 in magnitude (zero, FP32 subnormals) are not special-cased, so an exact double-float
+// zero is stored as 0 or +-2^-126.  Momenta and energies of a decay above threshold are never
+// below that scale (they carry a ~2^-46 relative error at the event scale), and the check
+// would cost three integer instructions per stored value.
 __device__ __forceinline__ double df_to_double(df x) {
-    return __dadd_rn(f32_to_f64_bits(x.hi), f32_to_f64_bits_lo(x.lo));
+    return __dadd_rn(f32_to_f64_bits_fast(x.hi), f32_to_f64_bits_fast(x.lo));
 }
 
 // Nearest double to hi + lo with zeros exact (for values whose zero has a meaning).

@@ -127,9 +127,12 @@ __device__ __forceinline__ double vegas_event(const DecayConsts& C, const uint64
         else gap = A::frac(y[k - 1] - y[k - 2]) * T;
         const R mk1 = P::m(C, k);
         const R twoMk = P::scale(Mk, 2.0f), twom = P::scale(mk1, 2.0f);
-        const R lam = ((gap * (gap + twoMk)) * (gap + twom)) * ((gap + twoMk) + twom);
+        const R a = gap + twoMk;
+        const R gm = gap * (gap + twom);  // Delta (Delta + 2 m_{k+1})
+        const R lam = (gm * a) * (a + twom);
         const R invM = P::rcp(Mnext);
-        const R p = P::sqrt_(lam) * P::scale(invM, 0.5f);
+        const R halfInvM = P::scale(invM, 0.5f);
+        const R p = P::sqrt_(lam) * halfInvM;
         w = P::w_mul(w, p);
         const uint64_t uc = U[N - 2 + 2 * j], up = U[N - 1 + 2 * j];
         const R one_p = P::scale(A::frac(uc), 2.0f);  // 1 + cos(theta) = 2u
@@ -140,7 +143,7 @@ __device__ __forceinline__ double vegas_event(const DecayConsts& C, const uint64
         A::sincos(up, &sphi, &cphi);
         const R ps = p * sin_t;
         const R px = ps * cphi, py = ps * sphi, pz = p * cos_t;
-        const R Es = P::sqrt_(P::fma_(p, p, Mk * Mk));
+        const R Es = P::fma_(gm, halfInvM, Mk);  // (M_{k+1}^2 + M_k^2 - m_{k+1}^2) / (2 M_{k+1})
         if (k == N - 1) {
             Q0 = Es; Qx = px; Qy = py; Qz = pz;
         } else {

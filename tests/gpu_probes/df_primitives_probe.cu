@@ -50,6 +50,15 @@ __global__ void k_weight(const float* p, int m, double c, double* out) {
     out[0] = df_weight_final(w, c);
 }
 
+// df (p[2i], p[2i+1]) to double: out[2i] the stored-kinematics conversion, out[2i+1] the exact one
+__global__ void k_to_double(const float* p, int n, double* out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const df v{p[2 * i], p[2 * i + 1]};
+    out[2 * i] = df_to_double(v);
+    out[2 * i + 1] = df_to_double_exact(v);
+}
+
 int finish(const double* dev_out, double* host_out, size_t out_bytes) {
     if (cudaDeviceSynchronize() != cudaSuccess) return 1;
     if (cudaMemcpy(host_out, dev_out, out_bytes, cudaMemcpyDeviceToHost) != cudaSuccess) return 2;
@@ -111,6 +120,20 @@ int probe_df_weight(const float* p, int m, double c, double* out) {
     cudaMemcpy(dp, p, 2 * m * sizeof(float), cudaMemcpyHostToDevice);
     k_weight<<<1, 32>>>(dp, m, c, dout);
     const int rc = finish(dout, out, sizeof(double));
+    cudaFree(dp);
+    cudaFree(dout);
+    return rc;
+}
+
+// out[2i], out[2i+1] = df_to_double, df_to_double_exact of the pair (p[2i], p[2i+1])
+int probe_df_to_double(const float* p, int n, double* out) {
+    float* dp = nullptr;
+    double* dout = nullptr;
+    if (cudaMalloc(&dp, 2 * n * sizeof(float)) != cudaSuccess) return 1;
+    if (cudaMalloc(&dout, 2 * n * sizeof(double)) != cudaSuccess) return 1;
+    cudaMemcpy(dp, p, 2 * n * sizeof(float), cudaMemcpyHostToDevice);
+    k_to_double<<<(n + 127) / 128, 128>>>(dp, n, dout);
+    const int rc = finish(dout, out, 2 * n * sizeof(double));
     cudaFree(dp);
     cudaFree(dout);
     return rc;

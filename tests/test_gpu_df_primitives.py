@@ -3,8 +3,10 @@ test probe on the GPU and compared with exact values: the integer-to-double-floa
 exactly (edge inputs 0, 255, 256, 2^31 - 1, 2^31, 2^32 - 1 and random ones), sin/cos of
 2 pi (x + 1/2) 2^-32 to 4e-14 absolute (double-float precision, ~2^-46, the product and sum
 of the angle-addition step) against 30-digit values (table edges, octant and quadrant
-boundaries), v 2^-64 to 2^-46 relative, and the weight product (mantissa and binary exponent)
-to 1e-14 relative, including factors at the FP32 range limits, a subnormal one and zero."""
+boundaries), v 2^-64 to 2^-46 relative, the weight product (mantissa and binary exponent)
+to 1e-14 relative, including factors at the FP32 range limits, a subnormal one and zero, and
+the double-float to double conversions (the nearest double for normal parts; zeros exact in
+the weight's conversion, within 2^-125 in the stored kinematics')."""
 import ctypes
 import os
 import subprocess
@@ -120,3 +122,38 @@ def test_weight_product(probe, factors):
         assert out[0] == 0.0
     else:
         assert abs(Fraction(out[0]) - exact) <= abs(exact) * Fraction(1, 10 ** 14)
+
+
+
+def _normal_or_zero(v: float) -> bool:
+    return v == 0.0 or abs(v) >= 2.0 ** -126
+
+
+def test_double_float_to_double(probe):
+    rng = np.random.default_rng(29)
+    pairs = [_df_split(float(v)) for v in rng.standard_normal(3000) * 10.0 ** rng.integers(-30, 30, size=3000)]
+    # low parts at the edge of the pair's range, exact halfway cases of the FP64 rounding, and
+    # powers of two with a negative low part (the sum drops below the binade of hi)
+    for hi in (1.0, -3.0, 2.0 ** 100, 0.75, 5.9e-36):
+        u = float(np.spacing(np.float32(hi)))
+        pairs += [(hi, u / 2), (hi, -u / 2), (hi, u / 4), (hi, -u / 4), (hi, u * 2.0 ** -29), (hi, -u * 2.0 ** -30)]
+    zeros = [(0.0, 0.0), (-0.0, 0.0), (0.0, -0.0), (-0.0, -0.0), (1.0e-39, 0.0)]
+    pairs += zeros + [(3.0, 0.0), (-7.5, -0.0)]
+    pairs = [(float(np.float32(h)), float(np.float32(l))) for h, l in pairs]
+    p = (ctypes.c_float * (2 * len(pairs)))(*[v for pr in pairs for v in pr])
+    out = (ctypes.c_double * (2 * len(pairs)))()
+    assert probe.probe_df_to_double(p, len(pairs), out) == 0
+    for i, (hi, lo) in enumerate(pairs):
+        exact = Fraction(hi) + Fraction(lo)
+        fast, exact_conv = out[2 * i], out[2 * i + 1]
+        bound = Fraction(2.0 ** -125) + abs(exact) * Fraction(1, 1 << 53)
+        if _normal_or_zero(hi) and _normal_or_zero(lo):
+            assert exact_conv == float(exact), (hi, lo)  # float(Fraction) is the nearest double
+        else:
+            assert abs(Fraction(exact_conv) - exact) <= bound, (hi, lo)  # FP32 subnormal parts flush
+        if hi != 0.0 and lo != 0.0 and _normal_or_zero(hi) and _normal_or_zero(lo):
+            assert fast == float(exact), (hi, lo)
+        else:
+            assert abs(Fraction(fast) - exact) <= bound, (hi, lo, fast)  # zero / subnormal parts
+    for i in range(len(pairs) - len(zeros) - 2, len(pairs) - 2):
+        assert out[2 * i + 1] == 0.0  # the weight's conversion keeps a zero exact
