@@ -12,9 +12,13 @@ replayed CUDA graph):
     counter, kept on the host as an integer) and its compensated segment partial sums
     (a caller-owned device array the batch kernels update in place).  A long integral
     therefore shares the GPU with requests that arrive while it runs.
-Two batch runners alternate so that tick i+1 is packed and enqueued while tick i runs.  A
-request completes when the host observes the event recorded after its last slice (and, for
-generation, after its copy to host memory); latency = completion time - arrival time.
+Two batch runners alternate so that tick i+1 is packed and enqueued while tick i runs.  The
+copies of finished generate outputs to pinned host memory go on a stream of their own, which
+waits for the tick's kernels: the next ticks compute while earlier outputs cross the host link,
+and requests that copy nothing (integrals) do not queue behind other requests' copies.  An
+integrate request completes when the host observes the event recorded after its last slice; a
+generate request when it observes the event recorded after its copy; latency = completion
+time - arrival time.
 
 The HBM budget is reserved when the server starts, as two device rings (staging outputs, and
 integral partials in a small ring of their own); requests take blocks of them and return them
@@ -146,6 +150,7 @@ class Server:
         self.use_graph = use_graph
         self.max_tick_events = max_tick_events
         self.stream = torch.cuda.current_stream()
+        self.copy_stream = torch.cuda.Stream()  # device-to-host copies of finished generate outputs
 
     # ------------------------------------------------------------------ state per request
     def _fits_ever(self, a: _Active) -> bool:
@@ -235,11 +240,21 @@ class Server:
         pending = deque(enumerate(requests))
         queue: deque[_Active] = deque()
         active: list[_Active] = []
-        inflight: deque = deque()  # (tick, event, runner index, [(slot, active)], [done actives])
+        inflight: deque = deque()  # (tick, event, runner index, [(slot, active)], [finished integrals])
+        copying: deque = deque()   # (copy-stream event, [finished generate requests])
         latencies, kinds, done = {}, {}, []
         tick = 0
         events_done = 0
-        while pending or queue or active or inflight:
+
+        def complete(a: _Active, tnow: float):
+            nonlocal events_done
+            a.latency = latencies[a.rid] = tnow - a.arrival
+            kinds[a.rid] = a.req.kind
+            events_done += a.req.nevents
+            done.append(a)
+            self._release(a)
+
+        while pending or queue or active or inflight or copying:
             now = time.perf_counter()
             if max_wall is not None and now - t0 > max_wall:
                 break
@@ -251,26 +266,29 @@ class Server:
                     refused.append(queue.popleft().rid)
                     continue
                 if not self._admit(queue[0]):
-                    if not active and not inflight:
+                    if not active and not inflight and not copying:
                         # nothing will release memory (kept outputs fill the pinned ring): refuse
                         refused.append(queue.popleft().rid)
                         continue
                     break
                 active.append(queue.popleft())
-            # harvest finished ticks (oldest first)
+            # harvest finished ticks (oldest first): integrals complete with their last slice
             while inflight and (len(inflight) >= 2 or inflight[0][1].query()):
                 t_i, ev, ri, slots, finishing = inflight.popleft()
                 ev.synchronize()
                 tnow = time.perf_counter()
+                ending = {id(a) for a in finishing}
                 for slot, a in slots:
-                    if a.req.kind == "integrate" and a in finishing:
+                    if id(a) in ending:
                         a.result = self.runners[ri].result(slot)
                 for a in finishing:
-                    a.latency = latencies[a.rid] = tnow - a.arrival
-                    kinds[a.rid] = a.req.kind
-                    events_done += a.req.nevents
-                    done.append(a)
-                    self._release(a)
+                    complete(a, tnow)
+            # generate requests complete when their copy to host memory has landed
+            while copying and copying[0][0].query():
+                _evc, copied = copying.popleft()
+                tnow = time.perf_counter()
+                for a in copied:
+                    complete(a, tnow)
             if cancel_after:
                 keep = []
                 for a in active:
@@ -303,20 +321,26 @@ class Server:
                     if a.next_first >= a.req.nevents:
                         finishing.append(a)
                 self.runners[ri].run(self.table, len(slots), use_graph=self.use_graph, stream=self.stream)
-                for a in finishing:
-                    if a.req.kind == "generate":
-                        a.host_out.copy_(a.dev_out, non_blocking=True)
-                        a.host_w.copy_(a.dev_w, non_blocking=True)
                 ev = torch.cuda.Event()
                 ev.record(self.stream)
-                inflight.append((tick, ev, ri, slots, finishing))
+                copied = [a for a in finishing if a.req.kind == "generate"]
+                if copied:
+                    self.copy_stream.wait_event(ev)
+                    with torch.cuda.stream(self.copy_stream):
+                        for a in copied:
+                            a.host_out.copy_(a.dev_out, non_blocking=True)
+                            a.host_w.copy_(a.dev_w, non_blocking=True)
+                    evc = torch.cuda.Event()
+                    evc.record(self.copy_stream)
+                    copying.append((evc, copied))
+                inflight.append((tick, ev, ri, slots, [a for a in finishing if a.req.kind == "integrate"]))
                 active = [a for a in active if a.next_first < a.req.nevents]
                 tick += 1
             elif not inflight and not active and not queue and pending:
                 wait = t0 + pending[0][1].arrival * time_scale - time.perf_counter()
                 if wait > 0:
                     time.sleep(min(wait, 2e-4))
-            elif inflight and not inflight[0][1].query():
+            elif (inflight and not inflight[0][1].query()) or (copying and not copying[0][0].query()):
                 time.sleep(2e-5)
         wall = time.perf_counter() - t0
         out = _summary(latencies, events_done, wall, ticks=tick, done=done, kinds=kinds)

@@ -82,7 +82,9 @@ def test_cancelled_request_leaves_the_others_intact():
 def test_tight_budget_waits_for_space_and_refuses_what_never_fits():
     """Admission by budget: with a 96 MB budget the requests are admitted as earlier ones free
     their blocks, every result still equals the single-request one, and a request larger than
-    the whole budget is refused instead of blocking the queue."""
+    the whole budget is refused instead of blocking the queue.  The device ring wraps several
+    times while outputs are still being copied to the host on the copy stream, so a block
+    handed out again before its copy had landed would show in the outputs."""
     from paper_1711_05683_b300 import serve
     reqs = workloads.serve_stream(rate_hz=4000, duration_s=0.05, gen_log_events=(5.0, 5.6),
                                   int_log_events=(4.0, 5.0), rng_seed=21)
@@ -95,6 +97,7 @@ def test_tight_budget_waits_for_space_and_refuses_what_never_fits():
     srv = serve.Server(max_slices=64, int_slice_segments=1, pinned_bytes=4 << 30, keep_outputs=True,
                        budget_bytes=96 * 10 ** 6)
     assert srv.dev_ring.size < gen_bytes < srv.ring.size  # the device budget is the tight one
+    srv_dev_ring_size = srv.dev_ring.size
     res = srv.run(reqs, max_wall=60.0)
     srv.close()
     assert res["refused"] == [big_rid]
@@ -103,10 +106,13 @@ def test_tight_budget_waits_for_space_and_refuses_what_never_fits():
         r = a.req
         if r.kind == "generate":
             p, w = hp.generate(r.M, r.masses, r.nevents, r.seed, dtype="f32")
+            torch.cuda.synchronize()
+            assert torch.equal(a.host_out[:, :, : r.nevents], p[:, :, : r.nevents].cpu())
             assert torch.equal(a.host_w[: r.nevents], w.cpu())
         else:
             assert a.result == hp.integrate(r.M, r.masses, r.nevents, r.seed, kin_dtype="f32", me=r.me,
                                             params=r.params)
+    assert gen_bytes > 3 * srv_dev_ring_size
 
 
 def test_kept_outputs_filling_the_pinned_ring_are_refused_not_waited_for():
