@@ -352,7 +352,9 @@ hydra_status hydra_batch_create(int max_requests, uint64_t max_integrate_tiles, 
 /*
  * Enqueue one run of nreq slices on `stream` (asynchronous): one host-to-device copy of
  * the slice table, one graph launch (use_graph != 0) or the same kernels launched one by
- * one, and one device-to-host copy of the results of the integral slices.  A run may be
+ * one, and one device-to-host copy of the results of the integral slices.  The tiles are
+ * handed out grouped by kind, matrix element and n (stable within a group); every event
+ * depends only on its request and counter, so results do not depend on the table order.  A run may be
  * issued while the previous run of the same batch is still executing; the call waits for
  * that run's slice table to be consumed before reusing its staging memory.
  * Errors: INVALID_ARG (validation of every slice, capacity), UNSUPPORTED_N,

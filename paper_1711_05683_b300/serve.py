@@ -71,11 +71,9 @@ class _Active:
     arrival: float                  # absolute wall time
     next_first: int = 0             # next event index (the request's RNG counter)
     nbytes: int = 0
-    dev_out: object = None          # generate: device staging [n, 4, ld]
-    dev_w: object = None
-    host_out: object = None         # generate: pinned host copy
-    host_w: object = None
-    seg: object = None              # integrate: device segment partials
+    ld: int = 0                     # generate: row stride of the [n, 4, ld] outputs
+    host_out: object = None         # generate, kept outputs: pinned host copy [n, 4, ld]
+    host_w: object = None           #   and its weights
     result: dict | None = None
     done_tick: int = -1
     ring_start: int = -1            # block of the pinned host ring (generate)
@@ -146,6 +144,7 @@ class Server:
         # split the large one) integral partials; together they are the HBM budget
         self.seg_ring = DeviceRing(min(256 << 20, budget_bytes // 16))
         self.dev_ring = DeviceRing(budget_bytes - self.seg_ring.size)
+        self.dev_base, self.seg_base = self.dev_ring.buf.data_ptr(), self.seg_ring.buf.data_ptr()
         self.keep_outputs = keep_outputs
         self.use_graph = use_graph
         self.max_tick_events = max_tick_events
@@ -162,12 +161,12 @@ class Server:
         return 64 * hp.segments(r.nevents) <= self.seg_ring.size
 
     def _admit(self, a: _Active) -> bool:
-        torch = self.torch
+        """Reserve the request's ring blocks (integer offsets only: admission runs for every
+        request inside the loop, so it creates no tensors) and build its record."""
         r = a.req
-        n = len(r.masses)
         if r.kind == "generate":
             ld = hp.padded_ld(r.nevents)
-            nbytes = (4 * n + 1) * ld * 4
+            nbytes = (4 * len(r.masses) + 1) * ld * 4
             dev = self.dev_ring.alloc(nbytes)
             if dev is None:
                 return False
@@ -175,36 +174,37 @@ class Server:
             if host is None:
                 self.dev_ring.free(dev)
                 return False
-            a.ring_start, a.dev_start = host, dev
-            hb = self.ring.view(host, nbytes, torch.float32)
-            a.host_out = hb[: 4 * n * ld].view(n, 4, ld)
-            a.host_w = hb[4 * n * ld:]
-            db = self.dev_ring.view(dev, nbytes, torch.float32)
-            a.dev_out = db[: 4 * n * ld].view(n, 4, ld)
-            a.dev_w = db[4 * n * ld:]
+            a.ring_start, a.dev_start, a.ld = host, dev, ld
         else:
             nbytes = 64 * hp.segments(r.nevents)
             dev = self.seg_ring.alloc(nbytes)
             if dev is None:
                 return False
             a.dev_start = dev
-            a.seg = self.seg_ring.view(dev, nbytes, torch.float64)
         a.nbytes = nbytes
         self.used += nbytes
         a.rec = np.zeros(1, dtype=self.table.dtype)[0]
         self._fill(a.rec, a)
         return True
 
+    def _copy_to_host(self, a: _Active):
+        """One copy of the request's whole block ([n, 4, ld] outputs then weights, the same
+        layout on both sides) from the device ring to the pinned ring, on the current stream."""
+        self.ring.buf[a.ring_start: a.ring_start + a.nbytes].copy_(
+            self.dev_ring.buf[a.dev_start: a.dev_start + a.nbytes], non_blocking=True)
+
     def _release(self, a: _Active):
         self.used -= a.nbytes
-        (self.dev_ring if a.req.kind == "generate" else self.seg_ring).free(a.dev_start)
         if a.req.kind == "generate":
-            if not self.keep_outputs:
+            self.dev_ring.free(a.dev_start)
+            if self.keep_outputs:
+                n, ld = len(a.req.masses), a.ld
+                hb = self.ring.view(a.ring_start, a.nbytes, self.torch.float32)
+                a.host_out, a.host_w = hb[: 4 * n * ld].view(n, 4, ld), hb[4 * n * ld:]
+            else:
                 self.ring.free(a.ring_start)
-                a.host_out = a.host_w = None
-            a.dev_out = a.dev_w = None
         else:
-            a.seg = None
+            self.seg_ring.free(a.dev_start)
 
     def _fill(self, rec, a: _Active):
         """The request's static fields (the slice start and count are set per tick)."""
@@ -214,12 +214,13 @@ class Server:
         rec["masses"][:n] = r.masses
         rec["seed"], rec["event_offset"] = r.seed, 0
         if r.kind == "generate":
+            out = self.dev_base + a.dev_start
             rec["kind"] = hp.REQ_GENERATE
-            rec["out"], rec["ld"], rec["weights"] = a.dev_out.data_ptr(), a.dev_out.shape[-1], a.dev_w.data_ptr()
+            rec["out"], rec["ld"], rec["weights"] = out, a.ld, out + 4 * n * a.ld * 4
         else:
             rec["kind"], rec["me"] = hp.REQ_INTEGRATE, r.me
             rec["params"][: len(r.params)] = r.params
-            rec["total"], rec["seg_partials"] = r.nevents, a.seg.data_ptr()
+            rec["total"], rec["seg_partials"] = r.nevents, self.seg_base + a.dev_start
 
     # ------------------------------------------------------------------ the loop
     def run(self, requests, time_scale: float = 1.0, max_wall: float | None = None,
@@ -328,8 +329,7 @@ class Server:
                     self.copy_stream.wait_event(ev)
                     with torch.cuda.stream(self.copy_stream):
                         for a in copied:
-                            a.host_out.copy_(a.dev_out, non_blocking=True)
-                            a.host_w.copy_(a.dev_w, non_blocking=True)
+                            self._copy_to_host(a)
                     evc = torch.cuda.Event()
                     evc.record(self.copy_stream)
                     copying.append((evc, copied))

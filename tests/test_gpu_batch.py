@@ -55,14 +55,17 @@ def int_record(rec, M, masses, total, seed, dtype, me, params, seg, first, count
 
 
 @pytest.mark.parametrize("dtype", ["f32", "f64"])
-@pytest.mark.parametrize("use_graph", [True, False])
-def test_batch_generate_matches_single_calls(dtype, use_graph):
+@pytest.mark.parametrize("use_graph,reverse", [(True, False), (False, False), (True, True)])
+def test_batch_generate_matches_single_calls(dtype, use_graph, reverse):
+    """Mixed N (the run hands out tiles grouped by N, in a different order from the table's),
+    ragged counts and tails of every events-per-thread group; the table also in reverse."""
     rng = np.random.default_rng(7)
     tdt = torch.float32 if dtype == "f32" else torch.float64
-    counts = [1, 3, 5, 2047, 2048, 2049, 10_001, 77_777, 300_000, 4, 123_457]
+    counts = [1, 3, 5, 2047, 2048, 2049, 10_001, 77_777, 300_000, 4, 123_457, 6, 7, 130, 2050]
     table = np.zeros(len(counts), dtype=hp.request_dtype())
     outs = []
-    for i, c in enumerate(counts):
+    slots = list(range(len(counts)))[::-1] if reverse else list(range(len(counts)))
+    for i, c in zip(slots, counts):
         n = int(rng.integers(2, 11))
         M, masses = workloads.random_decay(rng, n)
         ld = hp.padded_ld(c)
