@@ -11,8 +11,8 @@
 //               d/4, i + 1); bin and position from exact integers (below); the event's
 //               weight and |ME|^2; f = F(u) J and the point's D bins (one byte each, four
 //               to a word: word q of point s at [q][calls]) stored;
-//               the deterministic tile sums of f and f^2 (the integral's tile / segment
-//               order); the largest f^2.
+//               the deterministic tile sums of f and f^2 (the integral's group / tile /
+//               segment tree, with tiles of 512 points); the largest f^2.
 //   vegas_hist  per-bin sums of f^2 in 64-bit fixed point (order-independent integer adds)
 //               from the stored values and bins.
 //   host        estimate and variance; refinement of every dimension.
@@ -48,7 +48,16 @@ __global__ void eval_finalize(const double* __restrict__ seg, uint64_t nseg, uin
 constexpr int kVegasMaxCells = 6144;  // D * K bins (D * (K + 1) cells of 16 B in shared memory)
 constexpr int kVegasMaxD = 3 * kNMax - 4;
 constexpr int kVegasBlock = 256;
-constexpr int kVegasMaxChunks = 1 << 11;  // 2^36 points / (kChunkTiles tiles of 2048), as 64-bit words
+// A VEGAS tile is 512 points (16 per lane, two groups of 8): a quarter of the integral's tile,
+// because a VEGAS point over the 3n - 4 variables costs up to ~2500 instructions (n = 10) and
+// an iteration of 1e7 points must still spread over every resident warp several times (with
+// 2048-point tiles it was 1.4 waves of warps, run as two rounds).
+constexpr int kVegasTileEvents = 512;
+constexpr int kVegasLaneIters = kVegasTileEvents / 32;
+static_assert(kVegasLaneIters % kGroupEvents == 0, "groups tile the lane's points");
+constexpr uint64_t kVegasChunkTiles = kChunkTiles * (kTileEvents / kVegasTileEvents);  // 2^26 points per launch
+static_assert(kVegasChunkTiles % kSegTiles == 0, "a chunk holds whole segments");
+constexpr int kVegasMaxChunks = static_cast<int>((1ull << 36) / (kVegasChunkTiles * kVegasTileEvents));  // tile counters
 
 struct VegasCell {
     uint64_t G;  // left edge g_b 2^64 (the cell after the last bin holds 2^64 - 1)
@@ -221,9 +230,9 @@ __global__ void __launch_bounds__(kVegasBlock) vegas_eval(const __grid_constant_
         if (lane == 0) tn = atomicAdd(next_tile, 1u);
         const uint64_t t = __shfl_sync(0xffffffffu, tn, 0);
         if (t >= ntiles) break;
-        const uint64_t base = (tile_begin + t) * kTileEvents;
+        const uint64_t base = (tile_begin + t) * kVegasTileEvents;
         double af = 0.0, af2 = 0.0;
-        for (int g = 0; g < kLaneIters / kGroupEvents; ++g) {
+        for (int g = 0; g < kVegasLaneIters / kGroupEvents; ++g) {
             double sf = 0.0, sf2 = 0.0;
             for (int i = 0; i < kGroupEvents; ++i) {
                 const uint64_t s = base + static_cast<uint64_t>(32 * (g * kGroupEvents + i) + lane);
@@ -486,12 +495,12 @@ hydra_status hydra_phsp_vegas(double M, int n, const double* masses, uint64_t se
     VegasScratch* s = vegas_scratch();
     if (!s) return fail(HYDRA_ERR_CUDA, "no current CUDA device");
     std::lock_guard<std::mutex> lk(s->mu);
-    const uint64_t ntiles = (calls + kTileEvents - 1) / kTileEvents;
+    const uint64_t ntiles = (calls + kVegasTileEvents - 1) / kVegasTileEvents;
     const uint64_t nseg = (ntiles + kSegTiles - 1) / kSegTiles;
     const size_t hist_words = static_cast<size_t>(kVegasMaxCells) + 1 + kVegasMaxChunks;
     const size_t cell_bytes = static_cast<size_t>(kVegasMaxCells + kVegasMaxD) * sizeof(VegasCell);
     if (!s->tiles) {
-        if (cudaMalloc(&s->tiles, kChunkTiles * sizeof(TileSums)) != cudaSuccess ||
+        if (cudaMalloc(&s->tiles, kVegasChunkTiles * sizeof(TileSums)) != cudaSuccess ||
             cudaMalloc(&s->cells, cell_bytes) != cudaSuccess ||
             cudaMalloc(&s->hist, hist_words * sizeof(unsigned long long)) != cudaSuccess ||
             cudaMalloc(&s->d_res, sizeof(hydra_integral)) != cudaSuccess ||
@@ -557,8 +566,8 @@ hydra_status hydra_phsp_vegas(double M, int n, const double* masses, uint64_t se
         err = cudaMemcpyAsync(s->cells, h_cells, smem, cudaMemcpyHostToDevice, cs);
         if (err == cudaSuccess) err = cudaMemsetAsync(s->hist, 0, hist_words * sizeof(unsigned long long), cs);
         if (err != cudaSuccess) return cuda_fail(err, "VEGAS grid upload");
-        for (uint64_t t0 = 0; t0 < ntiles; t0 += kChunkTiles) {
-            const uint64_t nt = ntiles - t0 < kChunkTiles ? ntiles - t0 : kChunkTiles;
+        for (uint64_t t0 = 0; t0 < ntiles; t0 += kVegasChunkTiles) {
+            const uint64_t nt = ntiles - t0 < kVegasChunkTiles ? ntiles - t0 : kVegasChunkTiles;
             const uint64_t need = (nt * 32 + kVegasBlock - 1) / kVegasBlock;
             const uint64_t cap = static_cast<uint64_t>(sms) * per_sm;  // one persistent wave
             const unsigned grid = static_cast<unsigned>(need < cap ? need : cap);
@@ -570,7 +579,7 @@ hydra_status hydra_phsp_vegas(double M, int n, const double* masses, uint64_t se
             double* fv = s->fvals;
             uint32_t* bp = s->bins;
             unsigned long long* mp = d_max;
-            unsigned int* ctr = reinterpret_cast<unsigned int*>(d_max + 1 + t0 / kChunkTiles);
+            unsigned int* ctr = reinterpret_cast<unsigned int*>(d_max + 1 + t0 / kVegasChunkTiles);
             void* args[] = {&C, &PM, &gp, &Kv, &sid, &cl, &tb, &ntv, &tp, &fv, &bp, &mp, &ctr};
             err = cudaLaunchKernel(kern, dim3(grid), dim3(kVegasBlock), args, smem, cs);
             if (err != cudaSuccess) return cuda_fail(err, "VEGAS evaluation launch");

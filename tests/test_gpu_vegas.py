@@ -96,7 +96,8 @@ def test_vegas_is_deterministic(arith):
 
 
 def test_vegas_large_sample_against_quadrature(arith):
-    """2^24 + 3 points per iteration (8193 warp tiles, 9 segments): the first iteration equals
+    """2^24 + 3 points per iteration (32769 warp tiles of 512 points, 33 segments, a ragged
+    last tile): the first iteration equals
     the oracle's on the same draws; the combined result matches quadrature of the Dalitz
     integral within 5 sigma and the narrow peak's per-iteration error drops by 10x."""
     calls = (1 << 24) + 3
