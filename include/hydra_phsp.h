@@ -196,7 +196,8 @@ hydra_status hydra_phsp_evaluate(int n, uint64_t nevents, hydra_dtype dtype, hyd
  * (x + 1/2) 2^-32 from Philox word d%4 of counter (s low, s high, d/4, i + 1) with key
  * `seed`; bin b = floor(y_d K); u_d = g_d[b] + (y_d K - b)(g_d[b+1] - g_d[b]); f = F(u) J with
  * J = prod_d K (g_d[b+1] - g_d[b]).  Estimate = mean of f, variance (<f^2> - <f>^2)/(calls-1)
- * (both reduced in the deterministic tile / segment order of hydra_phsp_integrate).  Each bin
+ * (both reduced in the deterministic group / tile / segment tree of hydra_phsp_integrate, with
+ * tiles of 512 points).  Each bin
  * collects sum f^2 (64-bit fixed point relative to the iteration's largest f^2, so the
  * histogram is order independent); refinement smooths it (1,2,1)/4 inside and (1,1)/2 at the
  * ends, weights each bin ((r - 1)/ln r)^alpha with r its share, and places the new edges at
