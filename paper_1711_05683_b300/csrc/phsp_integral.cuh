@@ -262,18 +262,14 @@ __device__ __forceinline__ void segment_sums_block(const TileSums* __restrict__ 
         part[v][4] = w.s; part[v][5] = w.c; part[v][6] = w2.s; part[v][7] = w2.c;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        Comp q[4];
-        for (int k = 0; k < 4; ++k) {
-            q[k].s = part[0][2 * k];
-            q[k].c = part[0][2 * k + 1];
-        }
-        for (int u = 1; u < kSegWarps; ++u)
-            for (int k = 0; k < 4; ++k) q[k].merge(part[u][2 * k], part[u][2 * k + 1]);
-        for (int k = 0; k < 4; ++k) {
-            out[2 * k] = q[k].s;
-            out[2 * k + 1] = q[k].c;
-        }
+    if (threadIdx.x < 4) {  // lane k merges quantity k over the warps in order (FP64 pipe: 4 lanes, one pass)
+        const int k = threadIdx.x;
+        Comp q;
+        q.s = part[0][2 * k];
+        q.c = part[0][2 * k + 1];
+        for (int u = 1; u < kSegWarps; ++u) q.merge(part[u][2 * k], part[u][2 * k + 1]);
+        out[2 * k] = q.s;
+        out[2 * k + 1] = q.c;
     }
     __syncthreads();  // part is reused by the block's next segment
 }

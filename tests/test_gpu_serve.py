@@ -55,12 +55,14 @@ def test_plain_server_matches_too():
 
 def test_cancelled_request_leaves_the_others_intact():
     """Host-side fault injection: a client withdraws a long integral mid-flight; the server
-    drops it between ticks and every other request still gets its single-request result."""
+    drops it between ticks and every other request still gets its single-request result.  The
+    integral is 1000 ticks of 2^21 events (tens of ms of GPU work), so it is still running when
+    the client withdraws it 5 ms into the run on any GPU."""
     from paper_1711_05683_b300 import serve
     d = workloads.D0_DALITZ
     reqs = workloads.serve_stream(rate_hz=1000, duration_s=0.05, gen_log_events=(2.0, 4.0),
                                   int_log_events=(4.0, 5.0), rng_seed=11)
-    big = workloads.Request("integrate", d["M"], d["masses"], 60 * 2 ** 21, 123, me=1,
+    big = workloads.Request("integrate", d["M"], d["masses"], 1000 * 2 ** 21, 123, me=1,
                             params=d["params"], arrival=0.0)
     reqs = [big] + list(reqs)
     srv = serve.Server(max_slices=256, int_slice_segments=1, pinned_bytes=1 << 28, keep_outputs=True)
@@ -68,6 +70,7 @@ def test_cancelled_request_leaves_the_others_intact():
     srv.close()
     assert res["cancelled"] == [0]
     assert res["completed"] == len(reqs) - 1
+    assert res["ticks"] < 1000  # withdrawn before its last slice
     for a in res["done"]:
         r = a.req
         assert a.rid != 0
