@@ -363,6 +363,133 @@ __global__ void __launch_bounds__(256) evaluate_tiles(uint64_t nevents, const R*
     }
 }
 
+// The same with 16-byte loads: lane l takes the runs of W = 16 / sizeof(R) consecutive events
+// starting at base + 256 g + 32 W j + W l (j < 8 / W) of each group g of 256 events, so that a
+// warp reads whole lines of every component with a quarter (FP32) or half (FP64) of the load
+// instructions and several vectors in flight.  A lane still sums 8 events per group in R and
+// the groups in FP64, in a fixed order (the event-to-lane assignment differs from
+// evaluate_tiles, so the sums agree to rounding).  Needs 16-byte aligned events, weights and
+// values and ld % W == 0; a run that crosses nevents is taken element by element.
+template <typename R>
+struct Vec16;
+template <>
+struct Vec16<float> {
+    using T = float4;
+    static constexpr int W = 4;
+    __device__ static void get(const float* p, float (&v)[4]) {
+        const float4 x = *reinterpret_cast<const float4*>(p);
+        v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+    }
+    __device__ static void put(float* p, const float (&v)[4]) {
+        *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    }
+};
+template <>
+struct Vec16<double> {
+    using T = double2;
+    static constexpr int W = 2;
+    __device__ static void get(const double* p, double (&v)[2]) {
+        const double2 x = *reinterpret_cast<const double2*>(p);
+        v[0] = x.x; v[1] = x.y;
+    }
+    __device__ static void put(double* p, const double (&v)[2]) {
+        *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+    }
+};
+
+template <typename R, int ME>
+__device__ __forceinline__ R eval_event(const R* __restrict__ ev, uint64_t ld, const R* __restrict__ w,
+                                        const MEConsts& P, uint64_t e) {
+    const R we = w[e];
+    if constexpr (ME == HYDRA_ME_DALITZ_2BW)
+        return we * dalitz_2bw<R>(P, pair_mass2<R>(ev, ld, e, 0, 1), pair_mass2<R>(ev, ld, e, 1, 2));
+    return we;
+}
+
+template <typename R, int ME>
+__global__ void __launch_bounds__(256) evaluate_tiles_vec(uint64_t nevents, const R* __restrict__ ev, uint64_t ld,
+                                                          const R* __restrict__ w, const __grid_constant__ MEConsts P,
+                                                          R* __restrict__ values, uint64_t tile_begin, uint64_t ntiles,
+                                                          TileSums* __restrict__ partials) {
+    using V = Vec16<R>;
+    constexpr int W = V::W;
+    constexpr int kRuns = kGroupEvents / W;       // runs of W events per lane per group
+    constexpr int kGroupSpan = 32 * kGroupEvents;  // events of one group across the warp
+    const int lane = threadIdx.x & 31;
+    const uint64_t warp = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = (static_cast<uint64_t>(gridDim.x) * blockDim.x) >> 5;
+    for (uint64_t t = warp; t < ntiles; t += nwarps) {
+        const uint64_t base = (tile_begin + t) * kTileEvents;
+        double af = 0.0, af2 = 0.0, aw = 0.0, aw2 = 0.0;
+        for (int g = 0; g < kTileEvents / kGroupSpan; ++g) {
+            R sf = R(0), sf2 = R(0), sw = R(0), sw2 = R(0);
+#pragma unroll
+            for (int j = 0; j < kRuns; ++j) {
+                const uint64_t e0 = base + static_cast<uint64_t>(g * kGroupSpan + j * 32 * W + lane * W);
+                R f[W], we[W];
+                if (e0 + W <= nevents) {
+                    V::get(w + e0, we);
+                    if constexpr (ME == HYDRA_ME_DALITZ_2BW) {
+                        R c[3][4][W];
+#pragma unroll
+                        for (int a = 0; a < 3; ++a)
+#pragma unroll
+                            for (int k = 0; k < 4; ++k) V::get(ev + static_cast<uint64_t>(4 * a + k) * ld + e0, c[a][k]);
+#pragma unroll
+                        for (int q = 0; q < W; ++q) {
+                            using Q = Prec<R>;
+                            R m2[2];
+#pragma unroll
+                            for (int pr = 0; pr < 2; ++pr) {
+                                const R E = c[pr][0][q] + c[pr + 1][0][q];
+                                const R x = c[pr][1][q] + c[pr + 1][1][q];
+                                const R y = c[pr][2][q] + c[pr + 1][2][q];
+                                const R z = c[pr][3][q] + c[pr + 1][3][q];
+                                m2[pr] = Q::fma_(E, E, -Q::fma_(z, z, Q::fma_(y, y, x * x)));
+                            }
+                            f[q] = we[q] * dalitz_2bw<R>(P, m2[0], m2[1]);
+                        }
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < W; ++q) f[q] = we[q];
+                    }
+                    if (values) V::put(values + e0, f);
+                } else {
+#pragma unroll
+                    for (int q = 0; q < W; ++q) {
+                        we[q] = R(0);
+                        f[q] = R(0);
+                        if (e0 + q < nevents) {
+                            we[q] = w[e0 + q];
+                            f[q] = eval_event<R, ME>(ev, ld, w, P, e0 + q);
+                            if (values) values[e0 + q] = f[q];
+                        }
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < W; ++q) {
+                    sf += f[q];
+                    sf2 = Prec<R>::fma_(f[q], f[q], sf2);
+                    sw += we[q];
+                    sw2 = Prec<R>::fma_(we[q], we[q], sw2);
+                }
+            }
+            af += static_cast<double>(sf);
+            af2 += static_cast<double>(sf2);
+            aw += static_cast<double>(sw);
+            aw2 += static_cast<double>(sw2);
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            af += __shfl_xor_sync(0xffffffffu, af, off);
+            af2 += __shfl_xor_sync(0xffffffffu, af2, off);
+            aw += __shfl_xor_sync(0xffffffffu, aw, off);
+            aw2 += __shfl_xor_sync(0xffffffffu, aw2, off);
+        }
+        if (lane == 0) partials[t] = TileSums{af, af2, aw, aw2};
+    }
+}
+
 __global__ void __launch_bounds__(kSegBlock) eval_reduce_segments(const TileSums* __restrict__ partials, uint64_t ntiles,
                                                                   uint64_t seg_begin, double* __restrict__ seg_out) {
     const uint64_t seg = blockIdx.x;  // one block per segment
@@ -611,11 +738,30 @@ hydra_status hydra_phsp_evaluate(int n, uint64_t nevents, hydra_dtype dtype, hyd
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    // 16-byte loads when every array is 16-byte aligned and ld a multiple of the vector width
+    const uint64_t width = dtype == HYDRA_F32 ? 4 : 2;
+    const bool vec = (reinterpret_cast<uintptr_t>(weights) % 16 == 0) &&
+                     (!values || reinterpret_cast<uintptr_t>(values) % 16 == 0) &&
+                     (!events || (reinterpret_cast<uintptr_t>(events) % 16 == 0 && ld % width == 0));
     for (uint64_t t0 = 0; t0 < ntiles; t0 += kChunkTiles) {
         const uint64_t nt = ntiles - t0 < kChunkTiles ? ntiles - t0 : kChunkTiles;
         const uint64_t need = (nt * 32 + 255) / 256;
         const unsigned grid = static_cast<unsigned>(need < static_cast<uint64_t>(sms) * 8 ? need : static_cast<uint64_t>(sms) * 8);
-        if (dtype == HYDRA_F32) {
+        if (vec && dtype == HYDRA_F32) {
+            if (me == HYDRA_ME_DALITZ_2BW)
+                evaluate_tiles_vec<float, HYDRA_ME_DALITZ_2BW><<<grid, 256, 0, cs>>>(nevents, static_cast<const float*>(events), ld,
+                    static_cast<const float*>(weights), P, static_cast<float*>(values), t0, nt, s->tiles);
+            else
+                evaluate_tiles_vec<float, HYDRA_ME_FLAT><<<grid, 256, 0, cs>>>(nevents, static_cast<const float*>(events), ld,
+                    static_cast<const float*>(weights), P, static_cast<float*>(values), t0, nt, s->tiles);
+        } else if (vec) {
+            if (me == HYDRA_ME_DALITZ_2BW)
+                evaluate_tiles_vec<double, HYDRA_ME_DALITZ_2BW><<<grid, 256, 0, cs>>>(nevents, static_cast<const double*>(events), ld,
+                    static_cast<const double*>(weights), P, static_cast<double*>(values), t0, nt, s->tiles);
+            else
+                evaluate_tiles_vec<double, HYDRA_ME_FLAT><<<grid, 256, 0, cs>>>(nevents, static_cast<const double*>(events), ld,
+                    static_cast<const double*>(weights), P, static_cast<double*>(values), t0, nt, s->tiles);
+        } else if (dtype == HYDRA_F32) {
             if (me == HYDRA_ME_DALITZ_2BW)
                 evaluate_tiles<float, HYDRA_ME_DALITZ_2BW><<<grid, 256, 0, cs>>>(nevents, static_cast<const float*>(events), ld,
                     static_cast<const float*>(weights), P, static_cast<float*>(values), t0, nt, s->tiles);
