@@ -163,6 +163,8 @@ hydra_status hydra_phsp_generate_boosted(double M, int n, const double *masses, 
  *   indices     device array with room for nevents int64: receives the kept event indices
  *               in increasing order (deterministic)
  *   naccepted   host: number of kept events; w_max_used (host, optional): the bound used
+ * Keeps about nevents / 4 bytes of device scratch (one accept bit and the tile counts and
+ * offsets per event) until a larger call or hydra_shutdown.
  * Blocks until the count is on the host.  Errors: UNSUPPORTED_N, INVALID_ARG, OOM, CUDA.
  */
 hydra_status hydra_phsp_unweight(int n, uint64_t nevents, uint64_t seed, uint64_t event_offset,

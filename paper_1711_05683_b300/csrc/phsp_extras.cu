@@ -9,8 +9,9 @@
 //                                          accept-reject against w_max: event e is kept when
 //                                          u_e w_max < w_e (u_e its draw 3n-4); indices of the
 //                                          kept events are written in event order (stable,
-//                                          deterministic: counts per 4096-event tile, an
-//                                          exclusive scan, ranks by warp ballots)
+//                                          deterministic: accept bits and counts per
+//                                          4096-event tile, an exclusive scan, ranks by warp
+//                                          ballots over the stored bits)
 //   gather_events                          copies kept events into a compact SoA buffer
 #include <cuda_runtime.h>
 
@@ -148,17 +149,57 @@ static const void* boost_kernel_n(int n) {
 constexpr int kUwBlock = 256;
 constexpr int kUwPerThread = 16;
 constexpr int kUwTile = kUwBlock * kUwPerThread;  // 4096 events per block tile
+constexpr int kUwWarpRun = 32 * kUwPerThread;     // 512 consecutive events per warp within a tile
 
-// Largest weight (order-preserving integer bits of non-negative FP32 / FP64 values).
+// Largest weight (order-preserving integer bits of non-negative FP32 / FP64 values).  With
+// 16-byte aligned weights each thread reads four 16-byte vectors per pass (the scalar loop
+// kept too few bytes in flight: 1.35 TB/s); the remainder is read element by element.
+template <typename T>
+__device__ __forceinline__ unsigned long long weight_bits(T v) {
+    if constexpr (sizeof(T) == 4) return __float_as_uint(fmaxf(v, 0.0f));
+    else return static_cast<unsigned long long>(__double_as_longlong(fmax(v, 0.0)));
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kUwBlock) unweight_max(const T* __restrict__ w, uint64_t nevents,
                                                          unsigned long long* __restrict__ out_bits) {
+    constexpr int W = 16 / sizeof(T);  // weights per 16-byte vector
+    constexpr int kU = 4;              // vectors per thread per pass
     unsigned long long best = 0;
-    for (uint64_t e = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < nevents;
-         e += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
-        unsigned long long b;
-        if constexpr (sizeof(T) == 4) b = __float_as_uint(fmaxf(w[e], 0.0f));
-        else b = static_cast<unsigned long long>(__double_as_longlong(fmax(w[e], 0.0)));
+    const uint64_t nthreads = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+    const uint64_t tid = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    uint64_t head = 0;  // weights taken by the vector loop
+    if (reinterpret_cast<uintptr_t>(w) % 16 == 0) {
+        const uint64_t nvec = nevents / W;
+        const uint4* v = reinterpret_cast<const uint4*>(w);
+        uint64_t i = tid;
+        for (; i + (kU - 1) * nthreads < nvec; i += kU * nthreads) {
+            uint4 q[kU];
+#pragma unroll
+            for (int u = 0; u < kU; ++u) q[u] = v[i + u * nthreads];
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const T* x = reinterpret_cast<const T*>(&q[u]);
+#pragma unroll
+                for (int k = 0; k < W; ++k) {
+                    const unsigned long long b = weight_bits<T>(x[k]);
+                    best = b > best ? b : best;
+                }
+            }
+        }
+        for (; i < nvec; i += nthreads) {
+            const uint4 q = v[i];
+            const T* x = reinterpret_cast<const T*>(&q);
+#pragma unroll
+            for (int k = 0; k < W; ++k) {
+                const unsigned long long b = weight_bits<T>(x[k]);
+                best = b > best ? b : best;
+            }
+        }
+        head = nvec * W;
+    }
+    for (uint64_t e = head + tid; e < nevents; e += nthreads) {
+        const unsigned long long b = weight_bits<T>(w[e]);
         best = b > best ? b : best;
     }
 #pragma unroll
@@ -190,23 +231,38 @@ __device__ __forceinline__ T bits_to_value(unsigned long long b) {
     else return __longlong_as_double(static_cast<long long>(b));
 }
 
+// The accept decisions of one thread in a block tile, as a bit mask: warp v of the block takes
+// the run of 512 consecutive events base + 512 v .. (row j: 32 events, lane l: event j*32 + l).
+template <typename T>
+__device__ __forceinline__ uint32_t accept_mask(const DecayConsts& C, int draw, const T* __restrict__ w,
+                                                uint64_t nevents, uint64_t event_offset, T w_max, uint64_t run0,
+                                                int lane) {
+    uint32_t mask = 0;
+#pragma unroll
+    for (int j = 0; j < kUwPerThread; ++j) {
+        const uint64_t e = run0 + static_cast<uint64_t>(j * 32 + lane);
+        if (e < nevents && accept_event<T>(C, draw, event_offset + e, w[e], w_max)) mask |= 1u << j;
+    }
+    return mask;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kUwBlock) unweight_count(const __grid_constant__ DecayConsts C, int draw,
                                                            const T* __restrict__ w, uint64_t nevents,
                                                            uint64_t event_offset,
                                                            const unsigned long long* __restrict__ wmax_bits,
-                                                           uint32_t* __restrict__ tile_counts) {
+                                                           uint32_t* __restrict__ tile_counts,
+                                                           uint32_t* __restrict__ masks) {
     __shared__ uint32_t warp_cnt[kUwBlock / 32];
     const T w_max = bits_to_value<T>(*wmax_bits);
-    const uint64_t base = static_cast<uint64_t>(blockIdx.x) * kUwTile;
-    uint32_t cnt = 0;
-    for (int j = 0; j < kUwPerThread; ++j) {
-        const uint64_t e = base + static_cast<uint64_t>(j * kUwBlock + threadIdx.x);
-        if (e < nevents && accept_event<T>(C, draw, event_offset + e, w[e], w_max)) ++cnt;
-    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint64_t run0 = static_cast<uint64_t>(blockIdx.x) * kUwTile + static_cast<uint64_t>(warp) * kUwWarpRun;
+    const uint32_t mask = accept_mask<T>(C, draw, w, nevents, event_offset, w_max, run0, lane);
+    masks[static_cast<uint64_t>(blockIdx.x) * kUwBlock + threadIdx.x] = mask;
+    uint32_t cnt = __popc(mask);
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, off);
-    if ((threadIdx.x & 31) == 0) warp_cnt[threadIdx.x >> 5] = cnt;
+    if (lane == 0) warp_cnt[warp] = cnt;
     __syncthreads();
     if (threadIdx.x == 0) {
         uint32_t s = 0;
@@ -242,32 +298,32 @@ __global__ void __launch_bounds__(1024) unweight_scan(const uint32_t* __restrict
     }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kUwBlock) unweight_write(const __grid_constant__ DecayConsts C, int draw,
-                                                           const T* __restrict__ w, uint64_t nevents,
-                                                           uint64_t event_offset,
-                                                           const unsigned long long* __restrict__ wmax_bits,
+// Kept indices in event order, from the accept bits the count pass stored: each warp's run of
+// 512 events follows the runs of the warps before it in the tile (one block-wide prefix of the
+// warp totals), and within the run the rows follow each other with the lanes in order (a
+// ballot per row).  (Recomputing the decisions here instead, a second Philox block and weight
+// read per event, made this pass the slowest of the four.)
+__global__ void __launch_bounds__(kUwBlock) unweight_write(const uint32_t* __restrict__ masks,
                                                            const uint64_t* __restrict__ offsets,
                                                            int64_t* __restrict__ indices) {
     __shared__ uint32_t warp_cnt[kUwBlock / 32];
-    const T w_max = bits_to_value<T>(*wmax_bits);
-    const uint64_t base = static_cast<uint64_t>(blockIdx.x) * kUwTile;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint64_t run0 = static_cast<uint64_t>(blockIdx.x) * kUwTile + static_cast<uint64_t>(warp) * kUwWarpRun;
+    const uint32_t mask = masks[static_cast<uint64_t>(blockIdx.x) * kUwBlock + threadIdx.x];
+    uint32_t cnt = __popc(mask);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, off);
+    if (lane == 0) warp_cnt[warp] = cnt;
+    __syncthreads();
     uint64_t run = offsets[blockIdx.x];
+    for (int i = 0; i < warp; ++i) run += warp_cnt[i];
+    const uint32_t below = (1u << lane) - 1u;
+#pragma unroll
     for (int j = 0; j < kUwPerThread; ++j) {
-        const uint64_t e = base + static_cast<uint64_t>(j * kUwBlock + threadIdx.x);
-        const bool a = e < nevents && accept_event<T>(C, draw, event_offset + e, w[e], w_max);
+        const bool a = (mask >> j) & 1u;
         const uint32_t ballot = __ballot_sync(0xffffffffu, a);
-        if (lane == 0) warp_cnt[warp] = __popc(ballot);
-        __syncthreads();
-        uint64_t before = 0, total = 0;
-        for (int i = 0; i < kUwBlock / 32; ++i) {
-            if (i < warp) before += warp_cnt[i];
-            total += warp_cnt[i];
-        }
-        if (a) indices[run + before + __popc(ballot & ((1u << lane) - 1u))] = static_cast<int64_t>(e);
-        run += total;
-        __syncthreads();
+        if (a) indices[run + __popc(ballot & below)] = static_cast<int64_t>(run0 + static_cast<uint64_t>(j * 32 + lane));
+        run += __popc(ballot);
     }
 }
 
@@ -290,6 +346,7 @@ struct UwScratch {
     std::mutex mu;
     uint32_t* counts = nullptr;
     uint64_t* offsets = nullptr;
+    uint32_t* masks = nullptr;    // accept bits of the count pass, one word per thread of a tile
     uint64_t cap = 0;
     unsigned long long* wmax = nullptr;  // [0] max bits, [1] total
     unsigned long long* h = nullptr;     // pinned copy of the two
@@ -535,6 +592,7 @@ void release_extras_scratch() {
             cudaSetDevice(static_cast<int>(d));
             if (s->counts) cudaFree(s->counts);
             if (s->offsets) cudaFree(s->offsets);
+            if (s->masks) cudaFree(s->masks);
             if (s->wmax) cudaFree(s->wmax);
             if (s->h) cudaFreeHost(s->h);
             delete s;
@@ -635,11 +693,14 @@ hydra_status hydra_phsp_unweight(int n, uint64_t nevents, uint64_t seed, uint64_
     if (ntiles > s->cap) {
         if (s->counts) cudaFree(s->counts);
         if (s->offsets) cudaFree(s->offsets);
+        if (s->masks) cudaFree(s->masks);
         s->counts = nullptr;
         s->offsets = nullptr;
+        s->masks = nullptr;
         s->cap = 0;
         if (cudaMalloc(&s->counts, ntiles * sizeof(uint32_t)) != cudaSuccess ||
-            cudaMalloc(&s->offsets, ntiles * sizeof(uint64_t)) != cudaSuccess) {
+            cudaMalloc(&s->offsets, ntiles * sizeof(uint64_t)) != cudaSuccess ||
+            cudaMalloc(&s->masks, ntiles * kUwBlock * sizeof(uint32_t)) != cudaSuccess) {
             cudaGetLastError();
             return fail(HYDRA_ERR_OOM, "unweighting scratch for %llu tiles", static_cast<unsigned long long>(ntiles));
         }
@@ -662,25 +723,21 @@ hydra_status hydra_phsp_unweight(int n, uint64_t nevents, uint64_t seed, uint64_
             cudaGetDevice(&dev);
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
             if (dtype == HYDRA_F32)
-                unweight_max<float><<<sms * 4, kUwBlock, 0, cs>>>(static_cast<const float*>(weights), nevents, s->wmax);
+                unweight_max<float><<<sms * 8, kUwBlock, 0, cs>>>(static_cast<const float*>(weights), nevents, s->wmax);
             else
-                unweight_max<double><<<sms * 4, kUwBlock, 0, cs>>>(static_cast<const double*>(weights), nevents, s->wmax);
+                unweight_max<double><<<sms * 8, kUwBlock, 0, cs>>>(static_cast<const double*>(weights), nevents, s->wmax);
             err = cudaGetLastError();
         }
     }
     if (err != cudaSuccess) return cuda_fail(err, "unweighting max");
     const unsigned grid = static_cast<unsigned>(ntiles);
     if (dtype == HYDRA_F32) {
-        unweight_count<float><<<grid, kUwBlock, 0, cs>>>(C, draw, static_cast<const float*>(weights), nevents, event_offset, s->wmax, s->counts);
+        unweight_count<float><<<grid, kUwBlock, 0, cs>>>(C, draw, static_cast<const float*>(weights), nevents, event_offset, s->wmax, s->counts, s->masks);
     } else {
-        unweight_count<double><<<grid, kUwBlock, 0, cs>>>(C, draw, static_cast<const double*>(weights), nevents, event_offset, s->wmax, s->counts);
+        unweight_count<double><<<grid, kUwBlock, 0, cs>>>(C, draw, static_cast<const double*>(weights), nevents, event_offset, s->wmax, s->counts, s->masks);
     }
     unweight_scan<<<1, 1024, 0, cs>>>(s->counts, ntiles, s->offsets, reinterpret_cast<uint64_t*>(s->wmax + 1));
-    if (dtype == HYDRA_F32) {
-        unweight_write<float><<<grid, kUwBlock, 0, cs>>>(C, draw, static_cast<const float*>(weights), nevents, event_offset, s->wmax, s->offsets, indices);
-    } else {
-        unweight_write<double><<<grid, kUwBlock, 0, cs>>>(C, draw, static_cast<const double*>(weights), nevents, event_offset, s->wmax, s->offsets, indices);
-    }
+    unweight_write<<<grid, kUwBlock, 0, cs>>>(s->masks, s->offsets, indices);
     err = cudaGetLastError();
     if (err == cudaSuccess) err = cudaMemcpyAsync(s->h, s->wmax, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, cs);
     if (err == cudaSuccess) err = cudaStreamSynchronize(cs);

@@ -92,6 +92,23 @@ def test_unweighting_is_deterministic_and_chunkable():
     assert torch.equal(a, torch.cat([b1, b2 + h]))
 
 
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_unweighting_sample_maximum_any_alignment(dtype):
+    """The sample maximum (16-byte vector loads when the weights are aligned, element loads for
+    a misaligned view and the remainder) equals torch's max; the kept indices of an offset
+    view are those of the full call shifted, with the same bound."""
+    M, masses = 10.0, workloads.sweep_masses(4, True)
+    p, w = hp.generate(M, masses, 70_001, 5, dtype=dtype)
+    for lo, hi in ((0, 70_001), (1, 70_001), (3, 69_998), (0, 7), (1, 2)):
+        v = w[lo:hi]
+        _, used = hp.unweight(4, v, 5, dtype=dtype, event_offset=lo)
+        assert used == float(v.max())
+    wm = float(w.max())
+    full, _ = hp.unweight(4, w, 5, w_max=wm, dtype=dtype)
+    part, _ = hp.unweight(4, w[1:], 5, w_max=wm, dtype=dtype, event_offset=1)
+    assert torch.equal(full[full >= 1], part + 1)
+
+
 def test_evaluate_on_oracle_events_fp64():
     """The evaluation kernel on the oracle's own events (uploaded) reproduces the oracle's
     values and sums; on GPU-generated events it reproduces the generated-event integral."""
