@@ -37,6 +37,32 @@ def test_boosted_one_mother(n, dtype):
     np.testing.assert_allclose(w.double().cpu().numpy(), ref_w, rtol=TOL[dtype])
 
 
+@pytest.mark.parametrize("dtype,n", [("f32", 3), ("f32", 6), ("f32", 9), ("f64", 4)])
+def test_boosted_generation_independent_of_launch_shape(dtype, n):
+    """The moving-parent generator follows the generator's tuned shape (FP32 groups of up to
+    four events); every shape gives the same bits, ragged tails included, for one momentum and
+    for per-event momenta."""
+    rng = np.random.default_rng(70 + n)
+    M, masses = workloads.random_decay(rng, n)
+    nev = 10_003
+    tdt = torch.float32 if dtype == "f32" else torch.float64
+    moms = torch.as_tensor(rng.normal(0.0, 3.0 * M, size=(3, nev)), dtype=tdt, device="cuda").contiguous()
+    saved = hp.get_launch_config(hp.KERNEL_GENERATE, n, dtype)
+    runs = []
+    try:
+        for block, ept in ((256, 1), (128, 2), (256, 4), (512, 4)):
+            hp.set_launch_config(hp.KERNEL_GENERATE, n, dtype, block, ept)
+            a = hp.generate_boosted(M, masses, nev, 11, mother=(0.3 * M, 0.0, -1.7 * M), dtype=dtype)
+            b = hp.generate_boosted(M, masses, nev, 11, mothers=moms, dtype=dtype, event_offset=3)
+            torch.cuda.synchronize()
+            runs.append((a, b))
+    finally:
+        hp.set_launch_config(hp.KERNEL_GENERATE, n, dtype, *saved)
+    for (a, b) in runs[1:]:
+        for x, y in zip(a + b, runs[0][0] + runs[0][1]):
+            assert torch.equal(x[..., :nev], y[..., :nev])
+
+
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
 def test_boosted_per_event_mothers(dtype):
     M, masses = 3.0, (0.2, 0.3, 0.4, 0.5, 0.1)
