@@ -427,7 +427,7 @@ def run_ours(args) -> None:
     }
     if not args.no_batch:
         line["batch"] = run_batch_workload()
-        line["extensions"] = run_extras()
+        line["extensions"] = run_extras(hbm_peak_gbs=peaks["hbm_gbs"])
     if not args.no_serve:
         line["serve"] = run_serve_workload(duration_s=args.serve_seconds)
     if not args.no_cpu_baseline:
@@ -540,10 +540,14 @@ def run_batch_workload(count: int = 4096, reps: int = 2, arena_bytes: int = AREN
 
 
 # ----------------------------------------------------------------------------- extensions
-def run_extras(nev: int = 100_000_000, reps: int = 3) -> dict:
+def run_extras(nev: int = 100_000_000, reps: int = 3, hbm_peak_gbs: float | None = None) -> dict:
     """Events/s of the moving-parent generator (per-event parent momenta read from HBM),
     accept-reject unweighting and matrix-element evaluation on stored events (FP32, N=3,
-    Dalitz decay, 1e8 events; best of `reps` after one warm-up, CUDA events)."""
+    Dalitz decay, 1e8 events; best of `reps` after one warm-up, CUDA events), with each
+    kernel's algorithmic bytes per event and their rate as a fraction of the measured copy
+    bandwidth: moving parent 12 B read + 52 B written; unweighting the weights read twice (the
+    maximum and the accept pass, 8 B), one accept bit written and read back, and 8 B per kept
+    index; evaluation 12 components + the weight read (52 B)."""
     import torch
     import paper_1711_05683_b300 as hp
     d = INT_CFG
@@ -568,9 +572,14 @@ def run_extras(nev: int = 100_000_000, reps: int = 3) -> dict:
     res["boosted_generate_f32_n3"] = {"events_per_s": nev / t, "hbm_gbs": nev * (52 + 12) / t / 1e9}
     p, w = hp.generate(d["M"], d["masses"], nev, 3, dtype="f32")
     t = timed(lambda: hp.unweight(3, w, 3, dtype="f32"))
-    res["unweight_f32_n3"] = {"events_per_s": nev / t, "kept": len(hp.unweight(3, w, 3, dtype="f32")[0])}
+    kept = len(hp.unweight(3, w, 3, dtype="f32")[0])
+    res["unweight_f32_n3"] = {"events_per_s": nev / t, "kept": kept,
+                              "hbm_gbs": (nev * (8 + 0.25) + 8 * kept) / t / 1e9}
     t = timed(lambda: hp.evaluate(p, w, me=hp.ME_DALITZ_2BW, params=d["params"], dtype="f32"))
     res["evaluate_dalitz_f32"] = {"events_per_s": nev / t, "hbm_gbs": nev * 52 / t / 1e9}
+    if hbm_peak_gbs:
+        for key in ("boosted_generate_f32_n3", "unweight_f32_n3", "evaluate_dalitz_f32"):
+            res[key]["hbm_frac_of_measured_copy"] = round(res[key]["hbm_gbs"] / hbm_peak_gbs, 4)
     del p, w, moms
     torch.cuda.empty_cache()
     res.update(run_vegas(nev, 10, reps=reps))
