@@ -101,6 +101,10 @@ __global__ void __launch_bounds__(512) phsp_integrate_tiles(const __grid_constan
                                                             uint64_t nevents, uint64_t event_offset,
                                                             uint64_t tile_begin, uint64_t ntiles,
                                                             TileSums* __restrict__ partials) {
+    if constexpr (std::is_same<R, df>::value) {
+        df_sincos_table_init();
+        __syncthreads();
+    }
     const int lane = threadIdx.x & 31;
     const uint64_t warp = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = (static_cast<uint64_t>(gridDim.x) * blockDim.x) >> 5;
@@ -342,9 +346,12 @@ static Launch select_integrate(hydra_dtype dtype, hydra_me_id me, int n) {
     if (dtype == HYDRA_F32)
         k = me == HYDRA_ME_FLAT ? integrate_kernel_for<float, HYDRA_ME_FLAT>(n, ept)
                                 : integrate_kernel_for<float, HYDRA_ME_DALITZ_2BW>(n, ept);
-    else
+    else if (g_fp64_arith.load() == HYDRA_FP64_NATIVE)
         k = me == HYDRA_ME_FLAT ? integrate_kernel_for<double, HYDRA_ME_FLAT>(n, ept)
                                 : integrate_kernel_for<double, HYDRA_ME_DALITZ_2BW>(n, ept);
+    else
+        k = me == HYDRA_ME_FLAT ? integrate_kernel_for<df, HYDRA_ME_FLAT>(n, ept)
+                                : integrate_kernel_for<df, HYDRA_ME_DALITZ_2BW>(n, ept);
     return Launch{k, c.block.load(std::memory_order_relaxed), ept};
 }
 
@@ -466,6 +473,13 @@ hydra_status make_me(hydra_me_id me, int n, const double* params, int nparams, M
     P->b_mgf = static_cast<float>(P->b_mg);
     P->c_ref = static_cast<float>(P->c_re);
     P->c_imf = static_cast<float>(P->c_im);
+    // low parts of the double-float parameters: hi + lo = the FP64 value to ~2^-48
+    P->a_m2lo = static_cast<float>(P->a_m2 - static_cast<double>(P->a_m2f));
+    P->a_mglo = static_cast<float>(P->a_mg - static_cast<double>(P->a_mgf));
+    P->b_m2lo = static_cast<float>(P->b_m2 - static_cast<double>(P->b_m2f));
+    P->b_mglo = static_cast<float>(P->b_mg - static_cast<double>(P->b_mgf));
+    P->c_relo = static_cast<float>(P->c_re - static_cast<double>(P->c_ref));
+    P->c_imlo = static_cast<float>(P->c_im - static_cast<double>(P->c_imf));
     return HYDRA_OK;
 }
 

@@ -245,7 +245,7 @@ size_t table_size(int nreq, int nfinal) {
     return align_up(off, 256);
 }
 
-// Variant 0: FP32; 1: FP64 with native FP64 generation; 2: FP64 with double-float generation.
+// Variant 0: FP32; 1: FP64 with native FP64 arithmetic; 2: FP64 with double-float generation and integrals.
 int run_variant(int dtype) {
     if (dtype == HYDRA_F32) return 0;
     return g_fp64_arith.load(std::memory_order_relaxed) == HYDRA_FP64_NATIVE ? 1 : 2;
@@ -258,7 +258,7 @@ void launch_run_kernels(hydra_batch* b, int v, cudaStream_t s) {
     else if (v == 1)
         phsp_batch_kernel<double, double><<<b->grid_main[v], kBatchBlock, 0, s>>>(hdr, b->d_partials);
     else
-        phsp_batch_kernel<df, double><<<b->grid_main[v], kBatchBlock, 0, s>>>(hdr, b->d_partials);
+        phsp_batch_kernel<df, df><<<b->grid_main[v], kBatchBlock, 0, s>>>(hdr, b->d_partials);
     batch_reduce_segments<<<b->grid_aux, kSegBlock, 0, s>>>(hdr, b->d_partials);
     batch_finalize<<<b->grid_aux, kBatchBlock, 0, s>>>(hdr, b->d_results);
 }
@@ -314,7 +314,7 @@ hydra_status hydra_batch_create(int max_requests, uint64_t max_integrate_tiles, 
     b->grid_main[0] = sms * (occ > 0 ? occ : 1);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, phsp_batch_kernel<double, double>, kBatchBlock, 0);
     b->grid_main[1] = sms * (occ > 0 ? occ : 1);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, phsp_batch_kernel<df, double>, kBatchBlock, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, phsp_batch_kernel<df, df>, kBatchBlock, 0);
     b->grid_main[2] = sms * (occ > 0 ? occ : 1);
     b->grid_aux = sms;
     for (int v = 0; v < 3; ++v) {

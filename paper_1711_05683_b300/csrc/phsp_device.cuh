@@ -197,6 +197,12 @@ template <> struct Prec<df> {
     __device__ static df div(df a, df b) { return df_div(a, b); }
     __device__ static df fma_(df a, df b, df c) { return a * b + c; }
     __device__ static void sincos_2pi_u(uint32_t x, df* s, df* c) { df_sincos_2pi_u(x, s_sincos_table, s, c); }
+    // cos(phi_a - phi_b) = cos(2 pi (xa - xb) 2^-32), the integer difference taken mod 2^32
+    __device__ static df cos_2pi_diff(uint32_t xa, uint32_t xb) {
+        df sv, cv;
+        df_sincos_2pi_int(xa - xb, s_sincos_table, &sv, &cv);
+        return cv;
+    }
     using Wacc = DfWeight;  // double-float mantissa and binary exponent: no FP64 until the end
     __device__ static Wacc w_one() { return df_weight_one(); }
     __device__ static Wacc w_mul(Wacc w, df p) { return df_weight_mul(w, p); }

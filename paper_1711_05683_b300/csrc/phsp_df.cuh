@@ -290,9 +290,9 @@ __device__ __forceinline__ void df_sincos_table_init() {
     }
 }
 
-__device__ __forceinline__ void df_sincos_2pi_u(uint32_t x, const SinCosTable& T, df* s, df* c) {
-    const uint32_t k = x >> 21;                              // table index 0..2047
-    const uint32_t rem2 = ((x & 0x1FFFFFu) << 1) | 1u;      // 2r + 1 < 2^22: exact in FP32
+// sin and cos of theta_k + delta with delta = pi rem2 2^-32 (rem2 < 2^22) and k < 2048.
+__device__ __forceinline__ void df_sincos_table_step(uint32_t k, uint32_t rem2, const SinCosTable& T, df* s,
+                                                     df* c) {
     const df pi_scaled{7.31459059988282e-10f, -2.035470133961082e-17f};  // pi 2^-32 (hi + lo)
     const df d = pi_scaled * __uint2float_rn(rem2);                       // delta
     const float d2f = __fmul_rn(d.hi, d.hi);
@@ -310,6 +310,17 @@ __device__ __forceinline__ void df_sincos_2pi_u(uint32_t x, const SinCosTable& T
     const df sk{t.x, t.y}, ck{t.z, t.w};
     *s = sk * cd + ck * sd;  // sin(theta_k + delta)
     *c = ck * cd - sk * sd;  // cos(theta_k + delta)
+}
+
+__device__ __forceinline__ void df_sincos_2pi_u(uint32_t x, const SinCosTable& T, df* s, df* c) {
+    // k = top 11 bits; delta = pi (2r + 1) 2^-32 with r the low 21 bits (2r + 1 < 2^22, exact in FP32)
+    df_sincos_table_step(x >> 21, ((x & 0x1FFFFFu) << 1) | 1u, T, s, c);
+}
+
+// sin and cos of 2 pi d 2^-32 for a 32-bit integer d (no half-step offset: the difference of
+// two phi draws, whose offsets cancel).
+__device__ __forceinline__ void df_sincos_2pi_int(uint32_t d, const SinCosTable& T, df* s, df* c) {
+    df_sincos_table_step(d >> 21, (d & 0x1FFFFFu) << 1, T, s, c);
 }
 
 // The same as one out-of-line function.  The N >= 6 double-float generators call this

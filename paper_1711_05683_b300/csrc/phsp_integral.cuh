@@ -29,12 +29,15 @@ struct TileSums {
 // Matrix-element parameters in both precisions.
 struct MEConsts {
     double a_m2, a_mg, b_m2, b_mg, c_re, c_im;  // m0^2, m0*Gamma, Re c, Im c
-    float a_m2f, a_mgf, b_m2f, b_mgf, c_ref, c_imf;
+    float a_m2f, a_mgf, b_m2f, b_mgf, c_ref, c_imf;           // FP32 values (double-float high parts)
+    float a_m2lo, a_mglo, b_m2lo, b_mglo, c_relo, c_imlo;     // double-float low parts
 };
 
 template <typename R, int EPT>
 struct IntegrandSink {
-    R E1[EPT], M2[EPT], w[EPT];
+    using W = typename Prec<R>::W;  // weights: FP32, or FP64 for double and double-float kinematics
+    R E1[EPT], M2[EPT];
+    W w[EPT];
     __device__ __forceinline__ void subsystem_mass(int k, const R (&Mk)[EPT]) {
         if (k == 2) {
 #pragma unroll
@@ -48,25 +51,35 @@ struct IntegrandSink {
             for (int q = 0; q < EPT; ++q) E1[q] = E[q];
         }
     }
-    __device__ __forceinline__ void weight(const R (&wv)[EPT]) {
+    __device__ __forceinline__ void weight(const W (&wv)[EPT]) {
 #pragma unroll
         for (int q = 0; q < EPT; ++q) w[q] = wv[q];
     }
 };
 
-template <typename R> __device__ __forceinline__ R me_param(double d, float f);
-template <> __device__ __forceinline__ float me_param<float>(double, float f) { return f; }
-template <> __device__ __forceinline__ double me_param<double>(double d, float) { return d; }
+// A matrix-element parameter in arithmetic R: the FP32 value, the FP64 value, or the
+// double-float pair (hi, lo).
+template <typename R> __device__ __forceinline__ R me_param(double d, float f, float lo);
+template <> __device__ __forceinline__ float me_param<float>(double, float f, float) { return f; }
+template <> __device__ __forceinline__ double me_param<double>(double d, float, float) { return d; }
+template <> __device__ __forceinline__ df me_param<df>(double, float f, float lo) { return df{f, lo}; }
+
+// A value of arithmetic R in the weights' type (the double-float result rounded to FP64).
+template <typename R>
+__device__ __forceinline__ typename Prec<R>::W to_w(R v) {
+    if constexpr (std::is_same<R, df>::value) return df_to_double(v);
+    else return v;
+}
 
 // |BW(s12; a) + c BW(s23; b)|^2, BW(s) = (m0^2 - s + i m0 G) / ((m0^2 - s)^2 + (m0 G)^2).
 template <typename R>
 __device__ __forceinline__ R dalitz_2bw(const MEConsts& P, R s12, R s23) {
-    const R xa = me_param<R>(P.a_m2, P.a_m2f) - s12, ya = me_param<R>(P.a_mg, P.a_mgf);
-    const R xb = me_param<R>(P.b_m2, P.b_m2f) - s23, yb = me_param<R>(P.b_mg, P.b_mgf);
+    const R xa = me_param<R>(P.a_m2, P.a_m2f, P.a_m2lo) - s12, ya = me_param<R>(P.a_mg, P.a_mgf, P.a_mglo);
+    const R xb = me_param<R>(P.b_m2, P.b_m2f, P.b_m2lo) - s23, yb = me_param<R>(P.b_mg, P.b_mgf, P.b_mglo);
     using Q = Prec<R>;
     const R ia = Q::rcp(Q::fma_(xa, xa, ya * ya));
     const R ib = Q::rcp(Q::fma_(xb, xb, yb * yb));
-    const R cr = me_param<R>(P.c_re, P.c_ref), ci = me_param<R>(P.c_im, P.c_imf);
+    const R cr = me_param<R>(P.c_re, P.c_ref, P.c_relo), ci = me_param<R>(P.c_im, P.c_imf, P.c_imlo);
     const R re = Q::fma_(xa, ia, Q::fma_(cr, xb, -(ci * yb)) * ib);
     const R im = Q::fma_(ya, ia, Q::fma_(cr, yb, ci * xb) * ib);
     return Q::fma_(re, re, im * im);
@@ -83,9 +96,10 @@ __device__ __forceinline__ R dalitz_2bw(const MEConsts& P, R s12, R s23) {
 // s23 = M^2 + m1^2 - 2 M E1 as in the general path; one cosine instead of two sin/cos pairs
 // and no 3-vectors.
 template <typename R>
-__device__ __forceinline__ void dalitz3_point(const DecayConsts& C, const MEConsts& P, uint64_t e, R& f,
-                                              R& wout) {
+__device__ __forceinline__ void dalitz3_point(const DecayConsts& C, const MEConsts& P, uint64_t e,
+                                              typename Prec<R>::W& f, typename Prec<R>::W& wout) {
     using Q = Prec<R>;
+    using W = typename Q::W;
     uint32_t b0[4], b1[4];
     philox4x32_10(static_cast<uint32_t>(e), static_cast<uint32_t>(e >> 32), 0u, 0u, C.rk0, C.rk1, b0);
     philox4x32_10(static_cast<uint32_t>(e), static_cast<uint32_t>(e >> 32), 1u, 0u, C.rk0, C.rk1, b1);
@@ -102,7 +116,7 @@ __device__ __forceinline__ void dalitz3_point(const DecayConsts& C, const MECons
     const R invM2 = Q::rcp(M2);
     const R p2 = Q::sqrt_(lam2) * Q::scale(Q::rcp(M), 0.5f);
     const R p1 = Q::sqrt_(lam1) * Q::scale(invM2, 0.5f);
-    const R w = Q::w_final(Q::w_mul(Q::w_mul(Q::w_one(), p2), p1), C);
+    const W w = Q::w_final(Q::w_mul(Q::w_mul(Q::w_one(), p2), p1), C);
     const R ssq = (Q::one_minus_cos(xca) * Q::one_plus_cos(xca)) * (Q::one_minus_cos(xcb) * Q::one_plus_cos(xcb));
     const R cos_alpha = Q::fma_(Q::cos_of(xca), Q::cos_of(xcb), Q::sqrt_(ssq) * Q::cos_2pi_diff(xpa, xpb));
     const R Q0 = Q::sqrt_(Q::fma_(p2, p2, M2 * M2));
@@ -111,12 +125,12 @@ __device__ __forceinline__ void dalitz3_point(const DecayConsts& C, const MECons
     const R s12 = M2 * M2;
     const R s23 = Q::fma_(R(-2) * M, E1, Q::fma_(M, M, Q::m2(C, 0)));
     wout = w;
-    f = w * dalitz_2bw<R>(P, s12, s23);
+    f = w * to_w<R>(dalitz_2bw<R>(P, s12, s23));
 }
 
 template <int N, typename R, int ME, int EPT>
-__device__ __forceinline__ void integrand_group(const DecayConsts& C, const MEConsts& P,
-                                                const uint64_t (&ev)[EPT], R (&f)[EPT], R (&w)[EPT]) {
+__device__ __forceinline__ void integrand_group(const DecayConsts& C, const MEConsts& P, const uint64_t (&ev)[EPT],
+                                                typename Prec<R>::W (&f)[EPT], typename Prec<R>::W (&w)[EPT]) {
     if constexpr (ME == HYDRA_ME_DALITZ_2BW && N == 3) {
 #pragma unroll
         for (int q = 0; q < EPT; ++q) dalitz3_point<R>(C, P, ev[q], f[q], w[q]);
@@ -132,7 +146,7 @@ __device__ __forceinline__ void integrand_group(const DecayConsts& C, const MECo
             const R M = Prec<R>::M(C);
             const R s12 = s.M2[q] * s.M2[q];
             const R s23 = Prec<R>::fma_(R(-2) * M, s.E1[q], Prec<R>::fma_(M, M, Prec<R>::m2(C, 0)));
-            f[q] = s.w[q] * dalitz_2bw<R>(P, s12, s23);
+            f[q] = s.w[q] * to_w<R>(dalitz_2bw<R>(P, s12, s23));
         } else {
             f[q] = s.w[q];
         }
@@ -152,11 +166,12 @@ template <int N, typename R, int ME, int EPT>
 __device__ __forceinline__ TileSums tile_sums(const DecayConsts& C, const MEConsts& P, uint64_t nevents,
                                               uint64_t event_offset, uint64_t tile, int lane) {
     static_assert(kGroupEvents % EPT == 0, "a group holds whole event groups");
+    using W = typename Prec<R>::W;  // the group sums' type: FP32 kinematics sum in FP32, FP64 ones in FP64
     const uint64_t base = tile * kTileEvents;
     double af = 0.0, af2 = 0.0, aw = 0.0, aw2 = 0.0;
 #pragma unroll 1
     for (int g = 0; g < kLaneIters / kGroupEvents; ++g) {
-        R sf = R(0), sf2 = R(0), sw = R(0), sw2 = R(0);
+        W sf = W(0), sf2 = W(0), sw = W(0), sw2 = W(0);
 #pragma unroll 1
         for (int i0 = 0; i0 < kGroupEvents; i0 += EPT) {
             uint64_t ev[EPT];
@@ -167,15 +182,15 @@ __device__ __forceinline__ TileSums tile_sums(const DecayConsts& C, const MECons
                 valid[q] = e < nevents;
                 ev[q] = event_offset + e;
             }
-            R f[EPT], w[EPT];
+            W f[EPT], w[EPT];
             integrand_group<N, R, ME, EPT>(C, P, ev, f, w);
 #pragma unroll
             for (int q = 0; q < EPT; ++q) {
                 if (valid[q]) {
                     sf += f[q];
-                    sf2 = Prec<R>::fma_(f[q], f[q], sf2);
+                    sf2 = Prec<W>::fma_(f[q], f[q], sf2);
                     sw += w[q];
-                    sw2 = Prec<R>::fma_(w[q], w[q], sw2);
+                    sw2 = Prec<W>::fma_(w[q], w[q], sw2);
                 }
             }
         }
