@@ -209,6 +209,31 @@ def test_integrate_flat_parity(n, kin):
     assert g["sum_f"] == g["sum_w"]
 
 
+@pytest.mark.parametrize("n", [3, 7])
+def test_integrate_native_fp64_parity(n):
+    """The FP64 integral with native FP64 instructions (hydra_set_fp64_arith) against the
+    oracle, as the double-float default is above: the Dalitz closed form and a flat N=7."""
+    saved = hp.get_fp64_arith()
+    hp.set_fp64_arith(hp.FP64_NATIVE)
+    try:
+        if n == 3:
+            d = workloads.D0_DALITZ
+            nev = 2048 * 7 + 99
+            g = hp.integrate(d["M"], d["masses"], nev, d["seed"], kin_dtype="f64", me=hp.ME_DALITZ_2BW,
+                             params=d["params"])
+            r = oracle.integrate_sums(d["M"], d["masses"], nev, d["seed"], me=1, params=d["params"])
+            assert abs(g["sum_f"] - r[0]) <= 1e-12 * r[0]
+        else:
+            masses = workloads.sweep_masses(n, True)
+            nev = 3 * 2048 + 5
+            g = hp.integrate(workloads.SWEEP_M, masses, nev, 3 + n, kin_dtype="f64")
+            r = oracle.integrate_sums(workloads.SWEEP_M, masses, nev, 3 + n)
+        assert abs(g["sum_w"] - r[2]) <= 1e-12 * r[2]
+        assert abs(g["sum_w2"] - r[3]) <= 2e-12 * r[3]
+    finally:
+        hp.set_fp64_arith(saved)
+
+
 def test_integrate_is_deterministic():
     d = workloads.D0_DALITZ
     a = hp.integrate(d["M"], d["masses"], 3_000_001, d["seed"], me=hp.ME_DALITZ_2BW, params=d["params"])
