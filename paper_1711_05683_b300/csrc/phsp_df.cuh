@@ -179,6 +179,27 @@ __device__ __forceinline__ df df_half_odd_centered(uint32_t x) {
     return df_scale(df_fast_two_sum(a, b), 4.656612873077392578125e-10f);
 }
 
+// An FP64 value as a double-float pair by integer operations (an FP64-to-FP32 conversion would
+// run on the narrow FP64 pipe): hi = x truncated to 24 significant bits, lo = the remaining 29
+// bits of the significand converted to FP32 (rounded to 24 bits) and scaled by an exact power
+// of two, so |x - (hi + lo)| < 2^-47 |x|, with 0 <= |lo| < ulp(hi), for 2^-74 <= |x| < 2^128.
+// Below 2^-74 the low part is dropped (absolute error under 2^-98) and below 2^-126 the value
+// is a signed zero: far under any kinematic scale of these events.
+__device__ __forceinline__ df df_from_double(double x) {
+    const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
+    const uint32_t bh = static_cast<uint32_t>(b >> 32);
+    const uint32_t sign = bh & 0x80000000u;
+    const int ef = static_cast<int>((bh >> 20) & 0x7FFu) - 896;  // FP32 biased exponent of hi
+    if (ef <= 0) return df{__uint_as_float(sign), 0.0f};
+    const float hi = __uint_as_float(sign | (static_cast<uint32_t>(ef) << 23) |
+                                     (static_cast<uint32_t>(b >> 29) & 0x7FFFFFu));
+    const int el = ef - 52;                                       // FP32 biased exponent of 2^(e - 52)
+    const float mag = el > 0 ? __fmul_rn(__uint2float_rn(static_cast<uint32_t>(b) & 0x1FFFFFFFu),
+                                         __uint_as_float(static_cast<uint32_t>(el) << 23))
+                             : 0.0f;
+    return df{hi, sign ? -mag : mag};
+}
+
 // x + f for an FP32 f with |f| <= |x.hi| (a correction term): FastTwoSum and renormalise.
 __device__ __forceinline__ df df_add_small(df x, float f) {
     const float s = __fadd_rn(x.hi, f);

@@ -367,17 +367,47 @@ static UwScratch* uw_scratch() {
 // Model evaluation on stored events: f_e = w_e |ME|^2(p_e), values and the deterministic
 // integral (the tile / segment / fold tree of the generated-event integral).
 // ------------------------------------------------------------------------------------
-template <typename R>
-__device__ __forceinline__ R pair_mass2(const R* __restrict__ ev, uint64_t ld, uint64_t e, int a, int b) {
-    using P = Prec<R>;
-    const R E = ev[(4 * a) * ld + e] + ev[(4 * b) * ld + e];
-    const R x = ev[(4 * a + 1) * ld + e] + ev[(4 * b + 1) * ld + e];
-    const R y = ev[(4 * a + 2) * ld + e] + ev[(4 * b + 2) * ld + e];
-    const R z = ev[(4 * a + 3) * ld + e] + ev[(4 * b + 3) * ld + e];
-    return P::fma_(E, E, -P::fma_(z, z, P::fma_(y, y, x * x)));
+// f = w |ME|^2 from one event's components c[a][k] (daughter a = 0..2, k = E, px, py, pz), both
+// evaluation kernels: FP32 events in FP32, FP64 events with K = double (native FP64) or
+// K = df: there the pair masses s = E^2 - p^2 and m0^2 - s stay in native FP64 (cancellations
+// that a narrow resonance amplifies several hundredfold: double-float there left ~1e-11 on
+// |ME|^2 near the phi(1020)), and the well-conditioned rest of |ME|^2 runs in double-float
+// from m0^2 - s split by integer operations.
+template <typename R, typename K>
+__device__ __forceinline__ R dalitz_value(const MEConsts& P, R we, const R (&c)[3][4]) {
+    using Q = Prec<R>;
+    R m2[2];
+#pragma unroll
+    for (int pr = 0; pr < 2; ++pr) {
+        R v[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) v[k] = c[pr][k] + c[pr + 1][k];
+        m2[pr] = Q::fma_(v[0], v[0], -Q::fma_(v[3], v[3], Q::fma_(v[2], v[2], v[1] * v[1])));
+    }
+    if constexpr (std::is_same<K, df>::value) {
+        const df xa = df_from_double(P.a_m2 - m2[0]), xb = df_from_double(P.b_m2 - m2[1]);
+        return we * to_w<df>(dalitz_2bw_x<df>(P, xa, xb));
+    } else {
+        return we * dalitz_2bw<R>(P, m2[0], m2[1]);
+    }
 }
 
-template <typename R, int ME>
+template <typename R, int ME, typename K>
+__device__ __forceinline__ R eval_event(const R* __restrict__ ev, uint64_t ld, const R* __restrict__ w,
+                                        const MEConsts& P, uint64_t e) {
+    const R we = w[e];
+    if constexpr (ME == HYDRA_ME_DALITZ_2BW) {
+        R c[3][4];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) c[a][k] = ev[static_cast<uint64_t>(4 * a + k) * ld + e];
+        return dalitz_value<R, K>(P, we, c);
+    }
+    return we;
+}
+
+template <typename R, int ME, typename K>
 __global__ void __launch_bounds__(256) evaluate_tiles(uint64_t nevents, const R* __restrict__ ev, uint64_t ld,
                                                       const R* __restrict__ w, const __grid_constant__ MEConsts P,
                                                       R* __restrict__ values, uint64_t tile_begin, uint64_t ntiles,
@@ -394,9 +424,7 @@ __global__ void __launch_bounds__(256) evaluate_tiles(uint64_t nevents, const R*
                 const uint64_t e = base + static_cast<uint64_t>(32 * (g * kGroupEvents + i) + lane);
                 if (e < nevents) {
                     const R we = w[e];
-                    R f = we;
-                    if constexpr (ME == HYDRA_ME_DALITZ_2BW)
-                        f = we * dalitz_2bw<R>(P, pair_mass2<R>(ev, ld, e, 0, 1), pair_mass2<R>(ev, ld, e, 1, 2));
+                    const R f = eval_event<R, ME, K>(ev, ld, w, P, e);
                     if (values) values[e] = f;
                     sf += f;
                     sf2 = Prec<R>::fma_(f, f, sf2);
@@ -454,16 +482,7 @@ struct Vec16<double> {
     }
 };
 
-template <typename R, int ME>
-__device__ __forceinline__ R eval_event(const R* __restrict__ ev, uint64_t ld, const R* __restrict__ w,
-                                        const MEConsts& P, uint64_t e) {
-    const R we = w[e];
-    if constexpr (ME == HYDRA_ME_DALITZ_2BW)
-        return we * dalitz_2bw<R>(P, pair_mass2<R>(ev, ld, e, 0, 1), pair_mass2<R>(ev, ld, e, 1, 2));
-    return we;
-}
-
-template <typename R, int ME>
+template <typename R, int ME, typename K>
 __global__ void __launch_bounds__(256) evaluate_tiles_vec(uint64_t nevents, const R* __restrict__ ev, uint64_t ld,
                                                           const R* __restrict__ w, const __grid_constant__ MEConsts P,
                                                           R* __restrict__ values, uint64_t tile_begin, uint64_t ntiles,
@@ -494,17 +513,12 @@ __global__ void __launch_bounds__(256) evaluate_tiles_vec(uint64_t nevents, cons
                             for (int k = 0; k < 4; ++k) V::get(ev + static_cast<uint64_t>(4 * a + k) * ld + e0, c[a][k]);
 #pragma unroll
                         for (int q = 0; q < W; ++q) {
-                            using Q = Prec<R>;
-                            R m2[2];
+                            R cq[3][4];
 #pragma unroll
-                            for (int pr = 0; pr < 2; ++pr) {
-                                const R E = c[pr][0][q] + c[pr + 1][0][q];
-                                const R x = c[pr][1][q] + c[pr + 1][1][q];
-                                const R y = c[pr][2][q] + c[pr + 1][2][q];
-                                const R z = c[pr][3][q] + c[pr + 1][3][q];
-                                m2[pr] = Q::fma_(E, E, -Q::fma_(z, z, Q::fma_(y, y, x * x)));
-                            }
-                            f[q] = we[q] * dalitz_2bw<R>(P, m2[0], m2[1]);
+                            for (int a = 0; a < 3; ++a)
+#pragma unroll
+                                for (int k = 0; k < 4; ++k) cq[a][k] = c[a][k][q];
+                            f[q] = dalitz_value<R, K>(P, we[q], cq);
                         }
                     } else {
 #pragma unroll
@@ -518,7 +532,7 @@ __global__ void __launch_bounds__(256) evaluate_tiles_vec(uint64_t nevents, cons
                         f[q] = R(0);
                         if (e0 + q < nevents) {
                             we[q] = w[e0 + q];
-                            f[q] = eval_event<R, ME>(ev, ld, w, P, e0 + q);
+                            f[q] = eval_event<R, ME, K>(ev, ld, w, P, e0 + q);
                             if (values) values[e0 + q] = f[q];
                         }
                     }
@@ -803,39 +817,37 @@ hydra_status hydra_phsp_evaluate(int n, uint64_t nevents, hydra_dtype dtype, hyd
     const bool vec = (reinterpret_cast<uintptr_t>(weights) % 16 == 0) &&
                      (!values || reinterpret_cast<uintptr_t>(values) % 16 == 0) &&
                      (!events || (reinterpret_cast<uintptr_t>(events) % 16 == 0 && ld % width == 0));
+    // FP64 events: |ME|^2 in double-float unless native FP64 arithmetic is selected
+    const bool native = g_fp64_arith.load() == HYDRA_FP64_NATIVE;
+    const bool dalitz = me == HYDRA_ME_DALITZ_2BW;
+    const void* kern = nullptr;
+    if (dtype == HYDRA_F32) {
+        if (vec) kern = dalitz ? reinterpret_cast<const void*>(&evaluate_tiles_vec<float, HYDRA_ME_DALITZ_2BW, float>)
+                               : reinterpret_cast<const void*>(&evaluate_tiles_vec<float, HYDRA_ME_FLAT, float>);
+        else kern = dalitz ? reinterpret_cast<const void*>(&evaluate_tiles<float, HYDRA_ME_DALITZ_2BW, float>)
+                           : reinterpret_cast<const void*>(&evaluate_tiles<float, HYDRA_ME_FLAT, float>);
+    } else if (!dalitz) {
+        kern = vec ? reinterpret_cast<const void*>(&evaluate_tiles_vec<double, HYDRA_ME_FLAT, double>)
+                   : reinterpret_cast<const void*>(&evaluate_tiles<double, HYDRA_ME_FLAT, double>);
+    } else if (native) {
+        kern = vec ? reinterpret_cast<const void*>(&evaluate_tiles_vec<double, HYDRA_ME_DALITZ_2BW, double>)
+                   : reinterpret_cast<const void*>(&evaluate_tiles<double, HYDRA_ME_DALITZ_2BW, double>);
+    } else {
+        kern = vec ? reinterpret_cast<const void*>(&evaluate_tiles_vec<double, HYDRA_ME_DALITZ_2BW, df>)
+                   : reinterpret_cast<const void*>(&evaluate_tiles<double, HYDRA_ME_DALITZ_2BW, df>);
+    }
     for (uint64_t t0 = 0; t0 < ntiles; t0 += kChunkTiles) {
         const uint64_t nt = ntiles - t0 < kChunkTiles ? ntiles - t0 : kChunkTiles;
         const uint64_t need = (nt * 32 + 255) / 256;
         const unsigned grid = static_cast<unsigned>(need < static_cast<uint64_t>(sms) * 8 ? need : static_cast<uint64_t>(sms) * 8);
-        if (vec && dtype == HYDRA_F32) {
-            if (me == HYDRA_ME_DALITZ_2BW)
-                evaluate_tiles_vec<float, HYDRA_ME_DALITZ_2BW><<<grid, 256, 0, cs>>>(nevents, static_cast<const float*>(events), ld,
-                    static_cast<const float*>(weights), P, static_cast<float*>(values), t0, nt, s->tiles);
-            else
-                evaluate_tiles_vec<float, HYDRA_ME_FLAT><<<grid, 256, 0, cs>>>(nevents, static_cast<const float*>(events), ld,
-                    static_cast<const float*>(weights), P, static_cast<float*>(values), t0, nt, s->tiles);
-        } else if (vec) {
-            if (me == HYDRA_ME_DALITZ_2BW)
-                evaluate_tiles_vec<double, HYDRA_ME_DALITZ_2BW><<<grid, 256, 0, cs>>>(nevents, static_cast<const double*>(events), ld,
-                    static_cast<const double*>(weights), P, static_cast<double*>(values), t0, nt, s->tiles);
-            else
-                evaluate_tiles_vec<double, HYDRA_ME_FLAT><<<grid, 256, 0, cs>>>(nevents, static_cast<const double*>(events), ld,
-                    static_cast<const double*>(weights), P, static_cast<double*>(values), t0, nt, s->tiles);
-        } else if (dtype == HYDRA_F32) {
-            if (me == HYDRA_ME_DALITZ_2BW)
-                evaluate_tiles<float, HYDRA_ME_DALITZ_2BW><<<grid, 256, 0, cs>>>(nevents, static_cast<const float*>(events), ld,
-                    static_cast<const float*>(weights), P, static_cast<float*>(values), t0, nt, s->tiles);
-            else
-                evaluate_tiles<float, HYDRA_ME_FLAT><<<grid, 256, 0, cs>>>(nevents, static_cast<const float*>(events), ld,
-                    static_cast<const float*>(weights), P, static_cast<float*>(values), t0, nt, s->tiles);
-        } else {
-            if (me == HYDRA_ME_DALITZ_2BW)
-                evaluate_tiles<double, HYDRA_ME_DALITZ_2BW><<<grid, 256, 0, cs>>>(nevents, static_cast<const double*>(events), ld,
-                    static_cast<const double*>(weights), P, static_cast<double*>(values), t0, nt, s->tiles);
-            else
-                evaluate_tiles<double, HYDRA_ME_FLAT><<<grid, 256, 0, cs>>>(nevents, static_cast<const double*>(events), ld,
-                    static_cast<const double*>(weights), P, static_cast<double*>(values), t0, nt, s->tiles);
-        }
+        uint64_t nev = nevents, ldv = ld, tb = t0, ntv = nt;
+        const void* evp = events;
+        const void* wp = weights;
+        void* vp = values;
+        TileSums* tp = s->tiles;
+        void* args[] = {&nev, const_cast<void**>(&evp), &ldv, const_cast<void**>(&wp), &P, &vp, &tb, &ntv, &tp};
+        const cudaError_t lerr = cudaLaunchKernel(kern, dim3(grid), dim3(256), args, 0, cs);
+        if (lerr != cudaSuccess) return cuda_fail(lerr, "evaluate launch");
         const uint64_t ns = (nt + kSegTiles - 1) / kSegTiles;
         eval_reduce_segments<<<static_cast<unsigned>(ns), kSegBlock, 0, cs>>>(s->tiles, nt, t0 / kSegTiles, s->segs);
     }

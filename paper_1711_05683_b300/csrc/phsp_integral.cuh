@@ -71,11 +71,13 @@ __device__ __forceinline__ typename Prec<R>::W to_w(R v) {
     else return v;
 }
 
-// |BW(s12; a) + c BW(s23; b)|^2, BW(s) = (m0^2 - s + i m0 G) / ((m0^2 - s)^2 + (m0 G)^2).
+// |BW(s12; a) + c BW(s23; b)|^2, BW(s) = (m0^2 - s + i m0 G) / ((m0^2 - s)^2 + (m0 G)^2), from
+// xa = m0a^2 - s12 and xb = m0b^2 - s23 (near a narrow resonance the subtraction is the
+// ill-conditioned step; what follows is well conditioned).
 template <typename R>
-__device__ __forceinline__ R dalitz_2bw(const MEConsts& P, R s12, R s23) {
-    const R xa = me_param<R>(P.a_m2, P.a_m2f, P.a_m2lo) - s12, ya = me_param<R>(P.a_mg, P.a_mgf, P.a_mglo);
-    const R xb = me_param<R>(P.b_m2, P.b_m2f, P.b_m2lo) - s23, yb = me_param<R>(P.b_mg, P.b_mgf, P.b_mglo);
+__device__ __forceinline__ R dalitz_2bw_x(const MEConsts& P, R xa, R xb) {
+    const R ya = me_param<R>(P.a_mg, P.a_mgf, P.a_mglo);
+    const R yb = me_param<R>(P.b_mg, P.b_mgf, P.b_mglo);
     using Q = Prec<R>;
     const R ia = Q::rcp(Q::fma_(xa, xa, ya * ya));
     const R ib = Q::rcp(Q::fma_(xb, xb, yb * yb));
@@ -83,6 +85,11 @@ __device__ __forceinline__ R dalitz_2bw(const MEConsts& P, R s12, R s23) {
     const R re = Q::fma_(xa, ia, Q::fma_(cr, xb, -(ci * yb)) * ib);
     const R im = Q::fma_(ya, ia, Q::fma_(cr, yb, ci * xb) * ib);
     return Q::fma_(re, re, im * im);
+}
+
+template <typename R>
+__device__ __forceinline__ R dalitz_2bw(const MEConsts& P, R s12, R s23) {
+    return dalitz_2bw_x<R>(P, me_param<R>(P.a_m2, P.a_m2f, P.a_m2lo) - s12, me_param<R>(P.b_m2, P.b_m2f, P.b_m2lo) - s23);
 }
 
 // The N = 3 integrand from the event's five draws without its 4-vectors.  Same event as

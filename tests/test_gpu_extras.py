@@ -135,9 +135,20 @@ def test_unweighting_sample_maximum_any_alignment(dtype):
     assert torch.equal(full[full >= 1], part + 1)
 
 
-def test_evaluate_on_oracle_events_fp64():
+@pytest.mark.parametrize("arith", ["double-float", "native"])
+def test_evaluate_on_oracle_events_fp64(arith):
     """The evaluation kernel on the oracle's own events (uploaded) reproduces the oracle's
-    values and sums; on GPU-generated events it reproduces the generated-event integral."""
+    values and sums; on GPU-generated events it reproduces the generated-event integral; in
+    double-float (the FP64 components split by integer operations) and in native FP64."""
+    saved = hp.get_fp64_arith()
+    hp.set_fp64_arith(hp.FP64_NATIVE if arith == "native" else hp.FP64_DOUBLE_FLOAT)
+    try:
+        _evaluate_on_oracle_events_fp64()
+    finally:
+        hp.set_fp64_arith(saved)
+
+
+def _evaluate_on_oracle_events_fp64():
     d = workloads.D0_DALITZ
     nev = 3 * 2048 * 5 + 77
     p, w = oracle.generate(d["M"], d["masses"], nev, seed=12)
