@@ -181,6 +181,11 @@ hydra_status hydra_phsp_unweight(int n, uint64_t nevents, uint64_t seed, uint64_
  *   values       device array receiving f_e (dtype), or NULL
  *   result       host: mean, variance of the mean and sums of f and w, reduced in the fixed
  *                tile / segment order of hydra_phsp_integrate (deterministic)
+ * With events, weights and values 16-byte aligned and ld a multiple of 4 (FP32) or 2 (FP64)
+ * a lane reads runs of consecutive events with 16-byte loads; otherwise one event per lane
+ * (the same values; the sums differ by rounding in their grouping).  FP64 events: the pair
+ * masses and m0^2 - s in FP64, the rest of |ME|^2 in double-float (hydra_set_fp64_arith
+ * selects FP64 throughout).
  * Blocking.  Errors: UNSUPPORTED_N, INVALID_ARG, OOM, CUDA.
  */
 hydra_status hydra_phsp_evaluate(int n, uint64_t nevents, hydra_dtype dtype, hydra_me_id me,
@@ -236,7 +241,9 @@ hydra_status hydra_phsp_gather(int n, hydra_dtype dtype, const void *src, uint64
  * seed and event_offset, computed on the device and never stored).
  *
  *   kin_dtype     HYDRA_F32: FP32 kinematics and matrix element, FP64 accumulation;
- *                 HYDRA_F64: FP64 throughout.
+ *                 HYDRA_F64: FP64-accurate kinematics and matrix element (double-float by
+ *                 default, FP64 instructions after hydra_set_fp64_arith(HYDRA_FP64_NATIVE)),
+ *                 f, w and all sums in FP64.
  *   me, params, nparams  matrix element id and its parameters (host array).
  *   result        host struct that receives the sums, mean and variance of the mean.
  *
