@@ -97,7 +97,8 @@ __device__ __forceinline__ R dalitz_2bw(const MEConsts& P, R s12, R s23) {
 // momenta p2 (parent -> (12) + 3) and p1 ((12) -> 1 + 2) and the weight (p2 p1) C_3; draws
 // (1, 2) and (3, 4) are the directions n_a of subsystem (12) in the parent frame and n_b of
 // daughter 1 in the (12) frame, both in the parent's axes (pure boosts), so the boost gives
-//   E1 = (Q0 E1* + p2 p1 cos alpha) / M_2,  Q0 = sqrt(p2^2 + M_2^2),  E1* = sqrt(p1^2 + m1^2),
+//   E1 = (Q0 E1* + p2 p1 cos alpha) / M_2,  Q0 = sqrt(p2^2 + M_2^2),  E1* = sqrt(p1^2 + m1^2)
+//   (both energies taken from the gap factors of lambda, without a square root),
 //   cos alpha = n_a . n_b = c_a c_b + s_a s_b cos(phi_a - phi_b),
 // with phi_a - phi_b from the integer difference of the two phi draws.  Then s12 = M_2^2 and
 // s23 = M^2 + m1^2 - 2 M E1 as in the general path; one cosine instead of two sin/cos pairs
@@ -117,17 +118,22 @@ __device__ __forceinline__ void dalitz3_point(const DecayConsts& C, const MECons
     const R gap2 = Q::half_odd(~y) * Ts;  // T (1 - r)
     const R gap1 = Q::half_odd(y) * Ts;   // T r
     const R twoM2 = Q::scale(M2, 2.0f), twom3 = Q::scale(m3, 2.0f);
-    const R lam2 = ((gap2 * (gap2 + twoM2)) * (gap2 + twom3)) * ((gap2 + twoM2) + twom3);
+    const R a2 = gap2 + twoM2, g2 = gap2 * (gap2 + twom3);  // g2 = Delta2 (Delta2 + 2 m3)
+    const R lam2 = (g2 * a2) * (a2 + twom3);
     const R twom1 = Q::scale(m1, 2.0f), twom2 = Q::scale(m2, 2.0f);
-    const R lam1 = ((gap1 * (gap1 + twom1)) * (gap1 + twom2)) * ((gap1 + twom1) + twom2);
+    const R a1 = gap1 + twom1, g1 = gap1 * (gap1 + twom2);  // g1 = Delta1 (Delta1 + 2 m2)
+    const R lam1 = (g1 * a1) * (a1 + twom2);
     const R invM2 = Q::rcp(M2);
-    const R p2 = Q::sqrt_(lam2) * Q::scale(Q::rcp(M), 0.5f);
-    const R p1 = Q::sqrt_(lam1) * Q::scale(invM2, 0.5f);
+    const R halfInvM = Q::scale(Q::rcp(M), 0.5f), halfInvM2 = Q::scale(invM2, 0.5f);
+    const R p2 = Q::sqrt_(lam2) * halfInvM;
+    const R p1 = Q::sqrt_(lam1) * halfInvM2;
     const W w = Q::w_final(Q::w_mul(Q::w_mul(Q::w_one(), p2), p1), C);
     const R ssq = (Q::one_minus_cos(xca) * Q::one_plus_cos(xca)) * (Q::one_minus_cos(xcb) * Q::one_plus_cos(xcb));
     const R cos_alpha = Q::fma_(Q::cos_of(xca), Q::cos_of(xcb), Q::sqrt_(ssq) * Q::cos_2pi_diff(xpa, xpb));
-    const R Q0 = Q::sqrt_(Q::fma_(p2, p2, M2 * M2));
-    const R E1s = Q::sqrt_(Q::fma_(p1, p1, m1 * m1));
+    // two-body energies from the gap factors of lambda (as in the generator):
+    // Q0 = (M^2 + M2^2 - m3^2) / (2 M) = M2 + g2 / (2 M), E1* = (M2^2 + m1^2 - m2^2) / (2 M2) = m1 + g1 / (2 M2)
+    const R Q0 = Q::fma_(g2, halfInvM, M2);
+    const R E1s = Q::fma_(g1, halfInvM2, m1);
     const R E1 = Q::fma_(Q0, E1s, (p2 * p1) * cos_alpha) * invM2;
     const R s12 = M2 * M2;
     const R s23 = Q::fma_(R(-2) * M, E1, Q::fma_(M, M, Q::m2(C, 0)));
