@@ -170,6 +170,41 @@ __device__ __forceinline__ double vegas_event(const DecayConsts& C, const uint64
     return P::w_final(w, C);
 }
 
+// The N = 3 event of the same uniforms in closed form (the integrand's construction): the
+// weight, M2 and the lab energy E1 of daughter 1 without the event's 4-vectors.  Step 1 (parent
+// -> (12) + 3): gap T (1 - u0), momentum p2, direction n_a from (U1, U2); step 2 ((12) -> 1 + 2):
+// gap T u0, momentum p1, direction n_b from (U3, U4).  With the two-body energies from the gap
+// factors of lambda, Q0 = M2 + D2 (D2 + 2 m3) / (2 M) and E1* = m1 + D1 (D1 + 2 m2) / (2 M2),
+// the pure boost gives E1 = (Q0 E1* + p2 p1 n_a.n_b) / M2 with
+// n_a.n_b = c_a c_b + s_a s_b cos(phi_a - phi_b), the angle difference from U2 - U4 (mod 2^64).
+template <typename R>
+__device__ __forceinline__ double vegas_event3(const DecayConsts& C, const uint64_t (&U)[5], R& E1, R& M2) {
+    using P = Prec<R>;
+    using A = VegasArith<R>;
+    const R M = P::M(C), T = A::T(C);
+    const R m1 = P::m(C, 0), m2 = P::m(C, 1), m3 = P::m(C, 2);
+    M2 = P::fma_(A::frac(U[0]), T, P::mu(C, 1));
+    const R gap2 = A::comp(U[0]) * T, gap1 = A::frac(U[0]) * T;
+    const R twoM2 = P::scale(M2, 2.0f), twom3 = P::scale(m3, 2.0f);
+    const R a2 = gap2 + twoM2, g2 = gap2 * (gap2 + twom3);
+    const R twom1 = P::scale(m1, 2.0f), twom2 = P::scale(m2, 2.0f);
+    const R a1 = gap1 + twom1, g1 = gap1 * (gap1 + twom2);
+    const R invM2 = P::rcp(M2);
+    const R halfInvM = P::scale(P::rcp(M), 0.5f), halfInvM2 = P::scale(invM2, 0.5f);
+    const R p2 = P::sqrt_((g2 * a2) * (a2 + twom3)) * halfInvM;
+    const R p1 = P::sqrt_((g1 * a1) * (a1 + twom2)) * halfInvM2;
+    const R ca = A::frac(U[1]) - A::comp(U[1]), cb = A::frac(U[3]) - A::comp(U[3]);
+    const R sab2 = (P::scale(A::comp(U[1]), 2.0f) * P::scale(A::frac(U[1]), 2.0f)) *
+                   (P::scale(A::comp(U[3]), 2.0f) * P::scale(A::frac(U[3]), 2.0f));
+    R sd, cd;
+    A::sincos(U[2] - U[4], &sd, &cd);
+    const R cos_alpha = P::fma_(ca, cb, P::sqrt_(sab2) * cd);
+    const R Q0 = P::fma_(g2, halfInvM, M2);
+    const R E1s = P::fma_(g1, halfInvM2, m1);
+    E1 = P::fma_(Q0, E1s, (p2 * p1) * cos_alpha) * invM2;
+    return P::w_final(P::w_mul(P::w_mul(P::w_one(), p2), p1), C);
+}
+
 // |BW(s12; a) + c BW(s23; b)|^2 in arithmetic R (the integral's formula).
 template <typename R>
 __device__ __forceinline__ R vegas_dalitz(const VegasME& PM, R s12, R s23) {
@@ -250,7 +285,9 @@ __global__ void __launch_bounds__(kVegasBlock) vegas_eval(const __grid_constant_
 #pragma unroll
                     for (int q = 0; q < (D + 3) / 4; ++q) bins[static_cast<uint64_t>(q) * calls + s] = packed[q];
                     R E1, M2;
-                    const double w = vegas_event<N, R>(C, U, E1, M2);
+                    double w;
+                    if constexpr (ME == HYDRA_ME_DALITZ_2BW && N == 3) w = vegas_event3<R>(C, U, E1, M2);
+                    else w = vegas_event<N, R>(C, U, E1, M2);
                     double me2 = 1.0;
                     if constexpr (ME == HYDRA_ME_DALITZ_2BW) {
                         // s12 = M_2^2; s23 = (P - p1)^2 = M^2 + m1^2 - 2 M E1
