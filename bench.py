@@ -597,7 +597,7 @@ def run_vegas(calls: int = 100_000_000, iterations: int = 10, reps: int = 3,
               cases=("dalitz", "flat10")) -> dict:
     """Points/s of hp.vegas (FP64, double-float arithmetic, 100 bins per dimension): the
     Dalitz matrix element (N=3, `calls` points per iteration) and the flat N=10 integrand
-    (calls/10 points); the whole call timed (all iterations, host refinement included), best
+    (calls/10 points); the whole call timed (all iterations and grid refinements), best
     of `reps` after one warm-up, with the issue-limit fraction of its kernels."""
     import torch
     import paper_1711_05683_b300 as hp

@@ -217,8 +217,8 @@ hydra_status hydra_phsp_evaluate(int n, uint64_t nevents, hydra_dtype dtype, hyd
  *   result       host double[3]: combined estimate, its standard deviation, chi^2 per degree
  *                of freedom of the combined iterations (0 for one)
  *   grid_out     host double[(3n-4)(bins+1)] receiving the final grid edges, or NULL
- * Blocking (one host synchronisation per iteration).  Errors: UNSUPPORTED_N, BELOW_THRESHOLD,
- * INVALID_ARG, OOM, CUDA.
+ * Blocking (one host synchronisation per call: the grids are refined on the device).
+ * Errors: UNSUPPORTED_N, BELOW_THRESHOLD, INVALID_ARG, OOM, CUDA.
  */
 hydra_status hydra_phsp_vegas(double M, int n, const double *masses, uint64_t seed, hydra_me_id me,
                               const double *params, int nparams, uint64_t calls, int iterations,

@@ -15,7 +15,9 @@
 //               segment tree, with tiles of 512 points); the largest f^2.
 //   vegas_hist  per-bin sums of f^2 in 64-bit fixed point (order-independent integer adds)
 //               from the stored values and bins.
-//   host        estimate and variance; refinement of every dimension.
+//   vegas_refine  refinement of every dimension's grid and cells (one block per dimension).
+//   host        the per-iteration estimates and variances (copied back without waiting) and
+//               their combination, after one synchronisation at the end.
 //
 // Grid arithmetic.  With P = (2x + 1) K (< 2^41), the bin is b = floor(y K) = P >> 33 and the
 // position inside it is y K - b = rho 2^-33 with rho = P mod 2^33, both exact (y K has at
@@ -402,38 +404,75 @@ static const void* vegas_eval_for(int n) {
     }
 }
 
-// Grid refinement of one dimension (Lepage's rule): smooth the bin sums (1,2,1)/4 inside,
-// (1,1)/2 at the ends; importance weight ((r - 1)/ln r)^alpha of each bin's share r; move the
-// edges so that every new bin carries an equal share of the total weight.
-static void refine_dimension(double* g, const double* dsum, int K, double alpha) {
-    if (K == 1) return;
-    std::vector<double> sm(K), wt(K), ng(K + 1);
-    sm[0] = (dsum[0] + dsum[1]) / 2.0;
-    for (int i = 1; i < K - 1; ++i) sm[i] = (dsum[i - 1] + 2.0 * dsum[i] + dsum[i + 1]) / 4.0;
-    sm[K - 1] = (dsum[K - 2] + dsum[K - 1]) / 2.0;
-    double tot = 0.0;
-    for (int i = 0; i < K; ++i) tot += sm[i];
-    if (!(tot > 0.0)) return;
-    double wsum = 0.0;
-    for (int i = 0; i < K; ++i) {
-        const double r = sm[i] / tot;
-        wt[i] = (r > 0.0 && r < 1.0) ? std::pow((r - 1.0) / std::log(r), alpha) : (r >= 1.0 ? 1.0 : 0.0);
-        wsum += wt[i];
+// Refinement of every dimension on the device (one block per dimension): smoothed bin sums (1,2,1)/4 inside and (1,1)/2 at the ends,
+// weights ((r - 1)/ln r)^alpha of each bin's share r, and new edges at equal shares of the
+// total weight, linear inside a bin; then the dimension's fixed-point cells.  The sums and the
+// redistribution run on one thread in bin order, the weights on one thread per bin, so the
+// grid is the host rule's to the last bit of pow and log.  No refinement when K = 1 or all
+// sums are zero.  (On the host this took ~0.15 ms per iteration at 26 x 100 bins, plus a
+// synchronisation: a tenth of a 1e7-point N = 10 iteration.)
+__global__ void __launch_bounds__(256) vegas_refine(int K, double alpha, const unsigned long long* __restrict__ hist,
+                                                    double* __restrict__ grid, VegasCell* __restrict__ cells) {
+    __shared__ double sm[256], wt[256], g[257], ng[257];
+    __shared__ double tot_s;
+    const int d = blockIdx.x;
+    const unsigned long long* hd = hist + static_cast<size_t>(d) * K;
+    double* gd = grid + static_cast<size_t>(d) * (K + 1);
+    VegasCell* cd = cells + static_cast<size_t>(d) * (K + 1);
+    for (int t = threadIdx.x; t <= K; t += blockDim.x) g[t] = gd[t];
+    if (K > 1) {
+        for (int t = threadIdx.x; t < K; t += blockDim.x) {
+            const double c = static_cast<double>(hd[t]);
+            if (t == 0) sm[t] = (c + static_cast<double>(hd[1])) / 2.0;
+            else if (t == K - 1) sm[t] = (static_cast<double>(hd[K - 2]) + c) / 2.0;
+            else sm[t] = (static_cast<double>(hd[t - 1]) + 2.0 * c + static_cast<double>(hd[t + 1])) / 4.0;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double tot = 0.0;
+            for (int t = 0; t < K; ++t) tot += sm[t];
+            tot_s = tot;
+        }
+        __syncthreads();
+        const double tot = tot_s;
+        if (tot > 0.0) {
+            for (int t = threadIdx.x; t < K; t += blockDim.x) {
+                const double r = sm[t] / tot;
+                wt[t] = (r > 0.0 && r < 1.0) ? pow((r - 1.0) / log(r), alpha) : (r >= 1.0 ? 1.0 : 0.0);
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                double wsum = 0.0;
+                for (int t = 0; t < K; ++t) wsum += wt[t];
+                if (wsum > 0.0) {
+                    const double share = wsum / K;
+                    double acc = 0.0;
+                    int j = 0;
+                    ng[0] = 0.0;
+                    for (int i = 1; i < K; ++i) {
+                        const double need = share * i;
+                        while (j < K - 1 && acc + wt[j] < need) acc += wt[j++];
+                        double frac = wt[j] > 0.0 ? (need - acc) / wt[j] : 0.0;
+                        frac = frac < 0.0 ? 0.0 : (frac > 1.0 ? 1.0 : frac);
+                        ng[i] = g[j] + frac * (g[j + 1] - g[j]);
+                    }
+                    ng[K] = 1.0;
+                    for (int i = 0; i <= K; ++i) g[i] = ng[i];
+                }
+            }
+        }
+        __syncthreads();
     }
-    if (!(wsum > 0.0)) return;
-    const double share = wsum / K;
-    double acc = 0.0;
-    int j = 0;
-    ng[0] = 0.0;
-    for (int i = 1; i < K; ++i) {
-        const double need = share * i;
-        while (j < K - 1 && acc + wt[j] < need) acc += wt[j++];
-        double frac = wt[j] > 0.0 ? (need - acc) / wt[j] : 0.0;
-        frac = frac < 0.0 ? 0.0 : (frac > 1.0 ? 1.0 : frac);
-        ng[i] = g[j] + frac * (g[j + 1] - g[j]);
+    for (int t = threadIdx.x; t <= K; t += blockDim.x) {
+        gd[t] = g[t];
+        if (t < K) {
+            cd[t].G = g[t] < 1.0 ? static_cast<uint64_t>(ldexp(g[t], 64)) : ~uint64_t{0};  // exact below 2^64
+            cd[t].J = K * (g[t + 1] - g[t]);
+        } else {
+            cd[t].G = ~uint64_t{0};
+            cd[t].J = 0.0;
+        }
     }
-    ng[K] = 1.0;
-    for (int i = 0; i <= K; ++i) g[i] = ng[i];
 }
 
 // Fixed-point cells of one dimension's edges g[0..K] (K + 1 cells).
@@ -456,9 +495,12 @@ struct VegasScratch {
     uint64_t fcap = 0;
     int bins_d = 0;
     VegasCell* cells = nullptr;
+    double* grid = nullptr;              // [D][K+1] edges (refined on the device)
     unsigned long long* hist = nullptr;  // [D*K] bin sums, the largest f^2 (as bits), tile counters
     hydra_integral* d_res = nullptr;
     void* h_pin = nullptr;               // pinned: result, histogram, cells
+    hydra_integral* h_res_all = nullptr; // pinned: every iteration's result
+    int res_cap = 0;
 };
 static std::mutex g_vg_mu;
 static std::vector<VegasScratch*> g_vg;
@@ -486,9 +528,11 @@ void release_vegas_scratch() {
         if (s->fvals) cudaFree(s->fvals);
         if (s->bins) cudaFree(s->bins);
         if (s->cells) cudaFree(s->cells);
+        if (s->grid) cudaFree(s->grid);
         if (s->hist) cudaFree(s->hist);
         if (s->d_res) cudaFree(s->d_res);
         if (s->h_pin) cudaFreeHost(s->h_pin);
+        if (s->h_res_all) cudaFreeHost(s->h_res_all);
         delete s;
         g_vg[d] = nullptr;
     }
@@ -539,6 +583,7 @@ hydra_status hydra_phsp_vegas(double M, int n, const double* masses, uint64_t se
     if (!s->tiles) {
         if (cudaMalloc(&s->tiles, kVegasChunkTiles * sizeof(TileSums)) != cudaSuccess ||
             cudaMalloc(&s->cells, cell_bytes) != cudaSuccess ||
+            cudaMalloc(&s->grid, static_cast<size_t>(kVegasMaxCells + kVegasMaxD) * sizeof(double)) != cudaSuccess ||
             cudaMalloc(&s->hist, hist_words * sizeof(unsigned long long)) != cudaSuccess ||
             cudaMalloc(&s->d_res, sizeof(hydra_integral)) != cudaSuccess ||
             cudaMallocHost(&s->h_pin, sizeof(hydra_integral) + hist_words * sizeof(unsigned long long) + cell_bytes) !=
@@ -575,6 +620,16 @@ hydra_status hydra_phsp_vegas(double M, int n, const double* masses, uint64_t se
         s->fcap = cap;
         s->bins_d = dcap;
     }
+    if (iterations > s->res_cap) {
+        if (s->h_res_all) cudaFreeHost(s->h_res_all);
+        s->h_res_all = nullptr;
+        s->res_cap = 0;
+        if (cudaMallocHost(&s->h_res_all, static_cast<size_t>(iterations) * sizeof(hydra_integral)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(HYDRA_ERR_OOM, "VEGAS results (%d iterations)", iterations);
+        }
+        s->res_cap = iterations;
+    }
     const size_t smem = static_cast<size_t>(D) * (K + 1) * sizeof(VegasCell);
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(cell_bytes));
     if (err != cudaSuccess) return cuda_fail(err, "VEGAS shared-memory limit");
@@ -587,22 +642,23 @@ hydra_status hydra_phsp_vegas(double M, int n, const double* masses, uint64_t se
     for (int d = 0; d < D; ++d)
         for (int b = 0; b <= K; ++b) g[static_cast<size_t>(d) * (K + 1) + b] = static_cast<double>(b) / K;
     cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
-    hydra_integral* h_res = static_cast<hydra_integral*>(s->h_pin);
     unsigned long long* h_hist = reinterpret_cast<unsigned long long*>(static_cast<char*>(s->h_pin) + sizeof(hydra_integral));
     VegasCell* h_cells = reinterpret_cast<VegasCell*>(h_hist + hist_words);
     unsigned long long* d_max = s->hist + kVegasMaxCells;
     int lg = 0;
     while ((uint64_t{1} << lg) < calls) ++lg;
     const double qnum = std::ldexp(1.0, 62 - lg);
-    double sw = 0.0, swi = 0.0, swi2 = 0.0;
-    std::vector<double> dsum(K);
+    // the uniform grid and its cells; later grids are refined on the device
+    for (int d = 0; d < D; ++d)
+        grid_cells(&g[static_cast<size_t>(d) * (K + 1)], K, h_cells + static_cast<size_t>(d) * (K + 1));
+    err = cudaMemcpyAsync(s->cells, h_cells, smem, cudaMemcpyHostToDevice, cs);
+    if (err == cudaSuccess)
+        err = cudaMemcpyAsync(s->grid, g.data(), g.size() * sizeof(double), cudaMemcpyHostToDevice, cs);
+    if (err != cudaSuccess) return cuda_fail(err, "VEGAS grid upload");
     for (int it = 0; it < iterations; ++it) {
         const uint32_t stream_id = static_cast<uint32_t>(it + 1);
-        for (int d = 0; d < D; ++d)
-            grid_cells(&g[static_cast<size_t>(d) * (K + 1)], K, h_cells + static_cast<size_t>(d) * (K + 1));
-        err = cudaMemcpyAsync(s->cells, h_cells, smem, cudaMemcpyHostToDevice, cs);
-        if (err == cudaSuccess) err = cudaMemsetAsync(s->hist, 0, hist_words * sizeof(unsigned long long), cs);
-        if (err != cudaSuccess) return cuda_fail(err, "VEGAS grid upload");
+        err = cudaMemsetAsync(s->hist, 0, hist_words * sizeof(unsigned long long), cs);
+        if (err != cudaSuccess) return cuda_fail(err, "VEGAS histogram reset");
         for (uint64_t t0 = 0; t0 < ntiles; t0 += kVegasChunkTiles) {
             const uint64_t nt = ntiles - t0 < kVegasChunkTiles ? ntiles - t0 : kVegasChunkTiles;
             const uint64_t need = (nt * 32 + kVegasBlock - 1) / kVegasBlock;
@@ -639,25 +695,25 @@ hydra_status hydra_phsp_vegas(double M, int n, const double* masses, uint64_t se
             err = cudaLaunchKernel(vegas_hist_for(n), dim3(hgrid), dim3(kVegasBlock), hargs,
                                    static_cast<size_t>(D) * K * sizeof(unsigned long long), cs);
             if (err != cudaSuccess) return cuda_fail(err, "VEGAS histogram launch");
+            vegas_refine<<<static_cast<unsigned>(D), 256, 0, cs>>>(K, alpha, s->hist, s->grid, s->cells);
         }
         err = cudaGetLastError();
-        if (err == cudaSuccess) err = cudaMemcpyAsync(h_res, s->d_res, sizeof(hydra_integral), cudaMemcpyDeviceToHost, cs);
-        if (err == cudaSuccess && it < iterations - 1)
-            err = cudaMemcpyAsync(h_hist, s->hist, static_cast<size_t>(D) * K * sizeof(unsigned long long), cudaMemcpyDeviceToHost, cs);
-        if (err == cudaSuccess) err = cudaStreamSynchronize(cs);
+        if (err == cudaSuccess)
+            err = cudaMemcpyAsync(s->h_res_all + it, s->d_res, sizeof(hydra_integral), cudaMemcpyDeviceToHost, cs);
         if (err != cudaSuccess) return cuda_fail(err, "VEGAS iteration");
-        est[it] = h_res->mean;
-        var[it] = h_res->var_mean;
+    }
+    err = cudaStreamSynchronize(cs);
+    if (err == cudaSuccess && grid_out)
+        err = cudaMemcpy(grid_out, s->grid, g.size() * sizeof(double), cudaMemcpyDeviceToHost);
+    if (err != cudaSuccess) return cuda_fail(err, "VEGAS iterations");
+    double sw = 0.0, swi = 0.0, swi2 = 0.0;
+    for (int it = 0; it < iterations; ++it) {
+        est[it] = s->h_res_all[it].mean;
+        var[it] = s->h_res_all[it].var_mean;
         if (it >= skip && var[it] > 0.0) {
             sw += 1.0 / var[it];
             swi += est[it] / var[it];
             swi2 += est[it] * est[it] / var[it];
-        }
-        if (it < iterations - 1) {
-            for (int d = 0; d < D; ++d) {
-                for (int b = 0; b < K; ++b) dsum[b] = static_cast<double>(h_hist[static_cast<size_t>(d) * K + b]);
-                refine_dimension(&g[static_cast<size_t>(d) * (K + 1)], dsum.data(), K, alpha);
-            }
         }
     }
     const double res = sw > 0.0 ? swi / sw : est[iterations - 1];
@@ -665,7 +721,6 @@ hydra_status hydra_phsp_vegas(double M, int n, const double* masses, uint64_t se
     result[0] = res;
     result[1] = sw > 0.0 ? 1.0 / std::sqrt(sw) : std::sqrt(var[iterations - 1]);
     result[2] = used > 1 ? (swi2 - res * res * sw) / (used - 1) : 0.0;
-    if (grid_out) std::memcpy(grid_out, g.data(), g.size() * sizeof(double));
     return HYDRA_OK;
 }
 
