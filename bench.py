@@ -636,8 +636,9 @@ def run_vegas(calls: int = 100_000_000, iterations: int = 10, reps: int = 3,
 def run_serve_workload(duration_s: float = 30.0, rate_hz: float = 2000.0) -> dict:
     """Poisson stream (mean rate_hz) of generate (N 2..8, 1e3..1e6 events, float32 out to
     pinned host memory) and Dalitz integrate (1e5..1e8 events) requests, 50/50, served by
-    the continuous-batching server and by one-at-a-time plain calls; p50/p99 latency from
-    arrival to result in host memory, and events/s."""
+    the continuous-batching server (its loop in Python, and the same policy with the loop in
+    C++) and by one-at-a-time plain calls; p50/p99 latency from arrival to result in host
+    memory, and events/s."""
     import torch
     from paper_1711_05683_b300 import serve
     reqs = workloads.serve_stream(rate_hz=rate_hz, duration_s=duration_s)
@@ -649,6 +650,10 @@ def run_serve_workload(duration_s: float = 30.0, rate_hz: float = 2000.0) -> dic
     res_b = srv.run(reqs)
     srv.close()
     torch.cuda.synchronize()
+    nat = serve.NativeServer()  # the same policy with the loop in C++
+    nat.run(warm)
+    res_n = nat.run(reqs)
+    torch.cuda.synchronize()
     plain = serve.PlainServer()
     plain.run(warm)
     res_p = plain.run(reqs, max_wall=duration_s * 3)
@@ -657,13 +662,17 @@ def run_serve_workload(duration_s: float = 30.0, rate_hz: float = 2000.0) -> dic
     srv = serve.Server()
     res_b4 = srv.run(fast, time_scale=0.25)
     srv.close()
+    res_n4 = nat.run(fast, time_scale=0.25)
+    nat.close()
     res_p4 = serve.PlainServer().run(fast, time_scale=0.25, max_wall=duration_s * 2)
-    for r in (res_b, res_p, res_b4, res_p4):
+    for r in (res_b, res_n, res_p, res_b4, res_n4, res_p4):
         r.pop("done", None)
     return {"requests": len(reqs), "duration_s": duration_s, "rate_hz": rate_hz,
-            "offered_events": sum(r.nevents for r in reqs), "batched": res_b, "plain": res_p,
+            "offered_events": sum(r.nevents for r in reqs), "batched": res_b, "batched_native_loop": res_n,
+            "plain": res_p,
             "p99_ratio_plain_over_batched": res_p["p99_ms"] / res_b["p99_ms"] if res_b["p99_ms"] else None,
-            "at_4x_rate": {"requests": len(fast), "rate_hz": 4 * rate_hz, "batched": res_b4, "plain": res_p4}}
+            "at_4x_rate": {"requests": len(fast), "rate_hz": 4 * rate_hz, "batched": res_b4,
+                           "batched_native_loop": res_n4, "plain": res_p4}}
 
 
 # ----------------------------------------------------------------------------- CPU oracle arm

@@ -384,6 +384,68 @@ hydra_status hydra_batch_result(hydra_batch *batch, int i, hydra_integral *resul
 hydra_status hydra_batch_destroy(hydra_batch *batch);
 
 /*
+ * Continuous-batching server (section 4.2's generation and section 3's integration as a
+ * service): the serving loop in C++ over two batch runners.  Requests arrive over time; each
+ * turn of the loop admits arrived requests while their memory fits two device rings (generated
+ * FP32 outputs; integral segment partials, min(256 MiB, budget/16)) and the caller's pinned
+ * ring, harvests finished ticks and landed copies, and, with fewer than two ticks in flight,
+ * packs one slice of every active request, oldest first and up to max_tick_events events, into
+ * one hydra_batch_run.  A generate request is one slice; its [n][4][ld] FP32 outputs and ld
+ * weights (ld = nevents rounded up to a multiple of 4) are copied to the pinned ring on a copy
+ * stream that waits for the tick, and it completes when that copy has landed.  An integral
+ * (FP32 kinematics) advances by int_slice_segments x 2^21 events per tick and completes with
+ * its last slice.  A request that can never fit, or that cannot be admitted while nothing is
+ * active or in flight, is refused.  Every slice computes exactly the events of the
+ * single-request entry points (same seed, event offset 0).
+ */
+typedef struct hydra_server hydra_server; /* opaque; bound to the device current at creation */
+
+typedef struct hydra_serve_request {
+    double arrival;    /* seconds after the start of the run; requests sorted by arrival */
+    int32_t kind;      /* HYDRA_REQ_GENERATE or HYDRA_REQ_INTEGRATE */
+    int32_t n;         /* daughters, 2..10 */
+    double M;
+    double masses[10];
+    uint64_t nevents;  /* > 0 */
+    uint64_t seed;
+    int32_t me;        /* integrate: hydra_me_id */
+    int32_t reserved;
+    double params[6];  /* integrate: matrix-element parameters */
+} hydra_serve_request;
+
+typedef struct hydra_serve_outcome {
+    double latency;        /* seconds from arrival to completion; negative: refused */
+    uint64_t host_offset;  /* generate with kept outputs: byte offset of its block in the pinned
+                            * ring ([n][4][ld] floats, then ld weights); otherwise all ones */
+    uint64_t ld;
+    hydra_integral result; /* integrate */
+} hydra_serve_outcome;
+
+/*
+ * budget_bytes   device memory of the two rings (allocated here, >= 16 MiB)
+ * pinned         caller-owned page-locked host ring of pinned_bytes (generated outputs)
+ * max_slices     requests admitted at once (and slices per tick)
+ * keep_outputs   != 0: a generate request's pinned block is kept (host_offset) instead of
+ *                released when it completes
+ * Errors: INVALID_ARG, OOM, CUDA.
+ */
+hydra_status hydra_server_create(uint64_t budget_bytes, void *pinned, uint64_t pinned_bytes, int max_slices,
+                                 int int_slice_segments, uint64_t max_tick_events, int keep_outputs,
+                                 hydra_server **out);
+
+/*
+ * Serve nreq requests (blocking: returns when every request has completed or been refused).
+ * time_scale stretches the arrival times (0: all arrive at once).  outcomes[i] receives request
+ * i's latency and result; wall_s the run's wall time, ticks the batch runs.  Errors:
+ * INVALID_ARG (unsorted or invalid requests), UNSUPPORTED_N, and the batch runner's errors.
+ */
+hydra_status hydra_server_run(hydra_server *server, const hydra_serve_request *reqs, int nreq, double time_scale,
+                              hydra_serve_outcome *outcomes, double *wall_s, uint64_t *ticks);
+
+/* Wait for the server's work and release it (its rings, runners and streams). */
+hydra_status hydra_server_destroy(hydra_server *server);
+
+/*
  * Arithmetic of FP64 generation (HYDRA_F64 in hydra_phsp_generate, hydra_phsp_generate_host
  * and batched generation).  B300's FP64 pipe is a small fraction of its FP32 pipe, so by
  * default the kinematics run in double-float arithmetic (pairs of FP32 numbers, ~48

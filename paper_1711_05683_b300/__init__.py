@@ -88,13 +88,17 @@ def lib() -> ctypes.CDLL:
         L.hydra_batch_result.argtypes = [vp, i, ctypes.POINTER(Integral)]
         L.hydra_batch_destroy.argtypes = [vp]
         L.hydra_get_launch_config.argtypes = [i, i, i, ctypes.POINTER(i), ctypes.POINTER(i)]
+        L.hydra_server_create.argtypes = [u64, vp, u64, i, i, u64, i, ctypes.POINTER(vp)]
+        L.hydra_server_run.argtypes = [vp, vp, i, d, vp, dp, ctypes.POINTER(u64)]
+        L.hydra_server_destroy.argtypes = [vp]
         for name in ("hydra_phsp_volume_factor", "hydra_phsp_generate", "hydra_phsp_integrate",
                      "hydra_phsp_draws", "hydra_phsp_generate_host", "hydra_phsp_integrate_noalloc",
                      "hydra_set_launch_config", "hydra_get_launch_config", "hydra_set_fp64_arith",
                      "hydra_phsp_generate_boosted", "hydra_phsp_unweight", "hydra_phsp_gather",
                      "hydra_phsp_evaluate",
                      "hydra_batch_create",
-                     "hydra_batch_run", "hydra_batch_result", "hydra_batch_destroy", "hydra_shutdown"):
+                     "hydra_batch_run", "hydra_batch_result", "hydra_batch_destroy", "hydra_shutdown",
+                     "hydra_server_create", "hydra_server_run", "hydra_server_destroy"):
             getattr(L, name).restype = i
         _lib = L
     return _lib
@@ -367,6 +371,25 @@ def request_dtype():
                    ("ld", "<u8"), ("weights", "<u8"), ("total", "<u8"), ("seg_partials", "<u8")],
                   align=True)
     assert dt.itemsize == 224
+    return dt
+
+
+def serve_request_dtype():
+    """numpy record type with the layout of the C struct hydra_serve_request (176 bytes)."""
+    import numpy as np
+    dt = np.dtype([("arrival", "<f8"), ("kind", "<i4"), ("n", "<i4"), ("M", "<f8"), ("masses", "<f8", (10,)),
+                   ("nevents", "<u8"), ("seed", "<u8"), ("me", "<i4"), ("reserved", "<i4"), ("params", "<f8", (6,))])
+    assert dt.itemsize == 176
+    return dt
+
+
+def serve_outcome_dtype():
+    """numpy record type with the layout of the C struct hydra_serve_outcome (80 bytes)."""
+    import numpy as np
+    dt = np.dtype([("latency", "<f8"), ("host_offset", "<u8"), ("ld", "<u8"),
+                   ("result", [(k, "<f8") for k in ("mean", "var_mean", "sum_f", "sum_f2", "sum_w", "sum_w2")]
+                    + [("n", "<u8")])])
+    assert dt.itemsize == 80
     return dt
 
 

@@ -354,6 +354,80 @@ class Server:
         self.dev_ring = self.seg_ring = None
 
 
+class NativeServer:
+    """The same serving policy with the loop in C++ (hydra_server_run: rings, two batch runners,
+    the copy stream and the harvest without the interpreter in the loop).  The pinned ring is a
+    page-locked host tensor owned here; results match `Server`'s, request by request, bit for
+    bit.  Withdrawing requests mid-flight is a `Server` feature."""
+
+    def __init__(self, budget_bytes: int = 40 * 10 ** 9, max_slices: int = 4096, int_slice_segments: int = 16,
+                 pinned_bytes: int = 4 << 30, keep_outputs: bool = False, max_tick_events: int = 1 << 27):
+        import ctypes
+        import torch
+        self.torch = torch
+        self.keep_outputs = keep_outputs
+        self.pinned = torch.empty(pinned_bytes, dtype=torch.uint8, pin_memory=True)
+        h = ctypes.c_void_p()
+        hp._check(hp.lib().hydra_server_create(int(budget_bytes), ctypes.c_void_p(self.pinned.data_ptr()),
+                                               int(pinned_bytes), int(max_slices), int(int_slice_segments),
+                                               int(max_tick_events), int(bool(keep_outputs)), ctypes.byref(h)))
+        self._h = h
+
+    def run(self, requests, time_scale: float = 1.0, max_wall: float | None = None) -> dict:
+        import ctypes
+        torch = self.torch
+        reqs = list(requests)
+        table = np.zeros(len(reqs), dtype=hp.serve_request_dtype())
+        for i, r in enumerate(reqs):
+            rec = table[i]
+            n = len(r.masses)
+            rec["arrival"], rec["n"], rec["M"] = r.arrival, n, r.M
+            rec["kind"] = hp.REQ_GENERATE if r.kind == "generate" else hp.REQ_INTEGRATE
+            rec["masses"][:n] = r.masses
+            rec["nevents"], rec["seed"], rec["me"] = r.nevents, r.seed, r.me
+            rec["params"][: len(r.params)] = r.params
+        outc = np.zeros(max(1, len(reqs)), dtype=hp.serve_outcome_dtype())
+        wall, ticks = ctypes.c_double(), ctypes.c_uint64()
+        with _no_gc_pauses():
+            hp._check(hp.lib().hydra_server_run(self._h, ctypes.c_void_p(table.ctypes.data), len(reqs),
+                                                float(time_scale), ctypes.c_void_p(outc.ctypes.data),
+                                                ctypes.byref(wall), ctypes.byref(ticks)))
+        latencies, kinds, done, refused = {}, {}, [], []
+        events = 0
+        for i, r in enumerate(reqs):
+            o = outc[i]
+            if o["latency"] < 0:
+                refused.append(i)
+                continue
+            a = _Active(i, r, r.arrival * time_scale)
+            a.latency = latencies[i] = float(o["latency"])
+            kinds[i] = r.kind
+            events += r.nevents
+            if r.kind == "integrate":
+                a.result = {k: (int(o["result"][k]) if k == "n" else float(o["result"][k]))
+                            for k in o["result"].dtype.names}
+            elif self.keep_outputs:
+                n, ld, off = len(r.masses), int(o["ld"]), int(o["host_offset"])
+                hb = self.pinned[off: off + (4 * n + 1) * ld * 4].view(torch.float32)
+                a.host_out, a.host_w = hb[: 4 * n * ld].view(n, 4, ld), hb[4 * n * ld:]
+            done.append(a)
+        out = _summary(latencies, events, wall.value, ticks=int(ticks.value), done=done, kinds=kinds)
+        out["cancelled"] = []
+        out["refused"] = refused
+        return out
+
+    def close(self):
+        if self._h:
+            hp.lib().hydra_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class PlainServer:
     """One request at a time, in arrival order, with the single-request entry points; generated
     events are copied to the same kind of pinned ring as the batched server uses."""

@@ -19,16 +19,22 @@ def _cuda():
     torch.cuda.set_device(0)
 
 
-@pytest.mark.parametrize("tick_cap", [1 << 27, 1 << 18])
-def test_served_results_equal_single_requests(tick_cap):
-    """Every request's result alone equals its result in the mix; with a small per-tick event
-    cap the same stream runs as many short oldest-first ticks and still gives the same bits."""
+def _server(kind, **kw):
     from paper_1711_05683_b300 import serve
+    return (serve.NativeServer if kind == "native" else serve.Server)(**kw)
+
+
+@pytest.mark.parametrize("kind", ["python", "native"])
+@pytest.mark.parametrize("tick_cap", [1 << 27, 1 << 18])
+def test_served_results_equal_single_requests(tick_cap, kind):
+    """Every request's result alone equals its result in the mix; with a small per-tick event
+    cap the same stream runs as many short oldest-first ticks and still gives the same bits;
+    for the Python loop and the C++ loop (hydra_server_run)."""
     reqs = workloads.serve_stream(rate_hz=2000, duration_s=0.15, gen_log_events=(2.0, 5.0),
                                   int_log_events=(4.0, 7.4), rng_seed=99)
     assert any(r.kind == "integrate" and r.nevents > 2 ** 21 for r in reqs)  # sliced over ticks
-    srv = serve.Server(max_slices=512, int_slice_segments=1, pinned_bytes=1 << 30, keep_outputs=True,
-                       budget_bytes=8 * 10 ** 9, max_tick_events=tick_cap)
+    srv = _server(kind, max_slices=512, int_slice_segments=1, pinned_bytes=1 << 30, keep_outputs=True,
+                  budget_bytes=8 * 10 ** 9, max_tick_events=tick_cap)
     res = srv.run(reqs)
     srv.close()
     assert res["completed"] == len(reqs)
@@ -82,7 +88,8 @@ def test_cancelled_request_leaves_the_others_intact():
             assert torch.equal(a.host_w[: r.nevents], w.cpu())
 
 
-def test_tight_budget_waits_for_space_and_refuses_what_never_fits():
+@pytest.mark.parametrize("kind", ["python", "native"])
+def test_tight_budget_waits_for_space_and_refuses_what_never_fits(kind):
     """Admission by budget: with a 96 MB budget the requests are admitted as earlier ones free
     their blocks, every result still equals the single-request one, and a request larger than
     the whole budget is refused instead of blocking the queue.  The device ring wraps several
@@ -97,10 +104,10 @@ def test_tight_budget_waits_for_space_and_refuses_what_never_fits():
     big_rid = reqs.index(huge)
     gen_bytes = sum((4 * len(r.masses) + 1) * hp.padded_ld(r.nevents) * 4 for r in reqs
                     if r.kind == "generate" and r is not huge)
-    srv = serve.Server(max_slices=64, int_slice_segments=1, pinned_bytes=4 << 30, keep_outputs=True,
-                       budget_bytes=96 * 10 ** 6)
-    assert srv.dev_ring.size < gen_bytes < srv.ring.size  # the device budget is the tight one
-    srv_dev_ring_size = srv.dev_ring.size
+    srv = _server(kind, max_slices=64, int_slice_segments=1, pinned_bytes=4 << 30, keep_outputs=True,
+                  budget_bytes=96 * 10 ** 6)
+    srv_dev_ring_size = 96 * 10 ** 6 - min(256 << 20, 96 * 10 ** 6 // 16)
+    assert srv_dev_ring_size < gen_bytes < 4 << 30  # the device budget is the tight one
     res = srv.run(reqs, max_wall=60.0)
     srv.close()
     assert res["refused"] == [big_rid]
@@ -118,14 +125,15 @@ def test_tight_budget_waits_for_space_and_refuses_what_never_fits():
     assert gen_bytes > 3 * srv_dev_ring_size
 
 
-def test_kept_outputs_filling_the_pinned_ring_are_refused_not_waited_for():
+@pytest.mark.parametrize("kind", ["python", "native"])
+def test_kept_outputs_filling_the_pinned_ring_are_refused_not_waited_for(kind):
     """With keep_outputs the pinned ring is never released; once it is full, later generate
     requests are refused (nothing could ever free space) and the run ends."""
     from paper_1711_05683_b300 import serve
     reqs = workloads.serve_stream(rate_hz=2000, duration_s=0.05, gen_log_events=(5.0, 5.3),
                                   int_log_events=(4.0, 4.5), rng_seed=5)
-    srv = serve.Server(max_slices=64, int_slice_segments=1, pinned_bytes=64 << 20, keep_outputs=True,
-                       budget_bytes=2 * 10 ** 9)
+    srv = _server(kind, max_slices=64, int_slice_segments=1, pinned_bytes=64 << 20, keep_outputs=True,
+                  budget_bytes=2 * 10 ** 9)
     res = srv.run(reqs, max_wall=60.0)
     srv.close()
     gens = [i for i, r in enumerate(reqs) if r.kind == "generate"]
