@@ -411,14 +411,25 @@ typedef struct hydra_serve_request {
     int32_t me;        /* integrate: hydra_me_id */
     int32_t reserved;
     double params[6];  /* integrate: matrix-element parameters */
+    double withdraw;   /* seconds after the start of the run at which the client withdraws the
+                        * request if it is admitted and not yet fully launched (dropped between
+                        * ticks, memory released); negative: never */
 } hydra_serve_request;
 
+typedef enum hydra_serve_status {
+    HYDRA_SERVE_DONE = 0,
+    HYDRA_SERVE_REFUSED = 1,   /* could never fit, or could not be admitted with nothing in flight */
+    HYDRA_SERVE_WITHDRAWN = 2  /* withdrawn by the client (see withdraw) */
+} hydra_serve_status;
+
 typedef struct hydra_serve_outcome {
-    double latency;        /* seconds from arrival to completion; negative: refused */
+    double latency;        /* seconds from arrival to completion (HYDRA_SERVE_DONE) */
     uint64_t host_offset;  /* generate with kept outputs: byte offset of its block in the pinned
                             * ring ([n][4][ld] floats, then ld weights); otherwise all ones */
     uint64_t ld;
     hydra_integral result; /* integrate */
+    int32_t status;        /* hydra_serve_status */
+    int32_t reserved;
 } hydra_serve_outcome;
 
 /*

@@ -375,22 +375,26 @@ def request_dtype():
 
 
 def serve_request_dtype():
-    """numpy record type with the layout of the C struct hydra_serve_request (176 bytes)."""
+    """numpy record type with the layout of the C struct hydra_serve_request (184 bytes)."""
     import numpy as np
     dt = np.dtype([("arrival", "<f8"), ("kind", "<i4"), ("n", "<i4"), ("M", "<f8"), ("masses", "<f8", (10,)),
-                   ("nevents", "<u8"), ("seed", "<u8"), ("me", "<i4"), ("reserved", "<i4"), ("params", "<f8", (6,))])
-    assert dt.itemsize == 176
+                   ("nevents", "<u8"), ("seed", "<u8"), ("me", "<i4"), ("reserved", "<i4"), ("params", "<f8", (6,)),
+                   ("withdraw", "<f8")])
+    assert dt.itemsize == 184
     return dt
 
 
 def serve_outcome_dtype():
-    """numpy record type with the layout of the C struct hydra_serve_outcome (80 bytes)."""
+    """numpy record type with the layout of the C struct hydra_serve_outcome (88 bytes)."""
     import numpy as np
     dt = np.dtype([("latency", "<f8"), ("host_offset", "<u8"), ("ld", "<u8"),
                    ("result", [(k, "<f8") for k in ("mean", "var_mean", "sum_f", "sum_f2", "sum_w", "sum_w2")]
-                    + [("n", "<u8")])])
-    assert dt.itemsize == 80
+                    + [("n", "<u8")]), ("status", "<i4"), ("reserved", "<i4")])
+    assert dt.itemsize == 88
     return dt
+
+
+SERVE_DONE, SERVE_REFUSED, SERVE_WITHDRAWN = 0, 1, 2
 
 
 def segments(total: int) -> int:

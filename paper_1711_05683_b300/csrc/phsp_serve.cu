@@ -178,7 +178,10 @@ hydra_status hydra_server_run(hydra_server* s, const hydra_serve_request* reqs, 
         outcomes[i] = hydra_serve_outcome{};
         outcomes[i].latency = -1.0;
         outcomes[i].host_offset = ~uint64_t{0};
+        outcomes[i].status = HYDRA_SERVE_REFUSED;  // until it completes or is withdrawn
     }
+    bool any_withdraw = false;
+    for (int i = 0; i < nreq; ++i) any_withdraw = any_withdraw || reqs[i].withdraw >= 0.0;
     unsigned char* seg_base = s->dev_base + s->dev_ring.size;
     std::vector<Active> pool(static_cast<size_t>(nreq));
     std::deque<Active*> queue;
@@ -193,8 +196,17 @@ hydra_status hydra_server_run(hydra_server* s, const hydra_serve_request* reqs, 
     auto clock = [&]() { return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count(); };
     hydra_status st = HYDRA_OK;
 
+    auto release = [&](Active* a) {
+        if (a->rec.kind == HYDRA_REQ_GENERATE) {
+            s->dev_ring.release(a->dev);
+            s->host_ring.release(a->host);
+        } else {
+            s->seg_ring.release(a->dev);
+        }
+    };
     auto complete = [&](Active* a, double tnow) {
         outcomes[a->rid].latency = tnow - a->arrival;
+        outcomes[a->rid].status = HYDRA_SERVE_DONE;
         if (a->rec.kind == HYDRA_REQ_GENERATE) {
             s->dev_ring.release(a->dev);
             if (s->keep_outputs) {
@@ -301,6 +313,19 @@ hydra_status hydra_server_run(hydra_server* s, const hydra_serve_request* reqs, 
             s->events.push_back(t.ev);
         }
         if (st != HYDRA_OK) break;
+        // client withdrawal between ticks: an admitted request not yet fully launched is dropped
+        // and its memory released (slices already in flight finish on the compute stream before
+        // any later use of the released blocks)
+        if (any_withdraw) {
+            active.erase(std::remove_if(active.begin(), active.end(), [&](Active* a) {
+                             const hydra_serve_request& q = reqs[a->rid];
+                             if (q.withdraw < 0.0 || now < q.withdraw || a->next_first >= q.nevents) return false;
+                             outcomes[a->rid].status = HYDRA_SERVE_WITHDRAWN;
+                             release(a);
+                             return true;
+                         }),
+                         active.end());
+        }
         // generate requests complete when their copy to host memory has landed
         while (!copying.empty() && cudaEventQuery(copying.front().ev) == cudaSuccess) {
             Copy c = std::move(copying.front());

@@ -358,7 +358,7 @@ class NativeServer:
     """The same serving policy with the loop in C++ (hydra_server_run: rings, two batch runners,
     the copy stream and the harvest without the interpreter in the loop).  The pinned ring is a
     page-locked host tensor owned here; results match `Server`'s, request by request, bit for
-    bit.  Withdrawing requests mid-flight is a `Server` feature."""
+    bit, client withdrawal (cancel_after) included."""
 
     def __init__(self, budget_bytes: int = 40 * 10 ** 9, max_slices: int = 4096, int_slice_segments: int = 16,
                  pinned_bytes: int = 4 << 30, keep_outputs: bool = False, max_tick_events: int = 1 << 27):
@@ -373,13 +373,21 @@ class NativeServer:
                                                int(max_tick_events), int(bool(keep_outputs)), ctypes.byref(h)))
         self._h = h
 
-    def run(self, requests, time_scale: float = 1.0, max_wall: float | None = None) -> dict:
+    def run(self, requests, time_scale: float = 1.0, max_wall: float | None = None,
+            cancel_after: dict | None = None) -> dict:
+        """Serve `requests` (sorted by arrival); cancel_after maps a request index to the time
+        (seconds from the start) at which its client withdraws it.  max_wall is not used: the
+        C++ loop runs until every request has completed, been refused or been withdrawn."""
         import ctypes
         torch = self.torch
         reqs = list(requests)
+        cancel_after = dict(cancel_after or {})
         table = np.zeros(len(reqs), dtype=hp.serve_request_dtype())
+        table["withdraw"] = -1.0
         for i, r in enumerate(reqs):
             rec = table[i]
+            if i in cancel_after:
+                rec["withdraw"] = float(cancel_after[i])
             n = len(r.masses)
             rec["arrival"], rec["n"], rec["M"] = r.arrival, n, r.M
             rec["kind"] = hp.REQ_GENERATE if r.kind == "generate" else hp.REQ_INTEGRATE
@@ -392,12 +400,12 @@ class NativeServer:
             hp._check(hp.lib().hydra_server_run(self._h, ctypes.c_void_p(table.ctypes.data), len(reqs),
                                                 float(time_scale), ctypes.c_void_p(outc.ctypes.data),
                                                 ctypes.byref(wall), ctypes.byref(ticks)))
-        latencies, kinds, done, refused = {}, {}, [], []
+        latencies, kinds, done, refused, cancelled = {}, {}, [], [], []
         events = 0
         for i, r in enumerate(reqs):
             o = outc[i]
-            if o["latency"] < 0:
-                refused.append(i)
+            if o["status"] != hp.SERVE_DONE:
+                (cancelled if o["status"] == hp.SERVE_WITHDRAWN else refused).append(i)
                 continue
             a = _Active(i, r, r.arrival * time_scale)
             a.latency = latencies[i] = float(o["latency"])
@@ -412,7 +420,7 @@ class NativeServer:
                 a.host_out, a.host_w = hb[: 4 * n * ld].view(n, 4, ld), hb[4 * n * ld:]
             done.append(a)
         out = _summary(latencies, events, wall.value, ticks=int(ticks.value), done=done, kinds=kinds)
-        out["cancelled"] = []
+        out["cancelled"] = cancelled
         out["refused"] = refused
         return out
 

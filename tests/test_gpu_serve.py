@@ -59,7 +59,8 @@ def test_plain_server_matches_too():
     assert res["completed"] == len(reqs) and res["p99_ms"] >= res["p50_ms"]
 
 
-def test_cancelled_request_leaves_the_others_intact():
+@pytest.mark.parametrize("kind", ["python", "native"])
+def test_cancelled_request_leaves_the_others_intact(kind):
     """Host-side fault injection: a client withdraws a long integral mid-flight; the server
     drops it between ticks and every other request still gets its single-request result.  The
     integral is 1000 ticks of 2^21 events (tens of ms of GPU work), so it is still running when
@@ -71,7 +72,7 @@ def test_cancelled_request_leaves_the_others_intact():
     big = workloads.Request("integrate", d["M"], d["masses"], 1000 * 2 ** 21, 123, me=1,
                             params=d["params"], arrival=0.0)
     reqs = [big] + list(reqs)
-    srv = serve.Server(max_slices=256, int_slice_segments=1, pinned_bytes=1 << 28, keep_outputs=True)
+    srv = _server(kind, max_slices=256, int_slice_segments=1, pinned_bytes=1 << 28, keep_outputs=True)
     res = srv.run(reqs, cancel_after={0: 0.005})
     srv.close()
     assert res["cancelled"] == [0]
