@@ -53,16 +53,66 @@ INSTR_PER_EVENT = {
 }
 
 
-def fp_ops_per_event(n: int) -> int:
-    """Algorithmic floating-point operations of one Raubold-Lynch event (a multiply, add or
-    fused multiply-add counts 1; sqrt, reciprocal, division and a sin/cos pair count 1 each):
-    per boosted two-body step 48 -- the intermediate mass (2), gap (1), lambda's factors (8),
-    1/M and p (4), the weight factor (1), cos, 1 +- cos and sin theta (5), sin/cos phi (1), the
-    3-momentum (4), the energy M_k + Delta (Delta + 2 m) / (2 M_{k+1}) from a factor of lambda
-    (1), Q.p (5), the boosted energy (3), the boost factor (3), the boosted 3-momentum (6) and
-    the daughter by subtraction (4) -- and 31 for the parent's own decay (no boost), plus the
-    constant C_n."""
-    return 48 * (n - 2) + 31 + 1
+# DRAM bytes (ncu dram__bytes_read.sum + dram__bytes_write.sum) per launch of the dominant
+# kernel family at the benchmark's 1e8 events, averaged over the family's launches; None
+# until captured for the kernels as they stand.
+TRAFFIC_GB_PER_LAUNCH = {"f64": None, "f32": None}
+
+
+def emit_detail(detail: dict, path: str | None) -> None:
+    """The per-launch breakdown, measured ceilings, batch, serving and extension figures: one
+    JSON line on stderr (stdout carries only the result line), and to `path` if given."""
+    text = json.dumps(detail)
+    print("bench detail: " + text, file=sys.stderr, flush=True)
+    if path:
+        with open(path, "w") as fh:
+            fh.write(text + "\n")
+
+
+def method_ops(n: int, massless: bool = False) -> dict:
+    """Algorithmic floating-point operations of one Raubold-Lynch event by kind (an add,
+    multiply or fused multiply-add counts 1; a square root, reciprocal, division or sin/cos
+    pair counts 1 each).  A boosted two-body step (massive daughters) takes 48: the
+    intermediate mass r T + mu (mul, add), the gap (mul), lambda's four factors and their
+    product (2 M_k, 2 m by scaling; 3 adds, 3 muls), 1/M_{k+1} (rcp), p = sqrt(lambda) / (2 M_{k+1})
+    (sqrt, 2 muls), the weight factor (mul), cos theta, 1 -+ cos theta (3 adds), sin theta
+    (mul, sqrt), sin/cos phi (1), the 3-momentum (4 muls), the rest-frame energy M_k +
+    Delta (Delta + 2 m) / (2 M_{k+1}) (fma), Q.p (3 muls, 2 adds), the boosted energy (2 muls,
+    add), the boost factor (2 adds, div), the boosted 3-momentum (3 muls, 3 adds) and the
+    daughter by subtraction (4 adds); the parent's decay has no boost (31).  For all-massless
+    daughters lambda = (Delta (Delta + 2 M_k))^2 and the momentum needs 4 operations instead
+    of 10 (43 per boosted step, 26 for the parent).  Plus the constant C_n (mul)."""
+    k = n - 2  # boosted steps
+    ops = {"add": 19 * k + 11, "mul": 23 * k + 15 + 1, "fma": n - 1, "sqrt": 2 * (n - 1),
+           "rcp": n - 1, "div": k, "sincos": n - 1}
+    if massless:  # per step: 2 adds, 2 muls and the square root of lambda fewer
+        ops["add"] -= 2 * (n - 1)
+        ops["mul"] -= 2 * (n - 1)
+        ops["sqrt"] -= n - 1
+    return ops
+
+
+def fp_ops_per_event(n: int, massless: bool = False) -> int:
+    return sum(method_ops(n, massless).values())
+
+
+def fp_seconds_per_event(ops: dict, rates: dict) -> float:
+    """Time of one event's method operations at the measured rates of the arithmetic the
+    kernel runs.  A division counts as a reciprocal and a product; a sin/cos pair as one
+    square root (a generous ceiling: the kernels spend more on it)."""
+    t = ops["add"] / rates["add"] + ops["mul"] / rates["mul"] + ops["fma"] / rates["fma"]
+    t += ops["sqrt"] / rates["sqrt"] + ops["rcp"] / rates["rcp"]
+    t += ops["div"] * (1.0 / rates["rcp"] + 1.0 / rates["mul"]) + ops["sincos"] / rates["sqrt"]
+    return t
+
+
+def measure_op_rates(hp) -> dict:
+    """Rates (operations/s) of add, mul, fma, sqrt and rcp in FP32 (the FP32 kernels'
+    arithmetic) and in double-float (the FP64 generator's), from the library's probe."""
+    out = {}
+    for arith, iters in (("f32", 100_000), ("df", 20_000)):
+        out[arith] = {op: hp.probe_op_rate(arith, op, iters) for op in ("add", "mul", "fma", "sqrt", "rcp")}
+    return out
 
 
 def instr_per_event(dtype: str, n: int, massive: bool) -> int:
@@ -233,6 +283,9 @@ def run_ours(args) -> None:
                 "hbm_write_gbs": round(hp.probe_write_bandwidth(probe_buf, 5), 1),
                 "src": "hydra_probe_fma_rate (8 independent FMA chains per thread, all SMs) and "
                        "hydra_probe_write_bandwidth (16-byte stores over 4 GB), this run"}
+    op_rates = measure_op_rates(hp)
+    measured["op_rates"] = {a: {k: round(v / 1e12, 3) for k, v in r.items()} for a, r in op_rates.items()}
+    measured["op_rates_unit"] = "T operations/s (hydra_probe_op_rate: 8 independent chains per thread, all SMs)"
     del probe_buf
     torch.cuda.empty_cache()
 
@@ -325,115 +378,107 @@ def run_ours(args) -> None:
         return
 
     peaks = load_peaks()
-    n_sms = torch.cuda.get_device_properties(0).multi_processor_count
-    issue_limit = n_sms * 4 * 32 * (clk.get("sm_mhz") or clk.get("sm_max_mhz") or 2032.0) * 1e6
+    hbm = peaks["hbm_gbs"] * 1e9
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    sm_mhz = clk.get("sm_mhz") or clk.get("sm_max_mhz") or 2032.0
+    issue_limit = sms * 4 * 32 * sm_mhz * 1e6  # thread instructions per second
     breakdown = []
     for k, (dtype, massive, n) in enumerate(items):
         ms = per_launch_ms[k] / args.steps
-        gbs = bytes_per_event(n, dtype) * nev / (ms / 1e3) / 1e9
-        # per-kernel roofline: the slower of the output bytes at the measured HBM peak and the
-        # instructions at the SM issue limit
-        by_hbm = peaks["hbm_gbs"] * 1e9 / bytes_per_event(n, dtype)
-        by_issue = issue_limit / instr_per_event(dtype, n, massive)
-        roof_ev = min(by_hbm, by_issue)
-        breakdown.append({"kernel": f"phsp_generate_kernel<{n},{'float' if dtype == 'f32' else 'double'}>",
-                          "n": n, "dtype": dtype, "massive": massive, "events": nev,
-                          "ms": round(ms, 4), "events_per_s": nev / (ms / 1e3),
-                          "hbm_gbs": round(gbs, 1), "hbm_frac": round(gbs / peaks["hbm_gbs"], 4),
-                          "roofline_events_per_s": roof_ev, "roofline_bound": "hbm" if by_hbm <= by_issue else "issue",
-                          "roofline_frac": round(nev / (ms / 1e3) / roof_ev, 4)})
+        ev_s = nev / (ms / 1e3)
+        # the launch's roofline: the slower of its output bytes at the measured HBM
+        # copy peak and its method operations at the measured rates of the arithmetic it runs
+        ops = method_ops(n, massless=not massive)
+        by_hbm = hbm / bytes_per_event(n, dtype)
+        by_fp = 1.0 / fp_seconds_per_event(ops, op_rates["f32" if dtype == "f32" else "df"])
+        roof = min(by_hbm, by_fp)
+        breakdown.append({"kernel": f"phsp_generate_kernel<{n},{'float' if dtype == 'f32' else 'df'}>",
+                          "n": n, "dtype": dtype, "massive": massive, "events": nev, "ms": round(ms, 4),
+                          "events_per_s": ev_s, "hbm_gbs": round(bytes_per_event(n, dtype) * ev_s / 1e9, 1),
+                          "fp_ops_per_event": sum(ops.values()), "roof_hbm_events_per_s": by_hbm,
+                          "roof_fp_events_per_s": by_fp, "roofline_bound": "hbm" if by_hbm <= by_fp else "fp",
+                          "roofline_frac": round(ev_s / roof, 4),
+                          "issue_frac": round(instr_per_event(dtype, n, massive) * ev_s / issue_limit, 4)})
     int_ms = per_launch_ms[-1] / args.steps
     breakdown.append({"kernel": "phsp_integrate_tiles<3,float,DALITZ_2BW>+reduce", "events": int_events,
                       "ms": round(int_ms, 4), "events_per_s": int_events / (int_ms / 1e3),
                       "mean": res["mean"], "sigma": math.sqrt(res["var_mean"])})
 
-    # dominant kernel family by total time
-    fam = {}
-    for b in breakdown[:-1]:
-        fam.setdefault(b["dtype"], []).append(b)
-    fam_ms = {k: sum(x["ms"] for x in v) for k, v in fam.items()}
-    fam_ms["integrate"] = int_ms
+    def family(dtype):
+        rows = [x for x in breakdown[:-1] if x["dtype"] == dtype]
+        f_ms = sum(x["ms"] for x in rows)
+        roof_ms = sum(x["events"] / min(x["roof_hbm_events_per_s"], x["roof_fp_events_per_s"]) * 1e3 for x in rows)
+        f_bytes = sum(bytes_per_event(x["n"], dtype) * x["events"] for x in rows)
+        f_ops = sum(x["fp_ops_per_event"] * x["events"] for x in rows)
+        fp_ms = sum(x["ms"] for x in rows if x["roofline_bound"] == "fp")
+        return {"ms": f_ms, "roof_ms": roof_ms, "bytes": f_bytes, "ops": f_ops, "launches": len(rows),
+                "events": sum(x["events"] for x in rows), "fp_bound_ms": fp_ms}
+
+    fams = {"f64": family("f64"), "f32": family("f32")}
+    fam_ms = {"f64": fams["f64"]["ms"], "f32": fams["f32"]["ms"], "integrate": int_ms}
     dominant = max(fam_ms, key=fam_ms.get)
-    f32 = fam["f32"]
-    f32_bytes = sum(bytes_per_event(x["n"], "f32") * x["events"] for x in f32)
-    f32_ms = fam_ms["f32"]
-    import torch
-    sms = torch.cuda.get_device_properties(0).multi_processor_count
-    sm_mhz = clk.get("sm_mhz") or clk.get("sm_max_mhz") or 2032.0
-    issue_peak = sms * 4 * 32 * sm_mhz * 1e6 / 1e12  # thread instructions per second (1e12)
-    roof = None
-    if dominant in ("f32", "f64"):
-        rows = fam[dominant]
-        tot_bytes = sum(bytes_per_event(x["n"], dominant) * x["events"] for x in rows)
-        hbm = tot_bytes / (fam_ms[dominant] / 1e3) / 1e9
-        if dominant == "f64":
-            instr = sum(instr_per_event("f64", x["n"], x["massive"]) * x["events"] for x in rows)
-            achieved = instr / (fam_ms[dominant] / 1e3) / 1e12
-            roof = {"bound": "alu", "kernel": "phsp_generate_kernel<N, df, EPT> (FP64 outputs, double-float "
-                                              "arithmetic), N=2..10, 18 launches per step",
-                    "achieved": round(achieved, 2), "peak": round(issue_peak, 2),
-                    "unit": "T thread-instructions/s issued",
-                    "frac": round(achieved / issue_peak, 4),
-                    "peak_src": f"SM issue limit: {sms} SMs x 4 schedulers x 32 lanes x {sm_mhz:.0f} MHz (sampled)",
-                    "work_src": "instructions per event from ncu (INSTR_PER_EVENT)",
-                    "measured_issue_peak": round(measured["fp32_fma_per_s"] / 1e12, 2),
-                    "frac_of_measured_issue_peak": round(achieved / (measured["fp32_fma_per_s"] / 1e12), 4),
-                    "algorithmic": {
-                        "fp64_ops_per_s": round(sum(fp_ops_per_event(x["n"]) * x["events"] for x in rows)
-                                                / (fam_ms[dominant] / 1e3) / 1e12, 3),
-                        "unit": "T FP64 operations/s (fp_ops_per_event: 48 per boosted two-body step)",
-                        "native_fp64_peak": round(measured["fp64_fma_per_s"] / 1e12, 3),
-                        "frac_of_native_fp64_peak": round(sum(fp_ops_per_event(x["n"]) * x["events"] for x in rows)
-                                                          / (fam_ms[dominant] / 1e3) / measured["fp64_fma_per_s"], 3),
-                        "note": "FP64-accurate arithmetic done on the FP32 pipes in double-float; the "
-                                "native FP64 pipe's peak is the ceiling a native FP64 kernel would have"},
-                    "hbm_gbs": round(hbm, 1), "hbm_frac_of_measured": round(hbm / peaks["hbm_gbs"], 4),
-                    "traffic": round((tot_bytes / len(rows) - 64e6) / 1e9, 3),
-                    "traffic_note": "GB per launch: ncu dram read+write on 4e6-event launches is the algorithmic "
-                                    "bytes minus 64 MB left dirty in L2; scaled to the launch's events"}
-        else:
-            roof = {"bound": "hbm", "kernel": "phsp_generate_kernel<N, float, EPT> (N=2..10)",
-                    "achieved": round(hbm, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                    "frac": round(hbm / peaks["hbm_gbs"], 4), "peak_src": peaks["src"], "traffic": None}
-    line = {
-        "metric": METRIC,
-        "value": value, "unit": "events/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32,f64", "data": "synthetic",
-        "config": {"workload": "N-body sweep N=2..10 massless+massive, M=10 GeV, 1e8 events per "
-                               "(N, masses, precision), FP32 and FP64 SoA outputs; plus Dalitz "
-                               "|BW+0.5e^{1.2i}BW|^2 integral over 1e9 events (FP32 kinematics)",
-                   "events_per_launch": nev, "integrate_events": int_events,
-                   "events_per_step_per_gpu": per_step_events, "l2": "outputs >> L2 (126 MB); no flush",
-                   "parallelism": f"replicas x{world}"},
-        "gpu_launches": args.steps * (len(items) + 2 * math.ceil(int_events / 2 ** 26) + 1),
-        "roofline": roof,
-        "fp32_generator_roofline": {"bound": "hbm", "kernel": "phsp_generate_kernel<N, float, EPT> (N=2..10)",
-                                    "achieved": round(f32_bytes / (f32_ms / 1e3) / 1e9, 1),
-                                    "peak": peaks["hbm_gbs"], "unit": "GB/s", "peak_src": "MEASURED_PEAKS hbm_gbs (copy)",
-                                    "frac": round(f32_bytes / (f32_ms / 1e3) / 1e9 / peaks["hbm_gbs"], 4),
-                                    "issue_frac": round(sum(instr_per_event("f32", x["n"], x["massive"]) * x["events"] for x in f32)
-                                                        / (f32_ms / 1e3) / 1e12 / issue_peak, 4),
-                                    "frac_of_write_peak": round(f32_bytes / (f32_ms / 1e3) / 1e9 / measured["hbm_write_gbs"], 4),
-                                    "write_peak_gbs": measured["hbm_write_gbs"],
-                                    "frac_of_per_kernel_roofline": round(
-                                        sum(x["events"] / x["roofline_events_per_s"] for x in f32) / (f32_ms / 1e3), 4)},
-        "measured_peaks": measured,
-        "dominant": dominant, "family_ms_per_step": {k: round(v, 3) for k, v in fam_ms.items()},
-        "breakdown": breakdown, "clocks": clk, "e2e": e2e,
+    d = fams["f64" if dominant != "f32" else "f32"]
+    dk = "f64" if dominant != "f32" else "f32"
+    achieved = d["ops"] / (d["ms"] / 1e3) / 1e12
+    peak = d["ops"] / (d["roof_ms"] / 1e3) / 1e12
+    roof = {"bound": "alu" if d["fp_bound_ms"] > d["ms"] / 2 else "hbm",
+            "kernel": ("phsp_generate_kernel<N,df> (FP64 outputs, double-float arithmetic)" if dk == "f64"
+                       else "phsp_generate_kernel<N,float>") + f", N=2..10, {d['launches']} launches/step",
+            "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "T method-FP-ops/s",
+            "frac": round(d["roof_ms"] / d["ms"], 4),
+            "ms": round(d["ms"], 3), "roofline_ms": round(d["roof_ms"], 3),
+            "peak_src": f"per launch min(HBM {peaks['hbm_gbs']:.0f} GB/s {peaks['src']} / (32N+8) B, "
+                        f"{'double-float' if dk == 'f64' else 'FP32'} op rates of hydra_probe_op_rate "
+                        "this run / method ops per event)",
+            "hbm_frac": round(d["bytes"] / (d["ms"] / 1e3) / hbm, 4),
+            "traffic": TRAFFIC_GB_PER_LAUNCH.get(dk), "traffic_unit": "GB/launch (ncu dram read+write)"}
+    f32 = fams["f32"]
+    f32_roof = {"bound": "hbm", "achieved": round(f32["bytes"] / (f32["ms"] / 1e3) / 1e9, 1),
+                "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac_of_hbm": round(f32["bytes"] / (f32["ms"] / 1e3) / hbm, 4),
+                "frac": round(f32["roof_ms"] / f32["ms"], 4)}
+    detail = {
+        "measured_peaks": measured, "dominant": dominant, "family_ms_per_step": {k: round(v, 3) for k, v in fam_ms.items()},
+        "roofline": roof, "fp32_generator_roofline": f32_roof, "breakdown": breakdown, "clocks": clk, "e2e": e2e,
         "launch_shapes": {"source": tuning.get("source"),
                           "generate": {k: f"{v['block']}x{v['ept']}" for k, v in tuning["generate"].items()},
                           "integrate": {k: f"{v['block']}x{v['ept']}" for k, v in tuning["integrate"].items()}},
     }
+    line = {
+        "metric": METRIC,
+        "value": value, "unit": "events/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 + f64 (FP64 outputs from double-float arithmetic, within 1e-12 of FP64)",
+        "data": "synthetic",
+        "config": {"workload": "N-body sweep N=2..10 massless+massive, M=10 GeV, FP32 and FP64 SoA "
+                               "outputs, 1e8 events each; Dalitz 2-BW integral, 1e9 events",
+                   "events_per_launch": nev, "integrate_events": int_events,
+                   "l2": "outputs >> L2 (126 MB); no flush", "parallelism": f"replicas x{world}"},
+        "gpu_launches": args.steps * (len(items) + 2 * math.ceil(int_events / 2 ** 26) + 1),
+        "clocks": {k: clk.get(k) for k in ("sm_mhz", "sm_max_mhz", "reasons")},
+        "roofline": {k: roof[k] for k in ("bound", "achieved", "peak", "unit", "frac", "traffic", "ms", "roofline_ms")},
+        "fp32_generator_roofline": {k: f32_roof[k] for k in ("frac", "frac_of_hbm")},
+        "family_ms": {k: round(v, 2) for k, v in fam_ms.items()},
+    }
+    if e2e is not None:
+        line["e2e"] = {k: e2e[k] for k in ("value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step", "link_frac")}
     if not args.no_batch:
-        line["batch"] = run_batch_workload()
-        line["extensions"] = run_extras(hbm_peak_gbs=peaks["hbm_gbs"])
+        detail["batch"] = run_batch_workload()
+        detail["extensions"] = run_extras(hbm_peak_gbs=peaks["hbm_gbs"])
+        line["batch_speedup_vs_plain"] = round(detail["batch"]["speedup_vs_plain"], 3)
     if not args.no_serve:
-        line["serve"] = run_serve_workload(duration_s=args.serve_seconds)
+        detail["serve"] = run_serve_workload(duration_s=args.serve_seconds)
+        sv = detail["serve"]
+        line["serve"] = {"p50_ms": round(sv["batched_native_loop"]["p50_ms"], 3),
+                         "p99_ms": round(sv["batched_native_loop"]["p99_ms"], 3),
+                         "plain_p99_ms": round(sv["plain"]["p99_ms"], 3),
+                         "events_per_s": sv["batched_native_loop"]["events_per_s"]}
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds, nev, int_events)
-        line["cpu_baseline"]["value_ratio_note"] = "oracle, single thread, FP64; not a tuning target"
-        line["cpu_all_cores"] = cpu_all_cores(line["cpu_baseline"]["sample_events"], nev, int_events)
+        cb = cpu_baseline(args.cpu_seconds, nev, int_events)
+        detail["cpu_baseline"] = cb
+        detail["cpu_all_cores"] = cpu_all_cores(cb["sample_events"], nev, int_events)
+        line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+    emit_detail(detail, args.detail_out)
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -677,44 +722,21 @@ def run_serve_workload(duration_s: float = 30.0, rate_hz: float = 2000.0) -> dic
 
 # ----------------------------------------------------------------------------- CPU oracle arm
 def cpu_baseline(seconds: float, nev_full: int, int_full: int) -> dict:
-    """The oracle (single-threaded FP64 C) on a bounded sample of every item of the step;
-    each item's time is scaled to its full event count."""
+    """The oracle (single-threaded FP64 C) on a uniformly scaled-down copy of the step: every
+    item on the same fraction of its full event count, sized to take about `seconds`."""
     import oracle
     oracle.build()
-    items = sweep_items()
-    budget = seconds / (len(items) + 1)
-    total_t = 0.0
-    total_ev = 0
-    sample = {}
-    for dtype, massive, n in items:
-        masses = workloads.sweep_masses(n, massive)
-        m = 2000
-        t = 0.0
-        while True:
-            t0 = time.perf_counter()
-            oracle.generate(workloads.SWEEP_M, masses, m, 1000 + n)
-            t = time.perf_counter() - t0
-            if t > budget / 4 or m >= nev_full:
-                break
-            m *= 4
-        total_t += t * nev_full / m
-        total_ev += nev_full
-        sample[f"{dtype}/{'massive' if massive else 'massless'}/N{n}"] = m
-    m = 2000
-    while True:
-        t0 = time.perf_counter()
-        oracle.integrate(INT_CFG["M"], INT_CFG["masses"], m, INT_CFG["seed"], me=1, params=INT_CFG["params"])
-        t = time.perf_counter() - t0
-        if t > budget / 4 or m >= int_full:
-            break
-        m *= 4
-    total_t += t * int_full / m
-    total_ev += int_full
-    sample["integrate"] = m
-    return {"value": total_ev / total_t, "unit": "events/s", "cores": 1, "kind": "oracle",
-            "sample": "per item of the step: the oracle on the first k events (k doubled x4 until "
-                      "about %.1f s), time scaled to the item's full count; FP64 oracle stands in for both "
-                      "precisions" % (budget / 4), "sample_events": sample,
+    items = oracle_step_items(nev_full, int_full)
+    sizes = oracle_sample_sizes(items, seconds)
+    t0 = time.perf_counter()
+    run_oracle_step(items, sizes)
+    wall = time.perf_counter() - t0
+    ev = sum(sizes)
+    frac = sizes[0] / nev_full
+    return {"value": ev / wall, "unit": "events/s", "cores": 1, "kind": "oracle",
+            "sample": f"the step scaled down uniformly: {sizes[0]} events per generator item (36) and {sizes[-1]} "
+                      f"integrated ({frac:.2e} of the full counts), {wall:.1f} s; FP64 oracle for both precisions",
+            "sample_events": {label: k for (label, _, _), k in zip(items, sizes)},
             "host_cores_available": os.cpu_count()}
 
 
@@ -764,25 +786,79 @@ def cpu_all_cores(sample: dict, nev_full: int, int_full: int) -> dict:
                       "full count; context, not a baseline"}
 
 
+def oracle_step_items(nev_full: int, int_full: int):
+    """The step's 37 items for the oracle: (label, callable(k), full event count)."""
+    import oracle
+    items = []
+    for dtype, massive, n in sweep_items():
+        masses = workloads.sweep_masses(n, massive)
+        items.append((f"{dtype}/{'massive' if massive else 'massless'}/N{n}",
+                      (lambda k, masses=masses, n=n: oracle.generate(workloads.SWEEP_M, masses, k, 1000 + n)),
+                      nev_full))
+    items.append(("integrate", lambda k: oracle.integrate(INT_CFG["M"], INT_CFG["masses"], k, INT_CFG["seed"], me=1,
+                                                          params=INT_CFG["params"]), int_full))
+    return items
+
+
+def oracle_sample_sizes(items, seconds: float) -> list[int]:
+    """Event counts of a uniformly scaled-down step: each item's full count times one fraction,
+    chosen from each item's rate on 4096 events (best of two, untimed) so that the sampled step
+    takes about `seconds`; multiples of 64, at least 64."""
+    full_s = 0.0
+    for label, fn, full in items:
+        best = float("inf")
+        for _ in range(2):
+            t0 = time.perf_counter()
+            fn(4096)
+            best = min(best, time.perf_counter() - t0)
+        full_s += full * best / 4096
+    f = seconds / full_s
+    return [int(max(64, round(full * f / 64) * 64)) for _, _, full in items]
+
+
+def run_oracle_step(items, sizes) -> None:
+    for (label, fn, full), k in zip(items, sizes):
+        fn(k)
+
+
 def run_reference(args) -> None:
+    """The reference arm: the oracle (single-threaded FP64 C) on the host cores.  Every step
+    is a uniformly scaled-down copy of the CUDA arm's step (each item on the same fraction of
+    its full event count, sized once before the warm-up so that a step takes about
+    --ref-step-seconds); value = sampled events / timed wall time, ms_per_step = the wall time
+    of one such step as run."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    import oracle
+    oracle.build()
+    items = oracle_step_items(args.events, args.int_events)
+    sizes = oracle_sample_sizes(items, args.ref_step_seconds)
+    for _ in range(args.warmup):
+        run_oracle_step(items, sizes)
     t0 = time.perf_counter()
-    cb = cpu_baseline(args.cpu_seconds / max(1, args.steps + args.warmup) * (args.steps + args.warmup),
-                      args.events, args.int_events)
+    for _ in range(args.steps):
+        run_oracle_step(items, sizes)
     wall = time.perf_counter() - t0
-    per_step_events = len(sweep_items()) * args.events + args.int_events
+    ms_per_step = wall / args.steps * 1e3
+    ev_step = sum(sizes)
+    value = ev_step / (ms_per_step / 1e3)
+    full_events = sum(full for _, _, full in items)
+    sample = (f"each step: the CUDA arm's step scaled down uniformly, {sizes[0]} events per generator item (36) "
+              f"and {sizes[-1]} integrated ({sizes[0] / args.events:.2e} of the full counts); FP64 oracle for "
+              "both precisions")
     line = {"impl": "reference", "metric": METRIC,
-            "value": cb["value"], "unit": "events/s", "n_gpus": int(os.environ.get("WORLD_SIZE", "1")),
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step_events / cb["value"] * 1e3,
+            "value": value, "unit": "events/s", "n_gpus": int(os.environ.get("WORLD_SIZE", "1")),
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": "same as the CUDA arm; timed on a bounded sample per item and scaled",
-                       "events_per_launch": args.events, "integrate_events": args.int_events},
-            "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": cb["sample"], "value": cb["value"]},
-            "e2e": {"value": cb["value"], "unit": "events/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-            "wall_s": round(wall, 1)}
+            "config": {"workload": "the CUDA arm's step (N-body sweep N=2..10 massless+massive, M=10 GeV, FP32 "
+                                   "and FP64; Dalitz integral) scaled down uniformly",
+                       "events_per_launch": sizes[0], "integrate_events": sizes[-1], "events_per_step": ev_step,
+                       "full_step_events": full_events,
+                       "extrapolated_ms_per_full_step": round(full_events / value * 1e3, 1)},
+            "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": sample, "value": value},
+            "e2e": {"value": value, "unit": "events/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
@@ -807,6 +883,9 @@ def main():
     ap.add_argument("--vegas-iterations", type=int, default=10)
     ap.add_argument("--vegas-case", default="both", choices=["both", "dalitz", "flat10"])
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--ref-step-seconds", type=float, default=3.0,
+                    help="reference arm: wall time of one sampled step of the oracle")
+    ap.add_argument("--detail-out", default=None, help="also write the detail record (JSON) to this file")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -489,6 +489,36 @@ hydra_status hydra_probe_fma_rate(hydra_dtype dtype, int iterations, double *fma
 hydra_status hydra_probe_write_bandwidth(void *buffer, uint64_t bytes, int reps, double *gb_per_s,
                                          hydra_stream_t stream);
 
+/*
+ * Rate of one arithmetic operation in the arithmetic a generator runs (no counterpart in the
+ * paper: the floating-point ceiling of the generators' rooflines counts the method's
+ * operations at these rates).  Independent chains of the operation, 8 per thread, 256-thread
+ * blocks on every SM; returns operations per second (a fused multiply-add counts one).
+ *   HYDRA_ARITH_F32            FP32 instructions; square root and reciprocal are the
+ *                              hardware approximations the FP32 kernels use
+ *   HYDRA_ARITH_DOUBLE_FLOAT   double-float pairs with the FP64 generator's own operations
+ *                              (FMA = a double-float product then sum)
+ *   HYDRA_ARITH_F64            FP64 instructions (IEEE square root and reciprocal)
+ * Blocks until done.  Errors: INVALID_ARG (unknown arithmetic or operation, iterations < 1),
+ * OOM, CUDA.
+ */
+typedef enum hydra_probe_arith {
+    HYDRA_ARITH_F32 = 0,
+    HYDRA_ARITH_DOUBLE_FLOAT = 1,
+    HYDRA_ARITH_F64 = 2
+} hydra_probe_arith;
+
+typedef enum hydra_probe_op {
+    HYDRA_OP_ADD = 0,
+    HYDRA_OP_MUL = 1,
+    HYDRA_OP_FMA = 2,
+    HYDRA_OP_SQRT = 3,
+    HYDRA_OP_RCP = 4
+} hydra_probe_op;
+
+hydra_status hydra_probe_op_rate(hydra_probe_arith arith, hydra_probe_op op, int iterations, double *ops_per_s,
+                                 hydra_stream_t stream);
+
 /* Release the per-device scratch memory of the library (all devices).  Not thread safe
  * with respect to calls in flight. */
 hydra_status hydra_shutdown(void);

@@ -82,6 +82,7 @@ def lib() -> ctypes.CDLL:
         L.hydra_phsp_vegas.argtypes = [d, i, dp, u64, i, dp, i, u64, i, i, d, i, dp, dp, dp, dp, vp]
         L.hydra_probe_fma_rate.argtypes = [i, i, dp, vp]
         L.hydra_probe_write_bandwidth.argtypes = [vp, u64, i, dp, vp]
+        L.hydra_probe_op_rate.argtypes = [i, i, i, dp, vp]
         L.hydra_get_fp64_arith.restype = i
         L.hydra_batch_create.argtypes = [i, u64, ctypes.POINTER(vp)]
         L.hydra_batch_run.argtypes = [vp, vp, i, i, vp]
@@ -98,7 +99,8 @@ def lib() -> ctypes.CDLL:
                      "hydra_phsp_evaluate",
                      "hydra_batch_create",
                      "hydra_batch_run", "hydra_batch_result", "hydra_batch_destroy", "hydra_shutdown",
-                     "hydra_server_create", "hydra_server_run", "hydra_server_destroy"):
+                     "hydra_server_create", "hydra_server_run", "hydra_server_destroy",
+                     "hydra_probe_fma_rate", "hydra_probe_write_bandwidth", "hydra_probe_op_rate"):
             getattr(L, name).restype = i
         _lib = L
     return _lib
@@ -283,6 +285,20 @@ def probe_fma_rate(dtype="f32", iterations: int = 100_000, stream=None) -> float
     """Measured fused multiply-add rate of the device (FMA instructions per second)."""
     r = ctypes.c_double()
     _check(lib().hydra_probe_fma_rate(_dtype_code(dtype), int(iterations), ctypes.byref(r), _stream_handle(stream)))
+    return r.value
+
+
+ARITH = {"f32": 0, "df": 1, "f64": 2}
+OPS = {"add": 0, "mul": 1, "fma": 2, "sqrt": 3, "rcp": 4}
+
+
+def probe_op_rate(arith: str, op: str, iterations: int = 20_000, stream=None) -> float:
+    """Measured rate (operations per second) of one arithmetic operation: arith "f32" (the FP32
+    kernels' arithmetic, hardware sqrt/rcp approximations), "df" (double-float pairs, the FP64
+    generator's default) or "f64" (FP64 instructions); op one of OPS."""
+    r = ctypes.c_double()
+    _check(lib().hydra_probe_op_rate(ARITH[arith], OPS[op], int(iterations), ctypes.byref(r),
+                                     _stream_handle(stream)))
     return r.value
 
 
