@@ -631,6 +631,44 @@ def run_extras(nev: int = 100_000_000, reps: int = 3, hbm_peak_gbs: float | None
     return res
 
 
+# ----------------------------------------------------------------------------- lambda A/B
+def run_lambda_ab(nev: int = 100_000_000, reps: int = 3, ns=(3, 10)) -> dict:
+    """FP32 generation (the sweep's massive decays, nev events) with Kallen's lambda as the
+    FP32 product of its four gap factors (the default) against the same factors multiplied in
+    FP64 (hydra_set_fp32_lambda): ms per launch, best of `reps` after one warm-up, CUDA
+    events on the launching stream, both arms at the launch shape the library holds for the
+    kernel."""
+    import torch
+    import paper_1711_05683_b300 as hp
+    buf = torch.empty(max(4 * n + 1 for n in ns) * nev, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    out = {"events": nev}
+    saved = hp.get_fp32_lambda()
+    try:
+        for n in ns:
+            o = buf[: 4 * n * nev].view(n, 4, nev)
+            w = buf[4 * n * nev: (4 * n + 1) * nev]
+            masses = workloads.sweep_masses(n, True)
+            row = {}
+            for name, mode in (("lambda_f32", hp.LAMBDA_FACTORED_F32), ("lambda_f64", hp.LAMBDA_F64)):
+                hp.set_fp32_lambda(mode)
+                hp.generate_into(workloads.SWEEP_M, masses, nev, 1000 + n, o, w, dtype="f32")
+                best = float("inf")
+                for _ in range(reps):
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    hp.generate_into(workloads.SWEEP_M, masses, nev, 1000 + n, o, w, dtype="f32")
+                    b.record(stream)
+                    b.synchronize()
+                    best = min(best, a.elapsed_time(b))
+                row[name + "_ms"] = round(best, 4)
+            row["slowdown_f64"] = round(row["lambda_f64_ms"] / row["lambda_f32_ms"], 3)
+            out[f"N{n}"] = row
+    finally:
+        hp.set_fp32_lambda(saved)
+    return out
+
+
 # ----------------------------------------------------------------------------- VEGAS
 # Thread instructions per point of the double-float VEGAS kernels (ncu smsp__inst_executed.sum
 # x 32 / points on 4e6-point iterations, 100 bins; profiles/vegas_eval_df_dalitz_4e6.md).
@@ -803,7 +841,8 @@ def oracle_step_items(nev_full: int, int_full: int):
 def oracle_sample_sizes(items, seconds: float) -> list[int]:
     """Event counts of a uniformly scaled-down step: each item's full count times one fraction,
     chosen from each item's rate on 4096 events (best of two, untimed) so that the sampled step
-    takes about `seconds`; multiples of 64, at least 64."""
+    takes about `seconds`; the smallest item's count a multiple of 64 (at least 64) and the
+    others in exact proportion to their full counts."""
     full_s = 0.0
     for label, fn, full in items:
         best = float("inf")
@@ -813,7 +852,9 @@ def oracle_sample_sizes(items, seconds: float) -> list[int]:
             best = min(best, time.perf_counter() - t0)
         full_s += full * best / 4096
     f = seconds / full_s
-    return [int(max(64, round(full * f / 64) * 64)) for _, _, full in items]
+    smallest = min(full for _, _, full in items)
+    base = int(max(64, round(smallest * f / 64) * 64))  # the smallest item's sample
+    return [int(round(base * full / smallest)) for _, _, full in items]
 
 
 def run_oracle_step(items, sizes) -> None:
@@ -878,7 +919,7 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--batch-count", type=int, default=4096)
     ap.add_argument("--arena-gb", type=float, default=40.0)
-    ap.add_argument("--workload", default="sweep", choices=["sweep", "batch", "serve", "vegas"])
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "batch", "serve", "vegas", "lambda-ab"])
     ap.add_argument("--vegas-calls", type=int, default=100_000_000)
     ap.add_argument("--vegas-iterations", type=int, default=10)
     ap.add_argument("--vegas-case", default="both", choices=["both", "dalitz", "flat10"])
@@ -907,6 +948,14 @@ def main():
         torch.cuda.set_device(0)
         hp.lib()
         print(json.dumps({"workload": "serve", **run_serve_workload(duration_s=args.serve_seconds)}), flush=True)
+    elif args.workload == "lambda-ab":
+        import torch
+        import paper_1711_05683_b300 as hp
+        from paper_1711_05683_b300 import build as hp_build
+        hp_build.build()
+        torch.cuda.set_device(0)
+        hp.lib()
+        print(json.dumps({"workload": "lambda-ab", **run_lambda_ab(args.events, reps=args.steps)}), flush=True)
     elif args.workload == "vegas":
         import torch
         import paper_1711_05683_b300 as hp

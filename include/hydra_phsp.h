@@ -474,6 +474,25 @@ hydra_status hydra_set_fp64_arith(hydra_fp64_arith arith);
 hydra_fp64_arith hydra_get_fp64_arith(void);
 
 /*
+ * Arithmetic of Kallen's lambda in FP32 generation (HYDRA_F32 in hydra_phsp_generate and
+ * hydra_phsp_generate_host; section 4.2's two-body momenta p = sqrt(lambda) / (2 M)).  The
+ * default evaluates lambda(M_{k+1}^2, M_k^2, m^2) as the product of its four gap factors
+ * Delta (Delta + 2 m)(Delta + 2 M_k)(Delta + 2 M_k + 2 m) in FP32: every factor is a sum of
+ * non-negative terms, so the product has no cancellation and carries at most a few FP32
+ * roundings, also at threshold.  HYDRA_LAMBDA_F64 multiplies the same four factors in FP64
+ * and rounds the product once (FP64 instructions on every two-body step; the FP32 generator
+ * then runs several times slower on B300, whose FP64 pipe is narrow).  Process-wide; other
+ * entry points are unaffected.  Errors: INVALID_ARG.
+ */
+typedef enum hydra_lambda_arith {
+    HYDRA_LAMBDA_FACTORED_F32 = 0,
+    HYDRA_LAMBDA_F64 = 1
+} hydra_lambda_arith;
+
+hydra_status hydra_set_fp32_lambda(hydra_lambda_arith arith);
+hydra_lambda_arith hydra_get_fp32_lambda(void);
+
+/*
  * Device ceilings for rooflines (no counterpart in the paper: these measure the GPU the
  * library runs on).  hydra_probe_fma_rate runs independent chains of FP32 or FP64 fused
  * multiply-adds in registers on every SM and returns the rate in FMA instructions per second

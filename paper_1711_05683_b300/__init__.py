@@ -84,6 +84,8 @@ def lib() -> ctypes.CDLL:
         L.hydra_probe_write_bandwidth.argtypes = [vp, u64, i, dp, vp]
         L.hydra_probe_op_rate.argtypes = [i, i, i, dp, vp]
         L.hydra_get_fp64_arith.restype = i
+        L.hydra_set_fp32_lambda.argtypes = [i]
+        L.hydra_get_fp32_lambda.restype = i
         L.hydra_batch_create.argtypes = [i, u64, ctypes.POINTER(vp)]
         L.hydra_batch_run.argtypes = [vp, vp, i, i, vp]
         L.hydra_batch_result.argtypes = [vp, i, ctypes.POINTER(Integral)]
@@ -100,7 +102,8 @@ def lib() -> ctypes.CDLL:
                      "hydra_batch_create",
                      "hydra_batch_run", "hydra_batch_result", "hydra_batch_destroy", "hydra_shutdown",
                      "hydra_server_create", "hydra_server_run", "hydra_server_destroy",
-                     "hydra_probe_fma_rate", "hydra_probe_write_bandwidth", "hydra_probe_op_rate"):
+                     "hydra_probe_fma_rate", "hydra_probe_write_bandwidth", "hydra_probe_op_rate",
+                     "hydra_set_fp32_lambda"):
             getattr(L, name).restype = i
         _lib = L
     return _lib
@@ -364,6 +367,19 @@ def set_fp64_arith(arith: int) -> None:
 
 def get_fp64_arith() -> int:
     return int(lib().hydra_get_fp64_arith())
+
+
+LAMBDA_FACTORED_F32, LAMBDA_F64 = 0, 1
+
+
+def set_fp32_lambda(arith: int) -> None:
+    """Arithmetic of Kallen's lambda in FP32 generation: LAMBDA_FACTORED_F32 (default: the four
+    gap factors multiplied in FP32) or LAMBDA_F64 (the same factors multiplied in FP64)."""
+    _check(lib().hydra_set_fp32_lambda(int(arith)))
+
+
+def get_fp32_lambda() -> int:
+    return int(lib().hydra_get_fp32_lambda())
 
 
 def get_launch_config(kind: int, n: int, dtype) -> tuple[int, int]:

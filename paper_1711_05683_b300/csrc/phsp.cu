@@ -39,7 +39,7 @@ namespace hydra {
 // Thread t takes the group of EPT consecutive events g*EPT.. (grid-stride over groups); the
 // last nevents % EPT events are taken one each by the first threads of the grid.  R is the
 // kinematic arithmetic (float, double, or df = pairs of floats for FP64 outputs).
-template <int N, typename R, int EPT, bool kMassless = false>
+template <int N, typename R, int EPT, bool kMassless = false, bool kLambda64 = false>
 __global__ void __launch_bounds__(512) phsp_generate_kernel(const __grid_constant__ DecayConsts C,
                                                             uint64_t nevents, uint64_t event_offset,
                                                             typename Prec<R>::Out* __restrict__ out,
@@ -58,14 +58,14 @@ __global__ void __launch_bounds__(512) phsp_generate_kernel(const __grid_constan
 #pragma unroll
         for (int q = 0; q < EPT; ++q) ev[q] = event_offset + e0 + q;
         StoreSink<R, EPT> sink{out + e0, weights + e0, ld};
-        raubold_lynch_group<N, R, EPT, kMassless>(C, ev, sink);
+        raubold_lynch_group<N, R, EPT, kMassless, kLambda64>(C, ev, sink);
     }
     if constexpr (EPT > 1) {
         const uint64_t e = groups * EPT + tid;
         if (e < nevents) {
             uint64_t ev[1] = {event_offset + e};
             StoreSink<R, 1> sink{out + e, weights + e, ld};
-            raubold_lynch_group<N, R, 1, kMassless>(C, ev, sink);
+            raubold_lynch_group<N, R, 1, kMassless, kLambda64>(C, ev, sink);
         }
     }
 }
@@ -235,18 +235,28 @@ struct Launch {
     int ept;
 };
 
-template <typename R, int EPT, bool M0>
+template <typename R, int EPT, bool M0, bool L64 = false>
 static const void* generate_kernel_n(int n) {
     switch (n) {
-        case 2: return reinterpret_cast<const void*>(&phsp_generate_kernel<2, R, EPT, M0>);
-        case 3: return reinterpret_cast<const void*>(&phsp_generate_kernel<3, R, EPT, M0>);
-        case 4: return reinterpret_cast<const void*>(&phsp_generate_kernel<4, R, EPT, M0>);
-        case 5: return reinterpret_cast<const void*>(&phsp_generate_kernel<5, R, EPT, M0>);
-        case 6: return reinterpret_cast<const void*>(&phsp_generate_kernel<6, R, EPT, M0>);
-        case 7: return reinterpret_cast<const void*>(&phsp_generate_kernel<7, R, EPT, M0>);
-        case 8: return reinterpret_cast<const void*>(&phsp_generate_kernel<8, R, EPT, M0>);
-        case 9: return reinterpret_cast<const void*>(&phsp_generate_kernel<9, R, EPT, M0>);
-        case 10: return reinterpret_cast<const void*>(&phsp_generate_kernel<10, R, EPT, M0>);
+        case 2: return reinterpret_cast<const void*>(&phsp_generate_kernel<2, R, EPT, M0, L64>);
+        case 3: return reinterpret_cast<const void*>(&phsp_generate_kernel<3, R, EPT, M0, L64>);
+        case 4: return reinterpret_cast<const void*>(&phsp_generate_kernel<4, R, EPT, M0, L64>);
+        case 5: return reinterpret_cast<const void*>(&phsp_generate_kernel<5, R, EPT, M0, L64>);
+        case 6: return reinterpret_cast<const void*>(&phsp_generate_kernel<6, R, EPT, M0, L64>);
+        case 7: return reinterpret_cast<const void*>(&phsp_generate_kernel<7, R, EPT, M0, L64>);
+        case 8: return reinterpret_cast<const void*>(&phsp_generate_kernel<8, R, EPT, M0, L64>);
+        case 9: return reinterpret_cast<const void*>(&phsp_generate_kernel<9, R, EPT, M0, L64>);
+        case 10: return reinterpret_cast<const void*>(&phsp_generate_kernel<10, R, EPT, M0, L64>);
+    }
+    return nullptr;
+}
+
+// FP32 generation with the lambda product in FP64 (hydra_set_fp32_lambda)
+static const void* generate_kernel_f32_lambda64(int n, int ept) {
+    switch (ept) {
+        case 1: return generate_kernel_n<float, 1, false, true>(n);
+        case 2: return generate_kernel_n<float, 2, false, true>(n);
+        case 4: return generate_kernel_n<float, 4, false, true>(n);
     }
     return nullptr;
 }
@@ -327,13 +337,16 @@ struct LaunchCfg {
 static LaunchCfg g_cfg[2][2][kNMax + 1];
 
 std::atomic<int> g_fp64_arith{HYDRA_FP64_DOUBLE_FLOAT};
+std::atomic<int> g_fp32_lambda{HYDRA_LAMBDA_FACTORED_F32};
 
 static Launch select_generate(hydra_dtype dtype, int n, const DecayConsts& C) {
     LaunchCfg& c = g_cfg[HYDRA_KERNEL_GENERATE][dtype][n];
     const int ept = c.ept.load(std::memory_order_relaxed);
     const bool massless = C.massless == (1u << n) - 1u;
     const void* k = nullptr;
-    if (dtype == HYDRA_F32) k = generate_kernel_for<float>(n, ept, massless);
+    if (dtype == HYDRA_F32)
+        k = g_fp32_lambda.load(std::memory_order_relaxed) == HYDRA_LAMBDA_F64 ? generate_kernel_f32_lambda64(n, ept)
+                                                                               : generate_kernel_for<float>(n, ept, massless);
     else if (g_fp64_arith.load(std::memory_order_relaxed) == HYDRA_FP64_NATIVE) k = generate_kernel_for<double>(n, ept, massless);
     else k = generate_kernel_for<df>(n, ept, massless);
     return Launch{k, c.block.load(std::memory_order_relaxed), ept};
@@ -788,6 +801,15 @@ hydra_status hydra_set_fp64_arith(hydra_fp64_arith arith) {
 }
 
 hydra_fp64_arith hydra_get_fp64_arith(void) { return static_cast<hydra_fp64_arith>(g_fp64_arith.load()); }
+
+hydra_status hydra_set_fp32_lambda(hydra_lambda_arith arith) {
+    if (arith != HYDRA_LAMBDA_FACTORED_F32 && arith != HYDRA_LAMBDA_F64)
+        return fail(HYDRA_ERR_INVALID_ARG, "unknown lambda arithmetic %d", static_cast<int>(arith));
+    g_fp32_lambda.store(arith);
+    return HYDRA_OK;
+}
+
+hydra_lambda_arith hydra_get_fp32_lambda(void) { return static_cast<hydra_lambda_arith>(g_fp32_lambda.load()); }
 
 hydra_status hydra_get_launch_config(hydra_kernel_kind kind, int n, hydra_dtype dtype, int* block,
                                      int* events_per_thread) {

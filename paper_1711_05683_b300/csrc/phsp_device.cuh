@@ -9,6 +9,7 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
 #include <cuda_runtime.h>
 
 #include "phsp_df.cuh"
@@ -109,6 +110,11 @@ template <> struct Prec<float> {
     }
     __device__ static float div(float a, float b) { return a * rcp(b); }
     __device__ static float fma_(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+    // sums of terms that cannot cancel (the same operations in FP32)
+    __device__ static float add_pos(float a, float b) { return a + b; }
+    __device__ static float fma_pos(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+    __device__ static float fma_lazy(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+    __device__ static float sub_lazy(float a, float b) { return a - b; }
     // sin and cos of phi = 2 pi (x + 1/2) 2^-32: __sincosf is accurate (|err| < 2^-21.4) on
     // (-pi, pi), so evaluate it at phi - pi and flip both signs.
     __device__ static void sincos_2pi_u(uint32_t x, float* s, float* c) {
@@ -152,6 +158,10 @@ template <> struct Prec<double> {
     __device__ static double rcp(double v) { return 1.0 / v; }
     __device__ static double div(double a, double b) { return a / b; }
     __device__ static double fma_(double a, double b, double c) { return __fma_rn(a, b, c); }
+    __device__ static double add_pos(double a, double b) { return a + b; }
+    __device__ static double fma_pos(double a, double b, double c) { return __fma_rn(a, b, c); }
+    __device__ static double fma_lazy(double a, double b, double c) { return __fma_rn(a, b, c); }
+    __device__ static double sub_lazy(double a, double b) { return a - b; }
     // sin and cos of phi = 2 pi u with u = (x + 1/2) 2^-32: sincospi(2u), argument exact.
     __device__ static void sincos_2pi_u(uint32_t x, double* s, double* c) {
         sincospi(__fma_rn(__uint2double_rn(x), 4.656612873077392578125e-10, 2.3283064365386962890625e-10), s, c);
@@ -196,6 +206,13 @@ template <> struct Prec<df> {
     __device__ static df rcp(df v) { return df_rcp(v); }
     __device__ static df div(df a, df b) { return df_div(a, b); }
     __device__ static df fma_(df a, df b, df c) { return a * b + c; }
+    // a + b and a b + c whose terms are >= 0 (no cancellation): left unnormalised
+    __device__ static df add_pos(df a, df b) { return df_add_lazy(a, b); }
+    __device__ static df fma_pos(df a, df b, df c) { return df_add_lazy(a * b, c); }
+    // sums whose result only feeds products, sums and the conversion to double (the absolute
+    // error at the scale of the terms is what matters): left unnormalised
+    __device__ static df fma_lazy(df a, df b, df c) { return df_add_lazy(a * b, c); }
+    __device__ static df sub_lazy(df a, df b) { return df_add_lazy(a, -b); }
     __device__ static void sincos_2pi_u(uint32_t x, df* s, df* c) { df_sincos_2pi_u(x, s_sincos_table, s, c); }
     // cos(phi_a - phi_b) = cos(2 pi (xa - xb) 2^-32), the integer difference taken mod 2^32
     __device__ static df cos_2pi_diff(uint32_t xa, uint32_t xb) {
@@ -247,8 +264,10 @@ template <> struct Prec<df> {
 //   sink.weight(w)
 // kMassless: a variant for decays whose daughters are all massless (chosen by the host), where
 // lambda(M_{k+1}^2, M_k^2, 0) = (Delta (Delta + 2 M_k))^2 and the momentum needs no square root.
+// kLambda64 (FP32 kinematics only): the four factors of lambda multiplied in FP64 and the
+// product rounded once to FP32 before its square root.
 // ------------------------------------------------------------------------------------
-template <int N, typename R, int EPT, bool kMassless = false, typename Sink>
+template <int N, typename R, int EPT, bool kMassless = false, bool kLambda64 = false, typename Sink>
 __device__ __forceinline__ void raubold_lynch_group(const DecayConsts& C, const uint64_t (&ev)[EPT],
                                                     Sink& sink) {
     using P = Prec<R>;
@@ -317,7 +336,7 @@ __device__ __forceinline__ void raubold_lynch_group(const DecayConsts& C, const 
             // intermediate mass M_k
             R Mk;
             if (k == 1) Mk = P::m(C, 0);
-            else Mk = P::fma_(P::half_odd(y[q][k - 2]), Ts, P::mu(C, k - 1));
+            else Mk = P::fma_pos(P::half_odd(y[q][k - 2]), Ts, P::mu(C, k - 1));
             // kinetic gap Delta_k = T (r_k - r_{k-1}) from integer differences
             R gap;
             if constexpr (N == 2) {
@@ -338,12 +357,21 @@ __device__ __forceinline__ void raubold_lynch_group(const DecayConsts& C, const 
             if constexpr (kMassless) {
                 // every daughter massless: lambda = (Delta (Delta + 2 M_k))^2, no square root
                 gm = gap * gap;
-                p = (gap * (gap + twoMk)) * halfInvM;
+                p = (gap * P::add_pos(gap, twoMk)) * halfInvM;
             } else {
                 const R twom = P::scale(P::m(C, k), 2.0f);
-                const R a = gap + twoMk;
-                gm = gap * (gap + twom);
-                const R lam = (gm * a) * (a + twom);
+                const R a = P::add_pos(gap, twoMk);
+                const R gpm = P::add_pos(gap, twom);
+                gm = gap * gpm;
+                R lam;
+                if constexpr (kLambda64) {
+                    static_assert(std::is_same<R, float>::value, "the FP64 lambda product is an FP32-kinematics mode");
+                    lam = __double2float_rn(__dmul_rn(__dmul_rn(__dmul_rn(static_cast<double>(gap), static_cast<double>(gpm)),
+                                                                static_cast<double>(a)),
+                                                      static_cast<double>(P::add_pos(a, twom))));
+                } else {
+                    lam = (gm * a) * P::add_pos(a, twom);
+                }
                 p = P::sqrt_(lam) * halfInvM;
             }
             w[q] = P::w_mul(w[q], p);
@@ -363,17 +391,20 @@ __device__ __forceinline__ void raubold_lynch_group(const DecayConsts& C, const 
             const R px = ps * cphi, py = ps * sphi, pz = p * cos_t;
             // energy of subsystem k in the rest frame of k+1: (M_{k+1}^2 + M_k^2 - m_{k+1}^2) / (2 M_{k+1})
             // = M_k + Delta (Delta + 2 m_{k+1}) / (2 M_{k+1}), a sum of positive terms
-            const R Es = P::fma_(gm, halfInvM, Mk);
+            const R Es = P::fma_pos(gm, halfInvM, Mk);
             if (k == N - 1) {
                 // parent at rest: no boost
-                dE[q] = M - Es; dx[q] = -px; dy[q] = -py; dz[q] = -pz;
+                dE[q] = P::sub_lazy(M, Es); dx[q] = -px; dy[q] = -py; dz[q] = -pz;
                 Q0[q] = Es; Qx[q] = px; Qy[q] = py; Qz[q] = pz;
             } else {
-                const R qp = P::fma_(Qz[q], pz, P::fma_(Qy[q], py, Qx[q] * px));
+                // Q.p: its terms may cancel; left unnormalised (the sum below renormalises)
+                const R qp = P::fma_lazy(Qz[q], pz, P::fma_lazy(Qy[q], py, Qx[q] * px));
                 const R E1 = P::fma_(Q0[q], Es, qp) * invM;
-                const R f = P::div(E1 + Es, Q0[q] + Mnext[q]);
+                const R f = P::div(P::add_pos(E1, Es), P::add_pos(Q0[q], Mnext[q]));
                 const R nx = P::fma_(f, Qx[q], px), ny = P::fma_(f, Qy[q], py), nz = P::fma_(f, Qz[q], pz);
-                dE[q] = Q0[q] - E1; dx[q] = Qx[q] - nx; dy[q] = Qy[q] - ny; dz[q] = Qz[q] - nz;
+                // the daughter by 4-momentum conservation (stored: left unnormalised)
+                dE[q] = P::sub_lazy(Q0[q], E1); dx[q] = P::sub_lazy(Qx[q], nx);
+                dy[q] = P::sub_lazy(Qy[q], ny); dz[q] = P::sub_lazy(Qz[q], nz);
                 Q0[q] = E1; Qx[q] = nx; Qy[q] = ny; Qz[q] = nz;
             }
             Mnext[q] = Mk;

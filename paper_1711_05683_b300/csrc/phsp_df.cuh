@@ -10,8 +10,12 @@
 // Addition is the "sloppy" double-word sum (TwoSum of the high parts, low parts added,
 // renormalised): its error is bounded by ~2^-46 (|x| + |y|), i.e. relative to the operands,
 // which is the measure the generator's tolerance uses (error at the event scale).
-// Multiplication is the FMA-based double-word product (relative error ~2^-46).
-// Reciprocal, division and square root take an FP32 hardware approximation as the seed and
+// Multiplication is the FMA-based double-word product (relative error ~2^-46).  Sums that
+// cannot cancel, and sums whose result only feeds products, sums and the conversion to double,
+// may skip the final renormalisation (df_add_lazy): the low part then exceeds ulp(hi)/2 by a
+// few ulp, which products, sums and conversions absorb at ~2^-48 of the terms' scale.
+// Reciprocal, division and square root take an FP32 hardware approximation as the seed (of
+// the pair rounded to FP32, so an unnormalised operand still gives a seed within ~1 ulp) and
 // apply one Newton-Raphson correction evaluated in double-word arithmetic, which squares
 // the seed's ~2^-23 relative error to ~2^-46.
 //
@@ -54,6 +58,17 @@ __device__ __forceinline__ df operator+(df x, df y) {
     return df_fast_two_sum(s.hi, l);
 }
 
+// x + y without the final renormalisation: (fl(x.hi + y.hi), its exact error + x.lo + y.lo).
+// For operands that cannot cancel (both >= 0) the low part stays within a few ulp of the
+// high part, which every consumer here tolerates (products and sums fold the low part in
+// with its own rounding, reciprocal and square root form their residual from both parts,
+// the conversion to double adds both); 3 FP32 operations fewer than operator+.  Also used
+// where only the absolute error matters (sin/cos values that multiply momenta).
+__device__ __forceinline__ df df_add_lazy(df x, df y) {
+    const df s = df_two_sum(x.hi, y.hi);
+    return df{s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo))};
+}
+
 __device__ __forceinline__ df operator-(df x) { return df{-x.hi, -x.lo}; }
 __device__ __forceinline__ df operator-(df x, df y) { return x + (-y); }
 
@@ -77,10 +92,10 @@ __device__ __forceinline__ df operator*(df x, float a) {
     return df{p, e};
 }
 
-// 1/y: seed r = rcp.approx(hi); e = 1 - y r (exact to first order in df); r (1 + e)
+// 1/y: seed r = rcp.approx(fl(hi + lo)); e = 1 - y r (exact to first order in df); r (1 + e)
 __device__ __forceinline__ df df_rcp(df y) {
     float r;
-    asm("rcp.approx.f32 %0, %1;" : "=f"(r) : "f"(y.hi));
+    asm("rcp.approx.f32 %0, %1;" : "=f"(r) : "f"(__fadd_rn(y.hi, y.lo)));
     float e = __fmaf_rn(-y.hi, r, 1.0f);
     e = __fmaf_rn(-y.lo, r, e);
     return df_fast_two_sum(r, __fmul_rn(r, e));
@@ -93,13 +108,14 @@ __device__ __forceinline__ df& operator*=(df& x, df y) {
     return x;
 }
 
-// sqrt(x), x >= 0: s0 = x.hi rsqrt(x.hi); s = s0 + (x - s0^2) / (2 s0), the residual formed
-// with an exact product; 0 for x = 0.
+// sqrt(x), x >= 0: with xh = fl(hi + lo), s0 = xh rsqrt(xh); s = s0 + (x - s0^2) / (2 s0), the
+// residual formed from both parts with an exact product; 0 for x = 0.
 __device__ __forceinline__ df df_sqrt(df x) {
-    if (!(x.hi > 0.0f)) return df{0.0f, 0.0f};
+    const float xh = __fadd_rn(x.hi, x.lo);
+    if (!(xh > 0.0f)) return df{0.0f, 0.0f};
     float r;
-    asm("rsqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x.hi));
-    const float s0 = __fmul_rn(x.hi, r);
+    asm("rsqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(xh));
+    const float s0 = __fmul_rn(xh, r);
     const float p = __fmul_rn(s0, s0);
     const float pe = __fmaf_rn(s0, s0, -p);
     const float res = __fadd_rn(__fsub_rn(__fsub_rn(x.hi, p), pe), x.lo);
@@ -198,6 +214,13 @@ __device__ __forceinline__ df df_from_double(double x) {
                                          __uint_as_float(static_cast<uint32_t>(el) << 23))
                              : 0.0f;
     return df{hi, sign ? -mag : mag};
+}
+
+// x + f for an FP32 f with |f| <= |x.hi|, left unnormalised (df_add_small without its final
+// FastTwoSum), for a result that only feeds products.
+__device__ __forceinline__ df df_add_small_lazy(df x, float f) {
+    const float s = __fadd_rn(x.hi, f);
+    return df{s, __fadd_rn(__fsub_rn(f, __fsub_rn(s, x.hi)), x.lo)};
 }
 
 // x + f for an FP32 f with |f| <= |x.hi| (a correction term): FastTwoSum and renormalise.
@@ -320,17 +343,20 @@ __device__ __forceinline__ void df_sincos_table_step(uint32_t k, uint32_t rem2, 
     // sin(delta)
     const float corr = __fmul_rn(__fmul_rn(d.hi, __fmul_rn(d2f, 0.16666667163372039795f)),
                                  __fmaf_rn(d2f, -0.05f, 1.0f));
-    const df sd = df_add_small(d, -corr);
+    const df sd = df_add_small_lazy(d, -corr);
     // cos(delta): delta^2 = p + e exactly (TwoProd) plus 2 hi lo
     const float p2 = d2f;
     const float e2 = __fmaf_rn(2.0f * d.hi, d.lo, __fmaf_rn(d.hi, d.hi, -p2));
     const df one_minus = df_fast_two_sum(1.0f, -0.5f * p2);
     const float tail = __fmaf_rn(__fmul_rn(p2, p2), 1.0f / 24.0f, -0.5f * e2);
-    const df cd = df_fast_two_sum(one_minus.hi, __fadd_rn(one_minus.lo, tail));
+    const df cd{one_minus.hi, __fadd_rn(one_minus.lo, tail)};  // feeds products: unnormalised
     const float4 t = T.e[k];
     const df sk{t.x, t.y}, ck{t.z, t.w};
-    *s = sk * cd + ck * sd;  // sin(theta_k + delta)
-    *c = ck * cd - sk * sd;  // cos(theta_k + delta)
+    // sin(theta_k + delta), cos(theta_k + delta); near a zero of either the two products
+    // cancel and the pair is left unnormalised: its absolute error (what a direction
+    // component needs) stays at ~2^-48
+    *s = df_add_lazy(sk * cd, ck * sd);
+    *c = df_add_lazy(ck * cd, -(sk * sd));
 }
 
 __device__ __forceinline__ void df_sincos_2pi_u(uint32_t x, const SinCosTable& T, df* s, df* c) {

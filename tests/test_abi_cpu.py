@@ -122,3 +122,10 @@ def test_fp64_arith_switch(L):
     assert hp.STATUS[L.hydra_set_fp64_arith(7)] == "HYDRA_ERR_INVALID_ARG"
     assert L.hydra_set_fp64_arith(0) == 0 and L.hydra_get_fp64_arith() == 0
     assert L.hydra_set_fp64_arith(1) == 0 and L.hydra_get_fp64_arith() == 1
+
+
+def test_fp32_lambda_switch(L):
+    assert L.hydra_get_fp32_lambda() == 0
+    assert hp.STATUS[L.hydra_set_fp32_lambda(2)] == "HYDRA_ERR_INVALID_ARG"
+    assert L.hydra_set_fp32_lambda(1) == 0 and L.hydra_get_fp32_lambda() == 1
+    assert L.hydra_set_fp32_lambda(0) == 0 and L.hydra_get_fp32_lambda() == 0

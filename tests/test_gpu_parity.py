@@ -401,6 +401,27 @@ def test_fp64_arithmetics_against_oracle(arith, n):
         hp.set_fp64_arith(saved)
 
 
+@pytest.mark.parametrize("n", [2, 3, 6, 10])
+def test_fp32_lambda_in_fp64_against_oracle(n):
+    """FP32 generation with Kallen's lambda multiplied in FP64 (hydra_set_fp32_lambda) meets the
+    FP32 tolerance against the oracle, on the sweep's massive decays and near threshold, and
+    stays within that tolerance of the default factorised FP32 lambda."""
+    saved = hp.get_fp32_lambda()
+    try:
+        for M, masses in ((10.0, workloads.sweep_masses(n, True)), workloads.near_threshold_decay(n, rel_gap=1e-7)):
+            hp.set_fp32_lambda(hp.LAMBDA_F64)
+            err_p, err_w = compare_events(M, masses, 3001, 500 + n, "f32")
+            assert err_p <= TOL_P["f32"] and err_w <= TOL_W["f32"], (n, err_p, err_w)
+            p64, w64 = hp.generate(M, masses, 3001, 500 + n, dtype="f32")
+            hp.set_fp32_lambda(hp.LAMBDA_FACTORED_F32)
+            p32, w32 = hp.generate(M, masses, 3001, 500 + n, dtype="f32")
+            torch.cuda.synchronize()
+            scale = max(M, float(p32[:, 0, :3001].max()))
+            assert float((p64[:, :, :3001] - p32[:, :, :3001]).abs().max()) <= 2 * TOL_P["f32"] * scale
+    finally:
+        hp.set_fp32_lambda(saved)
+
+
 def test_double_float_directions_over_many_angles():
     """2e5 two-body events (two angle draws each, all octants of the double-float sine and
     cosine) against the oracle; the error is reported at ~1e-14 of the scale."""
