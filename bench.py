@@ -507,42 +507,49 @@ def batch_waves(reqs, arena_bytes=ARENA_BYTES):
 
 def run_batch_workload(count: int = 4096, reps: int = 2, arena_bytes: int = ARENA_BYTES) -> dict:
     """Uneven generate requests (N 2..8, M 1..10 GeV, masses U[0, M/2N], events log-uniform
-    1e3..1e7, per-request seeds): one persistent batch launch (graph) per wave against one
-    plain launch per request, same waves, same 40 GB output arena (overwritten per wave)."""
+    1e3..1e7, per-request seeds), FP32 outputs overwritten wave to wave: one hydra_phsp_batch_run
+    call with a device budget of arena_bytes (the library packs the waves, one persistent graph
+    launch each, shape from the autotuner) against one plain hydra_phsp_generate launch per
+    request into an arena of the same size (greedy waves in request order).  Wall time of the
+    blocking call (best of `reps` after a warm-up that allocates the library's kept arena)
+    against CUDA-event time of the plain launches plus their final synchronisation."""
     import numpy as np
     import torch
     import paper_1711_05683_b300 as hp
     reqs = workloads.batch_requests(count)
-    waves = batch_waves(reqs, arena_bytes)
+    total = sum(r.nevents for r in reqs)
+    out_bytes = sum((4 * len(r.masses) + 1) * r.nevents * 4 for r in reqs)
+    table = np.zeros(count, dtype=hp.batch_request_dtype())
+    for i, r in enumerate(reqs):
+        n = len(r.masses)
+        rec = table[i]
+        rec["kind"], rec["n"], rec["dtype"], rec["M"] = hp.REQ_GENERATE, n, hp.F32, r.M
+        rec["masses"][:n] = r.masses
+        rec["seed"], rec["nevents"], rec["dest"] = r.seed, r.nevents, hp.DEST_NONE
+    stream = torch.cuda.current_stream()
+    hp.batch_run(table, arena_bytes, stream=stream)  # warm-up: the library allocates and keeps its buffers
+    waves, slices = hp.batch_stats()
+    best_b = float("inf")
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        hp.batch_run(table, arena_bytes, stream=stream)
+        best_b = min(best_b, time.perf_counter() - t0)
+    shape = hp.get_batch_shape("f32")
+    hp.shutdown()  # release the kept arena before the plain arm allocates its own
+    # plain arm: one launch per request into a same-size arena, greedy waves
+    pwaves = batch_waves(reqs, arena_bytes)
     arena = torch.empty(arena_bytes // 4, dtype=torch.float32, device="cuda")
     base = arena.data_ptr()
-    tables = []
-    for wave in waves:
-        t = np.zeros(len(wave), dtype=hp.request_dtype())
-        for i, (r, off, ld) in enumerate(wave):
-            n = len(r.masses)
-            rec = t[i]
-            rec["kind"], rec["n"], rec["dtype"], rec["M"] = hp.REQ_GENERATE, n, hp.F32, r.M
-            rec["masses"][:n] = r.masses
-            rec["seed"], rec["count"], rec["ld"] = r.seed, r.nevents, ld
-            rec["out"] = base + off
-            rec["weights"] = base + off + 4 * n * ld * 4
-        tables.append(t)
-    batch = hp.Batch(max(len(w) for w in waves))
-    stream = torch.cuda.current_stream()
     L = hp.lib()
     import ctypes
     sh = ctypes.c_void_p(stream.cuda_stream)
     plain_args = []
-    for wave in waves:
+    for wave in pwaves:
         for r, off, ld in wave:
             n = len(r.masses)
             plain_args.append((r.M, n, (ctypes.c_double * n)(*r.masses), r.nevents, r.seed,
                                ctypes.c_void_p(base + off), ld, ctypes.c_void_p(base + off + 4 * n * ld * 4)))
-
-    def batched(use_graph=True):
-        for t in tables:
-            batch.run(t, use_graph=use_graph, stream=stream)
 
     def plain():
         for M, n, m, nev, seed, out, ld, w in plain_args:
@@ -550,38 +557,24 @@ def run_batch_workload(count: int = 4096, reps: int = 2, arena_bytes: int = AREN
             if rc:
                 raise hp.HydraError(rc, L.hydra_last_error().decode())
 
-    def timed(fn):
-        fn()
+    plain()
+    torch.cuda.synchronize()
+    best_p = float("inf")
+    for _ in range(reps):
         torch.cuda.synchronize()
-        best_dev, best_wall = float("inf"), float("inf")
-        for _ in range(reps):
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            a.record(stream)
-            fn()
-            b.record(stream)
-            b.synchronize()
-            best_wall = min(best_wall, time.perf_counter() - t0)
-            best_dev = min(best_dev, a.elapsed_time(b) / 1e3)
-        return best_dev, best_wall
-
-    total = sum(r.nevents for r in reqs)
-    out_bytes = sum((4 * len(r.masses) + 1) * r.nevents * 4 for r in reqs)
-    bd, bw = timed(batched)
-    gd, gw = timed(lambda: batched(False))
-    pd, pw = timed(plain)
-    batch.close()
+        t0 = time.perf_counter()
+        plain()
+        torch.cuda.synchronize()
+        best_p = min(best_p, time.perf_counter() - t0)
     del arena
     torch.cuda.empty_cache()
-    return {"requests": count, "events": total, "output_bytes": out_bytes, "waves": len(waves),
-            "arena_bytes": arena_bytes,
-            "batched_graph": {"events_per_s": total / bw, "s": bw, "device_s": bd,
-                              "hbm_gbs": out_bytes / bw / 1e9},
-            "batched_no_graph": {"events_per_s": total / gw, "s": gw, "device_s": gd},
-            "plain_launches": {"events_per_s": total / pw, "s": pw, "device_s": pd,
-                               "hbm_gbs": out_bytes / pw / 1e9},
-            "speedup_vs_plain": pw / bw}
+    return {"requests": count, "events": total, "output_bytes": out_bytes, "budget_bytes": arena_bytes,
+            "batched": {"call": "hydra_phsp_batch_run", "events_per_s": total / best_b, "s": best_b,
+                        "hbm_gbs": out_bytes / best_b / 1e9, "waves": waves, "slices": slices,
+                        "shape": {"block": shape[0], "ept_by_n": shape[1][2:]}},
+            "plain_launches": {"events_per_s": total / best_p, "s": best_p, "waves": len(pwaves),
+                               "hbm_gbs": out_bytes / best_p / 1e9},
+            "speedup_vs_plain": best_p / best_b}
 
 
 # ----------------------------------------------------------------------------- extensions
@@ -937,7 +930,10 @@ def main():
         hp_build.build()
         torch.cuda.set_device(0)
         hp.lib()
-        print(json.dumps({"workload": "batch", **run_batch_workload(args.batch_count, reps=args.steps,
+        from paper_1711_05683_b300 import autotune
+        tuning = autotune.load_or_tune()
+        print(json.dumps({"workload": "batch", "tuning_source": tuning.get("source"),
+                          **run_batch_workload(args.batch_count, reps=args.steps,
                                                                    arena_bytes=int(args.arena_gb * 1e9))}),
               flush=True)
     elif args.workload == "serve":

@@ -384,6 +384,72 @@ hydra_status hydra_batch_result(hydra_batch *batch, int i, hydra_integral *resul
 hydra_status hydra_batch_destroy(hydra_batch *batch);
 
 /*
+ * Launch shape of the persistent batch kernel (no counterpart in the paper; the autotuner sets
+ * it).  block: threads per block of FP32 runs, 128, 256 or 512 (FP64 runs: 256), read when a
+ * runner is created (hydra_batch_create, hydra_phsp_batch_run); ept_by_n[n], n = 2..10: events
+ * each thread of a generation tile computes in lockstep (FP32: 1, 2, or 4 for n <= 6; FP64: 2),
+ * read by every run.  Entries 0 and 1 are ignored.  Results do not depend on the shape.
+ * Process-wide.  Errors: INVALID_ARG.
+ */
+hydra_status hydra_set_batch_shape(hydra_dtype dtype, int block, const int32_t *ept_by_n);
+hydra_status hydra_get_batch_shape(hydra_dtype dtype, int *block, int32_t *ept_by_n);
+
+/* ------------------------------------------------------------------------------------
+ * Whole requests under a device-memory budget (section 4.2's generation and section 3's
+ * integration for many requests at once).
+ * ------------------------------------------------------------------------------------ */
+typedef enum hydra_dest {
+    HYDRA_DEST_NONE = 0,   /* generated outputs are computed and dropped with their wave */
+    HYDRA_DEST_HOST = 1,   /* out / weights are host buffers (page-locked memory copies fastest) */
+    HYDRA_DEST_DEVICE = 2  /* out / weights are device buffers, written in place */
+} hydra_dest;
+
+typedef struct hydra_batch_request {
+    int32_t kind;          /* HYDRA_REQ_GENERATE or HYDRA_REQ_INTEGRATE */
+    int32_t n;             /* daughters, 2..10 */
+    int32_t dtype;         /* hydra_dtype; all requests of one call share it */
+    int32_t me;            /* integrate: hydra_me_id (FP32 or FP64 kinematics as dtype) */
+    double M;              /* parent mass */
+    double masses[10];     /* daughter masses (first n used) */
+    double params[6];      /* integrate: matrix-element parameters */
+    uint64_t seed;         /* Philox key */
+    uint64_t event_offset; /* counter-event index of the request's event 0 */
+    uint64_t nevents;      /* > 0 */
+    int32_t dest;          /* generate: hydra_dest */
+    int32_t status;        /* out: HYDRA_OK, or the validation error of this request */
+    void *out;             /* generate, HOST or DEVICE: [n][4][ld] of dtype (DEVICE: 16-byte aligned) */
+    uint64_t ld;           /* >= nevents (DEVICE: a multiple of 4) */
+    void *weights;         /* generate, HOST or DEVICE: nevents values of dtype (DEVICE: 16-byte aligned) */
+    hydra_integral result; /* integrate, out: as hydra_phsp_integrate */
+} hydra_batch_request;
+
+/*
+ * Run nreq whole requests (generate or integrate, any n, masses and event counts) with at most
+ * budget_bytes of device memory allocated by the call, and block until every output is in its
+ * destination and every integral result is in its request.
+ *
+ * The call validates every request first (each one's status is set; on the first invalid one
+ * it returns that error and launches nothing).  From the budget it takes the batch runner's
+ * tables and tile partials and the integrals' segment storage (8 doubles per 2^21 events), and
+ * the rest is the output arena.  Requests are packed in order into waves: a generate request
+ * with destination NONE or HOST takes [4n+1][ld] values of the arena (ld = events rounded up
+ * to 4), a request larger than the arena (half of it when any output goes to the host) is
+ * split across waves, DEVICE outputs are written in place, and integrals run as slices of 2^26
+ * events (at most 16 per wave).  Each wave is one run of a batch runner (hydra_batch_run: one
+ * persistent launch, replayed from a CUDA graph, with the shape of hydra_set_batch_shape).
+ * Outputs bound for the host are copied out of one half of the arena on a copy stream while
+ * the next wave computes into the other half.  Every event and every integral is bit for bit
+ * what hydra_phsp_generate / hydra_phsp_integrate give for the same arguments.
+ *
+ * Errors: the validation errors of hydra_phsp_generate and hydra_phsp_integrate (per request),
+ * INVALID_ARG (no requests, mixed dtypes, a budget too small for these requests), OOM, CUDA.
+ */
+hydra_status hydra_phsp_batch_run(hydra_batch_request *reqs, int nreq, size_t budget_bytes, hydra_stream_t stream);
+
+/* Waves and slices of the calling thread's latest successful hydra_phsp_batch_run. */
+hydra_status hydra_phsp_batch_stats(uint64_t *waves, uint64_t *slices);
+
+/*
  * Continuous-batching server (section 4.2's generation and section 3's integration as a
  * service): the serving loop in C++ over two batch runners.  Requests arrive over time; each
  * turn of the loop admits arrived requests while their memory fits two device rings (generated

@@ -91,6 +91,10 @@ def lib() -> ctypes.CDLL:
         L.hydra_batch_result.argtypes = [vp, i, ctypes.POINTER(Integral)]
         L.hydra_batch_destroy.argtypes = [vp]
         L.hydra_get_launch_config.argtypes = [i, i, i, ctypes.POINTER(i), ctypes.POINTER(i)]
+        L.hydra_set_batch_shape.argtypes = [i, i, vp]
+        L.hydra_get_batch_shape.argtypes = [i, ctypes.POINTER(i), vp]
+        L.hydra_phsp_batch_run.argtypes = [vp, i, ctypes.c_size_t, vp]
+        L.hydra_phsp_batch_stats.argtypes = [ctypes.POINTER(u64), ctypes.POINTER(u64)]
         L.hydra_server_create.argtypes = [u64, vp, u64, i, i, u64, i, ctypes.POINTER(vp)]
         L.hydra_server_run.argtypes = [vp, vp, i, d, vp, dp, ctypes.POINTER(u64)]
         L.hydra_server_destroy.argtypes = [vp]
@@ -103,7 +107,8 @@ def lib() -> ctypes.CDLL:
                      "hydra_batch_run", "hydra_batch_result", "hydra_batch_destroy", "hydra_shutdown",
                      "hydra_server_create", "hydra_server_run", "hydra_server_destroy",
                      "hydra_probe_fma_rate", "hydra_probe_write_bandwidth", "hydra_probe_op_rate",
-                     "hydra_set_fp32_lambda"):
+                     "hydra_set_fp32_lambda", "hydra_set_batch_shape", "hydra_get_batch_shape",
+                     "hydra_phsp_batch_run", "hydra_phsp_batch_stats"):
             getattr(L, name).restype = i
         _lib = L
     return _lib
@@ -404,6 +409,52 @@ def request_dtype():
                   align=True)
     assert dt.itemsize == 224
     return dt
+
+
+def batch_request_dtype():
+    """numpy record type with the layout of the C struct hydra_batch_request (264 bytes)."""
+    import numpy as np
+    dt = np.dtype([("kind", "<i4"), ("n", "<i4"), ("dtype", "<i4"), ("me", "<i4"), ("M", "<f8"),
+                   ("masses", "<f8", (10,)), ("params", "<f8", (6,)), ("seed", "<u8"), ("event_offset", "<u8"),
+                   ("nevents", "<u8"), ("dest", "<i4"), ("status", "<i4"), ("out", "<u8"), ("ld", "<u8"),
+                   ("weights", "<u8"),
+                   ("result", [(k, "<f8") for k in ("mean", "var_mean", "sum_f", "sum_f2", "sum_w", "sum_w2")]
+                    + [("n", "<u8")])], align=True)
+    assert dt.itemsize == 264
+    return dt
+
+
+DEST_NONE, DEST_HOST, DEST_DEVICE = 0, 1, 2
+
+
+def batch_run(table, budget_bytes: int, stream=None) -> None:
+    """hydra_phsp_batch_run over a batch_request_dtype() array (in place: each record's status
+    and, for integrals, result are written); blocks until every output has landed."""
+    _check(lib().hydra_phsp_batch_run(ctypes.c_void_p(table.ctypes.data), len(table), int(budget_bytes),
+                                      _stream_handle(stream)))
+
+
+def batch_stats() -> tuple[int, int]:
+    """(waves, slices) of this thread's latest successful batch_run."""
+    w, s = ctypes.c_uint64(), ctypes.c_uint64()
+    _check(lib().hydra_phsp_batch_stats(ctypes.byref(w), ctypes.byref(s)))
+    return w.value, s.value
+
+
+def set_batch_shape(dtype, block: int, ept_by_n) -> None:
+    """Launch shape of the persistent batch kernel: threads per block (FP32 runs) and events per
+    thread of generation tiles for n = 2..10 (a mapping n -> ept or a sequence indexed by n)."""
+    arr = (ctypes.c_int32 * 11)(*([2] * 11))
+    for n in range(2, 11):
+        arr[n] = int(ept_by_n[n])
+    _check(lib().hydra_set_batch_shape(_dtype_code(dtype), int(block), ctypes.cast(arr, ctypes.c_void_p)))
+
+
+def get_batch_shape(dtype) -> tuple[int, list]:
+    arr = (ctypes.c_int32 * 11)()
+    b = ctypes.c_int()
+    _check(lib().hydra_get_batch_shape(_dtype_code(dtype), ctypes.byref(b), ctypes.cast(arr, ctypes.c_void_p)))
+    return b.value, list(arr)
 
 
 def serve_request_dtype():

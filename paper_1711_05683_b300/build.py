@@ -11,7 +11,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "libhydra_phsp.so")
-SOURCES = [os.path.join(CSRC, "phsp.cu"), os.path.join(CSRC, "phsp_batch.cu"),
+SOURCES = [os.path.join(CSRC, "phsp.cu"), os.path.join(CSRC, "phsp_batch.cu"), os.path.join(CSRC, "phsp_batch_f32.cu"),
            os.path.join(CSRC, "phsp_extras.cu"), os.path.join(CSRC, "phsp_vegas.cu"),
            os.path.join(CSRC, "phsp_peaks.cu"), os.path.join(CSRC, "phsp_serve.cu")]
 DEPS = SOURCES + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))] + \

@@ -827,6 +827,7 @@ hydra_status hydra_get_launch_config(hydra_kernel_kind kind, int n, hydra_dtype 
 hydra_status hydra_shutdown(void) {
     release_extras_scratch();
     release_vegas_scratch();
+    release_batch_run_scratch();
     std::lock_guard<std::mutex> lk(g_scratch_mu);
     int cur = 0;
     cudaGetDevice(&cur);

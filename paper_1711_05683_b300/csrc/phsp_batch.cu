@@ -26,155 +26,9 @@
 #include "phsp_host.h"
 #include "phsp_integral.cuh"
 
+#include "phsp_batch.cuh"
+
 namespace hydra {
-
-constexpr int kBatchBlock = 256;
-constexpr int kBatchWarps = kBatchBlock / 32;
-constexpr int kBatchEPT = 2;                 // events per thread in the batch kernel (integral tiles, FP64 generation)
-constexpr uint64_t kSegEvents = uint64_t(kTileEvents) * kSegTiles;  // 2^21
-
-struct BatchEntry {
-    DecayConsts C;
-    MEConsts P;
-    uint64_t event_offset, first, count, total;
-    void* out;
-    uint64_t ld;
-    void* weights;
-    double* seg;
-    uint64_t partial_begin;  // integrate: first slot of this slice in the run's tile partials
-    int32_t n, kind, me, dtype;
-};
-
-struct BatchHeader {
-    unsigned long long tile_counter;  // reset to 0 by every run's table copy
-    int32_t nreq, nfinal;
-    uint64_t ntiles, nsegjobs;
-    const BatchEntry* entries;
-    const uint64_t* tile_prefix;  // [nreq + 1], over the slices in tile_order
-    const uint64_t* seg_prefix;   // [nreq + 1], over the slices in table order
-    const int32_t* tile_order;    // [nreq]: table index of the j-th slice in tile order
-    const int32_t* final_idx;     // [nfinal]
-};
-
-// Largest r in [0, n) with prefix[r] <= x (prefix[0] = 0 <= x).
-__device__ __forceinline__ int find_slot(const uint64_t* __restrict__ prefix, int n, uint64_t x) {
-    int lo = 0, hi = n;
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (prefix[mid] <= x) lo = mid;
-        else hi = mid;
-    }
-    return lo;
-}
-
-// Events per thread of a generation tile: four for FP32 up to N = 6 (where the single-request
-// kernels are bound by HBM writes and 16-byte stores pay), two above and for FP64.
-template <int N, typename R>
-__host__ __device__ constexpr int gen_tile_ept() {
-    return (std::is_same<R, float>::value && N >= 3 && N <= 6) ? 4 : 2;
-}
-
-template <int N, typename R>
-__device__ __forceinline__ void generate_tile(const DecayConsts& C, const BatchEntry& e, uint64_t lt, int lane) {
-    constexpr int kEPT = gen_tile_ept<N, R>();
-    using Out = typename Prec<R>::Out;
-    Out* out = static_cast<Out*>(e.out);
-    Out* w = static_cast<Out*>(e.weights);
-    const uint64_t base = lt * kTileEvents;
-#pragma unroll 1
-    for (int it = 0; it < kTileEvents / (32 * kEPT); ++it) {
-        const uint64_t j0 = base + static_cast<uint64_t>(it * 32 + lane) * kEPT;
-        if (j0 + kEPT <= e.count) {
-            uint64_t ev[kEPT];
-#pragma unroll
-            for (int q = 0; q < kEPT; ++q) ev[q] = e.event_offset + e.first + j0 + q;
-            StoreSink<R, kEPT> sink{out + j0, w + j0, e.ld};
-            raubold_lynch_group<N, R, kEPT>(C, ev, sink);
-        } else {
-            for (uint64_t j = j0; j < e.count && j < j0 + kEPT; ++j) {
-                uint64_t ev[1] = {e.event_offset + e.first + j};
-                StoreSink<R, 1> sink{out + j, w + j, e.ld};
-                raubold_lynch_group<N, R, 1>(C, ev, sink);
-            }
-        }
-    }
-}
-
-template <typename R>
-__device__ __forceinline__ void generate_tile_n(int n, const DecayConsts& C, const BatchEntry& e, uint64_t lt, int lane) {
-    switch (n) {
-        case 2: generate_tile<2, R>(C, e, lt, lane); break;
-        case 3: generate_tile<3, R>(C, e, lt, lane); break;
-        case 4: generate_tile<4, R>(C, e, lt, lane); break;
-        case 5: generate_tile<5, R>(C, e, lt, lane); break;
-        case 6: generate_tile<6, R>(C, e, lt, lane); break;
-        case 7: generate_tile<7, R>(C, e, lt, lane); break;
-        case 8: generate_tile<8, R>(C, e, lt, lane); break;
-        case 9: generate_tile<9, R>(C, e, lt, lane); break;
-        case 10: generate_tile<10, R>(C, e, lt, lane); break;
-    }
-}
-
-template <typename R>
-__device__ __forceinline__ TileSums integrate_tile_n(int n, int me, const DecayConsts& C, const MEConsts& P,
-                                                     const BatchEntry& e, uint64_t tile, int lane) {
-    if (me == HYDRA_ME_DALITZ_2BW)
-        return tile_sums<3, R, HYDRA_ME_DALITZ_2BW, kBatchEPT>(C, P, e.total, e.event_offset, tile, lane);
-    switch (n) {
-        case 2: return tile_sums<2, R, HYDRA_ME_FLAT, kBatchEPT>(C, P, e.total, e.event_offset, tile, lane);
-        case 3: return tile_sums<3, R, HYDRA_ME_FLAT, kBatchEPT>(C, P, e.total, e.event_offset, tile, lane);
-        case 4: return tile_sums<4, R, HYDRA_ME_FLAT, kBatchEPT>(C, P, e.total, e.event_offset, tile, lane);
-        case 5: return tile_sums<5, R, HYDRA_ME_FLAT, kBatchEPT>(C, P, e.total, e.event_offset, tile, lane);
-        case 6: return tile_sums<6, R, HYDRA_ME_FLAT, kBatchEPT>(C, P, e.total, e.event_offset, tile, lane);
-        case 7: return tile_sums<7, R, HYDRA_ME_FLAT, kBatchEPT>(C, P, e.total, e.event_offset, tile, lane);
-        case 8: return tile_sums<8, R, HYDRA_ME_FLAT, kBatchEPT>(C, P, e.total, e.event_offset, tile, lane);
-        case 9: return tile_sums<9, R, HYDRA_ME_FLAT, kBatchEPT>(C, P, e.total, e.event_offset, tile, lane);
-        default: return tile_sums<10, R, HYDRA_ME_FLAT, kBatchEPT>(C, P, e.total, e.event_offset, tile, lane);
-    }
-}
-
-// RG: arithmetic of generation tiles (float, double or df); RI: of integral tiles.
-template <typename RG, typename RI>
-__global__ void __launch_bounds__(kBatchBlock) phsp_batch_kernel(BatchHeader* __restrict__ hdr,
-                                                                 TileSums* __restrict__ partials) {
-    if constexpr (std::is_same<RG, df>::value) {
-        df_sincos_table_init();
-        __syncthreads();
-    }
-    __shared__ DecayConsts sC[kBatchWarps];
-    __shared__ MEConsts sP[kBatchWarps];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nreq = hdr->nreq;
-    const uint64_t ntiles = hdr->ntiles;
-    const BatchEntry* __restrict__ entries = hdr->entries;
-    const uint64_t* __restrict__ prefix = hdr->tile_prefix;
-    const int32_t* __restrict__ order = hdr->tile_order;
-    for (;;) {
-        unsigned long long t = 0;
-        if (lane == 0) t = atomicAdd(&hdr->tile_counter, 1ull);
-        t = __shfl_sync(0xffffffffu, t, 0);
-        if (t >= ntiles) break;
-        const int j = find_slot(prefix, nreq, t);
-        const BatchEntry& e = entries[order[j]];
-        {
-            const uint32_t* src = reinterpret_cast<const uint32_t*>(&e.C);
-            uint32_t* dst = reinterpret_cast<uint32_t*>(&sC[warp]);
-            for (int i = lane; i < static_cast<int>(sizeof(DecayConsts) / 4); i += 32) dst[i] = src[i];
-            const uint32_t* srcp = reinterpret_cast<const uint32_t*>(&e.P);
-            uint32_t* dstp = reinterpret_cast<uint32_t*>(&sP[warp]);
-            for (int i = lane; i < static_cast<int>(sizeof(MEConsts) / 4); i += 32) dstp[i] = srcp[i];
-        }
-        __syncwarp();
-        const uint64_t lt = t - prefix[j];
-        if (e.kind == HYDRA_REQ_GENERATE) {
-            generate_tile_n<RG>(e.n, sC[warp], e, lt, lane);
-        } else {
-            const TileSums ts = integrate_tile_n<RI>(e.n, e.me, sC[warp], sP[warp], e, e.first / kTileEvents + lt, lane);
-            if (lane == 0) partials[e.partial_begin + lt] = ts;
-        }
-        __syncwarp();
-    }
-}
 
 // One warp per (integral slice, segment): the slice's tile partials -> the request's
 // segment storage, with the same segment_sums as the single-request path.
@@ -212,6 +66,7 @@ using namespace hydra;
 
 struct hydra_batch {
     int device = 0;
+    int block_f32 = kBatchBlock;  // threads per block of FP32 runs (the process-wide shape at creation)
     int max_requests = 0;
     uint64_t max_tiles = 0;
     size_t table_bytes = 0;
@@ -245,6 +100,14 @@ size_t table_size(int nreq, int nfinal) {
     return align_up(off, 256);
 }
 
+// Launch shape of the persistent kernel, process-wide (hydra_set_batch_shape): threads per block
+// of FP32 runs (read when a runner is created) and events per thread of generation tiles by n
+// (read by every run).  Defaults: 256 threads; FP32 four events per thread for n = 3..6 (where
+// generation is bound by HBM writes and 16-byte stores pay) and two otherwise; FP64 two.
+std::mutex g_shape_mu;
+int g_batch_block_f32 = kBatchBlock;
+int32_t g_batch_ept[2][kNMax + 1] = {{2, 2, 2, 4, 4, 4, 4, 2, 2, 2, 2}, {2, 2, 2, 2, 2, 2, 2, 2, 2, 2, 2}};
+
 // Variant 0: FP32; 1: FP64 with native FP64 arithmetic; 2: FP64 with double-float generation and integrals.
 int run_variant(int dtype) {
     if (dtype == HYDRA_F32) return 0;
@@ -253,12 +116,13 @@ int run_variant(int dtype) {
 
 void launch_run_kernels(hydra_batch* b, int v, cudaStream_t s) {
     BatchHeader* hdr = reinterpret_cast<BatchHeader*>(b->d_table);
-    if (v == 0)
-        phsp_batch_kernel<float, float><<<b->grid_main[v], kBatchBlock, 0, s>>>(hdr, b->d_partials);
-    else if (v == 1)
-        phsp_batch_kernel<double, double><<<b->grid_main[v], kBatchBlock, 0, s>>>(hdr, b->d_partials);
-    else
-        phsp_batch_kernel<df, df><<<b->grid_main[v], kBatchBlock, 0, s>>>(hdr, b->d_partials);
+    if (v == 0) {
+        launch_batch_kernel_f32(b->block_f32, b->grid_main[v], hdr, b->d_partials, s);
+    } else if (v == 1) {
+        phsp_batch_kernel<double, double, kBatchBlock><<<b->grid_main[v], kBatchBlock, 0, s>>>(hdr, b->d_partials);
+    } else {
+        phsp_batch_kernel<df, df, kBatchBlock><<<b->grid_main[v], kBatchBlock, 0, s>>>(hdr, b->d_partials);
+    }
     batch_reduce_segments<<<b->grid_aux, kSegBlock, 0, s>>>(hdr, b->d_partials);
     batch_finalize<<<b->grid_aux, kBatchBlock, 0, s>>>(hdr, b->d_results);
 }
@@ -308,13 +172,17 @@ hydra_status hydra_batch_create(int max_requests, uint64_t max_integrate_tiles, 
         hydra_batch_destroy(b);
         return st;
     }
+    {
+        std::lock_guard<std::mutex> lk(g_shape_mu);
+        b->block_f32 = g_batch_block_f32;
+    }
     int sms = 148, occ = 1;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, phsp_batch_kernel<float, float>, kBatchBlock, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_kernel_f32(b->block_f32), b->block_f32, 0);
     b->grid_main[0] = sms * (occ > 0 ? occ : 1);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, phsp_batch_kernel<double, double>, kBatchBlock, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, phsp_batch_kernel<double, double, kBatchBlock>, kBatchBlock, 0);
     b->grid_main[1] = sms * (occ > 0 ? occ : 1);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, phsp_batch_kernel<df, df>, kBatchBlock, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, phsp_batch_kernel<df, df, kBatchBlock>, kBatchBlock, 0);
     b->grid_main[2] = sms * (occ > 0 ? occ : 1);
     b->grid_aux = sms;
     for (int v = 0; v < 3; ++v) {
@@ -439,6 +307,10 @@ hydra_status hydra_batch_run(hydra_batch* b, const hydra_request* reqs, int nreq
                     static_cast<unsigned long long>(ptiles), static_cast<unsigned long long>(b->max_tiles));
     BatchHeader* H = reinterpret_cast<BatchHeader*>(h);
     H->tile_counter = 0;
+    {
+        std::lock_guard<std::mutex> lk(g_shape_mu);
+        std::memcpy(H->gen_ept, g_batch_ept[dt == HYDRA_F32 ? 0 : 1], sizeof H->gen_ept);
+    }
     H->nreq = nreq;
     H->nfinal = nfinal;
     H->ntiles = tiles;
@@ -473,6 +345,33 @@ hydra_status hydra_batch_run(hydra_batch* b, const hydra_request* reqs, int nreq
     return HYDRA_OK;
 }
 
+hydra_status hydra_set_batch_shape(hydra_dtype dtype, int block, const int32_t* ept_by_n) {
+    if (dtype != HYDRA_F32 && dtype != HYDRA_F64) return fail(HYDRA_ERR_INVALID_ARG, "unknown dtype %d", static_cast<int>(dtype));
+    if (!ept_by_n) return fail(HYDRA_ERR_INVALID_ARG, "ept_by_n is NULL");
+    if (dtype == HYDRA_F32 ? (block != 128 && block != 256 && block != 512) : block != kBatchBlock)
+        return fail(HYDRA_ERR_INVALID_ARG, "block = %d: FP32 runs take 128, 256 or 512 threads, FP64 runs 256", block);
+    for (int n = 2; n <= kNMax; ++n) {
+        const int e = ept_by_n[n];
+        const bool ok = dtype == HYDRA_F32 ? (e == 1 || e == 2 || (e == 4 && n <= 6)) : e == 2;
+        if (!ok)
+            return fail(HYDRA_ERR_INVALID_ARG, "events per thread %d for n = %d: FP32 takes 1, 2 (or 4 for n <= 6), "
+                        "FP64 2", e, n);
+    }
+    std::lock_guard<std::mutex> lk(g_shape_mu);
+    if (dtype == HYDRA_F32) g_batch_block_f32 = block;
+    for (int n = 2; n <= kNMax; ++n) g_batch_ept[dtype == HYDRA_F32 ? 0 : 1][n] = ept_by_n[n];
+    return HYDRA_OK;
+}
+
+hydra_status hydra_get_batch_shape(hydra_dtype dtype, int* block, int32_t* ept_by_n) {
+    if (dtype != HYDRA_F32 && dtype != HYDRA_F64) return fail(HYDRA_ERR_INVALID_ARG, "unknown dtype %d", static_cast<int>(dtype));
+    if (!block || !ept_by_n) return fail(HYDRA_ERR_INVALID_ARG, "NULL output");
+    std::lock_guard<std::mutex> lk(g_shape_mu);
+    *block = dtype == HYDRA_F32 ? g_batch_block_f32 : kBatchBlock;
+    std::memcpy(ept_by_n, g_batch_ept[dtype == HYDRA_F32 ? 0 : 1], sizeof(int32_t) * (kNMax + 1));
+    return HYDRA_OK;
+}
+
 hydra_status hydra_batch_result(hydra_batch* b, int i, hydra_integral* result) {
     if (!b || !result) return fail(HYDRA_ERR_INVALID_ARG, "NULL argument");
     std::lock_guard<std::mutex> lk(b->mu);
@@ -498,6 +397,368 @@ hydra_status hydra_batch_destroy(hydra_batch* b) {
     if (b->table_done) cudaEventDestroy(b->table_done);
     if (b->run_done) cudaEventDestroy(b->run_done);
     delete b;
+    return HYDRA_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------------------------
+// Whole requests under a device-memory budget (hydra_phsp_batch_run): the requests are cut
+// into waves whose generated outputs fit an arena inside the budget, each wave is one run of
+// a batch runner (one graph launch), and outputs bound for the host are copied out of the
+// arena on a copy stream while the next wave computes into the other half of the arena.
+// ------------------------------------------------------------------------------------
+namespace {
+
+constexpr uint64_t kRunIntSlice = uint64_t(1) << 26;   // events per integral slice (32768 tiles)
+constexpr uint64_t kRunIntSlicesPerWave = 16;          // integral slices per wave (16 MiB of tile partials)
+constexpr int kRunMaxSlices = 8192;                    // slices per wave
+
+thread_local uint64_t t_last_waves = 0, t_last_slices = 0;
+
+struct Slice {
+    int req;
+    uint64_t first, count;
+    uint64_t arena_off, ld;  // generate slices in the arena (NONE / HOST destinations)
+};
+
+size_t elem_of(int dtype) { return dtype == HYDRA_F32 ? sizeof(float) : sizeof(double); }
+
+hydra_status validate_request(hydra_batch_request& r, int i, int dt) {
+    DecayConsts C;
+    hydra_status st = make_consts(r.M, r.n, r.masses, r.seed, &C);
+    if (st == HYDRA_OK && r.dtype != dt)
+        st = fail(HYDRA_ERR_INVALID_ARG, "dtype %d differs from request 0 (%d)", r.dtype, dt);
+    if (st == HYDRA_OK && r.nevents == 0) st = fail(HYDRA_ERR_INVALID_ARG, "nevents must be > 0");
+    if (st == HYDRA_OK && r.event_offset + r.nevents < r.event_offset)
+        st = fail(HYDRA_ERR_INVALID_ARG, "event_offset + nevents overflows 64 bits");
+    if (st == HYDRA_OK && r.kind == HYDRA_REQ_GENERATE) {
+        if (r.dest != HYDRA_DEST_NONE && r.dest != HYDRA_DEST_HOST && r.dest != HYDRA_DEST_DEVICE)
+            st = fail(HYDRA_ERR_INVALID_ARG, "unknown destination %d", r.dest);
+        else if (r.dest != HYDRA_DEST_NONE && (!r.out || !r.weights))
+            st = fail(HYDRA_ERR_INVALID_ARG, "NULL output");
+        else if (r.dest != HYDRA_DEST_NONE && r.ld < r.nevents)
+            st = fail(HYDRA_ERR_INVALID_ARG, "ld = %llu < nevents", static_cast<unsigned long long>(r.ld));
+        else if (r.dest == HYDRA_DEST_DEVICE &&
+                 ((reinterpret_cast<uintptr_t>(r.out) & 15u) || (reinterpret_cast<uintptr_t>(r.weights) & 15u) || r.ld % 4))
+            st = fail(HYDRA_ERR_MISALIGNED, "device outputs must be 16-byte aligned with ld a multiple of 4");
+    } else if (st == HYDRA_OK && r.kind == HYDRA_REQ_INTEGRATE) {
+        MEConsts P;
+        st = make_me(static_cast<hydra_me_id>(r.me), r.n, r.params, 6, &P);
+    } else if (st == HYDRA_OK) {
+        st = fail(HYDRA_ERR_INVALID_ARG, "unknown kind %d", r.kind);
+    }
+    r.status = st;
+    if (st != HYDRA_OK) return fail(st, "request %d: %s", i, g_last_error.c_str());
+    return HYDRA_OK;
+}
+
+// What hydra_phsp_batch_run keeps on a device between calls (released by hydra_shutdown): the
+// arena, the integral segment storage, the batch runner and the copy stream with its events.
+// A call reuses them when they are large enough (and the runner's FP32 block is still the
+// process-wide one), else replaces them; calls on one device are serialised by `mu`.
+struct RunScratch {
+    std::mutex mu;
+    hydra_batch* batch = nullptr;
+    int batch_slices = 0;
+    uint64_t batch_tiles = 0;
+    unsigned char* arena = nullptr;
+    uint64_t arena_bytes = 0;
+    double* segs = nullptr;
+    uint64_t seg_cap = 0;
+    cudaStream_t copy = nullptr;
+    cudaEvent_t gen_done[2] = {nullptr, nullptr}, copy_done[2] = {nullptr, nullptr};
+
+    void release() {
+        if (copy) cudaStreamSynchronize(copy);
+        if (batch) hydra_batch_destroy(batch);
+        if (arena) cudaFree(arena);
+        if (segs) cudaFree(segs);
+        for (int k = 0; k < 2; ++k) {
+            if (gen_done[k]) cudaEventDestroy(gen_done[k]);
+            if (copy_done[k]) cudaEventDestroy(copy_done[k]);
+            gen_done[k] = copy_done[k] = nullptr;
+        }
+        if (copy) cudaStreamDestroy(copy);
+        batch = nullptr;
+        arena = nullptr;
+        segs = nullptr;
+        copy = nullptr;
+        batch_slices = 0;
+        batch_tiles = arena_bytes = seg_cap = 0;
+    }
+};
+
+std::mutex g_run_mu;
+std::vector<RunScratch*> g_run_scratch;
+
+RunScratch* run_scratch_for(int dev) {
+    std::lock_guard<std::mutex> lk(g_run_mu);
+    if (static_cast<int>(g_run_scratch.size()) <= dev) g_run_scratch.resize(dev + 1, nullptr);
+    if (!g_run_scratch[dev]) g_run_scratch[dev] = new RunScratch();
+    return g_run_scratch[dev];
+}
+
+// Make `rs` hold a runner for max_slices slices and ptiles integral tiles, an arena of at least
+// arena_need bytes and at most arena_bytes (this call's share of its budget), segment storage
+// for nsegs segments and, for host outputs, the copy stream.  Each buffer is allocated only when
+// the one held is missing or too small (an arena larger than this call's share, or a runner far
+// larger than needed, is released first).
+hydra_status ensure_run_scratch(RunScratch* rs, int max_slices, uint64_t ptiles, uint64_t arena_need,
+                                uint64_t arena_bytes, uint64_t nsegs, bool need_copy) {
+    int block = kBatchBlock;
+    {
+        std::lock_guard<std::mutex> lk(g_shape_mu);
+        block = g_batch_block_f32;
+    }
+    if (rs->batch && (rs->batch_slices < max_slices || rs->batch_tiles < ptiles || rs->batch->block_f32 != block ||
+                      rs->batch_slices > 2 * max_slices + 64)) {
+        hydra_batch_destroy(rs->batch);
+        rs->batch = nullptr;
+    }
+    if (rs->arena && (rs->arena_bytes < arena_need || rs->arena_bytes > arena_bytes)) {
+        cudaFree(rs->arena);
+        rs->arena = nullptr;
+        rs->arena_bytes = 0;
+    }
+    if (rs->segs && rs->seg_cap < nsegs) {
+        cudaFree(rs->segs);
+        rs->segs = nullptr;
+        rs->seg_cap = 0;
+    }
+    if (!rs->batch) {
+        const hydra_status st = hydra_batch_create(max_slices, ptiles ? ptiles : 1, &rs->batch);
+        if (st != HYDRA_OK) return st;
+        rs->batch_slices = max_slices;
+        rs->batch_tiles = ptiles ? ptiles : 1;
+    }
+    cudaError_t err = cudaSuccess;
+    if (arena_need && !rs->arena) {
+        err = cudaMalloc(&rs->arena, arena_need);
+        if (err == cudaSuccess) rs->arena_bytes = arena_need;
+        else rs->arena = nullptr;
+    }
+    if (err == cudaSuccess && nsegs && !rs->segs) {
+        err = cudaMalloc(&rs->segs, nsegs * 8 * sizeof(double));
+        if (err == cudaSuccess) rs->seg_cap = nsegs;
+        else rs->segs = nullptr;
+    }
+    if (err == cudaSuccess && need_copy && !rs->copy) {
+        err = cudaStreamCreateWithFlags(&rs->copy, cudaStreamNonBlocking);
+        for (int k = 0; k < 2 && err == cudaSuccess; ++k) {
+            err = cudaEventCreateWithFlags(&rs->gen_done[k], cudaEventDisableTiming);
+            if (err == cudaSuccess) err = cudaEventCreateWithFlags(&rs->copy_done[k], cudaEventDisableTiming);
+        }
+    }
+    if (err != cudaSuccess) {
+        cudaGetLastError();
+        return err == cudaErrorMemoryAllocation ? fail(HYDRA_ERR_OOM, "batch run buffers: %s", cudaGetErrorString(err))
+                                                : cuda_fail(err, "batch run set-up");
+    }
+    return HYDRA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+hydra_status hydra_phsp_batch_run(hydra_batch_request* reqs, int nreq, size_t budget_bytes, hydra_stream_t stream) {
+    t_last_waves = t_last_slices = 0;
+    if (!reqs || nreq < 1) return fail(HYDRA_ERR_INVALID_ARG, "need at least one request");
+    const int dt = reqs[0].dtype;
+    if (dt != HYDRA_F32 && dt != HYDRA_F64) return fail(HYDRA_ERR_INVALID_ARG, "request 0: unknown dtype %d", dt);
+    for (int i = 0; i < nreq; ++i) reqs[i].status = HYDRA_OK;
+    for (int i = 0; i < nreq; ++i) {
+        const hydra_status st = validate_request(reqs[i], i, dt);
+        if (st != HYDRA_OK) return st;
+    }
+    const size_t elem = elem_of(dt);
+    // integral segment storage (8 doubles per 2^21 events of each integral request) and the
+    // runner's fixed buffers come out of the budget first; the rest is the output arena
+    std::vector<uint64_t> seg_off(nreq, 0);
+    uint64_t nsegs = 0, int_slices = 0;
+    bool any_host = false;
+    for (int i = 0; i < nreq; ++i) {
+        if (reqs[i].kind == HYDRA_REQ_INTEGRATE) {
+            seg_off[i] = nsegs;
+            nsegs += (reqs[i].nevents + kSegEvents - 1) / kSegEvents;
+            int_slices += (reqs[i].nevents + kRunIntSlice - 1) / kRunIntSlice;
+        } else if (reqs[i].dest == HYDRA_DEST_HOST) {
+            any_host = true;
+        }
+    }
+    const uint64_t ptiles = (int_slices < kRunIntSlicesPerWave ? int_slices : kRunIntSlicesPerWave) * (kRunIntSlice / kTileEvents);
+    const int max_slices = nreq + 64 < kRunMaxSlices ? nreq + 64 : kRunMaxSlices;
+    const size_t fixed = table_size(max_slices, max_slices) + ptiles * sizeof(TileSums) +
+                         static_cast<size_t>(max_slices) * sizeof(hydra_integral) + nsegs * 8 * sizeof(double) + (1u << 20);
+    if (budget_bytes < fixed + (16u << 20))
+        return fail(HYDRA_ERR_INVALID_ARG, "budget_bytes = %zu is below the %zu bytes these requests need at least",
+                    budget_bytes, fixed + (16u << 20));
+    const uint64_t arena_bytes = (budget_bytes - fixed) / 256 * 256;
+    const uint64_t half = any_host ? arena_bytes / 2 / 256 * 256 : arena_bytes;
+
+    // waves: requests in order; a generate request takes arena space for [4n+1][ld] values
+    // (ld = count rounded up to 4, 256-byte aligned) and is split when it exceeds a half arena;
+    // device-destination requests are written in place; integrals go in 2^26-event slices
+    std::vector<std::vector<Slice>> waves(1);
+    uint64_t used = 0, wave_int = 0;
+    auto new_wave = [&]() {
+        waves.emplace_back();
+        used = 0;
+        wave_int = 0;
+    };
+    for (int i = 0; i < nreq; ++i) {
+        const hydra_batch_request& r = reqs[i];
+        uint64_t first = 0;
+        while (first < r.nevents) {
+            if (static_cast<int>(waves.back().size()) >= max_slices) new_wave();
+            Slice sl{i, first, 0, 0, 0};
+            if (r.kind == HYDRA_REQ_INTEGRATE) {
+                if (wave_int >= kRunIntSlicesPerWave) new_wave();
+                sl.count = r.nevents - first < kRunIntSlice ? r.nevents - first : kRunIntSlice;
+                ++wave_int;
+            } else if (r.dest == HYDRA_DEST_DEVICE) {
+                sl.count = r.nevents;
+            } else {
+                const uint64_t per_event = static_cast<uint64_t>(4 * r.n + 1) * elem;
+                const uint64_t fit_max = (half / per_event) / 4 * 4;  // events of one slice in an empty half
+                if (fit_max < 4) return fail(HYDRA_ERR_INVALID_ARG, "budget too small for one group of 4 events of request %d", i);
+                uint64_t avail = used < half ? (half - used) / per_event / 4 * 4 : 0;
+                if (avail < 4 || (avail < r.nevents - first && avail < fit_max / 8)) {
+                    new_wave();  // start a fresh half rather than leave a sliver
+                    avail = fit_max;
+                }
+                sl.count = r.nevents - first < avail ? r.nevents - first : avail;
+                sl.ld = (sl.count + 3) / 4 * 4;
+                sl.arena_off = used;
+                used += (per_event * sl.ld + 255) / 256 * 256;
+            }
+            waves.back().push_back(sl);
+            first += sl.count;
+        }
+    }
+    if (waves.back().empty()) waves.pop_back();
+
+    // arena bytes the waves use (both halves when outputs go to the host)
+    uint64_t arena_need = 0;
+    for (const auto& w : waves)
+        for (const Slice& sl : w)
+            if (reqs[sl.req].kind == HYDRA_REQ_GENERATE && reqs[sl.req].dest != HYDRA_DEST_DEVICE) {
+                const uint64_t end = sl.arena_off + (static_cast<uint64_t>(4 * reqs[sl.req].n + 1) * elem * sl.ld + 255) / 256 * 256;
+                arena_need = end > arena_need ? end : arena_need;
+            }
+    if (any_host && arena_need) arena_need = 2 * half;
+    int dev = 0;
+    cudaError_t err = cudaGetDevice(&dev);
+    if (err != cudaSuccess) return cuda_fail(err, "cudaGetDevice");
+    RunScratch* rsp = run_scratch_for(dev);
+    std::lock_guard<std::mutex> lk(rsp->mu);
+    RunScratch& res = *rsp;
+    hydra_status st = ensure_run_scratch(rsp, max_slices, ptiles, arena_need, arena_bytes, nsegs, any_host);
+    if (st != HYDRA_OK) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    std::vector<hydra_request> table;
+    for (size_t w = 0; w < waves.size(); ++w) {
+        const int b = static_cast<int>(w & 1);
+        unsigned char* base = res.arena + (any_host ? b * half : 0);
+        table.assign(waves[w].size(), hydra_request{});
+        bool host_copies = false;
+        std::vector<int> finals;
+        for (size_t j = 0; j < waves[w].size(); ++j) {
+            const Slice& sl = waves[w][j];
+            const hydra_batch_request& r = reqs[sl.req];
+            hydra_request& q = table[j];
+            q.kind = r.kind;
+            q.n = r.n;
+            q.dtype = r.dtype;
+            q.me = r.me;
+            q.M = r.M;
+            std::memcpy(q.masses, r.masses, sizeof q.masses);
+            std::memcpy(q.params, r.params, sizeof q.params);
+            q.seed = r.seed;
+            q.event_offset = r.event_offset;
+            q.first = sl.first;
+            q.count = sl.count;
+            if (r.kind == HYDRA_REQ_INTEGRATE) {
+                q.total = r.nevents;
+                q.seg_partials = res.segs + seg_off[sl.req] * 8;
+                if (sl.first + sl.count == r.nevents) finals.push_back(static_cast<int>(j));
+            } else if (r.dest == HYDRA_DEST_DEVICE) {
+                q.out = r.out;
+                q.ld = r.ld;
+                q.weights = r.weights;
+            } else {
+                q.out = base + sl.arena_off;
+                q.ld = sl.ld;
+                q.weights = base + sl.arena_off + static_cast<uint64_t>(4 * r.n) * sl.ld * elem;
+                host_copies |= r.dest == HYDRA_DEST_HOST;
+            }
+        }
+        // this half of the arena is free once the copies of the wave before the previous one are done
+        if (any_host && w >= 2) {
+            err = cudaStreamWaitEvent(s, res.copy_done[b], 0);
+            if (err != cudaSuccess) return cuda_fail(err, "batch run arena wait");
+        }
+        st = hydra_batch_run(res.batch, table.data(), static_cast<int>(table.size()), 1, stream);
+        if (st != HYDRA_OK) return st;
+        if (host_copies) {
+            err = cudaEventRecord(res.gen_done[b], s);
+            if (err == cudaSuccess) err = cudaStreamWaitEvent(res.copy, res.gen_done[b], 0);
+            for (size_t j = 0; j < waves[w].size() && err == cudaSuccess; ++j) {
+                const Slice& sl = waves[w][j];
+                const hydra_batch_request& r = reqs[sl.req];
+                if (r.kind != HYDRA_REQ_GENERATE || r.dest != HYDRA_DEST_HOST) continue;
+                const unsigned char* src = base + sl.arena_off;
+                err = cudaMemcpy2DAsync(static_cast<unsigned char*>(r.out) + sl.first * elem, r.ld * elem, src,
+                                        sl.ld * elem, sl.count * elem, static_cast<size_t>(4 * r.n),
+                                        cudaMemcpyDeviceToHost, res.copy);
+                if (err == cudaSuccess)
+                    err = cudaMemcpyAsync(static_cast<unsigned char*>(r.weights) + sl.first * elem,
+                                          src + static_cast<uint64_t>(4 * r.n) * sl.ld * elem, sl.count * elem,
+                                          cudaMemcpyDeviceToHost, res.copy);
+            }
+            if (err == cudaSuccess) err = cudaEventRecord(res.copy_done[b], res.copy);
+            if (err != cudaSuccess) return cuda_fail(err, "batch run output copy");
+        }
+        for (int j : finals) {
+            st = hydra_batch_result(res.batch, j, &reqs[waves[w][j].req].result);
+            if (st != HYDRA_OK) return st;
+        }
+    }
+    if (any_host) err = cudaStreamSynchronize(res.copy);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+    if (err != cudaSuccess) return cuda_fail(err, "batch run synchronize");
+    t_last_waves = waves.size();
+    for (const auto& w : waves) t_last_slices += w.size();
+    return HYDRA_OK;
+}
+
+}  // extern "C"
+
+namespace hydra {
+
+void release_batch_run_scratch() {
+    std::lock_guard<std::mutex> lk(g_run_mu);
+    int cur = 0;
+    cudaGetDevice(&cur);
+    for (size_t d = 0; d < g_run_scratch.size(); ++d) {
+        if (!g_run_scratch[d]) continue;
+        cudaSetDevice(static_cast<int>(d));
+        g_run_scratch[d]->release();
+        delete g_run_scratch[d];
+        g_run_scratch[d] = nullptr;
+    }
+    cudaSetDevice(cur);
+}
+
+}  // namespace hydra
+
+extern "C" {
+
+hydra_status hydra_phsp_batch_stats(uint64_t* waves, uint64_t* slices) {
+    if (!waves || !slices) return fail(HYDRA_ERR_INVALID_ARG, "NULL output");
+    *waves = t_last_waves;
+    *slices = t_last_slices;
     return HYDRA_OK;
 }
 

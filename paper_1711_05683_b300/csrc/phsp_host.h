@@ -35,5 +35,6 @@ int grid_for(const void* kernel, int block, uint64_t work_items);
 // Release of the scratch owned by the other translation units (called by hydra_shutdown).
 void release_extras_scratch();
 void release_vegas_scratch();
+void release_batch_run_scratch();
 
 }  // namespace hydra

@@ -3,6 +3,8 @@ bad arguments with the documented status codes before touching the device."""
 import ctypes
 import math
 
+import numpy as np
+
 import pytest
 
 import oracle
@@ -129,3 +131,62 @@ def test_fp32_lambda_switch(L):
     assert hp.STATUS[L.hydra_set_fp32_lambda(2)] == "HYDRA_ERR_INVALID_ARG"
     assert L.hydra_set_fp32_lambda(1) == 0 and L.hydra_get_fp32_lambda() == 1
     assert L.hydra_set_fp32_lambda(0) == 0 and L.hydra_get_fp32_lambda() == 0
+
+
+def test_batch_shape_validation(L):
+    block, ept = hp.get_batch_shape("f32")
+    assert block == 256 and ept[2:] == [2, 4, 4, 4, 4, 2, 2, 2, 2]
+    with pytest.raises(hp.HydraError):
+        hp.set_batch_shape("f32", 384, ept)            # block not offered
+    with pytest.raises(hp.HydraError):
+        hp.set_batch_shape("f32", 256, [4] * 11)       # four events per thread only up to n = 6
+    with pytest.raises(hp.HydraError):
+        hp.set_batch_shape("f64", 256, [1] * 11)       # FP64 tiles take two
+    hp.set_batch_shape("f32", 512, [1] * 11)
+    assert hp.get_batch_shape("f32") == (512, [2, 2] + [1] * 9)
+    hp.set_batch_shape("f32", block, ept)
+    assert hp.get_batch_shape("f64") == (256, [2] * 11)
+
+
+def test_batch_run_validates_before_any_launch(L):
+    """Errors found on the host, each request's status set; no CUDA call is needed to reach
+    them (this runs without a GPU)."""
+    class _E(Exception):
+        pass
+
+    class hp_:  # the C ABI directly, on the legacy default stream (no torch CUDA state here)
+        HydraError = _E
+
+        @staticmethod
+        def batch_run(t, budget):
+            rc = L.hydra_phsp_batch_run(ctypes.c_void_p(t.ctypes.data if len(t) else None), len(t), budget, None)
+            if rc:
+                raise _E(f"{hp.STATUS[rc]}: {L.hydra_last_error().decode()}")
+    t = np.zeros(3, dtype=hp.batch_request_dtype())
+    for i in range(3):
+        t[i]["kind"], t[i]["n"], t[i]["M"], t[i]["nevents"], t[i]["seed"] = hp.REQ_GENERATE, 3, 5.0, 100, i
+        t[i]["masses"][:3] = (0.1, 0.2, 0.3)
+    t[1]["masses"][:3] = (2.0, 2.0, 2.0)  # below threshold
+    with pytest.raises(hp_.HydraError) as e:
+        hp_.batch_run(t, 1 << 30)
+    assert "request 1" in str(e.value) and list(t["status"]) == [0, 2, 0]
+    t[1]["masses"][:3] = (0.1, 0.2, 0.3)
+    t[2]["dtype"] = hp.F64
+    with pytest.raises(hp_.HydraError):
+        hp_.batch_run(t, 1 << 30)            # mixed precisions
+    assert t["status"][2] == 1
+    t[2]["dtype"] = hp.F32
+    t[0]["dest"] = hp.DEST_DEVICE             # device destination without buffers
+    with pytest.raises(hp_.HydraError):
+        hp_.batch_run(t, 1 << 30)
+    t[0]["dest"] = hp.DEST_NONE
+    t[2]["kind"], t[2]["me"] = hp.REQ_INTEGRATE, hp.ME_DALITZ_2BW  # Dalitz needs its 6 params finite: zeros are fine
+    t[2]["params"][:6] = (0.892, 0.05, 1.02, 0.004, 0.5, float("nan"))
+    with pytest.raises(hp_.HydraError):
+        hp_.batch_run(t, 1 << 30)
+    t[2]["params"][5] = 1.2
+    with pytest.raises(hp_.HydraError) as e:
+        hp_.batch_run(t, 1 << 20)            # budget below what the runner needs
+    assert "budget" in str(e.value)
+    with pytest.raises(hp_.HydraError):
+        hp_.batch_run(t[:0], 1 << 30)        # no requests
