@@ -273,9 +273,9 @@ hydra_status hydra_phsp_integrate(double M, int n, const double *masses, uint64_
  *
  * Arguments, result and numerics are those of hydra_phsp_integrate, bit for bit, with one
  * extra limit: nevents <= 2^32 (larger counts return HYDRA_ERR_INVALID_ARG with a message).
- * The first call on each device looks up the device address of the array
- * (cudaGetSymbolAddress) with that device current; make that first call before any stream
- * capture begins.  All calls share the one array, which keeps the previous call's contents;
+ * Every call looks up the device address of the array on the current device
+ * (cudaGetSymbolAddress) and ends by synchronising the stream, so it cannot be recorded in a
+ * stream capture.  All calls share the one array, which keeps the previous call's contents;
  * every slot a call reads is written earlier in the same call, so nothing needs clearing.
  * Calls are serialized within the process by a lock and block until the result is on the
  * host; calls that overlap on the GPU (for instance issued around that lock) race on the
@@ -477,15 +477,17 @@ typedef struct hydra_serve_request {
     int32_t me;        /* integrate: hydra_me_id */
     int32_t reserved;
     double params[6];  /* integrate: matrix-element parameters */
-    double withdraw;   /* seconds after the start of the run at which the client withdraws the
-                        * request if it is admitted and not yet fully launched (dropped between
-                        * ticks, memory released); negative: never */
+    double withdraw;   /* seconds after the start of the run (live service: after submission) at which
+                        * the client withdraws the request if it is admitted and not yet fully
+                        * launched (dropped between ticks, memory released); negative: never */
 } hydra_serve_request;
 
 typedef enum hydra_serve_status {
     HYDRA_SERVE_DONE = 0,
     HYDRA_SERVE_REFUSED = 1,   /* could never fit, or could not be admitted with nothing in flight */
-    HYDRA_SERVE_WITHDRAWN = 2  /* withdrawn by the client (see withdraw) */
+    HYDRA_SERVE_WITHDRAWN = 2, /* withdrawn by the client (see withdraw) */
+    HYDRA_SERVE_INVALID = 3,   /* failed the checks of hydra_phsp_generate / hydra_phsp_integrate */
+    HYDRA_SERVE_TIMED_OUT = 4  /* not finished when the run's deadline passed */
 } hydra_serve_status;
 
 typedef struct hydra_serve_outcome {
@@ -511,13 +513,48 @@ hydra_status hydra_server_create(uint64_t budget_bytes, void *pinned, uint64_t p
                                  hydra_server **out);
 
 /*
- * Serve nreq requests (blocking: returns when every request has completed or been refused).
- * time_scale stretches the arrival times (0: all arrive at once).  outcomes[i] receives request
- * i's latency and result; wall_s the run's wall time, ticks the batch runs.  Errors:
- * INVALID_ARG (unsorted or invalid requests), UNSUPPORTED_N, and the batch runner's errors.
+ * Serve nreq requests (blocking: returns when every request has an outcome).  time_scale
+ * stretches the arrival times (0: all arrive at once).  outcomes[i] receives request i's status,
+ * latency and result: a request that fails the checks of the single-request entry points is
+ * answered HYDRA_SERVE_INVALID when it arrives and the others are served as usual.  wall_s the
+ * run's wall time, ticks the batch runs.  The loop makes the server's device current and
+ * restores the caller's on return.  Errors: INVALID_ARG (unsorted requests), BUSY (the server is
+ * serving live requests), TIMEOUT (the deadline of hydra_server_set_deadline passed: no further
+ * tick was launched, the ticks in flight were waited for, and unfinished requests are answered
+ * HYDRA_SERVE_TIMED_OUT), and the batch runner's errors.
  */
 hydra_status hydra_server_run(hydra_server *server, const hydra_serve_request *reqs, int nreq, double time_scale,
                               hydra_serve_outcome *outcomes, double *wall_s, uint64_t *ticks);
+
+/*
+ * Wall-clock limit of a run (hydra_server_run, or a live service started afterwards) in
+ * seconds from its start; 0 (the default) is no limit.  The loop never spins past it: it checks
+ * the clock on every turn and ends the run with HYDRA_ERR_TIMEOUT.  Errors: INVALID_ARG, BUSY.
+ */
+hydra_status hydra_server_set_deadline(hydra_server *server, double seconds);
+
+/*
+ * Live service: requests pushed from any thread while the loop runs on a worker thread the
+ * library starts (same policy, rings and results as hydra_server_run; the arrival time of a
+ * request is the moment it is submitted, its withdraw field counts from there).
+ *   hydra_server_start   start the worker (BUSY if already started).
+ *   hydra_server_submit  check the request as the single-request entry points do (their
+ *                        errors are returned at once) and queue it; *ticket identifies it
+ *                        (BUSY when the server is not started or is stopping).
+ *   hydra_server_poll    wait up to timeout_s seconds for the ticket's outcome (kept outputs
+ *                        at host_offset of the pinned ring, as for hydra_server_run); each
+ *                        outcome is returned once.  TIMEOUT if not finished in time;
+ *                        INVALID_ARG for an unknown or already returned ticket.
+ *   hydra_server_stop    stop accepting, let the worker finish what was submitted for up to
+ *                        timeout_s seconds, then end it as a deadline does (ticks in flight
+ *                        waited for, the rest answered HYDRA_SERVE_TIMED_OUT, TIMEOUT
+ *                        returned) and join it.  hydra_server_destroy stops a live server with
+ *                        timeout 0.
+ */
+hydra_status hydra_server_start(hydra_server *server);
+hydra_status hydra_server_submit(hydra_server *server, const hydra_serve_request *req, uint64_t *ticket);
+hydra_status hydra_server_poll(hydra_server *server, uint64_t ticket, double timeout_s, hydra_serve_outcome *outcome);
+hydra_status hydra_server_stop(hydra_server *server, double timeout_s);
 
 /* Wait for the server's work and release it (its rings, runners and streams). */
 hydra_status hydra_server_destroy(hydra_server *server);

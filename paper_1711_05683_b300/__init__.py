@@ -98,6 +98,11 @@ def lib() -> ctypes.CDLL:
         L.hydra_server_create.argtypes = [u64, vp, u64, i, i, u64, i, ctypes.POINTER(vp)]
         L.hydra_server_run.argtypes = [vp, vp, i, d, vp, dp, ctypes.POINTER(u64)]
         L.hydra_server_destroy.argtypes = [vp]
+        L.hydra_server_set_deadline.argtypes = [vp, d]
+        L.hydra_server_start.argtypes = [vp]
+        L.hydra_server_submit.argtypes = [vp, vp, ctypes.POINTER(u64)]
+        L.hydra_server_poll.argtypes = [vp, u64, d, vp]
+        L.hydra_server_stop.argtypes = [vp, d]
         for name in ("hydra_phsp_volume_factor", "hydra_phsp_generate", "hydra_phsp_integrate",
                      "hydra_phsp_draws", "hydra_phsp_generate_host", "hydra_phsp_integrate_noalloc",
                      "hydra_set_launch_config", "hydra_get_launch_config", "hydra_set_fp64_arith",
@@ -108,7 +113,8 @@ def lib() -> ctypes.CDLL:
                      "hydra_server_create", "hydra_server_run", "hydra_server_destroy",
                      "hydra_probe_fma_rate", "hydra_probe_write_bandwidth", "hydra_probe_op_rate",
                      "hydra_set_fp32_lambda", "hydra_set_batch_shape", "hydra_get_batch_shape",
-                     "hydra_phsp_batch_run", "hydra_phsp_batch_stats"):
+                     "hydra_phsp_batch_run", "hydra_phsp_batch_stats", "hydra_server_set_deadline",
+                     "hydra_server_start", "hydra_server_submit", "hydra_server_poll", "hydra_server_stop"):
             getattr(L, name).restype = i
         _lib = L
     return _lib
@@ -477,7 +483,7 @@ def serve_outcome_dtype():
     return dt
 
 
-SERVE_DONE, SERVE_REFUSED, SERVE_WITHDRAWN = 0, 1, 2
+SERVE_DONE, SERVE_REFUSED, SERVE_WITHDRAWN, SERVE_INVALID, SERVE_TIMED_OUT = 0, 1, 2, 3, 4
 
 
 def segments(total: int) -> int:

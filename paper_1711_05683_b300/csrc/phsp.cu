@@ -533,23 +533,16 @@ static_assert(sizeof(hydra_integral) <= 256, "result slot");
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
-constexpr int kNoAllocMaxDevices = 64;
 static std::mutex g_noalloc_mu;
-static unsigned char* g_noalloc_ptr[kNoAllocMaxDevices] = {};
 
-// Device address of g_noalloc_scratch on the current device, looked up once per device.
+// Device address of g_noalloc_scratch on the current device, looked up on every call (the
+// host-side name of the array is not a device address; a cached address could outlive the
+// context it belongs to, and the lookup is cheap next to the call's own synchronisation).
 static hydra_status noalloc_scratch(unsigned char** out) {
-    int dev = 0;
-    cudaError_t err = cudaGetDevice(&dev);
-    if (err != cudaSuccess) return cuda_fail(err, "cudaGetDevice");
-    if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(HYDRA_ERR_INVALID_ARG, "device %d out of range", dev);
-    if (!g_noalloc_ptr[dev]) {
-        void* ptr = nullptr;
-        err = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-        if (err != cudaSuccess) return cuda_fail(err, "cudaGetSymbolAddress(no-allocation scratch)");
-        g_noalloc_ptr[dev] = static_cast<unsigned char*>(ptr);
-    }
-    *out = g_noalloc_ptr[dev];
+    void* ptr = nullptr;
+    const cudaError_t err = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (err != cudaSuccess) return cuda_fail(err, "cudaGetSymbolAddress(no-allocation scratch)");
+    *out = static_cast<unsigned char*>(ptr);
     return HYDRA_OK;
 }
 

@@ -236,7 +236,7 @@ class Server:
     def _run(self, requests, time_scale, max_wall, cancel_after) -> dict:
         torch = self.torch
         cancel_after = dict(cancel_after or {})
-        cancelled, refused = [], []
+        cancelled, refused, invalid = [], [], []
         t0 = time.perf_counter()
         pending = deque(enumerate(requests))
         queue: deque[_Active] = deque()
@@ -261,6 +261,9 @@ class Server:
                 break
             while pending and t0 + pending[0][1].arrival * time_scale <= now:
                 rid, r = pending.popleft()
+                if not _valid(r):  # answered at once; the others are served as usual
+                    invalid.append(rid)
+                    continue
                 queue.append(_Active(rid, r, t0 + r.arrival * time_scale))
             while queue and len(active) < self.max_slices:
                 if not self._fits_ever(queue[0]):  # larger than the budget: refused, not queued forever
@@ -346,12 +349,31 @@ class Server:
         out = _summary(latencies, events_done, wall, ticks=tick, done=done, kinds=kinds)
         out["cancelled"] = cancelled
         out["refused"] = refused
+        out["invalid"] = invalid
         return out
 
     def close(self):
         for r in self.runners:
             r.close()
         self.dev_ring = self.seg_ring = None
+
+
+def _valid(r) -> bool:
+    """The checks of the single-request entry points, on the host: n, masses and threshold (the
+    library's hydra_phsp_volume_factor), the kind, a positive count and, for integrals, a known
+    matrix element with its parameters."""
+    import math
+    if r.kind not in ("generate", "integrate") or r.nevents <= 0:
+        return False
+    try:
+        hp.volume_factor(r.M, r.masses)
+    except hp.HydraError:
+        return False
+    if r.kind == "integrate":
+        if r.me == hp.ME_DALITZ_2BW:
+            return len(r.masses) == 3 and len(r.params) >= 6 and all(math.isfinite(v) for v in r.params[:6])
+        return r.me == hp.ME_FLAT
+    return True
 
 
 class NativeServer:
@@ -391,21 +413,25 @@ class NativeServer:
             n = len(r.masses)
             rec["arrival"], rec["n"], rec["M"] = r.arrival, n, r.M
             rec["kind"] = hp.REQ_GENERATE if r.kind == "generate" else hp.REQ_INTEGRATE
-            rec["masses"][:n] = r.masses
+            rec["masses"][: min(n, 10)] = r.masses[:10]  # n > 10 is answered invalid by the loop
             rec["nevents"], rec["seed"], rec["me"] = r.nevents, r.seed, r.me
             rec["params"][: len(r.params)] = r.params
         outc = np.zeros(max(1, len(reqs)), dtype=hp.serve_outcome_dtype())
         wall, ticks = ctypes.c_double(), ctypes.c_uint64()
         with _no_gc_pauses():
-            hp._check(hp.lib().hydra_server_run(self._h, ctypes.c_void_p(table.ctypes.data), len(reqs),
-                                                float(time_scale), ctypes.c_void_p(outc.ctypes.data),
-                                                ctypes.byref(wall), ctypes.byref(ticks)))
-        latencies, kinds, done, refused, cancelled = {}, {}, [], [], []
+            status = hp.lib().hydra_server_run(self._h, ctypes.c_void_p(table.ctypes.data), len(reqs),
+                                               float(time_scale), ctypes.c_void_p(outc.ctypes.data),
+                                               ctypes.byref(wall), ctypes.byref(ticks))
+        deadline_passed = status == 7  # HYDRA_ERR_TIMEOUT: every request has an outcome all the same
+        if not deadline_passed:
+            hp._check(status)
+        latencies, kinds, done, refused, cancelled, invalid, timed_out = {}, {}, [], [], [], [], []
         events = 0
         for i, r in enumerate(reqs):
             o = outc[i]
             if o["status"] != hp.SERVE_DONE:
-                (cancelled if o["status"] == hp.SERVE_WITHDRAWN else refused).append(i)
+                {hp.SERVE_WITHDRAWN: cancelled, hp.SERVE_INVALID: invalid,
+                 hp.SERVE_TIMED_OUT: timed_out}.get(int(o["status"]), refused).append(i)
                 continue
             a = _Active(i, r, r.arrival * time_scale)
             a.latency = latencies[i] = float(o["latency"])
@@ -422,7 +448,55 @@ class NativeServer:
         out = _summary(latencies, events, wall.value, ticks=int(ticks.value), done=done, kinds=kinds)
         out["cancelled"] = cancelled
         out["refused"] = refused
+        out["invalid"] = invalid
+        out["timed_out"] = timed_out
+        out["deadline_passed"] = deadline_passed
         return out
+
+    def set_deadline(self, seconds: float) -> None:
+        """Wall-clock limit of a run (0: none); a run that passes it raises HydraError with
+        HYDRA_ERR_TIMEOUT after its ticks in flight have finished."""
+        hp._check(hp.lib().hydra_server_set_deadline(self._h, float(seconds)))
+
+    # -- live service: requests submitted while the C++ loop runs on its worker thread
+    def start(self) -> None:
+        hp._check(hp.lib().hydra_server_start(self._h))
+
+    def submit(self, r, withdraw: float | None = None) -> int:
+        """Queue request `r` (a workloads.Request); returns its ticket.  Invalid requests raise
+        HydraError at once."""
+        import ctypes
+        rec = np.zeros(1, dtype=hp.serve_request_dtype())[0]
+        n = len(r.masses)
+        rec["kind"] = hp.REQ_GENERATE if r.kind == "generate" else hp.REQ_INTEGRATE
+        rec["n"], rec["M"], rec["nevents"], rec["seed"], rec["me"] = n, r.M, r.nevents, r.seed, r.me
+        rec["masses"][: min(n, 10)] = r.masses[:10]  # n > 10 is refused by the submission's checks
+        rec["params"][: len(r.params)] = r.params
+        rec["withdraw"] = -1.0 if withdraw is None else float(withdraw)
+        arr = np.array([rec])
+        ticket = ctypes.c_uint64()
+        hp._check(hp.lib().hydra_server_submit(self._h, ctypes.c_void_p(arr.ctypes.data), ctypes.byref(ticket)))
+        return ticket.value
+
+    def poll(self, ticket: int, timeout: float = 10.0, request=None) -> dict:
+        """Wait for a ticket's outcome: {"status", "latency", "result" or host views}."""
+        import ctypes
+        outc = np.zeros(1, dtype=hp.serve_outcome_dtype())
+        hp._check(hp.lib().hydra_server_poll(self._h, int(ticket), float(timeout), ctypes.c_void_p(outc.ctypes.data)))
+        o = outc[0]
+        res = {"status": int(o["status"]), "latency": float(o["latency"])}
+        if res["status"] == hp.SERVE_DONE and request is not None:
+            if request.kind == "integrate":
+                res["result"] = {k: (int(o["result"][k]) if k == "n" else float(o["result"][k]))
+                                 for k in o["result"].dtype.names}
+            elif self.keep_outputs:
+                n, ld, off = len(request.masses), int(o["ld"]), int(o["host_offset"])
+                hb = self.pinned[off: off + (4 * n + 1) * ld * 4].view(self.torch.float32)
+                res["host_out"], res["host_w"] = hb[: 4 * n * ld].view(n, 4, ld), hb[4 * n * ld:]
+        return res
+
+    def stop(self, timeout: float = 60.0) -> None:
+        hp._check(hp.lib().hydra_server_stop(self._h, float(timeout)))
 
     def close(self):
         if self._h:

@@ -140,3 +140,117 @@ def test_kept_outputs_filling_the_pinned_ring_are_refused_not_waited_for(kind):
     gens = [i for i, r in enumerate(reqs) if r.kind == "generate"]
     assert res["refused"] and set(res["refused"]) <= set(gens)
     assert res["completed"] + len(res["refused"]) == len(reqs)
+
+
+@pytest.mark.parametrize("kind", ["python", "native"])
+def test_invalid_request_does_not_end_service(kind):
+    """A request below threshold, one with an unknown matrix element and one with n = 11 among
+    valid ones: each is answered invalid when it arrives and every other request still gets its
+    single-request bits."""
+    d = workloads.D0_DALITZ
+    reqs = list(workloads.serve_stream(rate_hz=2000, duration_s=0.03, gen_log_events=(2.0, 4.0),
+                                       int_log_events=(4.0, 5.0), rng_seed=21))
+    bad = [workloads.Request("generate", 1.0, (0.5, 0.4, 0.3), 1000, 5, arrival=reqs[1].arrival),
+           workloads.Request("integrate", d["M"], d["masses"], 10_000, 6, me=7, params=d["params"],
+                             arrival=reqs[3].arrival),
+           workloads.Request("generate", 30.0, (0.1,) * 11, 1000, 7, arrival=reqs[5].arrival)]
+    reqs = sorted(reqs + bad, key=lambda r: r.arrival)
+    bad_ids = sorted(i for i, r in enumerate(reqs) if any(r is b for b in bad))
+    srv = _server(kind, max_slices=256, int_slice_segments=1, pinned_bytes=1 << 28, keep_outputs=True)
+    res = srv.run(reqs)
+    srv.close()
+    assert sorted(res["invalid"]) == bad_ids
+    assert res["completed"] == len(reqs) - len(bad)
+    for a in res["done"]:
+        r = a.req
+        if r.kind == "integrate":
+            assert a.result == hp.integrate(r.M, r.masses, r.nevents, r.seed, kin_dtype="f32", me=r.me,
+                                            params=r.params)
+        else:
+            p, w = hp.generate(r.M, r.masses, r.nevents, r.seed, dtype="f32")
+            torch.cuda.synchronize()
+            assert torch.equal(a.host_out[:, :, : r.nevents], p[:, :, : r.nevents].cpu())
+
+
+def test_native_live_requests_pushed_while_running():
+    """Live service: a client thread pushes a stream of generate and integrate requests (real
+    arrival spacing) while the C++ loop runs on its worker thread; each outcome, polled by
+    ticket from the main thread, equals the single-request result bit for bit."""
+    import threading
+    import time
+    from paper_1711_05683_b300 import serve
+    reqs = workloads.serve_stream(rate_hz=2000, duration_s=0.1, gen_log_events=(2.0, 4.5),
+                                  int_log_events=(4.0, 6.5), rng_seed=5)
+    srv = serve.NativeServer(max_slices=256, int_slice_segments=1, pinned_bytes=1 << 29, keep_outputs=True,
+                             budget_bytes=4 * 10 ** 9)
+    srv.start()
+    tickets = [None] * len(reqs)
+
+    def client():
+        t0 = time.perf_counter()
+        for i, r in enumerate(reqs):
+            wait = r.arrival - (time.perf_counter() - t0)
+            if wait > 0:
+                time.sleep(wait)
+            tickets[i] = srv.submit(r)
+
+    th = threading.Thread(target=client)
+    th.start()
+    th.join()
+    outs = [srv.poll(t, timeout=30.0, request=r) for t, r in zip(tickets, reqs)]
+    srv.stop(timeout=30.0)
+    assert len(set(tickets)) == len(reqs)
+    for r, o in zip(reqs, outs):
+        assert o["status"] == hp.SERVE_DONE and o["latency"] >= 0.0
+        if r.kind == "integrate":
+            assert o["result"] == hp.integrate(r.M, r.masses, r.nevents, r.seed, kin_dtype="f32", me=r.me,
+                                               params=r.params)
+        else:
+            p, w = hp.generate(r.M, r.masses, r.nevents, r.seed, dtype="f32")
+            torch.cuda.synchronize()
+            assert torch.equal(o["host_out"][:, :, : r.nevents], p[:, :, : r.nevents].cpu())
+            assert torch.equal(o["host_w"][: r.nevents], w.cpu())
+    # a polled ticket is consumed; submitting after stop is refused
+    with pytest.raises(hp.HydraError):
+        srv.poll(tickets[0], timeout=0.0)
+    with pytest.raises(hp.HydraError):
+        srv.submit(reqs[0])
+    srv.close()
+
+
+def test_native_live_submit_validates_at_once():
+    from paper_1711_05683_b300 import serve
+    srv = serve.NativeServer(max_slices=16, pinned_bytes=1 << 24, budget_bytes=1 << 28)
+    srv.start()
+    with pytest.raises(hp.HydraError) as e:
+        srv.submit(workloads.Request("generate", 1.0, (0.5, 0.6), 100, 1))
+    assert e.value.name == "HYDRA_ERR_BELOW_THRESHOLD"
+    srv.stop(timeout=5.0)
+    srv.close()
+
+
+def test_native_deadline_times_out_and_destroys_cleanly():
+    """A 20 ms deadline on a run whose integral needs thousands of 2^21-event ticks: the run ends
+    with HYDRA_ERR_TIMEOUT after its ticks in flight, the integral is answered timed out, small
+    requests that finished before keep their results, and the server is reusable and then
+    destroyed cleanly; the same for a live server stopped with a short timeout."""
+    from paper_1711_05683_b300 import serve
+    d = workloads.D0_DALITZ
+    big = workloads.Request("integrate", d["M"], d["masses"], 4000 * 2 ** 21, 9, me=1, params=d["params"],
+                            arrival=0.0)
+    small = workloads.Request("generate", 5.0, (0.1, 0.2, 0.3), 1000, 3, arrival=0.0)
+    srv = serve.NativeServer(max_slices=64, int_slice_segments=1, pinned_bytes=1 << 26, keep_outputs=True,
+                             budget_bytes=1 << 30)
+    srv.set_deadline(0.02)
+    res = srv.run([small, big])
+    assert res["deadline_passed"] and res["timed_out"] == [1]
+    srv.set_deadline(0.0)
+    again = srv.run([workloads.Request("generate", 5.0, (0.1, 0.2, 0.3), 1000, 4, arrival=0.0)])
+    assert again["completed"] == 1 and not again["deadline_passed"]
+    srv.start()
+    t_big = srv.submit(big)
+    with pytest.raises(hp.HydraError) as e:
+        srv.stop(timeout=0.005)
+    assert e.value.name == "HYDRA_ERR_TIMEOUT"
+    assert srv.poll(t_big, timeout=0.0)["status"] == hp.SERVE_TIMED_OUT
+    srv.close()
