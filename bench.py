@@ -38,9 +38,9 @@ INT_CFG = workloads.D0_DALITZ
 
 
 # Thread instructions issued per event by the generator kernels at their tuned launch shapes
-# (ncu smsp__inst_executed.sum x 32 / events on a 4e6-event launch of each kernel; the
-# command and table are in profiles/launches_instr_sweep_4e6.md).  They are the per-event
-# work of the issue-bound FP64 (double-float) generator, the dominant kernel of the step.
+# (ncu smsp__inst_executed.sum x 32 / events on a 4e6-event launch of each kernel, one capture
+# of a single generator kernel per row).  They explain the issue-bound double-float generator
+# (issue_frac in the per-launch breakdown); the roofline itself counts method operations.
 INSTR_PER_EVENT = {
     ("f32", 2): 90, ("f32", 3): 199, ("f32", 4): 282, ("f32", 5): 400, ("f32", 6): 515,
     ("f32", 7): 671, ("f32", 8): 762, ("f32", 9): 885, ("f32", 10): 999,
@@ -664,7 +664,7 @@ def run_lambda_ab(nev: int = 100_000_000, reps: int = 3, ns=(3, 10)) -> dict:
 
 # ----------------------------------------------------------------------------- VEGAS
 # Thread instructions per point of the double-float VEGAS kernels (ncu smsp__inst_executed.sum
-# x 32 / points on 4e6-point iterations, 100 bins; profiles/vegas_eval_df_dalitz_4e6.md).
+# x 32 / points on 4e6-point iterations, 100 bins).
 VEGAS_INSTR_PER_POINT = {("dalitz", "eval"): 1283, ("dalitz", "hist"): 108,
                          ("flat10", "eval"): 2479, ("flat10", "hist"): 457}
 

@@ -3,8 +3,8 @@
 // 192).  The integrand is F(u) = w(u) |ME|^2(event(u)) on the unit cube of the D = 3n-4
 // variables of one event (n-2 intermediate-mass uniforms, then one (cos theta, phi) pair per
 // top-down two-body step), so that Int F du = Int |ME|^2 dR_n.  Each dimension has a grid of
-// K bins refined after every iteration; all sampling, kinematics and sums run on the GPU in
-// FP64 (native or double-float, hydra_set_fp64_arith), the refinement on the host.
+// K bins refined after every iteration; sampling, kinematics, sums and the grid refinement all
+// run on the GPU (FP64: native or double-float, hydra_set_fp64_arith).
 //
 // Per iteration i (Philox stream i + 1):
 //   vegas_eval  point s: y_d = (x + 1/2) 2^-32 from Philox word d%4 of counter (s low, s high,

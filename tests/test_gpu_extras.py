@@ -165,15 +165,52 @@ def _evaluate_on_oracle_events_fp64():
     assert res2["sum_w"] == pytest.approx(ref2["sum_w"], rel=1e-12)
 
 
+def fp32_dalitz_value_bound(ev, w, params):
+    """Per-event bound on |f_FP32 - f| for f = w |A|^2, A = BW(s12; a) + c BW(s23; b), evaluated
+    in FP32 from the same stored events (ev [3, 4, n] and w in FP64, from the FP32 outputs).
+
+    * A pair mass s = (E_i + E_j)^2 - |p_i + p_j|^2 from FP32 components: four sums and three
+      fused multiply-adds, each rounding by at most 2^-24 of a term bounded by (E_i + E_j)^2, so
+      |ds| <= 8 2^-24 (E_i + E_j)^2.
+    * BW(s) = 1/(m0^2 - s - i m0 G) has dBW/ds = BW^2, so |dA| <= |BW_a|^2 |ds12| + |c| |BW_b|^2 |ds23|
+      and d|A|^2 <= 2 |A| |dA|; near the phi(1020) (m0 G = 4.1e-3 GeV^2) this is the large term.
+    * The rest (m0^2 - s, the reciprocal of |m0^2 - s|^2 + (m0 G)^2 by rcp.approx, the real and
+      imaginary parts, their squares) is about a dozen FP32 roundings (rcp.approx: up to 2 ulp)
+      of terms no larger than the amplitudes before they interfere; 32 2^-24 (|BW_a| + |c| |BW_b|)^2
+      bounds them, also where the two amplitudes cancel and |A|^2 itself is small.
+    * The product with w rounds once more: 2^-24 f (2^-23 with the rcp.approx ulp)."""
+    m0a, ga, m0b, gb, cabs, carg = params
+    c = cabs * np.exp(1j * carg)
+    u = 2.0 ** -24
+    s, ds = [], []
+    for i, j in ((0, 1), (1, 2)):
+        v = ev[i] + ev[j]
+        s.append(v[0] ** 2 - v[1] ** 2 - v[2] ** 2 - v[3] ** 2)
+        ds.append(8 * u * v[0] ** 2)
+    bwa = 1.0 / (m0a ** 2 - s[0] - 1j * m0a * ga)
+    bwb = 1.0 / (m0b ** 2 - s[1] - 1j * m0b * gb)
+    amp = np.abs(bwa + c * bwb)
+    f = w * amp ** 2
+    return (w * (2 * amp * (np.abs(bwa) ** 2 * ds[0] + cabs * np.abs(bwb) ** 2 * ds[1])
+                 + 32 * u * (np.abs(bwa) + cabs * np.abs(bwb)) ** 2) + 2 * u * f)
+
+
 def test_evaluate_fp32_and_flat():
+    """FP32 evaluation on FP32 events against the oracle on the same events: every value within
+    its derived per-event bound (fp32_dalitz_value_bound), the sum within 2e-4 relative (the
+    bound of the parity module for FP32 sums near the narrow pole)."""
     d = workloads.D0_DALITZ
     nev = 50_001
     gp, gw = hp.generate(d["M"], d["masses"], nev, 2, dtype="f32")
     res, vals = hp.evaluate(gp, gw, me=hp.ME_DALITZ_2BW, params=d["params"], dtype="f32", want_values=True)
-    ref_vals, ref_sums = oracle.evaluate(gp[:, :, :nev].double().cpu().numpy(), gw.double().cpu().numpy(),
-                                         me=1, params=d["params"])
+    ev64 = gp[:, :, :nev].double().cpu().numpy()
+    w64 = gw.double().cpu().numpy()
+    ref_vals, ref_sums = oracle.evaluate(ev64, w64, me=1, params=d["params"])
     assert abs(res["sum_f"] - ref_sums[0]) <= 2e-4 * ref_sums[0]
-    np.testing.assert_allclose(vals.double().cpu().numpy(), ref_vals, rtol=2e-3)
+    bound = fp32_dalitz_value_bound(ev64, w64, d["params"])
+    err = np.abs(vals.double().cpu().numpy() - ref_vals)
+    assert (err <= bound).all(), float((err / bound).max())
+    assert float(np.median(bound / ref_vals)) < 1e-4  # the bound is tight where nothing cancels
     flat, fv = hp.evaluate(gp, gw, dtype="f32", want_values=True)
     assert torch.equal(fv, gw)
     assert flat["sum_w"] == flat["sum_f"]
