@@ -657,6 +657,13 @@ hydra_status hydra_phsp_batch_run(hydra_batch_request* reqs, int nreq, size_t bu
     hydra_status st = ensure_run_scratch(rsp, max_slices, ptiles, arena_need, arena_bytes, nsegs, any_host);
     if (st != HYDRA_OK) return st;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    // on a failure after the first wave was enqueued, wait for the work already queued (it writes
+    // the kept arena) before returning, so that no later call can race with it
+    auto drain = [&](hydra_status status) {
+        if (any_host) cudaStreamSynchronize(res.copy);
+        cudaStreamSynchronize(s);
+        return status;
+    };
     std::vector<hydra_request> table;
     for (size_t w = 0; w < waves.size(); ++w) {
         const int b = static_cast<int>(w & 1);
@@ -697,10 +704,10 @@ hydra_status hydra_phsp_batch_run(hydra_batch_request* reqs, int nreq, size_t bu
         // this half of the arena is free once the copies of the wave before the previous one are done
         if (any_host && w >= 2) {
             err = cudaStreamWaitEvent(s, res.copy_done[b], 0);
-            if (err != cudaSuccess) return cuda_fail(err, "batch run arena wait");
+            if (err != cudaSuccess) return drain(cuda_fail(err, "batch run arena wait"));
         }
         st = hydra_batch_run(res.batch, table.data(), static_cast<int>(table.size()), 1, stream);
-        if (st != HYDRA_OK) return st;
+        if (st != HYDRA_OK) return drain(st);
         if (host_copies) {
             err = cudaEventRecord(res.gen_done[b], s);
             if (err == cudaSuccess) err = cudaStreamWaitEvent(res.copy, res.gen_done[b], 0);
@@ -718,11 +725,11 @@ hydra_status hydra_phsp_batch_run(hydra_batch_request* reqs, int nreq, size_t bu
                                           cudaMemcpyDeviceToHost, res.copy);
             }
             if (err == cudaSuccess) err = cudaEventRecord(res.copy_done[b], res.copy);
-            if (err != cudaSuccess) return cuda_fail(err, "batch run output copy");
+            if (err != cudaSuccess) return drain(cuda_fail(err, "batch run output copy"));
         }
         for (int j : finals) {
             st = hydra_batch_result(res.batch, j, &reqs[waves[w][j].req].result);
-            if (st != HYDRA_OK) return st;
+            if (st != HYDRA_OK) return drain(st);
         }
     }
     if (any_host) err = cudaStreamSynchronize(res.copy);

@@ -190,3 +190,11 @@ def test_batch_run_validates_before_any_launch(L):
     assert "budget" in str(e.value)
     with pytest.raises(hp_.HydraError):
         hp_.batch_run(t[:0], 1 << 30)        # no requests
+
+
+def test_op_rate_probe_rejects_bad_arguments(L):
+    """Host-side checks of hydra_probe_op_rate (no GPU needed to reach them)."""
+    r = ctypes.c_double()
+    assert hp.STATUS[L.hydra_probe_op_rate(0, 0, 0, ctypes.byref(r), None)] == "HYDRA_ERR_INVALID_ARG"  # iterations
+    assert hp.STATUS[L.hydra_probe_op_rate(0, 0, 10, None, None)] == "HYDRA_ERR_INVALID_ARG"            # no output
+    assert hp.STATUS[L.hydra_probe_op_rate(7, 0, 10, ctypes.byref(r), None)] == "HYDRA_ERR_INVALID_ARG"  # arithmetic

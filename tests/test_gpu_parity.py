@@ -427,3 +427,16 @@ def test_double_float_directions_over_many_angles():
     cosine) against the oracle; the error is reported at ~1e-14 of the scale."""
     err_p, err_w = compare_events(10.0, (0.0, 0.0), 200_000, 4242, "f64")
     assert err_p <= 1e-13 and err_w <= 1e-13, (err_p, err_w)
+
+
+def test_op_rate_probe_is_consistent():
+    """The arithmetic-rate probe behind the roofline's FP ceiling: FP32 add, mul and fma run at
+    one rate (the FP32 pipe's), a double-float op costs several FP32 instructions (sum ~11,
+    product ~4, product-and-sum ~15), and FP64 instructions run on the narrow FP64 pipe."""
+    f32 = {op: hp.probe_op_rate("f32", op, 20_000) for op in ("add", "mul", "fma")}
+    df = {op: hp.probe_op_rate("df", op, 4_000) for op in ("add", "mul", "fma", "sqrt", "rcp")}
+    f64 = hp.probe_op_rate("f64", "fma", 2_000)
+    assert max(f32.values()) < 1.2 * min(f32.values())
+    assert 6 < f32["add"] / df["add"] < 20 and 2.5 < f32["mul"] / df["mul"] < 8 and 9 < f32["fma"] / df["fma"] < 30
+    assert df["fma"] < df["add"] < df["mul"] and all(v > 0 for v in df.values())
+    assert f64 < f32["fma"] / 20
