@@ -581,6 +581,7 @@ hydra_status hydra_phsp_volume_factor(double M, int n, const double* masses, dou
 hydra_status hydra_phsp_generate(double M, int n, const double* masses, uint64_t nevents,
                                  uint64_t seed, uint64_t event_offset, hydra_dtype dtype,
                                  void* out, uint64_t ld, void* weights, hydra_stream_t stream) {
+    const NvtxRange nvtx_range("hydra_phsp_generate");
     DecayConsts C;
     hydra_status st = make_consts(M, n, masses, seed, &C);
     if (st != HYDRA_OK) return st;
@@ -605,6 +606,7 @@ hydra_status hydra_phsp_generate_host(double M, int n, const double* masses, uin
                                       uint64_t seed, uint64_t event_offset, hydra_dtype dtype,
                                       void* out_host, uint64_t ld, void* weights_host,
                                       hydra_stream_t stream) {
+    const NvtxRange nvtx_range("hydra_phsp_generate_host");
     DecayConsts C;
     hydra_status st = make_consts(M, n, masses, seed, &C);
     if (st != HYDRA_OK) return st;
@@ -663,6 +665,7 @@ hydra_status hydra_phsp_generate_host(double M, int n, const double* masses, uin
 
 hydra_status hydra_phsp_draws(int n, uint64_t nevents, uint64_t seed, uint64_t event_offset,
                               uint32_t* out, uint64_t ld, hydra_stream_t stream) {
+    const NvtxRange nvtx_range("hydra_phsp_draws");
     if (n < 2 || n > kNMax) return fail(HYDRA_ERR_UNSUPPORTED_N, "n = %d outside [2, %d]", n, kNMax);
     if (event_offset + nevents < event_offset) return fail(HYDRA_ERR_INVALID_ARG, "event_offset + nevents overflows 64 bits");
     if (nevents == 0) return HYDRA_OK;
@@ -690,6 +693,7 @@ hydra_status hydra_phsp_integrate(double M, int n, const double* masses, uint64_
                                   uint64_t seed, uint64_t event_offset, hydra_dtype kin_dtype,
                                   hydra_me_id me, const double* params, int nparams,
                                   hydra_integral* result, hydra_stream_t stream) {
+    const NvtxRange nvtx_range("hydra_phsp_integrate");
     DecayConsts C;
     hydra_status st = make_consts(M, n, masses, seed, &C);
     if (st != HYDRA_OK) return st;
@@ -728,6 +732,7 @@ hydra_status hydra_phsp_integrate_noalloc(double M, int n, const double* masses,
                                           uint64_t seed, uint64_t event_offset, hydra_dtype kin_dtype,
                                           hydra_me_id me, const double* params, int nparams,
                                           hydra_integral* result, hydra_stream_t stream) {
+    const NvtxRange nvtx_range("hydra_phsp_integrate_noalloc");
     DecayConsts C;
     hydra_status st = make_consts(M, n, masses, seed, &C);
     if (st != HYDRA_OK) return st;

@@ -198,6 +198,7 @@ hydra_status hydra_batch_create(int max_requests, uint64_t max_integrate_tiles, 
 
 hydra_status hydra_batch_run(hydra_batch* b, const hydra_request* reqs, int nreq, int use_graph,
                              hydra_stream_t stream) {
+    const NvtxRange nvtx_range("hydra_batch_run");
     if (!b) return fail(HYDRA_ERR_INVALID_ARG, "batch is NULL");
     if (nreq < 1 || nreq > b->max_requests)
         return fail(HYDRA_ERR_INVALID_ARG, "nreq = %d outside [1, %d]", nreq, b->max_requests);
@@ -563,6 +564,7 @@ hydra_status ensure_run_scratch(RunScratch* rs, int max_slices, uint64_t ptiles,
 extern "C" {
 
 hydra_status hydra_phsp_batch_run(hydra_batch_request* reqs, int nreq, size_t budget_bytes, hydra_stream_t stream) {
+    const NvtxRange nvtx_range("hydra_phsp_batch_run");
     t_last_waves = t_last_slices = 0;
     if (!reqs || nreq < 1) return fail(HYDRA_ERR_INVALID_ARG, "need at least one request");
     const int dt = reqs[0].dtype;

@@ -640,6 +640,7 @@ hydra_status hydra_phsp_generate_boosted(double M, int n, const double* masses, 
                                          uint64_t seed, uint64_t event_offset, hydra_dtype dtype,
                                          const double* mother_p, const void* mothers, uint64_t mld,
                                          void* out, uint64_t ld, void* weights, hydra_stream_t stream) {
+    const NvtxRange nvtx_range("hydra_phsp_generate_boosted");
     DecayConsts C;
     hydra_status st = make_consts(M, n, masses, seed, &C);
     if (st != HYDRA_OK) return st;
@@ -677,6 +678,7 @@ hydra_status hydra_phsp_generate_boosted(double M, int n, const double* masses, 
 hydra_status hydra_phsp_unweight(int n, uint64_t nevents, uint64_t seed, uint64_t event_offset, hydra_dtype dtype,
                                  const void* weights, double w_max, int64_t* indices, uint64_t* naccepted,
                                  double* w_max_used, hydra_stream_t stream) {
+    const NvtxRange nvtx_range("hydra_phsp_unweight");
     if (n < 2 || n > kNMax) return fail(HYDRA_ERR_UNSUPPORTED_N, "n = %d outside [2, %d]", n, kNMax);
     if (dtype != HYDRA_F32 && dtype != HYDRA_F64) return fail(HYDRA_ERR_INVALID_ARG, "unknown dtype %d", static_cast<int>(dtype));
     if (!naccepted) return fail(HYDRA_ERR_INVALID_ARG, "naccepted is NULL");
@@ -776,6 +778,7 @@ hydra_status hydra_phsp_unweight(int n, uint64_t nevents, uint64_t seed, uint64_
 hydra_status hydra_phsp_evaluate(int n, uint64_t nevents, hydra_dtype dtype, hydra_me_id me, const double* params,
                                  int nparams, const void* events, uint64_t ld, const void* weights, void* values,
                                  hydra_integral* result, hydra_stream_t stream) {
+    const NvtxRange nvtx_range("hydra_phsp_evaluate");
     if (n < 2 || n > kNMax) return fail(HYDRA_ERR_UNSUPPORTED_N, "n = %d outside [2, %d]", n, kNMax);
     if (dtype != HYDRA_F32 && dtype != HYDRA_F64) return fail(HYDRA_ERR_INVALID_ARG, "unknown dtype %d", static_cast<int>(dtype));
     if (!result) return fail(HYDRA_ERR_INVALID_ARG, "result is NULL");
@@ -863,6 +866,7 @@ hydra_status hydra_phsp_evaluate(int n, uint64_t nevents, hydra_dtype dtype, hyd
 hydra_status hydra_phsp_gather(int n, hydra_dtype dtype, const void* src, uint64_t src_ld, const void* src_weights,
                                const int64_t* indices, uint64_t count, void* dst, uint64_t dst_ld, void* dst_weights,
                                hydra_stream_t stream) {
+    const NvtxRange nvtx_range("hydra_phsp_gather");
     if (n < 2 || n > kNMax) return fail(HYDRA_ERR_UNSUPPORTED_N, "n = %d outside [2, %d]", n, kNMax);
     if (dtype != HYDRA_F32 && dtype != HYDRA_F64) return fail(HYDRA_ERR_INVALID_ARG, "unknown dtype %d", static_cast<int>(dtype));
     if (count == 0) return HYDRA_OK;

@@ -7,6 +7,8 @@
 #include <cstdint>
 #include <string>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "hydra_phsp.h"
 #include "phsp_device.cuh"
 
@@ -31,6 +33,15 @@ extern std::atomic<int> g_fp64_arith;
 
 // Grid for a grid-stride kernel: min(blocks needed, resident blocks per SM x SMs).
 int grid_for(const void* kernel, int block, uint64_t work_items);
+
+// An NVTX range named after a C-ABI call (or a serving tick) for profiler timelines: pushed
+// on construction, popped on destruction; a no-op check when no tool is attached.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Release of the scratch owned by the other translation units (called by hydra_shutdown).
 void release_extras_scratch();

@@ -366,6 +366,7 @@ hydra_status serve_loop(hydra_server* s, Source& src, Clock::time_point t0, doub
                 if (static_cast<int>(table.size()) >= s->max_slices) break;
             }
             if (!table.empty()) {
+                const NvtxRange nvtx_tick("hydra_server_tick");
                 st = hydra_batch_run(s->runners[t.runner], table.data(), static_cast<int>(table.size()), 1,
                                      reinterpret_cast<hydra_stream_t>(s->compute));
                 if (st != HYDRA_OK) break;
@@ -540,6 +541,7 @@ hydra_status hydra_server_set_deadline(hydra_server* s, double seconds) {
 
 hydra_status hydra_server_run(hydra_server* s, const hydra_serve_request* reqs, int nreq, double time_scale,
                               hydra_serve_outcome* outcomes, double* wall_s, uint64_t* ticks_out) {
+    const NvtxRange nvtx_range("hydra_server_run");
     if (!s || !outcomes || (nreq > 0 && !reqs) || nreq < 0 || !(time_scale >= 0.0))
         return fail(HYDRA_ERR_INVALID_ARG, "bad run arguments");
     {

@@ -548,6 +548,7 @@ extern "C" {
 hydra_status hydra_phsp_vegas(double M, int n, const double* masses, uint64_t seed, hydra_me_id me, const double* params,
                               int nparams, uint64_t calls, int iterations, int bins, double alpha, int skip,
                               double* est, double* var, double* result, double* grid_out, hydra_stream_t stream) {
+    const NvtxRange nvtx_range("hydra_phsp_vegas");
     DecayConsts C;
     hydra_status st = make_consts(M, n, masses, seed, &C);
     if (st != HYDRA_OK) return st;
