@@ -173,3 +173,49 @@ def test_invalid_request_launches_nothing():
         hp.batch_run(table, 64 << 20)
     assert table["status"][1] == 2 and table["status"][0] == 0
     assert all(torch.isnan(o).all() for o, _ in outs)
+
+
+def test_integrals_only_fp64():
+    """Only integral requests (FP64, flat and Dalitz, one longer than 2^26 events): no arena is
+    needed; every result equals hydra_phsp_integrate bit for bit."""
+    d = workloads.D0_DALITZ
+    specs = [(d["M"], d["masses"], 5_000_003, hp.ME_DALITZ_2BW, d["params"]),
+             (10.0, workloads.sweep_masses(6, True), (1 << 26) + 1, hp.ME_FLAT, ()),
+             (3.0, (0.1, 0.2), 77, hp.ME_FLAT, ())]
+    table = np.zeros(len(specs), dtype=hp.batch_request_dtype())
+    for i, (M, masses, nev, me, par) in enumerate(specs):
+        fill(table[i], hp.REQ_INTEGRATE, M, masses, nev, 100 + i, "f64", event_offset=i << 40, me=me, params=par)
+    hp.batch_run(table, 256 << 20)
+    for i, (M, masses, nev, me, par) in enumerate(specs):
+        ref = hp.integrate(M, masses, nev, 100 + i, kin_dtype="f64", me=me, params=par, event_offset=i << 40)
+        for k in ("mean", "var_mean", "sum_f", "sum_f2", "sum_w", "sum_w2"):
+            assert float(table[i]["result"][k]) == ref[k], (i, k)
+
+
+def test_one_wave_per_request_then_a_larger_budget():
+    """A budget that holds one request's outputs per wave (every request its own wave), then the
+    same requests with a budget 16 times larger (the kept arena is replaced): same bits."""
+    rng = np.random.default_rng(3)
+    reqs = []
+    for i in range(6):
+        n = 8 - i % 2  # 17-20 MB of outputs each: more than half of the small budget's arena
+        M, masses = workloads.random_decay(rng, n)
+        reqs.append((M, masses, 150_000 + 1000 * i, 900 + i))
+    outs = []
+    for budget in (24 << 20, 384 << 20):
+        table = np.zeros(len(reqs), dtype=hp.batch_request_dtype())
+        keep = []
+        for i, (M, masses, nev, seed) in enumerate(reqs):
+            out, w = host_arrays(len(masses), nev, nev, "f32")
+            fill(table[i], hp.REQ_GENERATE, M, masses, nev, seed, dest=hp.DEST_HOST, out=out.data_ptr(),
+                 weights=w.data_ptr(), ld=nev)
+            keep.append((out, w))
+        hp.batch_run(table, budget)
+        outs.append((hp.batch_stats(), keep))
+    (w_small, _), small = outs[0]
+    (w_large, _), large = outs[1]
+    assert w_small >= len(reqs) > w_large
+    for (a, b), (c, e), (M, masses, nev, seed) in zip(small, large, reqs):
+        assert torch.equal(a, c) and torch.equal(b, e)
+        p1, w1 = single(M, masses, nev, seed, "f32")
+        assert torch.equal(a, p1) and torch.equal(b, w1)

@@ -254,3 +254,49 @@ def test_native_deadline_times_out_and_destroys_cleanly():
     assert e.value.name == "HYDRA_ERR_TIMEOUT"
     assert srv.poll(t_big, timeout=0.0)["status"] == hp.SERVE_TIMED_OUT
     srv.close()
+
+
+def test_native_live_concurrent_clients_and_withdrawal():
+    """Four client threads submit at once (the server's inbox is shared); one client withdraws
+    its long integral 2 ms after submitting it.  Every other outcome equals the single-request
+    result; the withdrawn one is reported withdrawn."""
+    import threading
+    from paper_1711_05683_b300 import serve
+    d = workloads.D0_DALITZ
+    reqs = list(workloads.serve_stream(rate_hz=4000, duration_s=0.05, gen_log_events=(2.0, 4.0),
+                                       int_log_events=(4.0, 6.0), rng_seed=8))
+    big = workloads.Request("integrate", d["M"], d["masses"], 2000 * 2 ** 21, 77, me=1, params=d["params"])
+    srv = serve.NativeServer(max_slices=256, int_slice_segments=1, pinned_bytes=1 << 28, keep_outputs=True,
+                             budget_bytes=2 * 10 ** 9)
+    srv.start()
+    tickets = {}
+    lock = threading.Lock()
+
+    def client(c):
+        for i in range(c, len(reqs), 4):
+            t = srv.submit(reqs[i])
+            with lock:
+                tickets[i] = t
+
+    threads = [threading.Thread(target=client, args=(c,)) for c in range(4)]
+    for th in threads:
+        th.start()
+    t_big = srv.submit(big, withdraw=0.002)
+    for th in threads:
+        th.join()
+    outs = {i: srv.poll(t, timeout=30.0, request=reqs[i]) for i, t in tickets.items()}
+    o_big = srv.poll(t_big, timeout=30.0, request=big)
+    srv.stop(timeout=30.0)
+    srv.close()
+    assert o_big["status"] == hp.SERVE_WITHDRAWN
+    assert len(set(tickets.values()) | {t_big}) == len(reqs) + 1
+    for i, o in outs.items():
+        r = reqs[i]
+        assert o["status"] == hp.SERVE_DONE
+        if r.kind == "integrate":
+            assert o["result"] == hp.integrate(r.M, r.masses, r.nevents, r.seed, kin_dtype="f32", me=r.me,
+                                               params=r.params)
+        else:
+            p, w = hp.generate(r.M, r.masses, r.nevents, r.seed, dtype="f32")
+            torch.cuda.synchronize()
+            assert torch.equal(o["host_out"][:, :, : r.nevents], p[:, :, : r.nevents].cpu())
