@@ -219,3 +219,44 @@ def test_one_wave_per_request_then_a_larger_budget():
         assert torch.equal(a, c) and torch.equal(b, e)
         p1, w1 = single(M, masses, nev, seed, "f32")
         assert torch.equal(a, p1) and torch.equal(b, w1)
+
+
+def test_c4_full_mix_sampled():
+    """Config C4 at full size, as bench.py runs it: the 4096 uneven requests (4.6e9 events,
+    ~390 GB of FP32 outputs) through one hydra_phsp_batch_run call with a 40 GB budget; the
+    outputs of every request are dropped with their wave except those of 8 sampled requests
+    (first, last, the largest, and five others), which go to device buffers.  Each sampled
+    request equals a single call bit for bit and, on 64 of its events, the oracle."""
+    reqs = workloads.batch_requests(4096)
+    sample = sorted({0, 4095, max(range(4096), key=lambda i: reqs[i].nevents), 17, 1000, 2048, 3001, 3999})
+    table = np.zeros(len(reqs), dtype=hp.batch_request_dtype())
+    bufs = {}
+    for i, r in enumerate(reqs):
+        if i in sample:
+            ld = hp.padded_ld(r.nevents)
+            out = torch.empty((len(r.masses), 4, ld), dtype=torch.float32, device="cuda")
+            w = torch.empty(ld, dtype=torch.float32, device="cuda")
+            bufs[i] = (out, w)
+            fill(table[i], hp.REQ_GENERATE, r.M, r.masses, r.nevents, r.seed, dest=hp.DEST_DEVICE,
+                 out=out.data_ptr(), weights=w.data_ptr(), ld=ld)
+        else:
+            fill(table[i], hp.REQ_GENERATE, r.M, r.masses, r.nevents, r.seed)
+    try:
+        hp.batch_run(table, 40 * 10 ** 9)
+        waves, slices = hp.batch_stats()
+        assert waves >= 9 and slices >= len(reqs)
+        torch.cuda.synchronize()
+        for i in sample:
+            r = reqs[i]
+            out, w = bufs[i]
+            p1, w1 = single(r.M, r.masses, r.nevents, r.seed, "f32")
+            assert torch.equal(out[:, :, : r.nevents].cpu(), p1) and torch.equal(w[: r.nevents].cpu(), w1), i
+            k = min(64, r.nevents)
+            ref_p, ref_w = oracle.generate(r.M, r.masses, k, r.seed)
+            scale = np.maximum(r.M, ref_p[:, 0, :].max(axis=0))
+            assert float((np.abs(out[:, :, :k].double().cpu().numpy() - ref_p) / scale).max()) <= 2e-5
+            assert float((np.abs(w[:k].double().cpu().numpy() - ref_w) / ref_w).max()) <= 2e-5
+    finally:
+        del bufs
+        hp.shutdown()  # release the call's kept 40 GB arena
+        torch.cuda.empty_cache()
