@@ -44,12 +44,12 @@ INT_CFG = workloads.D0_DALITZ
 INSTR_PER_EVENT = {
     ("f32", 2): 90, ("f32", 3): 199, ("f32", 4): 282, ("f32", 5): 400, ("f32", 6): 515,
     ("f32", 7): 671, ("f32", 8): 762, ("f32", 9): 885, ("f32", 10): 999,
-    ("f64", 2): 383, ("f64", 3): 943, ("f64", 4): 1454, ("f64", 5): 1973, ("f64", 6): 2624,
-    ("f64", 7): 3157, ("f64", 8): 3695, ("f64", 9): 4246, ("f64", 10): 4802,
+    ("f64", 2): 383, ("f64", 3): 980, ("f64", 4): 1454, ("f64", 5): 1973, ("f64", 6): 2564,
+    ("f64", 7): 3106, ("f64", 8): 3617, ("f64", 9): 4152, ("f64", 10): 4714,
     # the double-float variant for all-massless decays (no square root per two-body momentum)
-    ("f64", 2, "massless"): 328, ("f64", 3, "massless"): 853, ("f64", 4, "massless"): 1323,
-    ("f64", 5, "massless"): 1809, ("f64", 6, "massless"): 2393, ("f64", 7, "massless"): 2889,
-    ("f64", 8, "massless"): 3356, ("f64", 9, "massless"): 3881, ("f64", 10, "massless"): 4406,
+    ("f64", 2, "massless"): 328, ("f64", 3, "massless"): 889, ("f64", 4, "massless"): 1323,
+    ("f64", 5, "massless"): 1809, ("f64", 6, "massless"): 2355, ("f64", 7, "massless"): 2842,
+    ("f64", 8, "massless"): 3300, ("f64", 9, "massless"): 3801, ("f64", 10, "massless"): 4284,
 }
 
 

@@ -233,6 +233,29 @@ template <> struct Prec<df> {
     __device__ static df m2(const DecayConsts& C, int i) { return df{C.m2df[i][0], C.m2df[i][1]}; }
 };
 
+// Direction of subsystem k in the rest frame of subsystem k+1 for the double-float generators
+// with N >= 6, as one out-of-line function: p (sin theta cos phi, sin theta sin phi, cos theta)
+// from the cos(theta) draw xc and the phi draw xp.  Their unrolled bodies are long enough that a
+// single copy of this code (sin(theta) by its square root, the sin/cos table step for phi and the
+// five products) saves more in instruction fetch than the call costs.  Measured over the FP64
+// sweep, against the sin/cos step alone out of line with its results through pointers (itself 3%
+// faster than all inline): 2.2% faster, 3.5-4.5% at N = 9, 10, with bit-identical results; below
+// N = 6 the inline code is faster.  The six FP32 parts come back by value, in registers.
+struct DfDirection {
+    float v[6];  // px, py, pz as (hi, lo) pairs
+};
+
+static __device__ __noinline__ DfDirection df_direction_outlined(df p, uint32_t xc, uint32_t xp) {
+    using P = Prec<df>;
+    const df cos_t = P::cos_of(xc);
+    const df sin_t = P::sqrt_(P::one_minus_cos(xc) * P::one_plus_cos(xc));
+    df sphi, cphi;
+    P::sincos_2pi_u(xp, &sphi, &cphi);
+    const df ps = p * sin_t;
+    const df px = ps * cphi, py = ps * sphi, pz = p * cos_t;
+    return DfDirection{{px.hi, px.lo, py.hi, py.lo, pz.hi, pz.lo}};
+}
+
 // ------------------------------------------------------------------------------------
 // A group of EPT Raubold-Lynch events computed in lockstep (EPT independent dependency
 // chains per thread).  The library is compiled with -fmad=false and every fused
@@ -378,17 +401,20 @@ __device__ __forceinline__ void raubold_lynch_group(const DecayConsts& C, const 
             // isotropic direction of subsystem k in the rest frame of subsystem k+1
             const uint32_t xc = xcs[q];
             const uint32_t xp = xps[q];
-            const R cos_t = P::cos_of(xc);         // 2u - 1
-            const R one_m = P::one_minus_cos(xc);  // 1 - cos(theta)
-            const R one_p = P::one_plus_cos(xc);   // 1 + cos(theta)
-            const R sin_t = P::sqrt_(one_m * one_p);
-            R sphi, cphi;
-            if constexpr (std::is_same<R, df>::value && N >= 6)
-                df_sincos_2pi_u_outlined(xp, &sphi, &cphi);  // phi = 2 pi u (one copy of the code)
-            else
+            R px, py, pz;
+            if constexpr (std::is_same<R, df>::value && N >= 6) {
+                const DfDirection d = df_direction_outlined(p, xc, xp);  // one copy of the code
+                px = df{d.v[0], d.v[1]}; py = df{d.v[2], d.v[3]}; pz = df{d.v[4], d.v[5]};
+            } else {
+                const R cos_t = P::cos_of(xc);         // 2u - 1
+                const R one_m = P::one_minus_cos(xc);  // 1 - cos(theta)
+                const R one_p = P::one_plus_cos(xc);   // 1 + cos(theta)
+                const R sin_t = P::sqrt_(one_m * one_p);
+                R sphi, cphi;
                 P::sincos_2pi_u(xp, &sphi, &cphi);  // phi = 2 pi u
-            const R ps = p * sin_t;
-            const R px = ps * cphi, py = ps * sphi, pz = p * cos_t;
+                const R ps = p * sin_t;
+                px = ps * cphi; py = ps * sphi; pz = p * cos_t;
+            }
             // energy of subsystem k in the rest frame of k+1: (M_{k+1}^2 + M_k^2 - m_{k+1}^2) / (2 M_{k+1})
             // = M_k + Delta (Delta + 2 m_{k+1}) / (2 M_{k+1}), a sum of positive terms
             const R Es = P::fma_pos(gm, halfInvM, Mk);

@@ -370,12 +370,4 @@ __device__ __forceinline__ void df_sincos_2pi_int(uint32_t d, const SinCosTable&
     df_sincos_table_step(d >> 21, (d & 0x1FFFFFu) << 1, T, s, c);
 }
 
-// The same as one out-of-line function.  The N >= 6 double-float generators call this
-// (nine calls at N = 10): their unrolled bodies are long enough that a single copy of the
-// sin/cos code saves more in instruction fetch than the call costs (measured 3% over the FP64
-// sweep; inline is faster below N = 6).
-static __device__ __noinline__ void df_sincos_2pi_u_outlined(uint32_t x, df* s, df* c) {
-    df_sincos_2pi_u(x, s_sincos_table, s, c);
-}
-
 }  // namespace hydra
