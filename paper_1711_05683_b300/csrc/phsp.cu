@@ -167,6 +167,7 @@ hydra_status make_consts(double M, int n, const double* masses, uint64_t seed,
         C->m[i] = m;
         C->mu[i] = sum;
         C->m2[i] = m * m;
+        C->tm[i] = 2.0 * m;
         if (m == 0.0) C->massless |= 1u << i;
     }
     const double T = M - sum;
@@ -197,11 +198,13 @@ hydra_status make_consts(double M, int n, const double* masses, uint64_t seed,
         split(C->m[i], C->mdf[i]);
         split(C->mu[i], C->mudf[i]);
         split(C->m2[i], C->m2df[i]);
+        split(C->tm[i], C->tmdf[i]);
     }
     for (int i = 0; i < n; ++i) {
         C->mf[i] = static_cast<float>(C->m[i]);
         C->muf[i] = static_cast<float>(C->mu[i]);
         C->m2f[i] = static_cast<float>(C->m2[i]);
+        C->tmf[i] = static_cast<float>(C->tm[i]);
     }
     uint32_t k0 = static_cast<uint32_t>(seed), k1 = static_cast<uint32_t>(seed >> 32);
     for (int r = 0; r < 10; ++r) {

@@ -28,12 +28,13 @@ struct DecayConsts {
     double m[kNMax];    // daughter masses m_1..m_n at [0..n-1]
     double mu[kNMax];   // mu[k-1] = m_1 + ... + m_k
     double m2[kNMax];   // m_i^2
+    double tm[kNMax];   // 2 m_i
     // FP32 copies (rounded from the FP64 values)
     float Mf, Tsf, Ts_halff, Cf;
-    float mf[kNMax], muf[kNMax], m2f[kNMax];
+    float mf[kNMax], muf[kNMax], m2f[kNMax], tmf[kNMax];
     // double-float copies (hi, lo) for the df kinematics of the FP64 generator
     float Mdf[2], Tsdf[2], Ts_halfdf[2];
-    float mdf[kNMax][2], mudf[kNMax][2], m2df[kNMax][2];
+    float mdf[kNMax][2], mudf[kNMax][2], m2df[kNMax][2], tmdf[kNMax][2];
     // Philox round keys: key + r * (W0, W1), r = 0..9
     uint32_t rk0[10], rk1[10];
     uint32_t massless;  // bit i set when daughter i+1 has mass 0
@@ -115,6 +116,7 @@ template <> struct Prec<float> {
     __device__ static float fma_pos(float a, float b, float c) { return __fmaf_rn(a, b, c); }
     __device__ static float fma_lazy(float a, float b, float c) { return __fmaf_rn(a, b, c); }
     __device__ static float sub_lazy(float a, float b) { return a - b; }
+    __device__ static float sub_le(float a, float b) { return a - b; }
     // sin and cos of phi = 2 pi (x + 1/2) 2^-32: __sincosf is accurate (|err| < 2^-21.4) on
     // (-pi, pi), so evaluate it at phi - pi and flip both signs.
     __device__ static void sincos_2pi_u(uint32_t x, float* s, float* c) {
@@ -149,6 +151,7 @@ template <> struct Prec<float> {
     __device__ static float m(const DecayConsts& C, int i) { return C.mf[i]; }
     __device__ static float mu(const DecayConsts& C, int i) { return C.muf[i]; }
     __device__ static float m2(const DecayConsts& C, int i) { return C.m2f[i]; }
+    __device__ static float twom(const DecayConsts& C, int i) { return C.tmf[i]; }
 };
 
 template <> struct Prec<double> {
@@ -162,6 +165,7 @@ template <> struct Prec<double> {
     __device__ static double fma_pos(double a, double b, double c) { return __fma_rn(a, b, c); }
     __device__ static double fma_lazy(double a, double b, double c) { return __fma_rn(a, b, c); }
     __device__ static double sub_lazy(double a, double b) { return a - b; }
+    __device__ static double sub_le(double a, double b) { return a - b; }
     // sin and cos of phi = 2 pi u with u = (x + 1/2) 2^-32: sincospi(2u), argument exact.
     __device__ static void sincos_2pi_u(uint32_t x, double* s, double* c) {
         sincospi(__fma_rn(__uint2double_rn(x), 4.656612873077392578125e-10, 2.3283064365386962890625e-10), s, c);
@@ -188,6 +192,7 @@ template <> struct Prec<double> {
     __device__ static double m(const DecayConsts& C, int i) { return C.m[i]; }
     __device__ static double mu(const DecayConsts& C, int i) { return C.mu[i]; }
     __device__ static double m2(const DecayConsts& C, int i) { return C.m2[i]; }
+    __device__ static double twom(const DecayConsts& C, int i) { return C.tm[i]; }
 };
 
 // Double-float kinematics for the FP64 generator: arithmetic on the FP32 pipe with ~48
@@ -206,13 +211,16 @@ template <> struct Prec<df> {
     __device__ static df rcp(df v) { return df_rcp(v); }
     __device__ static df div(df a, df b) { return df_div(a, b); }
     __device__ static df fma_(df a, df b, df c) { return a * b + c; }
-    // a + b and a b + c whose terms are >= 0 (no cancellation): left unnormalised
-    __device__ static df add_pos(df a, df b) { return df_add_lazy(a, b); }
-    __device__ static df fma_pos(df a, df b, df c) { return df_add_lazy(a * b, c); }
+    // a + b and a b + c whose terms are >= 0 (no cancellation): left unnormalised, the larger
+    // high part first (FastTwoSum)
+    __device__ static df add_pos(df a, df b) { return df_add_pos_lazy(a, b); }
+    __device__ static df fma_pos(df a, df b, df c) { return df_add_pos_lazy(a * b, c); }
     // sums whose result only feeds products, sums and the conversion to double (the absolute
     // error at the scale of the terms is what matters): left unnormalised
     __device__ static df fma_lazy(df a, df b, df c) { return df_add_lazy(a * b, c); }
     __device__ static df sub_lazy(df a, df b) { return df_add_lazy(a, -b); }
+    // a - b for 0 <= b <= a (an energy less a part of it), left unnormalised
+    __device__ static df sub_le(df a, df b) { return df_sub_le_lazy(a, b); }
     __device__ static void sincos_2pi_u(uint32_t x, df* s, df* c) { df_sincos_2pi_u(x, s_sincos_table, s, c); }
     // cos(phi_a - phi_b) = cos(2 pi (xa - xb) 2^-32), the integer difference taken mod 2^32
     __device__ static df cos_2pi_diff(uint32_t xa, uint32_t xb) {
@@ -231,6 +239,7 @@ template <> struct Prec<df> {
     __device__ static df m(const DecayConsts& C, int i) { return df{C.mdf[i][0], C.mdf[i][1]}; }
     __device__ static df mu(const DecayConsts& C, int i) { return df{C.mudf[i][0], C.mudf[i][1]}; }
     __device__ static df m2(const DecayConsts& C, int i) { return df{C.m2df[i][0], C.m2df[i][1]}; }
+    __device__ static df twom(const DecayConsts& C, int i) { return df{C.tmdf[i][0], C.tmdf[i][1]}; }
 };
 
 // Direction of subsystem k in the rest frame of subsystem k+1 for the double-float generators
@@ -382,7 +391,7 @@ __device__ __forceinline__ void raubold_lynch_group(const DecayConsts& C, const 
                 gm = gap * gap;
                 p = (gap * P::add_pos(gap, twoMk)) * halfInvM;
             } else {
-                const R twom = P::scale(P::m(C, k), 2.0f);
+                const R twom = P::twom(C, k);
                 const R a = P::add_pos(gap, twoMk);
                 const R gpm = P::add_pos(gap, twom);
                 gm = gap * gpm;
@@ -420,16 +429,19 @@ __device__ __forceinline__ void raubold_lynch_group(const DecayConsts& C, const 
             const R Es = P::fma_pos(gm, halfInvM, Mk);
             if (k == N - 1) {
                 // parent at rest: no boost
-                dE[q] = P::sub_lazy(M, Es); dx[q] = -px; dy[q] = -py; dz[q] = -pz;
+                dE[q] = P::sub_le(M, Es); dx[q] = -px; dy[q] = -py; dz[q] = -pz;
                 Q0[q] = Es; Qx[q] = px; Qy[q] = py; Qz[q] = pz;
             } else {
-                // Q.p: its terms may cancel; left unnormalised (the sum below renormalises)
+                // Q.p, the lab energy E1 and the lab momentum n: their sums may cancel and are left
+                // unnormalised.  What they feed (products, sums, the conversion to double) keeps
+                // the absolute error at ~2^-47 of the terms' scale, the event scale, whatever
+                // their low parts; a reciprocal or square root seeds from the rounded pair.
                 const R qp = P::fma_lazy(Qz[q], pz, P::fma_lazy(Qy[q], py, Qx[q] * px));
-                const R E1 = P::fma_(Q0[q], Es, qp) * invM;
+                const R E1 = P::fma_lazy(Q0[q], Es, qp) * invM;
                 const R f = P::div(P::add_pos(E1, Es), P::add_pos(Q0[q], Mnext[q]));
-                const R nx = P::fma_(f, Qx[q], px), ny = P::fma_(f, Qy[q], py), nz = P::fma_(f, Qz[q], pz);
+                const R nx = P::fma_lazy(f, Qx[q], px), ny = P::fma_lazy(f, Qy[q], py), nz = P::fma_lazy(f, Qz[q], pz);
                 // the daughter by 4-momentum conservation (stored: left unnormalised)
-                dE[q] = P::sub_lazy(Q0[q], E1); dx[q] = P::sub_lazy(Qx[q], nx);
+                dE[q] = P::sub_le(Q0[q], E1); dx[q] = P::sub_lazy(Qx[q], nx);
                 dy[q] = P::sub_lazy(Qy[q], ny); dz[q] = P::sub_lazy(Qz[q], nz);
                 Q0[q] = E1; Qx[q] = nx; Qy[q] = ny; Qz[q] = nz;
             }

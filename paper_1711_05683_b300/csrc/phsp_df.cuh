@@ -69,6 +69,24 @@ __device__ __forceinline__ df df_add_lazy(df x, df y) {
     return df{s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo))};
 }
 
+// x + y for x, y >= 0, unnormalised like df_add_lazy.  With the larger high part first, Dekker's
+// FastTwoSum yields the same exact pair (fl(x.hi + y.hi), its rounding error) as TwoSum, so the
+// result is bit-identical to df_add_lazy in one FP32 instruction fewer (a max and a min on the
+// ALU pipe replace two dependent additions).
+__device__ __forceinline__ df df_add_pos_lazy(df x, df y) {
+    const df s = df_fast_two_sum(fmaxf(x.hi, y.hi), fminf(x.hi, y.hi));
+    return df{s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo))};
+}
+
+// x - y for 0 <= y <= x (up to the rounding of either), unnormalised like df_add_lazy(x, -y) and
+// bit-identical to it: FastTwoSum(x.hi, -y.hi) is exact when y.hi <= x.hi, and when rounding
+// leaves y.hi above x.hi the two lie within a factor of two, where the difference itself is
+// exact (Sterbenz) and so is the zero error term.  Three FP32 instructions fewer than TwoSum.
+__device__ __forceinline__ df df_sub_le_lazy(df x, df y) {
+    const df s = df_fast_two_sum(x.hi, -y.hi);
+    return df{s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, -y.lo))};
+}
+
 __device__ __forceinline__ df operator-(df x) { return df{-x.hi, -x.lo}; }
 __device__ __forceinline__ df operator-(df x, df y) { return x + (-y); }
 
@@ -92,13 +110,15 @@ __device__ __forceinline__ df operator*(df x, float a) {
     return df{p, e};
 }
 
-// 1/y: seed r = rcp.approx(fl(hi + lo)); e = 1 - y r (exact to first order in df); r (1 + e)
+// 1/y: seed r = rcp.approx(fl(hi + lo)); e = 1 - y r (exact to first order in df); r (1 + e),
+// returned as the unnormalised pair (r, r e): |r e| is ~2^-23 |r| (the seed's error), every
+// consumer is a product, and the pair has the value FastTwoSum would renormalise it to.
 __device__ __forceinline__ df df_rcp(df y) {
     float r;
     asm("rcp.approx.f32 %0, %1;" : "=f"(r) : "f"(__fadd_rn(y.hi, y.lo)));
     float e = __fmaf_rn(-y.hi, r, 1.0f);
     e = __fmaf_rn(-y.lo, r, e);
-    return df_fast_two_sum(r, __fmul_rn(r, e));
+    return df{r, __fmul_rn(r, e)};
 }
 
 __device__ __forceinline__ df df_div(df x, df y) { return x * df_rcp(y); }
@@ -109,7 +129,8 @@ __device__ __forceinline__ df& operator*=(df& x, df y) {
 }
 
 // sqrt(x), x >= 0: with xh = fl(hi + lo), s0 = xh rsqrt(xh); s = s0 + (x - s0^2) / (2 s0), the
-// residual formed from both parts with an exact product; 0 for x = 0.
+// residual formed from both parts with an exact product; 0 for x = 0.  Returned as the
+// unnormalised pair (s0, correction), |correction| ~2^-23 s0, like the reciprocal.
 __device__ __forceinline__ df df_sqrt(df x) {
     const float xh = __fadd_rn(x.hi, x.lo);
     if (!(xh > 0.0f)) return df{0.0f, 0.0f};
@@ -119,7 +140,7 @@ __device__ __forceinline__ df df_sqrt(df x) {
     const float p = __fmul_rn(s0, s0);
     const float pe = __fmaf_rn(s0, s0, -p);
     const float res = __fadd_rn(__fsub_rn(__fsub_rn(x.hi, p), pe), x.lo);
-    return df_fast_two_sum(s0, __fmul_rn(res, __fmul_rn(0.5f, r)));
+    return df{s0, __fmul_rn(res, __fmul_rn(0.5f, r))};
 }
 
 // Exact conversion of a 32-bit unsigned / signed integer: v = (v & ~0xFF) + (v & 0xFF), both
@@ -264,10 +285,12 @@ __device__ __forceinline__ DfWeight df_weight_one() { return DfWeight{df{1.0f, 0
 
 __device__ __forceinline__ DfWeight df_weight_mul(DfWeight w, df p) {
     // p >= 0; 0 and FP32 subnormals read as exponent -127 (a zero stays zero, a subnormal is
-    // scaled into the normal range)
-    const int ep = static_cast<int>((__float_as_uint(p.hi) >> 23) & 0xFFu) - 127;
-    const float s = __uint_as_float(static_cast<uint32_t>(127 - ep) << 23);  // 2^-ep
-    return DfWeight{w.m * df{__fmul_rn(p.hi, s), __fmul_rn(p.lo, s)}, w.e + ep};
+    // scaled into the normal range).  With b the biased exponent field of p.hi, the scale
+    // 2^(127 - b) has the field 254 - b: one subtraction from the masked bits.
+    const uint32_t field = __float_as_uint(p.hi) & 0x7F800000u;
+    const float s = __uint_as_float(0x7F000000u - field);  // 2^-ep, ep = b - 127
+    return DfWeight{w.m * df{__fmul_rn(p.hi, s), __fmul_rn(p.lo, s)},
+                    w.e + static_cast<int>(field >> 23) - 127};
 }
 
 // w as the nearest double, times an FP64 factor c.  The power 2^e is applied to the bits of
