@@ -254,15 +254,22 @@ struct DfDirection {
     float v[6];  // px, py, pz as (hi, lo) pairs
 };
 
-static __device__ __noinline__ DfDirection df_direction_outlined(df p, uint32_t xc, uint32_t xp) {
-    using P = Prec<df>;
-    const df cos_t = P::cos_of(xc);
-    const df sin_t = P::sqrt_(P::one_minus_cos(xc) * P::one_plus_cos(xc));
+// The direction in double-float.  1 - cos(theta), 1 + cos(theta) and cos(theta) are the exact
+// integers ~x + 1/2, x + 1/2 and x - 2^31 + 1/2 times 2^-31; the factor 2^-31 is applied once,
+// to p, instead of to each of them (an exact power of two either way).
+__device__ __forceinline__ DfDirection df_direction(df p, uint32_t xc, uint32_t xp) {
+    const df p31 = df_scale(p, 4.656612873077392578125e-10f);  // p 2^-31
+    const df cos_t31 = df_half_odd_centered_raw(xc);            // cos(theta) 2^31
+    const df sin_t31 = df_sqrt(df_half_odd_raw(~xc) * df_half_odd_raw(xc));  // sin(theta) 2^31
     df sphi, cphi;
-    P::sincos_2pi_u(xp, &sphi, &cphi);
-    const df ps = p * sin_t;
-    const df px = ps * cphi, py = ps * sphi, pz = p * cos_t;
+    df_sincos_2pi_u(xp, s_sincos_table, &sphi, &cphi);
+    const df ps = p31 * sin_t31;
+    const df px = ps * cphi, py = ps * sphi, pz = p31 * cos_t31;
     return DfDirection{{px.hi, px.lo, py.hi, py.lo, pz.hi, pz.lo}};
+}
+
+static __device__ __noinline__ DfDirection df_direction_outlined(df p, uint32_t xc, uint32_t xp) {
+    return df_direction(p, xc, xp);
 }
 
 // ------------------------------------------------------------------------------------
@@ -411,8 +418,10 @@ __device__ __forceinline__ void raubold_lynch_group(const DecayConsts& C, const 
             const uint32_t xc = xcs[q];
             const uint32_t xp = xps[q];
             R px, py, pz;
-            if constexpr (std::is_same<R, df>::value && N >= 6) {
-                const DfDirection d = df_direction_outlined(p, xc, xp);  // one copy of the code
+            if constexpr (std::is_same<R, df>::value) {
+                DfDirection d;
+                if constexpr (N >= 6) d = df_direction_outlined(p, xc, xp);  // one copy of the code
+                else d = df_direction(p, xc, xp);
                 px = df{d.v[0], d.v[1]}; py = df{d.v[2], d.v[3]}; pz = df{d.v[4], d.v[5]};
             } else {
                 const R cos_t = P::cos_of(xc);         // 2u - 1

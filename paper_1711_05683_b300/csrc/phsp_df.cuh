@@ -208,12 +208,17 @@ __device__ __forceinline__ df df_half_odd_u32(uint32_t x) {
     return df_scale(df_half_odd_raw(x), 4.656612873077392578125e-10f);
 }
 
-// (x - 2^31 + 1/2) 2^-31 for a 32-bit unsigned x (= cos(theta) = 2u - 1 exactly)
-__device__ __forceinline__ df df_half_odd_centered(uint32_t x) {
+// x - 2^31 + 1/2 for a 32-bit unsigned x, exact (cos(theta) 2^31 of a cos(theta) draw x)
+__device__ __forceinline__ df df_half_odd_centered_raw(uint32_t x) {
     const int32_t c = static_cast<int32_t>(x ^ 0x80000000u);
     const float a = __int2float_rz(static_cast<int32_t>(static_cast<uint32_t>(c) & 0xFFFFFF00u));
     const float b = __fadd_rn(__uint2float_rz(x & 0xFFu), 0.5f);
-    return df_scale(df_fast_two_sum(a, b), 4.656612873077392578125e-10f);
+    return df_fast_two_sum(a, b);
+}
+
+// (x - 2^31 + 1/2) 2^-31 for a 32-bit unsigned x (= cos(theta) = 2u - 1 exactly)
+__device__ __forceinline__ df df_half_odd_centered(uint32_t x) {
+    return df_scale(df_half_odd_centered_raw(x), 4.656612873077392578125e-10f);
 }
 
 // An FP64 value as a double-float pair by integer operations (an FP64-to-FP32 conversion would
