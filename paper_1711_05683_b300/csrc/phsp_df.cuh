@@ -172,9 +172,16 @@ __device__ __forceinline__ double f32_to_f64_bits(float f) {
 
 // The same rebias without the zero / subnormal case: exact for normal numbers; a zero or an
 // FP32 subnormal maps to a value of magnitude in [2^-127, 2^-126) with its sign.
+//
+// The high word sign | (e + 896) << 20 | m >> 3 from an arithmetic shift: xs = b >> 3 (signed)
+// copies the sign into bits 31..28, so xs & 0x90000000 is 0x90000000 times the sign, and
+// xs + (xs & 0x90000000) + 0x38000000 = ((b & 0x7FFFFFFF) >> 3) + 0x38000000 + sign (mod 2^32):
+// a shift, a logic operation and a three-input addition (checked against the masked form for
+// all 2^32 bit patterns).
 __device__ __forceinline__ double f32_to_f64_bits_fast(float f) {
     const uint32_t b = __float_as_uint(f);
-    const uint32_t hi = (((b & 0x7FFFFFFFu) >> 3) + 0x38000000u) | (b & 0x80000000u);
+    const uint32_t xs = static_cast<uint32_t>(static_cast<int32_t>(b) >> 3);
+    const uint32_t hi = xs + (xs & 0x90000000u) + 0x38000000u;
     return __hiloint2double(static_cast<int>(hi), static_cast<int>(b << 29));
 }
 
