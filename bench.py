@@ -44,12 +44,12 @@ INT_CFG = workloads.D0_DALITZ
 INSTR_PER_EVENT = {
     ("f32", 2): 90, ("f32", 3): 199, ("f32", 4): 282, ("f32", 5): 400, ("f32", 6): 515,
     ("f32", 7): 671, ("f32", 8): 762, ("f32", 9): 885, ("f32", 10): 999,
-    ("f64", 2): 383, ("f64", 3): 980, ("f64", 4): 1454, ("f64", 5): 1973, ("f64", 6): 2564,
-    ("f64", 7): 3106, ("f64", 8): 3617, ("f64", 9): 4152, ("f64", 10): 4714,
+    ("f64", 2): 353, ("f64", 3): 895, ("f64", 4): 1333, ("f64", 5): 1807, ("f64", 6): 2342,
+    ("f64", 7): 2835, ("f64", 8): 3307, ("f64", 9): 3790, ("f64", 10): 4299,
     # the double-float variant for all-massless decays (no square root per two-body momentum)
-    ("f64", 2, "massless"): 328, ("f64", 3, "massless"): 889, ("f64", 4, "massless"): 1323,
-    ("f64", 5, "massless"): 1809, ("f64", 6, "massless"): 2355, ("f64", 7, "massless"): 2842,
-    ("f64", 8, "massless"): 3300, ("f64", 9, "massless"): 3801, ("f64", 10, "massless"): 4284,
+    ("f64", 2, "massless"): 320, ("f64", 3, "massless"): 825, ("f64", 4, "massless"): 1230,
+    ("f64", 5, "massless"): 1654, ("f64", 6, "massless"): 2140, ("f64", 7, "massless"): 2605,
+    ("f64", 8, "massless"): 3024, ("f64", 9, "massless"): 3462, ("f64", 10, "massless"): 3899,
 }
 
 
