@@ -42,8 +42,8 @@ INT_CFG = workloads.D0_DALITZ
 # of a single generator kernel per row).  They explain the issue-bound double-float generator
 # (issue_frac in the per-launch breakdown); the roofline itself counts method operations.
 INSTR_PER_EVENT = {
-    ("f32", 2): 90, ("f32", 3): 199, ("f32", 4): 282, ("f32", 5): 400, ("f32", 6): 515,
-    ("f32", 7): 671, ("f32", 8): 762, ("f32", 9): 885, ("f32", 10): 999,
+    ("f32", 2): 80, ("f32", 3): 198, ("f32", 4): 280, ("f32", 5): 399, ("f32", 6): 512,
+    ("f32", 7): 632, ("f32", 8): 718, ("f32", 9): 880, ("f32", 10): 996,
     ("f64", 2): 353, ("f64", 3): 895, ("f64", 4): 1333, ("f64", 5): 1807, ("f64", 6): 2342,
     ("f64", 7): 2835, ("f64", 8): 3307, ("f64", 9): 3790, ("f64", 10): 4299,
     # the double-float variant for all-massless decays (no square root per two-body momentum)
