@@ -14,6 +14,7 @@ Tolerances (from the arithmetic of each precision):
   largest relative term error.
 """
 import ctypes
+import functools
 import math
 import os
 import subprocess
@@ -122,6 +123,47 @@ def test_generate_near_threshold(dtype):
         M, masses = workloads.near_threshold_decay(n, rel_gap=1e-7)
         err_p, err_w = compare_events(M, masses, 1000, 31, dtype)
         assert err_p <= TOL_P[dtype] and err_w <= TOL_W[dtype], (n, err_p, err_w)
+
+
+@functools.lru_cache(maxsize=None)
+def _events_with_small_mass_draw(seed, n, nscan, frac):
+    """Event indices whose smallest intermediate-mass draw is below frac 2^32 (oracle Philox):
+    subsystem 2 then has a kinetic energy of at most frac T, and with light daughters 1, 2 it
+    reaches the lab with a Lorentz factor of order 1 / frac."""
+    found = []
+    limit = int(frac * 2 ** 32)
+    key = (seed & 0xFFFFFFFF, seed >> 32)
+    for e in range(nscan):
+        ctr = (e & 0xFFFFFFFF, e >> 32)
+        words = list(oracle.philox4x32_10((ctr[0], ctr[1], 0, 0), key))
+        if n - 2 > 4:
+            words += list(oracle.philox4x32_10((ctr[0], ctr[1], 1, 0), key))
+        if min(words[: n - 2]) < limit:
+            found.append(e)
+    return tuple(found)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("light", [False, True])
+@pytest.mark.parametrize("n", [4, 7, 10])
+def test_generate_extreme_boosts(n, light, dtype):
+    """Parity where the boost factors are largest: events whose smallest intermediate-mass draw
+    is below 3e-5 of its range, with massless (or very light) daughters 1 and 2, so that
+    subsystem 2 moves with a Lorentz factor of up to ~1e5 and the lab energies and momenta of
+    the last steps cancel by as much.  The double-float generator keeps the boosted energies and
+    momenta as unnormalised sums; the error of either precision must stay within its tolerance
+    at the event scale."""
+    seed = 0x5EED_0000_0000_0000 + 97 * n + light
+    masses = [0.0] * n
+    if light:
+        masses = [1e-6, 2e-6] + [0.1 * (i + 1) for i in range(n - 2)]
+    events = _events_with_small_mass_draw(seed, n, 300_000, 3e-5)
+    assert len(events) >= 5, len(events)
+    worst_p = worst_w = 0.0
+    for e in events:
+        err_p, err_w = compare_events(workloads.SWEEP_M, masses, 1, seed, dtype, offset=e)
+        worst_p, worst_w = max(worst_p, err_p), max(worst_w, err_w)
+    assert worst_p <= TOL_P[dtype] and worst_w <= TOL_W[dtype], (len(events), worst_p, worst_w)
 
 
 @pytest.mark.parametrize("nev", [1, 2, 3, 4, 5, 31, 33, 255, 257, 4097])
