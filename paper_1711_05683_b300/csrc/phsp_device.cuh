@@ -256,11 +256,20 @@ struct DfDirection {
 
 // The direction in double-float.  1 - cos(theta), 1 + cos(theta) and cos(theta) are the exact
 // integers ~x + 1/2, x + 1/2 and x - 2^31 + 1/2 times 2^-31; the factor 2^-31 is applied once,
-// to p, instead of to each of them (an exact power of two either way).
+// to p, instead of to each of them (an exact power of two either way).  x + 1/2 is the exact
+// pair a + b, a = x & ~0xFF and b = (x & 0xFF) + 1/2, and the other two follow from a and b by
+// exact FP32 subtractions: ~x + 1/2 = (2^32 - 256 - a) + (256 - b) and
+// x - 2^31 + 1/2 = (a - 2^31) + b (every result a multiple of 256 below 2^32 in magnitude, or
+// below 256: representable, so the subtractions round nothing and the pairs are the ones the
+// integer conversions give).  (~x + 1/2)(x + 1/2) >= 2^31, so the square root needs no zero test.
 __device__ __forceinline__ DfDirection df_direction(df p, uint32_t xc, uint32_t xp) {
     const df p31 = df_scale(p, 4.656612873077392578125e-10f);  // p 2^-31
-    const df cos_t31 = df_half_odd_centered_raw(xc);            // cos(theta) 2^31
-    const df sin_t31 = df_sqrt(df_half_odd_raw(~xc) * df_half_odd_raw(xc));  // sin(theta) 2^31
+    const float a = __uint2float_rz(xc & 0xFFFFFF00u);
+    const float b = __fadd_rn(__uint2float_rz(xc & 0xFFu), 0.5f);
+    const df one_p31 = df_fast_two_sum(a, b);                                        // x + 1/2
+    const df one_m31 = df_fast_two_sum(__fsub_rn(4294967040.0f, a), __fsub_rn(256.0f, b));  // ~x + 1/2
+    const df cos_t31 = df_fast_two_sum(__fsub_rn(a, 2147483648.0f), b);              // cos(theta) 2^31
+    const df sin_t31 = df_sqrt_pos(one_m31 * one_p31);                               // sin(theta) 2^31
     df sphi, cphi;
     df_sincos_2pi_u(xp, s_sincos_table, &sphi, &cphi);
     const df ps = p31 * sin_t31;

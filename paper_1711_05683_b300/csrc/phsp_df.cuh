@@ -131,9 +131,9 @@ __device__ __forceinline__ df& operator*=(df& x, df y) {
 // sqrt(x), x >= 0: with xh = fl(hi + lo), s0 = xh rsqrt(xh); s = s0 + (x - s0^2) / (2 s0), the
 // residual formed from both parts with an exact product; 0 for x = 0.  Returned as the
 // unnormalised pair (s0, correction), |correction| ~2^-23 s0, like the reciprocal.
-__device__ __forceinline__ df df_sqrt(df x) {
+// The square root of an x known to be positive and normal (no zero test).
+__device__ __forceinline__ df df_sqrt_pos(df x) {
     const float xh = __fadd_rn(x.hi, x.lo);
-    if (!(xh > 0.0f)) return df{0.0f, 0.0f};
     float r;
     asm("rsqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(xh));
     const float s0 = __fmul_rn(xh, r);
@@ -141,6 +141,11 @@ __device__ __forceinline__ df df_sqrt(df x) {
     const float pe = __fmaf_rn(s0, s0, -p);
     const float res = __fadd_rn(__fsub_rn(__fsub_rn(x.hi, p), pe), x.lo);
     return df{s0, __fmul_rn(res, __fmul_rn(0.5f, r))};
+}
+
+__device__ __forceinline__ df df_sqrt(df x) {
+    if (!(__fadd_rn(x.hi, x.lo) > 0.0f)) return df{0.0f, 0.0f};
+    return df_sqrt_pos(x);
 }
 
 // Exact conversion of a 32-bit unsigned / signed integer: v = (v & ~0xFF) + (v & 0xFF), both
