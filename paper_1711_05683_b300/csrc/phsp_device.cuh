@@ -354,6 +354,9 @@ __device__ __forceinline__ void raubold_lynch_group(const DecayConsts& C, const 
         Mnext[q] = M;  // M_{k+1}
     }
 
+    // double-float only: the parts of the previous step's draw and its (y + 1/2) T 2^-32
+    float draw_a[EPT], draw_b[EPT];
+    df draw_T[EPT];
     int cur = kMassBlocks - 1;  // Philox block held in blk (-1: none); known at compile time
 #pragma unroll
     for (int k = N - 1; k >= 1; --k) {
@@ -383,10 +386,33 @@ __device__ __forceinline__ void raubold_lynch_group(const DecayConsts& C, const 
         for (int q = 0; q < EPT; ++q) {
             // intermediate mass M_k
             R Mk;
-            if (k == 1) Mk = P::m(C, 0);
-            else Mk = P::fma_pos(P::half_odd(y[q][k - 2]), Ts, P::mu(C, k - 1));
             // kinetic gap Delta_k = T (r_k - r_{k-1}) from integer differences
             R gap;
+            if constexpr (std::is_same<R, df>::value && N > 2) {
+                // Double-float: each sorted draw's y + 1/2 as the exact pair a + b, a = y & ~0xFF,
+                // b = (y & 0xFF) + 1/2, converted once.  The gaps follow from neighbouring parts by
+                // exact FP32 subtractions (multiples of 256 below 2^32, or below 256 in magnitude):
+                // y_k - y_{k-1} = (a_k - a_{k-1}) + (b_k - b_{k-1}) and 2^32 - 1 - y + 1/2 =
+                // (2^32 - 256 - a) + (256 - b); FastTwoSum then gives the same pair as converting
+                // the integer difference.
+                float a = 0.0f, b = 0.0f;
+                df hT{0.0f, 0.0f};
+                if (k >= 2) {
+                    const uint32_t yv = y[q][k - 2];
+                    a = __uint2float_rz(yv & 0xFFFFFF00u);
+                    b = __fadd_rn(__uint2float_rz(yv & 0xFFu), 0.5f);
+                    hT = df_fast_two_sum(a, b) * Ts;  // (y + 1/2) T 2^-32
+                    Mk = df_add_pos_lazy(hT, P::mu(C, k - 1));
+                } else {
+                    Mk = P::m(C, 0);
+                }
+                if (k == N - 1) gap = df_fast_two_sum(__fsub_rn(4294967040.0f, a), __fsub_rn(256.0f, b)) * Ts;
+                else if (k == 1) gap = draw_T[q];
+                else gap = df_fast_two_sum(__fsub_rn(draw_a[q], a), __fsub_rn(draw_b[q], b)) * Ts;
+                draw_a[q] = a; draw_b[q] = b; draw_T[q] = hT;
+            } else {
+            if (k == 1) Mk = P::m(C, 0);
+            else Mk = P::fma_pos(P::half_odd(y[q][k - 2]), Ts, P::mu(C, k - 1));
             if constexpr (N == 2) {
                 gap = Ts * R(4294967296.0);  // T exactly: Ts = T * 2^-32
             } else if (k == 1) {
@@ -395,6 +421,7 @@ __device__ __forceinline__ void raubold_lynch_group(const DecayConsts& C, const 
                 gap = P::half_odd(~y[q][kY - 1]) * Ts;
             } else {
                 gap = P::u32(y[q][k - 1] - y[q][k - 2]) * Ts;
+            }
             }
             Mk_out[q] = Mk;
             // two-body momentum
