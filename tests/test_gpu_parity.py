@@ -125,6 +125,22 @@ def test_generate_near_threshold(dtype):
         assert err_p <= TOL_P[dtype] and err_w <= TOL_W[dtype], (n, err_p, err_w)
 
 
+@pytest.mark.parametrize("massive", [False, True])
+@pytest.mark.parametrize("n", [8, 9, 10])
+def test_fp64_error_budget_on_long_decays(n, massive):
+    """The double-float generator against the oracle on 2e5 events of the longest decays, with a
+    budget tighter than the 1e-12 tolerance, so that a loss of double-float precision shows
+    before it reaches the tolerance.  A double-float operation errs by ~2^-46 of its operands'
+    scale (the event scale for the kinematics); the last daughter of an N = 10 decay depends on
+    ~250 operations (nine two-body steps: momentum, direction and boost), whose independent
+    roundings add to ~sqrt(250) 2^-46 ~ 2.2e-13: budget 3e-13.  (Measured on the current code:
+    below 1e-13.  Low parts left unnormalised along the chain of boosts once gave 9.4e-13.)"""
+    masses = workloads.sweep_masses(n, massive)
+    err_p, err_w = compare_events(workloads.SWEEP_M, masses, 200_000, 1000 + n, "f64")
+    assert err_p <= 3e-13, err_p
+    assert err_w <= TOL_W["f64"], err_w
+
+
 @functools.lru_cache(maxsize=None)
 def _events_with_small_mass_draw(seed, n, nscan, frac):
     """Event indices whose smallest intermediate-mass draw is below frac 2^32 (oracle Philox):
