@@ -187,11 +187,20 @@ hydra_status make_consts(double M, int n, const double* masses, uint64_t seed,
     C->Tsf = static_cast<float>(C->Ts);
     C->Ts_halff = static_cast<float>(C->Ts_half);
     C->Cf = static_cast<float>(Cn);
+    C->invM = 1.0 / M;
+    C->halfInvM = 0.5 / M;
+    C->invMf = static_cast<float>(C->invM);
+    C->halfInvMf = static_cast<float>(C->halfInvM);
+    C->Mm1 = M * M + masses[0] * masses[0];
+    C->Mm1f = static_cast<float>(C->Mm1);
     auto split = [](double v, float* o) {
         o[0] = static_cast<float>(v);
         o[1] = static_cast<float>(v - static_cast<double>(o[0]));
     };
     split(M, C->Mdf);
+    split(C->invM, C->invMdf);
+    split(C->halfInvM, C->halfInvMdf);
+    split(C->Mm1, C->Mm1df);
     split(C->Ts, C->Tsdf);
     split(C->Ts_half, C->Ts_halfdf);
     for (int i = 0; i < n; ++i) {

@@ -25,15 +25,17 @@ struct DecayConsts {
     double Ts;          // T * 2^-32 (T = M - sum m)
     double Ts_half;     // T * 2^-33
     double C;           // weight constant C_n
+    double invM, halfInvM;  // 1/M and 1/(2M) (the parent's decay, the same for every event)
+    double Mm1;             // M^2 + m_1^2 (s23 = M^2 + m_1^2 - 2 M E_1 of the Dalitz variables)
     double m[kNMax];    // daughter masses m_1..m_n at [0..n-1]
     double mu[kNMax];   // mu[k-1] = m_1 + ... + m_k
     double m2[kNMax];   // m_i^2
     double tm[kNMax];   // 2 m_i
     // FP32 copies (rounded from the FP64 values)
-    float Mf, Tsf, Ts_halff, Cf;
+    float Mf, Tsf, Ts_halff, Cf, invMf, halfInvMf, Mm1f;
     float mf[kNMax], muf[kNMax], m2f[kNMax], tmf[kNMax];
     // double-float copies (hi, lo) for the df kinematics of the FP64 generator
-    float Mdf[2], Tsdf[2], Ts_halfdf[2];
+    float Mdf[2], Tsdf[2], Ts_halfdf[2], invMdf[2], halfInvMdf[2], Mm1df[2];
     float mdf[kNMax][2], mudf[kNMax][2], m2df[kNMax][2], tmdf[kNMax][2];
     // Philox round keys: key + r * (W0, W1), r = 0..9
     uint32_t rk0[10], rk1[10];
@@ -152,6 +154,9 @@ template <> struct Prec<float> {
     __device__ static float mu(const DecayConsts& C, int i) { return C.muf[i]; }
     __device__ static float m2(const DecayConsts& C, int i) { return C.m2f[i]; }
     __device__ static float twom(const DecayConsts& C, int i) { return C.tmf[i]; }
+    __device__ static float invM(const DecayConsts& C) { return C.invMf; }
+    __device__ static float halfInvM(const DecayConsts& C) { return C.halfInvMf; }
+    __device__ static float Mm1(const DecayConsts& C) { return C.Mm1f; }
 };
 
 template <> struct Prec<double> {
@@ -193,6 +198,9 @@ template <> struct Prec<double> {
     __device__ static double mu(const DecayConsts& C, int i) { return C.mu[i]; }
     __device__ static double m2(const DecayConsts& C, int i) { return C.m2[i]; }
     __device__ static double twom(const DecayConsts& C, int i) { return C.tm[i]; }
+    __device__ static double invM(const DecayConsts& C) { return C.invM; }
+    __device__ static double halfInvM(const DecayConsts& C) { return C.halfInvM; }
+    __device__ static double Mm1(const DecayConsts& C) { return C.Mm1; }
 };
 
 // Double-float kinematics for the FP64 generator: arithmetic on the FP32 pipe with ~48
@@ -240,6 +248,9 @@ template <> struct Prec<df> {
     __device__ static df mu(const DecayConsts& C, int i) { return df{C.mudf[i][0], C.mudf[i][1]}; }
     __device__ static df m2(const DecayConsts& C, int i) { return df{C.m2df[i][0], C.m2df[i][1]}; }
     __device__ static df twom(const DecayConsts& C, int i) { return df{C.tmdf[i][0], C.tmdf[i][1]}; }
+    __device__ static df invM(const DecayConsts& C) { return df{C.invMdf[0], C.invMdf[1]}; }
+    __device__ static df halfInvM(const DecayConsts& C) { return df{C.halfInvMdf[0], C.halfInvMdf[1]}; }
+    __device__ static df Mm1(const DecayConsts& C) { return df{C.Mm1df[0], C.Mm1df[1]}; }
 };
 
 // Direction of subsystem k in the rest frame of subsystem k+1 for the double-float generators
@@ -426,8 +437,9 @@ __device__ __forceinline__ void raubold_lynch_group(const DecayConsts& C, const 
             Mk_out[q] = Mk;
             // two-body momentum
             const R twoMk = P::scale(Mk, 2.0f);
-            const R invM = P::rcp(Mnext[q]);
-            const R halfInvM = P::scale(invM, 0.5f);
+            // 1/M_{k+1}; for the parent's decay a host constant
+            const R invM = k == N - 1 ? P::invM(C) : P::rcp(Mnext[q]);
+            const R halfInvM = k == N - 1 ? P::halfInvM(C) : P::scale(invM, 0.5f);
             R p, gm;  // gm = Delta (Delta + 2 m_{k+1})
             if constexpr (kMassless) {
                 // every daughter massless: lambda = (Delta (Delta + 2 M_k))^2, no square root

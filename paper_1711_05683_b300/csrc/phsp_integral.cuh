@@ -113,18 +113,18 @@ __device__ __forceinline__ void dalitz3_point(const DecayConsts& C, const MECons
     philox4x32_10(static_cast<uint32_t>(e), static_cast<uint32_t>(e >> 32), 1u, 0u, C.rk0, C.rk1, b1);
     const uint32_t y = b0[0], xca = b0[1], xpa = b0[2], xcb = b0[3], xpb = b1[0];
     const R M = Q::M(C), Ts = Q::Ts(C);
-    const R m1 = Q::m(C, 0), m2 = Q::m(C, 1), m3 = Q::m(C, 2);
+    const R m1 = Q::m(C, 0);
     const R M2 = Q::fma_(Q::half_odd(y), Ts, Q::mu(C, 1));
     const R gap2 = Q::half_odd(~y) * Ts;  // T (1 - r)
     const R gap1 = Q::half_odd(y) * Ts;   // T r
-    const R twoM2 = Q::scale(M2, 2.0f), twom3 = Q::scale(m3, 2.0f);
+    const R twoM2 = Q::scale(M2, 2.0f), twom3 = Q::twom(C, 2);
     const R a2 = gap2 + twoM2, g2 = gap2 * (gap2 + twom3);  // g2 = Delta2 (Delta2 + 2 m3)
     const R lam2 = (g2 * a2) * (a2 + twom3);
-    const R twom1 = Q::scale(m1, 2.0f), twom2 = Q::scale(m2, 2.0f);
+    const R twom1 = Q::twom(C, 0), twom2 = Q::twom(C, 1);
     const R a1 = gap1 + twom1, g1 = gap1 * (gap1 + twom2);  // g1 = Delta1 (Delta1 + 2 m2)
     const R lam1 = (g1 * a1) * (a1 + twom2);
     const R invM2 = Q::rcp(M2);
-    const R halfInvM = Q::scale(Q::rcp(M), 0.5f), halfInvM2 = Q::scale(invM2, 0.5f);
+    const R halfInvM = Q::halfInvM(C), halfInvM2 = Q::scale(invM2, 0.5f);
     const R p2 = Q::sqrt_(lam2) * halfInvM;
     const R p1 = Q::sqrt_(lam1) * halfInvM2;
     const W w = Q::w_final(Q::w_mul(Q::w_mul(Q::w_one(), p2), p1), C);
@@ -136,7 +136,7 @@ __device__ __forceinline__ void dalitz3_point(const DecayConsts& C, const MECons
     const R E1s = Q::fma_(g1, halfInvM2, m1);
     const R E1 = Q::fma_(Q0, E1s, (p2 * p1) * cos_alpha) * invM2;
     const R s12 = M2 * M2;
-    const R s23 = Q::fma_(R(-2) * M, E1, Q::fma_(M, M, Q::m2(C, 0)));
+    const R s23 = Q::fma_(R(-2) * M, E1, Q::Mm1(C));
     wout = w;
     f = w * to_w<R>(dalitz_2bw<R>(P, s12, s23));
 }
@@ -158,7 +158,7 @@ __device__ __forceinline__ void integrand_group(const DecayConsts& C, const MECo
             // s12 = M_2^2 (subsystem of daughters 1, 2); s23 = (P - p1)^2 = M^2 + m1^2 - 2 M E1
             const R M = Prec<R>::M(C);
             const R s12 = s.M2[q] * s.M2[q];
-            const R s23 = Prec<R>::fma_(R(-2) * M, s.E1[q], Prec<R>::fma_(M, M, Prec<R>::m2(C, 0)));
+            const R s23 = Prec<R>::fma_(R(-2) * M, s.E1[q], Prec<R>::Mm1(C));
             f[q] = s.w[q] * to_w<R>(dalitz_2bw<R>(P, s12, s23));
         } else {
             f[q] = s.w[q];
