@@ -44,12 +44,12 @@ INT_CFG = workloads.D0_DALITZ
 INSTR_PER_EVENT = {
     ("f32", 2): 80, ("f32", 3): 198, ("f32", 4): 280, ("f32", 5): 399, ("f32", 6): 512,
     ("f32", 7): 632, ("f32", 8): 718, ("f32", 9): 880, ("f32", 10): 996,
-    ("f64", 2): 356, ("f64", 3): 874, ("f64", 4): 1315, ("f64", 5): 1764, ("f64", 6): 2302,
-    ("f64", 7): 2780, ("f64", 8): 3230, ("f64", 9): 3721, ("f64", 10): 4212,
+    ("f64", 2): 333, ("f64", 3): 874, ("f64", 4): 1309, ("f64", 5): 1768, ("f64", 6): 2293,
+    ("f64", 7): 2791, ("f64", 8): 3243, ("f64", 9): 3708, ("f64", 10): 4198,
     # the double-float variant for all-massless decays (no square root per two-body momentum)
-    ("f64", 2, "massless"): 305, ("f64", 3, "massless"): 796, ("f64", 4, "massless"): 1190,
-    ("f64", 5, "massless"): 1615, ("f64", 6, "massless"): 2101, ("f64", 7, "massless"): 2547,
-    ("f64", 8, "massless"): 2955, ("f64", 9, "massless"): 3403, ("f64", 10, "massless"): 3836,
+    ("f64", 2, "massless"): 261, ("f64", 3, "massless"): 810, ("f64", 4, "massless"): 1188,
+    ("f64", 5, "massless"): 1618, ("f64", 6, "massless"): 2104, ("f64", 7, "massless"): 2543,
+    ("f64", 8, "massless"): 2956, ("f64", 9, "massless"): 3406, ("f64", 10, "massless"): 3840,
 }
 
 
