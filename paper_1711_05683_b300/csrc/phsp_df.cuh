@@ -306,8 +306,11 @@ __device__ __forceinline__ DfWeight df_weight_mul(DfWeight w, df p) {
     // 2^(127 - b) has the field 254 - b: one subtraction from the masked bits.
     const uint32_t field = __float_as_uint(p.hi) & 0x7F800000u;
     const float s = __uint_as_float(0x7F000000u - field);  // 2^-ep, ep = b - 127
-    return DfWeight{w.m * df{__fmul_rn(p.hi, s), __fmul_rn(p.lo, s)},
-                    w.e + static_cast<int>(field >> 23) - 127};
+    // the running product is renormalised after each factor: carried unnormalised, its low part
+    // grows factor by factor and the product's dropped lo x lo term with it (worst weight error
+    // over a 3.6e6-event survey 6.1e-13 unnormalised, 2.7e-13 renormalised)
+    const df m = w.m * df{__fmul_rn(p.hi, s), __fmul_rn(p.lo, s)};
+    return DfWeight{df_fast_two_sum(m.hi, m.lo), w.e + static_cast<int>(field >> 23) - 127};
 }
 
 // w as the nearest double, times an FP64 factor c.  The power 2^e is applied to the bits of
