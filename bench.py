@@ -44,12 +44,12 @@ INT_CFG = workloads.D0_DALITZ
 INSTR_PER_EVENT = {
     ("f32", 2): 80, ("f32", 3): 198, ("f32", 4): 280, ("f32", 5): 399, ("f32", 6): 512,
     ("f32", 7): 632, ("f32", 8): 718, ("f32", 9): 880, ("f32", 10): 996,
-    ("f64", 2): 333, ("f64", 3): 874, ("f64", 4): 1309, ("f64", 5): 1768, ("f64", 6): 2293,
-    ("f64", 7): 2791, ("f64", 8): 3243, ("f64", 9): 3708, ("f64", 10): 4198,
+    ("f64", 2): 336, ("f64", 3): 884, ("f64", 4): 1317, ("f64", 5): 1780, ("f64", 6): 2314,
+    ("f64", 7): 2805, ("f64", 8): 3261, ("f64", 9): 3736, ("f64", 10): 4236,
     # the double-float variant for all-massless decays (no square root per two-body momentum)
-    ("f64", 2, "massless"): 261, ("f64", 3, "massless"): 810, ("f64", 4, "massless"): 1188,
-    ("f64", 5, "massless"): 1618, ("f64", 6, "massless"): 2104, ("f64", 7, "massless"): 2543,
-    ("f64", 8, "massless"): 2956, ("f64", 9, "massless"): 3406, ("f64", 10, "massless"): 3840,
+    ("f64", 2, "massless"): 261, ("f64", 3, "massless"): 818, ("f64", 4, "massless"): 1200,
+    ("f64", 5, "massless"): 1630, ("f64", 6, "massless"): 2121, ("f64", 7, "massless"): 2566,
+    ("f64", 8, "massless"): 2979, ("f64", 9, "massless"): 3426, ("f64", 10, "massless"): 3867,
 }
 
 
