@@ -13,7 +13,11 @@
 // Multiplication is the FMA-based double-word product (relative error ~2^-46).  Sums that
 // cannot cancel, and sums whose result only feeds products, sums and the conversion to double,
 // may skip the final renormalisation (df_add_lazy): the low part then exceeds ulp(hi)/2 by a
-// few ulp, which products, sums and conversions absorb at ~2^-48 of the terms' scale.
+// few ulp, which products, sums and conversions absorb at ~2^-48 of the terms' scale.  The
+// limit is a value carried through a chain of products and reciprocals (the boosted lab energy
+// from step to step, the weight's running product): unnormalised there, its low part grows
+// link by link until the product's dropped lo x lo term costs precision, so those are
+// renormalised.
 // Reciprocal, division and square root take an FP32 hardware approximation as the seed (of
 // the pair rounded to FP32, so an unnormalised operand still gives a seed within ~1 ulp) and
 // apply one Newton-Raphson correction evaluated in double-word arithmetic, which squares
