@@ -436,15 +436,18 @@ __device__ __forceinline__ void raubold_lynch_group(const DecayConsts& C, const 
             }
             Mk_out[q] = Mk;
             // two-body momentum
-            const R twoMk = P::scale(Mk, 2.0f);
+            const R twoMk = k == 1 ? P::twom(C, 0) : P::scale(Mk, 2.0f);  // 2 M_1 = 2 m_1
             // 1/M_{k+1}; for the parent's decay a host constant
             const R invM = k == N - 1 ? P::invM(C) : P::rcp(Mnext[q]);
             const R halfInvM = k == N - 1 ? P::halfInvM(C) : P::scale(invM, 0.5f);
             R p, gm;  // gm = Delta (Delta + 2 m_{k+1})
             if constexpr (kMassless) {
-                // every daughter massless: lambda = (Delta (Delta + 2 M_k))^2, no square root
+                // every daughter massless: lambda = (Delta (Delta + 2 M_k))^2, no square root;
+                // the last step has M_1 = 0, so p = Delta^2 / (2 M_2) (the same operations with
+                // the zero terms dropped: bit-identical)
                 gm = gap * gap;
-                p = (gap * P::add_pos(gap, twoMk)) * halfInvM;
+                if (k == 1) p = gm * halfInvM;
+                else p = (gap * P::add_pos(gap, twoMk)) * halfInvM;
             } else {
                 const R twom = P::twom(C, k);
                 const R a = P::add_pos(gap, twoMk);
@@ -483,7 +486,8 @@ __device__ __forceinline__ void raubold_lynch_group(const DecayConsts& C, const 
             }
             // energy of subsystem k in the rest frame of k+1: (M_{k+1}^2 + M_k^2 - m_{k+1}^2) / (2 M_{k+1})
             // = M_k + Delta (Delta + 2 m_{k+1}) / (2 M_{k+1}), a sum of positive terms
-            const R Es = P::fma_pos(gm, halfInvM, Mk);
+            // (massless last step: M_1 = 0 and Es = p, the energy of a massless daughter)
+            const R Es = (kMassless && k == 1) ? p : P::fma_pos(gm, halfInvM, Mk);
             if (k == N - 1) {
                 // parent at rest: no boost
                 dE[q] = P::sub_le(M, Es); dx[q] = -px; dy[q] = -py; dz[q] = -pz;
